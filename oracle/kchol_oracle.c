@@ -1,0 +1,638 @@
+/*
+ * CPU FP64 oracle for the sparse Cholesky factorisation of dense kernel
+ * matrices (Schaefer, Sullivan, Owhadi, "Compression, inversion, and
+ * approximate PCA of dense kernel matrices at near-linear computational
+ * complexity").
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test-suite, the smoke check and the
+ * bench's CPU-baseline leg may load this library; the product path never does.
+ *
+ * Plain, slow, single-threaded C in IEEE double precision.  It must be
+ * compiled with -O2 -ffp-contract=off so that no multiply-add is fused: the
+ * squared distance of two points is then the same bit pattern on every
+ * machine, which the exact (bit-identical) comparisons of orderings and
+ * patterns rely on.
+ *
+ * Conventions (readings of the paper where it is silent):
+ *  - Points are row-major x[i*d + t], i in original order.
+ *  - d2(a,b) = sum_{t=0}^{d-1} (x_a,t - x_b,t)^2, each operation rounded
+ *    separately, summed in t order; dist = sqrt(d2) (correctly rounded).
+ *  - Maximin ordering (Section 2.3): the first point is original index 0
+ *    (the whole-space case lets it be arbitrary); each next point maximises the
+ *    squared distance to the points already chosen; ties go to the smallest
+ *    original index.  l[k] = sqrt(that squared distance), l[0] = +inf.
+ *  - Positions in the ordering are the indices of the factor: "i" below is the
+ *    i-th point of the maximin order.
+ *  - Pattern S_rho (Section 2.3): for positions i < j, (j,i) is in S iff
+ *    dist(i,j) <= rho * l[i] (the max rule, since l is non-increasing); the
+ *    min rule (used in Section 6 for the reverse-order factor of the inverse)
+ *    takes rho * l[j] instead.  The diagonal is always in S.
+ *  - The factor L is stored as CSR by rows in ordered positions, column
+ *    indices ascending, the diagonal last in each row.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+typedef int64_t i64;
+typedef int32_t i32;
+
+/* ------------------------------------------------------------------------ */
+/* Geometry                                                                  */
+/* ------------------------------------------------------------------------ */
+
+static double d2_of(const double* a, const double* b, int d) {
+    double s = 0.0;
+    for (int t = 0; t < d; ++t) {
+        double u = a[t] - b[t];
+        double v = u * u;
+        s = s + v;
+    }
+    return s;
+}
+
+double ko_d2(const double* a, const double* b, i32 d) { return d2_of(a, b, d); }
+
+/* ------------------------------------------------------------------------ */
+/* Maximin ordering by its definition, O(N^2) (Section 2.3, Eq. for i_{k+1})  */
+/* ------------------------------------------------------------------------ */
+
+/* perm[k] = original index of the k-th point; l[k] its length scale. */
+void ko_maximin_brute(const double* x, i64 N, i32 d, i32* perm, double* l) {
+    if (N <= 0) return;
+    double* cur = (double*)malloc(sizeof(double) * (size_t)N);
+    char* taken = (char*)calloc((size_t)N, 1);
+    perm[0] = 0;
+    l[0] = INFINITY;
+    taken[0] = 1;
+    for (i64 i = 0; i < N; ++i) cur[i] = d2_of(x + i * d, x, d);
+    for (i64 k = 1; k < N; ++k) {
+        i64 best = -1;
+        for (i64 i = 0; i < N; ++i) {
+            if (taken[i]) continue;
+            if (best < 0 || cur[i] > cur[best]) best = i; /* strict: ties keep the smaller index */
+        }
+        perm[k] = (i32)best;
+        l[k] = sqrt(cur[best]);
+        taken[best] = 1;
+        const double* xb = x + best * d;
+        for (i64 i = 0; i < N; ++i) {
+            if (taken[i]) continue;
+            double v = d2_of(x + i * d, xb, d);
+            if (v < cur[i]) cur[i] = v;
+        }
+    }
+    free(cur);
+    free(taken);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Ordering and pattern by the paper's heap algorithm (Algorithm 3,          */
+/* "Ordering and sparsity pattern algorithm", Section 4.1).                  */
+/* Readings: the symmetric entry pushed in the final aggregation is (j,i);    */
+/* c[i] is sorted once after the loop that fills it.  The two pruning tests   */
+/* get a relative slack of 1e-12 so that rounding in the triangle inequality  */
+/* can only widen the candidate set, never drop a point.                     */
+/* ------------------------------------------------------------------------ */
+
+typedef struct { i32 j; double dist; } child_t;
+typedef struct { child_t* a; i64 n, cap; } childvec;
+typedef struct { i32* a; i64 n, cap; } intvec;
+
+static void cv_push(childvec* v, i32 j, double dist) {
+    if (v->n == v->cap) { v->cap = v->cap ? 2 * v->cap : 8; v->a = (child_t*)realloc(v->a, sizeof(child_t) * (size_t)v->cap); }
+    v->a[v->n].j = j; v->a[v->n].dist = dist; v->n++;
+}
+static void iv_push(intvec* v, i32 j) {
+    if (v->n == v->cap) { v->cap = v->cap ? 2 * v->cap : 8; v->a = (i32*)realloc(v->a, sizeof(i32) * (size_t)v->cap); }
+    v->a[v->n++] = j;
+}
+static int child_cmp(const void* pa, const void* pb) {
+    const child_t* a = (const child_t*)pa; const child_t* b = (const child_t*)pb;
+    if (a->dist < b->dist) return -1;
+    if (a->dist > b->dist) return 1;
+    return (a->j < b->j) ? -1 : (a->j > b->j);
+}
+
+/* mutable max-heap of original indices keyed by (key desc, index asc) */
+typedef struct { i32* h; i64* where; double* key; i64 n; } heap_t;
+static int h_above(const heap_t* H, i32 a, i32 b) {
+    return H->key[a] > H->key[b] || (H->key[a] == H->key[b] && a < b);
+}
+static void h_swap(heap_t* H, i64 p, i64 q) {
+    i32 a = H->h[p], b = H->h[q];
+    H->h[p] = b; H->h[q] = a; H->where[b] = p; H->where[a] = q;
+}
+static void h_down(heap_t* H, i64 p) {
+    for (;;) {
+        i64 c1 = 2 * p + 1, c2 = c1 + 1, m = p;
+        if (c1 < H->n && h_above(H, H->h[c1], H->h[m])) m = c1;
+        if (c2 < H->n && h_above(H, H->h[c2], H->h[m])) m = c2;
+        if (m == p) return;
+        h_swap(H, p, m); p = m;
+    }
+}
+static i32 h_pop(heap_t* H) {
+    i32 top = H->h[0];
+    h_swap(H, 0, H->n - 1);
+    H->n--;
+    H->where[top] = -1;
+    if (H->n > 0) h_down(H, 0);
+    return top;
+}
+/* lower the key of j to v if j is still in the heap and v is smaller */
+static void h_decrease(heap_t* H, i32 j, double v) {
+    i64 p = H->where[j];
+    if (p < 0 || !(v < H->key[j])) return;
+    H->key[j] = v;
+    h_down(H, p);
+}
+
+typedef struct {
+    i64 N;
+    i32* perm;        /* ordered -> original */
+    double* l;
+    i64 nnz;          /* entries of L incl. diagonal */
+    i64* rowptr;      /* CSR of L in ordered positions */
+    i32* col;
+} ko_sortsparse_result;
+
+/* Returns a heap-allocated result; free with ko_sortsparse_free. */
+ko_sortsparse_result* ko_sortsparse(const double* x, i64 N, i32 d, double rho, i32 rule_min) {
+    ko_sortsparse_result* R = (ko_sortsparse_result*)calloc(1, sizeof(ko_sortsparse_result));
+    R->N = N;
+    if (N <= 0) { R->rowptr = (i64*)calloc(1, sizeof(i64)); return R; }
+    R->perm = (i32*)malloc(sizeof(i32) * (size_t)N);
+    R->l = (double*)malloc(sizeof(double) * (size_t)N);
+    double* lo = (double*)malloc(sizeof(double) * (size_t)N); /* l by original index */
+    i64* pos = (i64*)malloc(sizeof(i64) * (size_t)N);          /* original -> ordered */
+    childvec* c = (childvec*)calloc((size_t)N, sizeof(childvec));
+    intvec* p = (intvec*)calloc((size_t)N, sizeof(intvec));
+    heap_t H;
+    H.h = (i32*)malloc(sizeof(i32) * (size_t)N);
+    H.where = (i64*)malloc(sizeof(i64) * (size_t)N);
+    H.key = (double*)malloc(sizeof(double) * (size_t)N);
+    H.n = N;
+    for (i64 i = 0; i < N; ++i) { H.h[i] = (i32)i; H.where[i] = i; H.key[i] = INFINITY; lo[i] = INFINITY; }
+    /* all keys equal: index order already satisfies the heap property */
+
+    const double slack_lo = 1.0 - 1e-12, slack_hi = 1.0 + 1e-12;
+    i64 k_ord = 0;
+    /* first index: every point is its child */
+    {
+        i32 i = h_pop(&H);
+        lo[i] = INFINITY;
+        for (i64 j = 0; j < N; ++j) {
+            double dd2 = d2_of(x + (i64)i * d, x + j * d, d);
+            cv_push(&c[i], (i32)j, sqrt(dd2));
+            iv_push(&p[j], i);
+            h_decrease(&H, (i32)j, dd2);
+        }
+        qsort(c[i].a, (size_t)c[i].n, sizeof(child_t), child_cmp);
+        R->perm[k_ord] = i; R->l[k_ord] = INFINITY; pos[i] = k_ord; k_ord++;
+    }
+    while (H.n > 0) {
+        double key = H.key[H.h[0]];
+        i32 i = h_pop(&H);
+        double li = sqrt(key);
+        lo[i] = li;
+        double rli = rho * li;
+        /* parent k: the closest earlier point whose children cover B(x_i, rho l[i]) */
+        i32 k = -1; double dk = INFINITY;
+        for (i64 t = 0; t < p[i].n; ++t) {
+            i32 j = p[i].a[t];
+            double dij = sqrt(d2_of(x + (i64)i * d, x + (i64)j * d, d));
+            double rlj = rho * lo[j];
+            if ((dij + rli) <= rlj * slack_lo || isinf(rlj)) {
+                if (dij < dk || (dij == dk && j < k)) { dk = dij; k = j; }
+            }
+        }
+        double dik = dk;
+        double reach = (dik + rli) * slack_hi;
+        for (i64 t = 0; t < c[k].n; ++t) {
+            if (c[k].a[t].dist > reach) break; /* c[k] is sorted by distance to k */
+            i32 j = c[k].a[t].j;
+            double dd2 = d2_of(x + (i64)i * d, x + (i64)j * d, d);
+            h_decrease(&H, j, dd2);
+            double dij = sqrt(dd2);
+            if (dij <= rli) { cv_push(&c[i], j, dij); iv_push(&p[j], i); }
+        }
+        qsort(c[i].a, (size_t)c[i].n, sizeof(child_t), child_cmp);
+        R->perm[k_ord] = i; R->l[k_ord] = li; pos[i] = k_ord; k_ord++;
+    }
+
+    /* aggregate: column pos[i] of L holds the later children j of i */
+    i64* cnt = (i64*)calloc((size_t)N + 1, sizeof(i64));
+    if (!rule_min) {
+        for (i64 i = 0; i < N; ++i)
+            for (i64 t = 0; t < c[i].n; ++t) {
+                i32 j = c[i].a[t].j;
+                if (pos[j] >= pos[i]) cnt[pos[j] + 1]++;   /* includes the diagonal j == i */
+            }
+    } else {
+        /* min rule: (j,i), i before j, iff dist <= rho * l[j]; children lists
+           of i hold dist <= rho l[i] >= rho l[j], so they are a superset */
+        for (i64 i = 0; i < N; ++i)
+            for (i64 t = 0; t < c[i].n; ++t) {
+                i32 j = c[i].a[t].j;
+                if (pos[j] > pos[i] && c[i].a[t].dist <= rho * lo[j]) cnt[pos[j] + 1]++;
+                else if (j == i) cnt[pos[j] + 1]++;
+            }
+    }
+    R->rowptr = (i64*)malloc(sizeof(i64) * ((size_t)N + 1));
+    R->rowptr[0] = 0;
+    for (i64 r = 0; r < N; ++r) R->rowptr[r + 1] = R->rowptr[r] + cnt[r + 1];
+    R->nnz = R->rowptr[N];
+    R->col = (i32*)malloc(sizeof(i32) * (size_t)(R->nnz > 0 ? R->nnz : 1));
+    i64* fill = (i64*)malloc(sizeof(i64) * (size_t)N);
+    for (i64 r = 0; r < N; ++r) fill[r] = R->rowptr[r];
+    /* visit columns in ordered position so that each row's entries come ascending */
+    for (i64 q = 0; q < N; ++q) {
+        i32 i = R->perm[q];
+        for (i64 t = 0; t < c[i].n; ++t) {
+            i32 j = c[i].a[t].j;
+            int keep;
+            if (!rule_min) keep = pos[j] >= pos[i];
+            else keep = (j == i) || (pos[j] > pos[i] && c[i].a[t].dist <= rho * lo[j]);
+            if (keep) R->col[fill[pos[j]]++] = (i32)q;
+        }
+    }
+    free(fill); free(cnt);
+    for (i64 i = 0; i < N; ++i) { free(c[i].a); free(p[i].a); }
+    free(c); free(p); free(H.h); free(H.where); free(H.key); free(lo); free(pos);
+    return R;
+}
+
+void ko_sortsparse_free(ko_sortsparse_result* R) {
+    if (!R) return;
+    free(R->perm); free(R->l); free(R->rowptr); free(R->col); free(R);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Pattern S_rho by its definition, O(N^2) (Section 2.3)                     */
+/* xo: coordinates in ordered positions.  Two passes: count, then fill.      */
+/* ------------------------------------------------------------------------ */
+
+static int in_pattern(const double* xo, const double* l, i64 i, i64 j, i32 d, double rho, i32 rule_min) {
+    /* i < j */
+    double dist = sqrt(d2_of(xo + i * d, xo + j * d, d));
+    double r = rule_min ? l[j] : l[i];
+    if (isinf(r)) return 1;
+    return dist <= rho * r;
+}
+
+void ko_pattern_count(const double* xo, const double* l, i64 N, i32 d, double rho, i32 rule_min, i64* rowptr) {
+    rowptr[0] = 0;
+    for (i64 j = 0; j < N; ++j) {
+        i64 c = 1;
+        for (i64 i = 0; i < j; ++i) c += in_pattern(xo, l, i, j, d, rho, rule_min);
+        rowptr[j + 1] = rowptr[j] + c;
+    }
+}
+
+void ko_pattern_fill(const double* xo, const double* l, i64 N, i32 d, double rho, i32 rule_min,
+                     const i64* rowptr, i32* col) {
+    for (i64 j = 0; j < N; ++j) {
+        i64 w = rowptr[j];
+        for (i64 i = 0; i < j; ++i)
+            if (in_pattern(xo, l, i, j, d, rho, rule_min)) col[w++] = (i32)i;
+        col[w++] = (i32)j;
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Matern covariance, Eq. (Matern) of Section 4.4, closed forms for          */
+/* nu = 1/2, 3/2, 5/2 (K_{nu} of half-integer order is elementary):          */
+/*   t = sqrt(2 nu) r / ell                                                  */
+/*   nu=1/2: sigma2 e^{-t};  3/2: sigma2 (1+t) e^{-t};                        */
+/*   5/2: sigma2 (1 + t + t^2/3) e^{-t}.  Nugget added on the diagonal only.  */
+/* ------------------------------------------------------------------------ */
+
+double ko_matern(double r, double nu, double ell, double sigma2) {
+    if (nu == 0.5) {
+        double t = r / ell;
+        return sigma2 * exp(-t);
+    } else if (nu == 1.5) {
+        double t = sqrt(3.0) * r / ell;
+        return sigma2 * (1.0 + t) * exp(-t);
+    } else if (nu == 2.5) {
+        double t = sqrt(5.0) * r / ell;
+        return sigma2 * (1.0 + t + t * t / 3.0) * exp(-t);
+    }
+    return NAN;
+}
+
+typedef struct { double nu, ell, sigma2, nugget; } ko_kernel;
+
+static double theta_pos(const double* xo, i32 d, i64 a, i64 b, const ko_kernel* K) {
+    double r = sqrt(d2_of(xo + a * d, xo + b * d, d));
+    double v = ko_matern(r, K->nu, K->ell, K->sigma2);
+    if (a == b) v += K->nugget;
+    return v;
+}
+
+double ko_theta(const double* xo, i32 d, i64 a, i64 b, double nu, double ell, double sigma2, double nugget) {
+    ko_kernel K = {nu, ell, sigma2, nugget};
+    return theta_pos(xo, d, a, b, &K);
+}
+
+/* ------------------------------------------------------------------------ */
+/* CSC (columns of L) from the CSR rows: colptr, rowidx ascending, and the   */
+/* CSR slot of every CSC entry.                                              */
+/* ------------------------------------------------------------------------ */
+
+void ko_csr_to_csc(i64 N, const i64* rowptr, const i32* col, i64* colptr, i32* rowidx, i64* slot) {
+    i64 nnz = rowptr[N];
+    for (i64 i = 0; i <= N; ++i) colptr[i] = 0;
+    for (i64 e = 0; e < nnz; ++e) colptr[col[e] + 1]++;
+    for (i64 i = 0; i < N; ++i) colptr[i + 1] += colptr[i];
+    i64* fill = (i64*)malloc(sizeof(i64) * (size_t)(N > 0 ? N : 1));
+    for (i64 i = 0; i < N; ++i) fill[i] = colptr[i];
+    for (i64 j = 0; j < N; ++j)
+        for (i64 e = rowptr[j]; e < rowptr[j + 1]; ++e) {
+            i64 w = fill[col[e]]++;
+            rowidx[w] = (i32)j;
+            slot[w] = e;
+        }
+    free(fill);
+}
+
+/* ------------------------------------------------------------------------ */
+/* ICHOL(0), Algorithm 2 ("Incomplete Cholesky factorization with sparsity   */
+/* pattern S"), written in its left-looking form:                            */
+/*   for i ascending:  p = Theta_ii - sum_{k in R_i} L_ik^2                  */
+/*     if p <= 0 the whole column i is set to zero (Section 4.4: a           */
+/*     nonpositive pivot zeroes that column of L);                           */
+/*     else L_ii = sqrt(p) and for j in C_i:                                 */
+/*       L_ji = (Theta_ji - sum_{k in R_j cap R_i} L_jk L_ik) / L_ii          */
+/* where R_i = {k < i : (i,k) in S} and C_i = {j > i : (j,i) in S}.  In       */
+/* exact arithmetic this is the same as the algorithm's right-looking update  */
+/* A_kj -= A_ki A_ji / A_ii applied iff (i,j),(k,i),(k,j) in S.              */
+/* Sums run in ascending k.  val[] follows the CSR layout.  Returns the       */
+/* number of zeroed columns.                                                 */
+/* ------------------------------------------------------------------------ */
+
+i64 ko_ichol(const double* xo, i64 N, i32 d, double nu, double ell, double sigma2, double nugget,
+             const i64* rowptr, const i32* col, double* val, char* zero_col) {
+    ko_kernel K = {nu, ell, sigma2, nugget};
+    i64 nnz = rowptr[N];
+    i64* colptr = (i64*)malloc(sizeof(i64) * ((size_t)N + 1));
+    i32* rowidx = (i32*)malloc(sizeof(i32) * (size_t)(nnz > 0 ? nnz : 1));
+    i64* slot = (i64*)malloc(sizeof(i64) * (size_t)(nnz > 0 ? nnz : 1));
+    ko_csr_to_csc(N, rowptr, col, colptr, rowidx, slot);
+    for (i64 e = 0; e < nnz; ++e) val[e] = 0.0;
+    i64 zeroed = 0;
+    for (i64 i = 0; i < N; ++i) {
+        i64 a0 = rowptr[i], a1 = rowptr[i + 1] - 1; /* row i without its diagonal: [a0, a1) */
+        double p = theta_pos(xo, d, i, i, &K);
+        for (i64 e = a0; e < a1; ++e) p -= val[e] * val[e];
+        if (!(p > 0.0)) {
+            zero_col[i] = 1; zeroed++;
+            continue; /* column stays zero, diagonal included */
+        }
+        zero_col[i] = 0;
+        double Lii = sqrt(p);
+        val[a1] = Lii;
+        for (i64 q = colptr[i] + 1; q < colptr[i + 1]; ++q) { /* skip the diagonal entry (first) */
+            i64 j = rowidx[q];
+            i64 b0 = rowptr[j];
+            i64 bij = slot[q];                 /* position of (j,i) in row j */
+            /* merge row j (k < i) with row i (k < i) */
+            double s = theta_pos(xo, d, j, i, &K);
+            i64 u = a0, v = b0;
+            while (u < a1 && v < bij) {
+                i32 ku = col[u], kv = col[v];
+                if (ku == kv) { s -= val[v] * val[u]; ++u; ++v; }
+                else if (ku < kv) ++u;
+                else ++v;
+            }
+            val[bij] = s / Lii;
+        }
+    }
+    free(colptr); free(rowidx); free(slot);
+    return zeroed;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Triangular solves with L (task (2), Section 1): y = L^{-1} b, x = L^{-T} y.*/
+/* A zeroed column i uses diag[i] supplied by the caller.                    */
+/* ------------------------------------------------------------------------ */
+
+void ko_solve_lower(i64 N, const i64* rowptr, const i32* col, const double* val, const double* diag,
+                    const double* b, double* y) {
+    for (i64 j = 0; j < N; ++j) {
+        double s = b[j];
+        for (i64 e = rowptr[j]; e < rowptr[j + 1] - 1; ++e) s -= val[e] * y[col[e]];
+        y[j] = s / diag[j];
+    }
+}
+
+void ko_solve_upper(i64 N, const i64* rowptr, const i32* col, const double* val, const double* diag,
+                    const double* y, double* x) {
+    for (i64 i = 0; i < N; ++i) x[i] = y[i];
+    for (i64 j = N - 1; j >= 0; --j) {
+        x[j] = x[j] / diag[j];
+        for (i64 e = rowptr[j]; e < rowptr[j + 1] - 1; ++e) x[col[e]] -= val[e] * x[j];
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* y = Theta^S v: the kernel matrix restricted to the symmetric pattern S,   */
+/* entries from the coordinates (the sparse matrix the factorisation sees).  */
+/* ------------------------------------------------------------------------ */
+
+void ko_theta_s_matvec(const double* xo, i64 N, i32 d, double nu, double ell, double sigma2, double nugget,
+                       const i64* rowptr, const i32* col, const double* v, double* y) {
+    ko_kernel K = {nu, ell, sigma2, nugget};
+    for (i64 j = 0; j < N; ++j) y[j] = 0.0;
+    for (i64 j = 0; j < N; ++j) {
+        for (i64 e = rowptr[j]; e < rowptr[j + 1] - 1; ++e) {
+            i64 k = col[e];
+            double t = theta_pos(xo, d, j, k, &K);
+            y[j] += t * v[k];
+            y[k] += t * v[j];
+        }
+        y[j] += theta_pos(xo, d, j, j, &K) * v[j];
+    }
+}
+
+/* y = Theta v with the dense kernel matrix (O(N^2)). */
+void ko_theta_dense_matvec(const double* xo, i64 N, i32 d, double nu, double ell, double sigma2, double nugget,
+                           const double* v, double* y) {
+    ko_kernel K = {nu, ell, sigma2, nugget};
+    for (i64 j = 0; j < N; ++j) {
+        double s = 0.0;
+        for (i64 k = 0; k < N; ++k) s += theta_pos(xo, d, j, k, &K) * v[k];
+        y[j] = s;
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Preconditioned CG on A x = b with A = Theta^S (op=1) or dense Theta       */
+/* (op=2), preconditioner M = L L^T (Section 4.3: CG preconditioned with the */
+/* factor).  Starts from x = 0.  Returns iterations; relres gets the final   */
+/* ||b - A x|| / ||b||; status 0 converged, 1 not converged, 2 p^T A p <= 0.   */
+/* ------------------------------------------------------------------------ */
+
+static double dotv(i64 n, const double* a, const double* b) {
+    double s = 0.0;
+    for (i64 i = 0; i < n; ++i) s += a[i] * b[i];
+    return s;
+}
+
+i32 ko_pcg(const double* xo, i64 N, i32 d, double nu, double ell, double sigma2, double nugget,
+           const i64* rowptr, const i32* col, const double* val, const double* diag, i32 op,
+           const double* b, double rtol, i32 maxit, double* x, double* relres, i32* status) {
+    double* r = (double*)malloc(sizeof(double) * (size_t)N);
+    double* z = (double*)malloc(sizeof(double) * (size_t)N);
+    double* p = (double*)malloc(sizeof(double) * (size_t)N);
+    double* q = (double*)malloc(sizeof(double) * (size_t)N);
+    double* t = (double*)malloc(sizeof(double) * (size_t)N);
+    for (i64 i = 0; i < N; ++i) { x[i] = 0.0; r[i] = b[i]; }
+    double bn = sqrt(dotv(N, b, b));
+    *status = 1;
+    i32 it = 0;
+    double rn = bn;
+    if (bn == 0.0) { *relres = 0.0; *status = 0; goto done; }
+    ko_solve_lower(N, rowptr, col, val, diag, r, t);
+    ko_solve_upper(N, rowptr, col, val, diag, t, z);
+    for (i64 i = 0; i < N; ++i) p[i] = z[i];
+    double rz = dotv(N, r, z);
+    for (it = 0; it < maxit; ++it) {
+        if (rn / bn <= rtol) { *status = 0; break; }
+        if (op == 2) ko_theta_dense_matvec(xo, N, d, nu, ell, sigma2, nugget, p, q);
+        else ko_theta_s_matvec(xo, N, d, nu, ell, sigma2, nugget, rowptr, col, p, q);
+        double pq = dotv(N, p, q);
+        if (!(pq > 0.0)) { *status = 2; break; }
+        double alpha = rz / pq;
+        for (i64 i = 0; i < N; ++i) { x[i] += alpha * p[i]; r[i] -= alpha * q[i]; }
+        rn = sqrt(dotv(N, r, r));
+        ko_solve_lower(N, rowptr, col, val, diag, r, t);
+        ko_solve_upper(N, rowptr, col, val, diag, t, z);
+        double rz2 = dotv(N, r, z);
+        double beta = rz2 / rz;
+        rz = rz2;
+        for (i64 i = 0; i < N; ++i) p[i] = z[i] + beta * p[i];
+    }
+    if (it == maxit && rn / bn <= rtol) *status = 0;
+    /* true residual */
+    if (op == 2) ko_theta_dense_matvec(xo, N, d, nu, ell, sigma2, nugget, x, q);
+    else ko_theta_s_matvec(xo, N, d, nu, ell, sigma2, nugget, rowptr, col, x, q);
+    for (i64 i = 0; i < N; ++i) q[i] = b[i] - q[i];
+    *relres = sqrt(dotv(N, q, q)) / bn;
+done:
+    free(r); free(z); free(p); free(q); free(t);
+    return it;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Sampled relative Frobenius error E (Section 4.4):                          */
+/*   E ~ sqrt(sum_k ((L L^T)_{ik jk} - Theta_{ik jk})^2) / sqrt(sum_k Theta^2) */
+/* over given index pairs in ORIGINAL numbering; pos maps original ->       */
+/* ordered.  (L L^T)_ij is the merge of rows i and j of L.                    */
+/* ------------------------------------------------------------------------ */
+
+static double llt_entry(const i64* rowptr, const i32* col, const double* val, i64 a, i64 b) {
+    i64 u = rowptr[a], ue = rowptr[a + 1], v = rowptr[b], ve = rowptr[b + 1];
+    double s = 0.0;
+    while (u < ue && v < ve) {
+        if (col[u] == col[v]) { s += val[u] * val[v]; ++u; ++v; }
+        else if (col[u] < col[v]) ++u;
+        else ++v;
+    }
+    return s;
+}
+
+double ko_llt_entry(const i64* rowptr, const i32* col, const double* val, i64 a, i64 b) {
+    return llt_entry(rowptr, col, val, a, b);
+}
+
+void ko_frob_error(const double* xo, i64 N, i32 d, double nu, double ell, double sigma2, double nugget,
+                   const i64* rowptr, const i32* col, const double* val, const i64* pos,
+                   i64 m, const i64* pi, const i64* pj, const char* keep,
+                   double* num2, double* den2, i64* kept) {
+    ko_kernel K = {nu, ell, sigma2, nugget};
+    double a = 0.0, b = 0.0; i64 c = 0;
+    (void)N;
+    for (i64 t = 0; t < m; ++t) {
+        if (keep && !keep[t]) continue;
+        i64 i = pos[pi[t]], j = pos[pj[t]];
+        double th = theta_pos(xo, d, i, j, &K);
+        double e = llt_entry(rowptr, col, val, i, j) - th;
+        a += e * e; b += th * th; c++;
+    }
+    *num2 = a; *den2 = b; *kept = c;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Approximate PCA (Section 2.5, Theorem on rank-k approximation): the first  */
+/* k columns of L, rows scattered back to original order, column-major.      */
+/* ------------------------------------------------------------------------ */
+
+void ko_pca_truncate(i64 N, const i64* rowptr, const i32* col, const double* val, const i32* perm,
+                     i32 k, double* Lk) {
+    for (i64 e = 0; e < N * (i64)k; ++e) Lk[e] = 0.0;
+    for (i64 j = 0; j < N; ++j)
+        for (i64 e = rowptr[j]; e < rowptr[j + 1]; ++e)
+            if (col[e] < k) Lk[(i64)perm[j] + N * (i64)col[e]] = val[e];
+}
+
+/* Power iteration for ||Theta - Lk Lk^T||_2 on ORIGINAL order coordinates x.
+   v0: unit start vector.  Returns |v^T B v| after iters steps. */
+double ko_pca_error_power(const double* x, i64 N, i32 d, double nu, double ell, double sigma2, double nugget,
+                          i32 k, const double* Lk, const double* v0, i32 iters) {
+    double* v = (double*)malloc(sizeof(double) * (size_t)N);
+    double* w = (double*)malloc(sizeof(double) * (size_t)N);
+    double* c = (double*)malloc(sizeof(double) * (size_t)(k > 0 ? k : 1));
+    for (i64 i = 0; i < N; ++i) v[i] = v0[i];
+    double est = 0.0;
+    for (i32 it = 0; it < iters; ++it) {
+        ko_theta_dense_matvec(x, N, d, nu, ell, sigma2, nugget, v, w);
+        for (i32 a = 0; a < k; ++a) { double s = 0.0; for (i64 i = 0; i < N; ++i) s += Lk[i + N * a] * v[i]; c[a] = s; }
+        for (i32 a = 0; a < k; ++a) for (i64 i = 0; i < N; ++i) w[i] -= Lk[i + N * a] * c[a];
+        est = fabs(dotv(N, v, w));
+        double nw = sqrt(dotv(N, w, w));
+        if (nw == 0.0) break;
+        for (i64 i = 0; i < N; ++i) v[i] = w[i] / nw;
+    }
+    free(v); free(w); free(c);
+    return est;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Work counters of the left-looking factor:                                 */
+/*   F = sum_{(j,i) in S, j>i} |R_j cap R_i| + sum_i |R_i|   (multiply-adds)  */
+/*   M = sum_{(j,i) in S, j>i} (|R_j cap [0,i)| + |R_i|)     (merge steps)    */
+/*   P = sum_{(j,i) in S, j>i} |R_j cap [0,i)|               (row prefixes)   */
+/*   Rsum = sum_i |R_i|                                                       */
+/* ------------------------------------------------------------------------ */
+
+void ko_work_counters(i64 N, const i64* rowptr, const i32* col, i64* F, i64* M, i64* P, i64* Rsum) {
+    i64 nnz = rowptr[N];
+    i64* colptr = (i64*)malloc(sizeof(i64) * ((size_t)N + 1));
+    i32* rowidx = (i32*)malloc(sizeof(i32) * (size_t)(nnz > 0 ? nnz : 1));
+    i64* slot = (i64*)malloc(sizeof(i64) * (size_t)(nnz > 0 ? nnz : 1));
+    ko_csr_to_csc(N, rowptr, col, colptr, rowidx, slot);
+    i64 f = 0, mm = 0, pp = 0, rs = 0;
+    for (i64 i = 0; i < N; ++i) {
+        i64 a0 = rowptr[i], a1 = rowptr[i + 1] - 1;
+        i64 ri = a1 - a0;
+        rs += ri; f += ri;
+        for (i64 q = colptr[i] + 1; q < colptr[i + 1]; ++q) {
+            i64 j = rowidx[q];
+            i64 b0 = rowptr[j], bij = slot[q];
+            i64 u = a0, v = b0, inter = 0;
+            while (u < a1 && v < bij) {
+                if (col[u] == col[v]) { inter++; ++u; ++v; }
+                else if (col[u] < col[v]) ++u;
+                else ++v;
+            }
+            f += inter;
+            pp += bij - b0;
+            mm += (bij - b0) + ri;
+        }
+    }
+    *F = f; *M = mm; *P = pp; *Rsum = rs;
+    free(colptr); free(rowidx); free(slot);
+}

@@ -1,0 +1,145 @@
+"""Seeded synthetic inputs shaped like the paper's workloads (Section 4.4).
+
+This module only draws random numbers: it holds none of the method's
+arithmetic (no distances, no kernel, no ordering), so both the CPU oracle's
+tests and the CUDA path consume the very same arrays.
+
+Every generator uses NumPy's PCG64 bit generator; the default seed of a
+workload is ``SEED_BASE + 1000 * workload_id + replicate``.
+
+Workloads
+---------
+* ``uniform(N, d)``: x ~ U[0,1]^d i.i.d., the paper's default point cloud
+  (Section 4.4, Tables 1-5).
+* ``jittered_grid(n_side)``: a regular n_side x n_side grid of cell centres in
+  [0,1]^2 with i.i.d. uniform jitter of +-0.25 cell, listed in a seeded random
+  order so that the input order carries no structure.
+* ``swiss_roll(N, ambient)``: a 2-D swiss-roll surface embedded by a seeded
+  orthonormal map into R^ambient, plus Gaussian noise sigma=1e-3 (stands in for
+  the paper's high-dimensional point sets of Section 4.4, whose exact
+  structures are shown only in a figure).
+* ``batch_sets`` / ``serving_requests``: the mixes of many independent sets.
+* ``rhs(N, nrhs)``: right-hand sides ~ N(0, I), column-major (N x nrhs).
+* ``sample_pairs(N, m)``: index pairs i.i.d. uniform on I x I, the sample the
+  paper's error estimator E draws (Section 4.4).
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+SEED_BASE = 1706_02205
+
+
+def rng(seed: int) -> np.random.Generator:
+    return np.random.Generator(np.random.PCG64(seed))
+
+
+def seed_for(workload: int, replicate: int = 0) -> int:
+    return SEED_BASE + 1000 * workload + replicate
+
+
+def uniform(N: int, d: int, seed: int = seed_for(1)) -> np.ndarray:
+    """N points i.i.d. uniform in [0,1]^d, float64, row-major (N, d)."""
+    return rng(seed).random((N, d), dtype=np.float64)
+
+
+def jittered_grid(n_side: int, jitter: float = 0.25, seed: int = seed_for(2)) -> np.ndarray:
+    """n_side^2 cell-centred grid points in [0,1]^2, jitter +-``jitter`` cell.
+
+    x = (c + 0.5 + u) / n_side with c in {0..n_side-1}^2 and u ~ U[-jitter,
+    jitter]^2, then shuffled by a seeded permutation.
+    """
+    g = rng(seed)
+    c = np.arange(n_side, dtype=np.float64)
+    cx, cy = np.meshgrid(c, c, indexing="ij")
+    base = np.stack([cx.ravel(), cy.ravel()], axis=1)
+    u = g.uniform(-jitter, jitter, size=base.shape)
+    x = (base + 0.5 + u) / float(n_side)
+    p = g.permutation(x.shape[0])
+    return np.ascontiguousarray(x[p])
+
+
+def swiss_roll(N: int, ambient: int = 20, noise: float = 1e-3, seed: int = seed_for(5)) -> np.ndarray:
+    """Swiss roll (intrinsic dimension 2) embedded in R^ambient.
+
+    t ~ U[1.5 pi, 4.5 pi], h ~ U[0, 1]; y = (t cos t, 10 h, t sin t) / (4.5 pi);
+    x = Q y + noise * xi with Q an ambient x 3 orthonormal matrix (QR of a seeded
+    Gaussian matrix) and xi ~ N(0, I).
+    """
+    g = rng(seed)
+    t = g.uniform(1.5 * math.pi, 4.5 * math.pi, size=N)
+    h = g.uniform(0.0, 1.0, size=N)
+    y = np.stack([t * np.cos(t), 10.0 * h, t * np.sin(t)], axis=1) / (4.5 * math.pi)
+    q, _ = np.linalg.qr(g.standard_normal((ambient, 3)))
+    x = y @ q.T + noise * g.standard_normal((N, ambient))
+    return np.ascontiguousarray(x)
+
+
+def rhs(N: int, nrhs: int = 1, seed: int = seed_for(1, 7)) -> np.ndarray:
+    """Right-hand sides b ~ N(0, I), column-major: shape (nrhs, N), b[r] is RHS r."""
+    return np.ascontiguousarray(rng(seed).standard_normal((nrhs, N)))
+
+
+def sample_pairs(N: int, m: int, seed: int) -> tuple[np.ndarray, np.ndarray]:
+    """m index pairs i.i.d. uniform on {0..N-1}^2 with replacement (diagonal allowed)."""
+    g = rng(seed)
+    i = g.integers(0, N, size=m, dtype=np.int64)
+    j = g.integers(0, N, size=m, dtype=np.int64)
+    return i, j
+
+
+def unit_vector(N: int, seed: int) -> np.ndarray:
+    """A start vector ~ N(0, I) normalised to unit 2-norm (power iteration)."""
+    v = rng(seed).standard_normal(N)
+    return v / np.linalg.norm(v)
+
+
+def batch_sets(n_sets: int = 256, n_min: int = 2000, n_max: int = 50000, n_d3: int = 64,
+               ell_lo: float = 0.05, ell_hi: float = 0.3, seed: int = seed_for(4)):
+    """Independent point sets of uneven size for one batched launch.
+
+    N_s = floor(exp(U[ln n_min, ln n_max])); the last ``n_d3`` sets are 3-D, the
+    rest 2-D; points U[0,1]^d; Matern length scale ell_s ~ U[ell_lo, ell_hi].
+    Returns a list of dicts {"x": (N_s, d) float64, "ell": float}.
+    """
+    g = rng(seed)
+    out = []
+    for s in range(n_sets):
+        n = int(math.floor(math.exp(g.uniform(math.log(n_min), math.log(n_max)))))
+        d = 3 if s >= n_sets - n_d3 else 2
+        ell = float(g.uniform(ell_lo, ell_hi))
+        out.append({"x": g.random((n, d), dtype=np.float64), "ell": ell})
+    return out
+
+
+def serving_requests(n_req: int, rate_hz: float, n_min: int = 10_000, n_max: int = 1_000_000,
+                     seed: int = seed_for(5, 1)):
+    """A Poisson stream of factor+solve requests of mixed size and dimension.
+
+    Inter-arrival times ~ Exp(rate); N ~ log-U[n_min, n_max]; half of the
+    requests are U[0,1]^d with d uniform in {2, 3}, half a swiss roll in R^20;
+    rho uniform in {3, 4}; nrhs uniform in {1..8}.  Points are not drawn here:
+    each request carries its own seed so that a request can be regenerated
+    alone.
+    """
+    g = rng(seed)
+    t = 0.0
+    reqs = []
+    for r in range(n_req):
+        t += float(g.exponential(1.0 / rate_hz))
+        n = int(math.floor(math.exp(g.uniform(math.log(n_min), math.log(n_max)))))
+        kind = "swiss" if g.random() < 0.5 else "cube"
+        d = 20 if kind == "swiss" else int(g.integers(2, 4))
+        rho = float(g.choice([3.0, 4.0]))
+        nrhs = int(g.integers(1, 9))
+        reqs.append({"id": r, "t_arrival": t, "N": n, "kind": kind, "d": d, "rho": rho,
+                     "nrhs": nrhs, "seed": int(g.integers(0, 2**62))})
+    return reqs
+
+
+def request_points(req) -> np.ndarray:
+    if req["kind"] == "swiss":
+        return swiss_roll(req["N"], ambient=req["d"], seed=req["seed"])
+    return uniform(req["N"], req["d"], seed=req["seed"])

@@ -1,0 +1,72 @@
+"""Independent textbook/library computations used to pin the oracle.
+
+Nothing here calls the oracle: the Matern kernel is evaluated from its
+general Bessel-function definition (Eq. (Matern), Section 4.4) with SciPy's
+``kv``, distances with SciPy's ``cdist``, and factors with NumPy/SciPy's dense
+LAPACK routines.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+from scipy.spatial.distance import cdist
+from scipy.special import gamma, kv
+
+
+def matern_general(r, nu, ell, sigma2=1.0):
+    """sigma2 * 2^{1-nu}/Gamma(nu) * (sqrt(2 nu) r / ell)^nu K_nu(sqrt(2 nu) r / ell), value sigma2 at r=0."""
+    r = np.asarray(r, dtype=np.float64)
+    t = math.sqrt(2.0 * nu) * r / ell
+    out = np.full(r.shape, sigma2, dtype=np.float64)
+    nz = t > 0
+    tt = t[nz]
+    out[nz] = sigma2 * (2.0 ** (1.0 - nu) / gamma(nu)) * tt ** nu * kv(nu, tt)
+    return out
+
+
+def dense_theta(x, nu, ell, sigma2=1.0, nugget=0.0):
+    D = cdist(x, x)
+    T = matern_general(D, nu, ell, sigma2)
+    T[np.diag_indices_from(T)] = sigma2 + nugget
+    return T
+
+
+def dense_lower(rowptr, col, val, N):
+    L = np.zeros((N, N))
+    for j in range(N):
+        for e in range(rowptr[j], rowptr[j + 1]):
+            L[j, col[e]] = val[e]
+    return L
+
+
+def pattern_mask(rowptr, col, N):
+    M = np.zeros((N, N), dtype=bool)
+    for j in range(N):
+        M[j, col[rowptr[j]:rowptr[j + 1]]] = True
+    return M | M.T
+
+
+def ichol_right_looking(A, S):
+    """The paper's Algorithm 2 as printed (right-looking), on a dense array.
+
+    Entries outside S are zeroed first; at step i the column is divided by
+    sqrt(A_ii) and A_kj -= A_ki A_ji / A_ii for j > i with (i,j) in S and
+    k >= j with (k,i), (k,j) in S.  A nonpositive pivot zeroes column i and
+    skips its updates (Section 4.4).
+    """
+    A = np.where(S, A, 0.0).astype(np.float64).copy()
+    N = A.shape[0]
+    L = np.zeros_like(A)
+    for i in range(N):
+        piv = A[i, i]
+        if not piv > 0.0:
+            continue
+        L[i:, i] = A[i:, i] / math.sqrt(piv)
+        for j in range(i + 1, N):
+            if not S[i, j]:
+                continue
+            ks = np.arange(j, N)
+            ks = ks[S[ks, i] & S[ks, j]]
+            A[ks, j] -= A[ks, i] * A[j, i] / piv
+    return np.tril(L)

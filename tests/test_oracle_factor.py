@@ -1,0 +1,132 @@
+"""Pins of the oracle's kernel entries, ICHOL(0) factor and error estimator.
+
+* Matern closed forms against the general Bessel definition (SciPy ``kv``).
+* rho = infinity: ICHOL(0) is the dense Cholesky factor (NumPy/LAPACK).
+* The paper's Algorithm 2 as printed (right-looking, dense, tests/refmath.py)
+  equals the oracle's left-looking form, zeroed columns included.
+* (L L^T)_ij = Theta_ij on S when no pivot is dropped.
+* E: the sampled estimator against the exact dense Frobenius ratio; the
+  paper's magnitude E ~ 1.2e-3 (Table 1) and its exponential decay in rho
+  (Tables 3 and 4).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1706_02205_gb300 import inputs
+from tests import refmath
+
+
+@pytest.mark.parametrize("nu", [0.5, 1.5, 2.5])
+def test_matern_closed_forms_vs_bessel(nu):
+    r = np.concatenate([[0.0], np.geomspace(1e-6, 5.0, 200)])
+    for ell in (0.05, 0.2, 1.0):
+        want = refmath.matern_general(r, nu, ell, 1.7)
+        got = np.array([oracle.matern(v, nu, ell, 1.7) for v in r])
+        np.testing.assert_allclose(got, want, rtol=1e-12, atol=1e-300)
+
+
+def _row_rel_err(A, B):
+    """max_j max_i |A_ji - B_ji| / ||B_j,:||_2."""
+    nrm = np.linalg.norm(B, axis=1)
+    nrm[nrm == 0] = 1.0
+    return np.max(np.abs(A - B) / nrm[:, None])
+
+
+@pytest.mark.parametrize("nu,ell,d", [(0.5, 0.2, 2), (1.5, 0.3, 3), (2.5, 0.5, 2)])
+def test_rho_infinity_is_dense_cholesky(nu, ell, d):
+    N = 300
+    x = inputs.uniform(N, d, seed=31)
+    kern = oracle.Kernel(nu, ell, 1.0, 1e-3 if nu > 0.5 else 0.0)
+    perm, l = oracle.maximin_brute(x)
+    xo = x[perm]
+    rp, col = oracle.pattern(xo, l, 1e300)
+    assert rp[-1] == N * (N + 1) // 2
+    val, zc = oracle.ichol(xo, rp, col, kern)
+    assert not zc.any()
+    L = refmath.dense_lower(rp, col, val, N)
+    T = refmath.dense_theta(xo, nu, ell, 1.0, kern.nugget)
+    Lref = np.linalg.cholesky(T)
+    assert _row_rel_err(L, Lref) < 1e-11
+
+
+@pytest.mark.parametrize("nu,rho", [(0.5, 2.0), (1.5, 2.0), (1.5, 3.0), (2.5, 2.5)])
+def test_left_looking_equals_right_looking_algorithm(nu, rho):
+    N = 220
+    x = inputs.uniform(N, 2, seed=41)
+    kern = oracle.Kernel(nu, 0.2)
+    perm, l = oracle.maximin_brute(x)
+    xo = x[perm]
+    rp, col = oracle.pattern(xo, l, rho)
+    val, zc = oracle.ichol(xo, rp, col, kern)
+    L = refmath.dense_lower(rp, col, val, N)
+    S = refmath.pattern_mask(rp, col, N)
+    T = refmath.dense_theta(xo, nu, 0.2)
+    Lr = refmath.ichol_right_looking(T, S)
+    zr = ~(np.diag(Lr) > 0)
+    assert np.array_equal(zr, zc)
+    assert _row_rel_err(L, Lr) < 1e-11
+
+
+def test_zero_pivot_rule_present_for_smooth_kernel():
+    """Matern-3/2, l=0.2, rho=3 on 2000 uniform points drops some pivots
+    (Section 4.4: the column is zeroed and rank(L) < N is reported)."""
+    x = inputs.uniform(2000, 2, seed=inputs.seed_for(1))
+    r = oracle.pipeline(x, 3.0, oracle.Kernel(1.5, 0.2))
+    z = r["zero_col"]
+    assert 0 < z.sum() < 200
+    rp, col, val = r["rowptr"], r["col"], r["val"]
+    # every entry of a zeroed column is exactly zero
+    colmask = z[col]
+    assert np.all(val[colmask] == 0.0)
+
+
+@pytest.mark.parametrize("nu,rho,nugget", [(0.5, 3.0, 0.0), (1.5, 4.0, 0.0), (2.5, 5.0, 1e-4)])
+def test_llt_reproduces_theta_on_pattern(nu, rho, nugget):
+    N = 1500
+    x = inputs.uniform(N, 2, seed=51)
+    kern = oracle.Kernel(nu, 0.1, 1.0, nugget)
+    r = oracle.pipeline(x, rho, kern)
+    assert not r["zero_col"].any()      # the identity holds only without drops
+    rp, col, val, xo = r["rowptr"], r["col"], r["val"], r["x_ord"]
+    L = refmath.dense_lower(rp, col, val, N)
+    LLt = L @ L.T
+    T = refmath.dense_theta(xo, nu, 0.1, 1.0, nugget)
+    S = refmath.pattern_mask(rp, col, N)
+    assert np.max(np.abs(LLt - T)[S]) < 1e-13
+
+
+def test_sampled_error_estimator_vs_dense():
+    N = 2000
+    x = inputs.uniform(N, 2, seed=61)
+    kern = oracle.Kernel(0.5, 0.2)
+    r = oracle.pipeline(x, 2.0, kern)
+    rp, col, val, xo, perm = r["rowptr"], r["col"], r["val"], r["x_ord"], r["perm"]
+    L = refmath.dense_lower(rp, col, val, N)
+    T = refmath.dense_theta(xo, 0.5, 0.2)
+    exact = np.linalg.norm(L @ L.T - T) / np.linalg.norm(T)
+    pi, pj = inputs.sample_pairs(N, 500_000, seed=5)
+    a, b, c = oracle.frob_error(xo, rp, col, val, perm, kern, pi, pj)
+    est = np.sqrt(a / b)
+    assert c == 500_000
+    assert abs(est / exact - 1) < 0.05, (est, exact)
+    # and one entry by hand
+    i, j = 17, 1234
+    assert abs(oracle.llt_entry(rp, col, val, i, j) - (L @ L.T)[i, j]) < 1e-15
+
+
+def test_error_magnitude_and_rho_decay_like_paper():
+    """Table 1: E ~ 1.2e-3 for nu=1/2, l=0.2, rho=3, d=2 (N >= 2e4); Tables
+    3/4: E drops by a factor 0.1-0.3 per unit of rho."""
+    N = 20000
+    x = inputs.uniform(N, 2, seed=inputs.seed_for(1, 102))
+    kern = oracle.Kernel(0.5, 0.2)
+    pi, pj = inputs.sample_pairs(N, 500_000, seed=9)
+    E = {}
+    for rho in (2.0, 3.0, 4.0, 5.0):
+        r = oracle.pipeline(x, rho, kern)
+        a, b, _ = oracle.frob_error(r["x_ord"], r["rowptr"], r["col"], r["val"], r["perm"], kern, pi, pj)
+        E[rho] = np.sqrt(a / b)
+    assert 0.8e-3 < E[3.0] < 1.8e-3, E
+    for rho in (2.0, 3.0, 4.0):
+        assert E[rho + 1] / E[rho] < 0.35, E
