@@ -1,0 +1,181 @@
+/*
+ * libkchol -- sparse Cholesky factorisation of dense Matern kernel matrices
+ * on one GB300 (sm_103a), following Schaefer, Sullivan and Owhadi,
+ * "Compression, inversion, and approximate PCA of dense kernel matrices at
+ * near-linear computational complexity" (arXiv:1706.02205).
+ *
+ * The method: order the points x_1..x_N by the maximin ordering (Section 2.3),
+ * keep the sparsity pattern S_rho = {(i,j): dist(x_i,x_j) <= rho max(l_i,l_j)}
+ * (Section 2.3), and run zero fill-in incomplete Cholesky ICHOL(0) (Algorithm 2)
+ * on the kernel matrix Theta restricted to S, with Theta_ij evaluated from the
+ * coordinates.  The factor L then serves the tasks of Section 1: solves with
+ * Theta (task (2)) and rank-k PCA (task (5), Section 2.5).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  - Plain C ABI.  Pointers marked "device" are CUDA device pointers owned by
+ *    the caller; pointers marked "host" are ordinary host memory.  The library
+ *    never frees caller memory.  Internal scratch is taken with
+ *    cudaMallocAsync on the given stream and released before the call returns
+ *    (stream-ordered).
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *    Kernels are enqueued on it.  A call that returns a size to the host
+ *    (marked "synchronises") waits for the stream.
+ *  - Points: double x[N*d], row-major, original order.  After ordering,
+ *    "position" k means the k-th point of the maximin order; perm[k] is its
+ *    original index and x_ord[k*d+t] its coordinates.
+ *  - The pattern of L is CSR by rows in positions: rowptr[N+1] (int64),
+ *    col[nnz] (int32) ascending in each row, the diagonal last in each row.
+ *  - Every call returns a kc_status; KC_OK is 0.  kc_last_error() gives a
+ *    message for the calling thread's last failure.
+ *  - Squared distances are summed coordinate by coordinate, each operation
+ *    rounded separately (no fused multiply-add), so ordering and pattern are
+ *    bit-identical to a CPU implementation of their definitions.
+ */
+#ifndef KCHOL_H
+#define KCHOL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    KC_OK = 0,
+    KC_EINVAL = 1,     /* bad argument */
+    KC_ENOMEM = 2,     /* scratch allocation failed */
+    KC_ECUDA = 3,      /* a CUDA runtime call failed */
+    KC_ETIMEOUT = 4,   /* a bounded device-side wait ran out (no hang, no trap) */
+    KC_ENOTCONV = 5,   /* iterative refinement did not reach rtol */
+    KC_ERANKDEF = 6,   /* informational: some pivots were dropped */
+    KC_EINDEF = 7      /* CG met nonpositive curvature */
+} kc_status;
+
+/* Matern covariance (Eq. (Matern), Section 4.4) with nu in {0.5, 1.5, 2.5}
+ * (closed forms of K_nu for half-integer nu), length scale ell, variance
+ * sigma2; nugget is added on the diagonal only (Section 4.3). */
+typedef struct {
+    double nu;
+    double ell;
+    double sigma2;
+    double nugget;
+} kc_kernel;
+
+typedef enum { KC_RULE_MAX = 0, KC_RULE_MIN = 1 } kc_rule;
+/* KC_RULE_MAX: (j,i), i before j, is in S iff dist <= rho*l[i] (Section 2.3).
+ * KC_RULE_MIN: iff dist <= rho*l[j] (the pattern of Section 6). */
+
+typedef enum { KC_FP64 = 0, KC_FP32_FORM = 1 } kc_prec;
+/* KC_FP64: values, entries and sums in double; val is double[nnz].
+ * KC_FP32_FORM: val is float[nnz]; dot products in float with compensated
+ * (Dot2, Ogita-Rump-Oishi) accumulation, combined in double; the pivot
+ * Theta_ii - sum L_ik^2 and its square root in double (diag[] keeps it). */
+
+/* Device view of a pattern and its schedule (all pointers device, caller-owned). */
+typedef struct {
+    int64_t N;
+    int64_t nnz;
+    const int64_t* rowptr;   /* [N+1] CSR rows of L */
+    const int32_t* col;      /* [nnz] */
+    const int64_t* colptr;   /* [N+1] CSC columns of L (from kc_schedule) */
+    const int32_t* rowidx;   /* [nnz] rows of each column, ascending, diagonal first */
+    const int64_t* slot;     /* [nnz] CSR position of each CSC entry */
+    const int32_t* order;    /* [N]   columns sorted by (dependency level, index) */
+    int32_t depth;           /* number of dependency levels */
+} kc_pattern;
+
+/* Options of the persistent kernels (zero-initialise for defaults). */
+typedef struct {
+    int64_t spin_limit_cycles;     /* bound of every device wait; 0 -> ~4e9 cycles */
+    int32_t rows_per_task;         /* rows of a column per task; 0 -> 64 */
+    int32_t ctas_per_sm;           /* persistent grid = SMs x this; 0 -> occupancy */
+    int32_t warps_per_cta;         /* 0 -> 8 */
+    int32_t test_hold_column;      /* test hook: 0 = off; c+1 makes column c never signal
+                                      ready, so a wait on it runs out (KC_ETIMEOUT) */
+} kc_opts;
+
+const char* kc_last_error(void);
+int32_t kc_abi_version(void);
+
+/* ---- a2: maximin ordering (Section 2.3) -------------------------------- *
+ * x: device double[N*d].  Outputs (device): perm int32[N] (position ->
+ * original index), l double[N] (l[0] = +inf; first point = original index 0;
+ * ties of the squared distance go to the smaller original index), x_ord
+ * double[N*d] (x permuted).  d >= 1, N >= 1.  Exact: equals the greedy
+ * definition bit for bit.  Synchronises. */
+kc_status kc_order_points(const double* x, int64_t N, int32_t d, int32_t* perm, double* l,
+                          double* x_ord, void* stream);
+
+/* ---- a3: sparsity pattern S_rho (Section 2.3), two phases --------------- *
+ * kc_pattern_count fills rowptr (device int64[N+1]) and returns nnz through
+ * nnz_out (host); synchronises.  kc_pattern_fill writes col (device
+ * int32[nnz]), ascending per row, diagonal last.  rho > 0. */
+kc_status kc_pattern_count(const double* x_ord, const double* l, int64_t N, int32_t d, double rho,
+                           int32_t rule, int64_t* rowptr, int64_t* nnz_out, void* stream);
+kc_status kc_pattern_fill(const double* x_ord, const double* l, int64_t N, int32_t d, double rho,
+                          int32_t rule, const int64_t* rowptr, int32_t* col, void* stream);
+
+/* ---- a4: schedule ------------------------------------------------------ *
+ * From the CSR rows: CSC (colptr int64[N+1], rowidx int32[nnz], slot
+ * int64[nnz]), dependency levels level int32[N] with level(i) = 1 + max over
+ * k in row i of level(k), and order int32[N] = columns sorted by (level,
+ * index).  depth_out (host) = number of levels.  Synchronises. */
+kc_status kc_schedule(int64_t N, const int64_t* rowptr, const int32_t* col, int64_t* colptr,
+                      int32_t* rowidx, int64_t* slot, int32_t* level, int32_t* order,
+                      int32_t* depth_out, void* stream);
+
+/* ---- a5+a6: ICHOL(0) factor (Algorithm 2, left-looking form) ------------ *
+ * For each column i in dependency order: p = Theta_ii - sum_k L_ik^2; if
+ * p <= 0 the whole column is zero (Section 4.4); else L_ii = sqrt(p) and
+ * L_ji = (Theta_ji - sum_{k in R_j and R_i} L_jk L_ik) / L_ii.  Theta is
+ * evaluated from x_ord (device double[N*d]) inside the kernel.
+ * val: device double[nnz] (KC_FP64) or float[nnz] (KC_FP32_FORM), CSR layout.
+ * diag: device double[N], the FP64 L_ii (0 for a dropped pivot).
+ * zero_pivots_out (host, may be NULL): dropped pivots.  One persistent launch.
+ * Returns KC_ETIMEOUT if a dependency wait ran out.  Synchronises. */
+kc_status kc_factor(const kc_pattern* pat, const double* x_ord, int32_t d, const kc_kernel* kern,
+                    int32_t prec, void* val, double* diag, int64_t* zero_pivots_out,
+                    const kc_opts* opts, void* stream);
+
+/* ---- a7: solve L L^T x = b (task (2) with the factor) ------------------- *
+ * b, x: device double[nrhs*N], column-major (rhs r at offset r*N), original
+ * point order.  perm: device int32[N].  A dropped pivot uses
+ * sqrt(Theta_ii) = sqrt(sigma2 + nugget) on the diagonal (kern gives it).
+ * 1 <= nrhs <= 16.  Level-scheduled sparse triangular solves, FP64 sums. */
+kc_status kc_solve(const kc_pattern* pat, int32_t prec, const void* val, const double* diag,
+                   const kc_kernel* kern, const int32_t* perm, const double* b, int32_t nrhs,
+                   double* x, const kc_opts* opts, void* stream);
+
+/* ---- a8: refinement: CG on the dense Theta preconditioned by L L^T ------ *
+ * (task (2); CG with the factor as preconditioner, Section 4.3).  The
+ * matrix-vector product with Theta is evaluated from the coordinates in
+ * FP64, O(N^2) per iteration.  Starts from x = 0; stops when every rhs has
+ * ||b - Theta x||_2 <= rtol ||b||_2 or after maxit iterations.
+ * iters_out (host int32[1]), relres_out (host double[nrhs]): recursive
+ * relative residuals.  Returns KC_ENOTCONV or KC_EINDEF on failure. */
+kc_status kc_refine(const kc_pattern* pat, const double* x_ord, int32_t d, const kc_kernel* kern,
+                    int32_t prec, const void* val, const double* diag, const int32_t* perm,
+                    const double* b, int32_t nrhs, double rtol, int32_t maxit, double* x,
+                    int32_t* iters_out, double* relres_out, const kc_opts* opts, void* stream);
+
+/* ---- a9: rank-k PCA (Section 2.5) --------------------------------------- *
+ * Lk: device float[k*N] column-major (column a at offset a*N), the first k
+ * columns of L with rows scattered back to original order. */
+kc_status kc_pca_truncate(const kc_pattern* pat, int32_t prec, const void* val, const int32_t* perm,
+                          int32_t k, float* Lk, void* stream);
+
+/* Power iteration estimate of ||Theta - Lk Lk^T||_2 on original-order points
+ * x (device double[N*d]): iters steps from the unit vector v0 (device
+ * double[N]); estimate_out (host) = |v^T B v|.  Theta v is evaluated on the
+ * fly (FP32 entries, FP64 sums). */
+kc_status kc_pca_error(const double* x, int64_t N, int32_t d, const kc_kernel* kern, int32_t k,
+                       const float* Lk, const double* v0, int32_t iters, double* estimate_out,
+                       void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* KCHOL_H */

@@ -1,0 +1,132 @@
+// The C ABI of libkchol (declared in include/kchol.h): argument checks and
+// dispatch to the device implementations.  No torch types cross it.
+#include "common.cuh"
+
+namespace kc {
+kc_status order_impl(const double* x, int64_t N, int d, int32_t* perm, double* l, double* x_ord, cudaStream_t s);
+kc_status pattern_count_impl(const double* x_ord, const double* l, int64_t N, int d, double rho, int rule,
+                             int64_t* rowptr, int64_t* nnz_out, cudaStream_t s);
+kc_status pattern_fill_impl(const double* x_ord, const double* l, int64_t N, int d, double rho, int rule,
+                            const int64_t* rowptr, int32_t* col, cudaStream_t s);
+kc_status schedule_impl(int64_t N, const int64_t* rowptr, const int32_t* col, int64_t nnz, int64_t* colptr,
+                        int32_t* rowidx, int64_t* slot, int32_t* level, int32_t* order, int32_t* depth_out,
+                        cudaStream_t s);
+kc_status factor_impl(const kc_pattern* P, const double* x, int d, const kc_kernel* kern, int prec, void* val,
+                      double* diag, int64_t* zero_out, const kc_opts* o, cudaStream_t s);
+kc_status solve_impl(const kc_pattern* P, int prec, const void* val, const double* diag, const kc_kernel* kern,
+                     const int32_t* perm, const double* b, int nrhs, double* x, const kc_opts* o, cudaStream_t s);
+kc_status refine_impl(const kc_pattern* P, const double* x_ord, int d, const kc_kernel* kern, int prec,
+                      const void* val, const double* diag, const int32_t* perm, const double* b, int nrhs,
+                      double rtol, int maxit, double* x_out, int32_t* iters_out, double* relres_out,
+                      const kc_opts* o, cudaStream_t s);
+kc_status pca_truncate_impl(const kc_pattern* P, int prec, const void* val, const int32_t* perm, int k, float* Lk,
+                            cudaStream_t s);
+kc_status pca_error_impl(const double* x, int64_t N, int d, const kc_kernel* kern, int k, const float* Lk,
+                         const double* v0, int iters, double* est_out, cudaStream_t s);
+}  // namespace kc
+
+using namespace kc;
+
+static kc_status check_pattern(const kc_pattern* P) {
+    if (!P) return fail(KC_EINVAL, "pattern is NULL");
+    if (P->N < 1) return fail(KC_EINVAL, "pattern N must be >= 1");
+    if (P->N > INT32_MAX) return fail(KC_EINVAL, "N must fit in int32");
+    if (P->nnz < P->N) return fail(KC_EINVAL, "pattern nnz must be >= N (every row holds its diagonal)");
+    if (!P->rowptr || !P->col || !P->colptr || !P->rowidx || !P->slot || !P->order)
+        return fail(KC_EINVAL, "pattern has a NULL array (run kc_schedule first)");
+    return KC_OK;
+}
+
+static kc_status check_points(const void* x, int64_t N, int32_t d) {
+    if (!x) return fail(KC_EINVAL, "points are NULL");
+    if (N < 1 || N > INT32_MAX) return fail(KC_EINVAL, "N must be in 1..2^31-1");
+    if (d < 1 || d > 32) return fail(KC_EINVAL, "d must be in 1..32");
+    return KC_OK;
+}
+
+extern "C" {
+
+const char* kc_last_error(void) { return last_error_cstr(); }
+
+int32_t kc_abi_version(void) { return 1; }
+
+kc_status kc_order_points(const double* x, int64_t N, int32_t d, int32_t* perm, double* l, double* x_ord,
+                          void* stream) {
+    KC_TRY(check_points(x, N, d));
+    if (!perm || !l || !x_ord) return fail(KC_EINVAL, "output arrays must be non-NULL");
+    return order_impl(x, N, d, perm, l, x_ord, (cudaStream_t)stream);
+}
+
+kc_status kc_pattern_count(const double* x_ord, const double* l, int64_t N, int32_t d, double rho, int32_t rule,
+                           int64_t* rowptr, int64_t* nnz_out, void* stream) {
+    KC_TRY(check_points(x_ord, N, d));
+    if (!l || !rowptr) return fail(KC_EINVAL, "l and rowptr must be non-NULL");
+    if (!(rho > 0.0)) return fail(KC_EINVAL, "rho must be > 0");
+    if (rule != KC_RULE_MAX && rule != KC_RULE_MIN) return fail(KC_EINVAL, "rule must be KC_RULE_MAX or KC_RULE_MIN");
+    return pattern_count_impl(x_ord, l, N, d, rho, rule, rowptr, nnz_out, (cudaStream_t)stream);
+}
+
+kc_status kc_pattern_fill(const double* x_ord, const double* l, int64_t N, int32_t d, double rho, int32_t rule,
+                          const int64_t* rowptr, int32_t* col, void* stream) {
+    KC_TRY(check_points(x_ord, N, d));
+    if (!l || !rowptr || !col) return fail(KC_EINVAL, "l, rowptr and col must be non-NULL");
+    if (!(rho > 0.0)) return fail(KC_EINVAL, "rho must be > 0");
+    if (rule != KC_RULE_MAX && rule != KC_RULE_MIN) return fail(KC_EINVAL, "rule must be KC_RULE_MAX or KC_RULE_MIN");
+    return pattern_fill_impl(x_ord, l, N, d, rho, rule, rowptr, col, (cudaStream_t)stream);
+}
+
+kc_status kc_schedule(int64_t N, const int64_t* rowptr, const int32_t* col, int64_t* colptr, int32_t* rowidx,
+                      int64_t* slot, int32_t* level, int32_t* order, int32_t* depth_out, void* stream) {
+    if (N < 1 || N > INT32_MAX) return fail(KC_EINVAL, "N must be in 1..2^31-1");
+    if (!rowptr || !col || !colptr || !rowidx || !slot || !level || !order)
+        return fail(KC_EINVAL, "arrays must be non-NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    int64_t nnz = 0;
+    KC_CUDA(cudaMemcpyAsync(&nnz, rowptr + N, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    KC_CUDA(cudaStreamSynchronize(s));
+    if (nnz < N) return fail(KC_EINVAL, "rowptr[N] must be >= N");
+    return schedule_impl(N, rowptr, col, nnz, colptr, rowidx, slot, level, order, depth_out, s);
+}
+
+kc_status kc_factor(const kc_pattern* pat, const double* x_ord, int32_t d, const kc_kernel* kern, int32_t prec,
+                    void* val, double* diag, int64_t* zero_pivots_out, const kc_opts* opts, void* stream) {
+    KC_TRY(check_pattern(pat));
+    KC_TRY(check_points(x_ord, pat->N, d));
+    if (!val || !diag) return fail(KC_EINVAL, "val and diag must be non-NULL");
+    return factor_impl(pat, x_ord, d, kern, prec, val, diag, zero_pivots_out, opts, (cudaStream_t)stream);
+}
+
+kc_status kc_solve(const kc_pattern* pat, int32_t prec, const void* val, const double* diag, const kc_kernel* kern,
+                   const int32_t* perm, const double* b, int32_t nrhs, double* x, const kc_opts* opts, void* stream) {
+    KC_TRY(check_pattern(pat));
+    if (!val || !diag || !perm || !b || !x) return fail(KC_EINVAL, "arrays must be non-NULL");
+    return solve_impl(pat, prec, val, diag, kern, perm, b, nrhs, x, opts, (cudaStream_t)stream);
+}
+
+kc_status kc_refine(const kc_pattern* pat, const double* x_ord, int32_t d, const kc_kernel* kern, int32_t prec,
+                    const void* val, const double* diag, const int32_t* perm, const double* b, int32_t nrhs,
+                    double rtol, int32_t maxit, double* x, int32_t* iters_out, double* relres_out,
+                    const kc_opts* opts, void* stream) {
+    KC_TRY(check_pattern(pat));
+    KC_TRY(check_points(x_ord, pat->N, d));
+    if (!val || !diag || !perm || !b || !x) return fail(KC_EINVAL, "arrays must be non-NULL");
+    if (!(rtol > 0.0) || maxit < 0) return fail(KC_EINVAL, "need rtol > 0 and maxit >= 0");
+    return refine_impl(pat, x_ord, d, kern, prec, val, diag, perm, b, nrhs, rtol, maxit, x, iters_out, relres_out,
+                       opts, (cudaStream_t)stream);
+}
+
+kc_status kc_pca_truncate(const kc_pattern* pat, int32_t prec, const void* val, const int32_t* perm, int32_t k,
+                          float* Lk, void* stream) {
+    KC_TRY(check_pattern(pat));
+    if (!val || !perm || (!Lk && k > 0)) return fail(KC_EINVAL, "arrays must be non-NULL");
+    return pca_truncate_impl(pat, prec, val, perm, k, Lk, (cudaStream_t)stream);
+}
+
+kc_status kc_pca_error(const double* x, int64_t N, int32_t d, const kc_kernel* kern, int32_t k, const float* Lk,
+                       const double* v0, int32_t iters, double* estimate_out, void* stream) {
+    KC_TRY(check_points(x, N, d));
+    if (k < 0 || k > N || (k > 0 && !Lk) || !v0 || iters < 1) return fail(KC_EINVAL, "bad PCA error arguments");
+    return pca_error_impl(x, N, d, kern, k, Lk, v0, iters, estimate_out, (cudaStream_t)stream);
+}
+
+}  // extern "C"

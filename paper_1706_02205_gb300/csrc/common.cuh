@@ -1,0 +1,145 @@
+// Shared device helpers of libkchol (sm_103a).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/kchol.h"
+
+namespace kc {
+
+// ---------------------------------------------------------------- errors
+void set_error(const std::string& msg);
+const char* last_error_cstr();
+kc_status fail(kc_status st, const std::string& msg);
+kc_status cuda_fail(cudaError_t e, const char* what);
+
+#define KC_CUDA(call)                                                        \
+    do {                                                                     \
+        cudaError_t _e = (call);                                             \
+        if (_e != cudaSuccess) return ::kc::cuda_fail(_e, #call);            \
+    } while (0)
+
+#define KC_TRY(expr)                                                         \
+    do {                                                                     \
+        kc_status _s = (expr);                                               \
+        if (_s != KC_OK) return _s;                                          \
+    } while (0)
+
+// Device status word values written by kernels (0 = fine).
+enum : int { DEV_OK = 0, DEV_TIMEOUT = 1, DEV_BAD_INPUT = 2 };
+
+// ------------------------------------------------------- stream scratch
+// Stream-ordered scratch: every buffer is freed (cudaFreeAsync) when the
+// arena goes out of scope, after the work enqueued before that point.
+struct Arena {
+    cudaStream_t s;
+    void* ptrs[64];
+    int n = 0;
+    explicit Arena(cudaStream_t st) : s(st) {}
+    ~Arena() {
+        for (int i = n - 1; i >= 0; --i) cudaFreeAsync(ptrs[i], s);
+    }
+    template <typename T>
+    kc_status get(T** out, size_t count) {
+        if (n == 64) return fail(KC_ENOMEM, "scratch arena full");
+        void* p = nullptr;
+        size_t bytes = count * sizeof(T);
+        if (bytes == 0) bytes = 16;
+        cudaError_t e = cudaMallocAsync(&p, bytes, s);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync(scratch)");
+        ptrs[n++] = p;
+        *out = (T*)p;
+        return KC_OK;
+    }
+};
+
+int sm_count();
+
+// ------------------------------------------------------ device helpers
+__device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ int ld_acquire_s32(const int* p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_s32(int* p, int v) {
+    asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ void red_release_add_u32(unsigned* p, unsigned v) {
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ int ld_volatile_s32(const int* p) { return *(volatile const int*)p; }
+
+// Loads that bypass L1 (values written by other SMs during the same launch).
+__device__ __forceinline__ double ldcg(const double* p) { return __ldcg(p); }
+__device__ __forceinline__ float ldcg(const float* p) { return __ldcg(p); }
+
+// Squared distance summed in coordinate order, every operation rounded on its
+// own (no FMA contraction), so the bits equal a plain CPU evaluation.
+__device__ __forceinline__ double dist2_exact(const double* a, const double* b, int d) {
+    double s = 0.0;
+    for (int t = 0; t < d; ++t) {
+        double u = __dsub_rn(a[t], b[t]);
+        s = __dadd_rn(s, __dmul_rn(u, u));
+    }
+    return s;
+}
+
+// Matern covariance, closed forms for nu in {1/2, 3/2, 5/2}; nu_code = 0,1,2.
+// scale = sqrt(2 nu)/ell.
+__device__ __forceinline__ double matern_f64(double r, int nu_code, double scale, double sigma2) {
+    double t = r * scale;
+    double e = exp(-t);
+    if (nu_code == 0) return sigma2 * e;
+    if (nu_code == 1) return sigma2 * (1.0 + t) * e;
+    return sigma2 * (1.0 + t + t * t * (1.0 / 3.0)) * e;
+}
+__device__ __forceinline__ float matern_f32(float r, int nu_code, float scale, float sigma2) {
+    float t = r * scale;
+    float e = expf(-t);
+    if (nu_code == 0) return sigma2 * e;
+    if (nu_code == 1) return sigma2 * (1.0f + t) * e;
+    return sigma2 * (1.0f + t + t * t * (1.0f / 3.0f)) * e;
+}
+
+struct KernelParams {
+    int nu_code;
+    double scale;   // sqrt(2 nu) / ell
+    double sigma2;
+    double nugget;
+};
+kc_status kernel_params(const kc_kernel* k, KernelParams* out);
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// ------------------------------------------------------- primitives
+// Exclusive scan of n int64 values: out[0..n] with out[n] = total.
+// `out` may alias `in` only if out has n+1 slots starting at in.
+kc_status exclusive_scan_i64(const int64_t* in, int64_t* out, int64_t n, Arena& A, cudaStream_t s);
+kc_status exclusive_scan_i32_to_i64(const int32_t* in, int64_t* out, int64_t n, Arena& A, cudaStream_t s);
+
+// Stable LSD radix sort of (key, value) pairs by the low `bits` bits of key.
+// Keys/values are sorted from (k_in, v_in) into (k_out, v_out); the inputs are
+// used as ping-pong buffers and are clobbered.
+kc_status radix_sort_u64_i64(uint64_t* k_in, int64_t* v_in, uint64_t* k_out, int64_t* v_out, int64_t n,
+                             int bits, Arena& A, cudaStream_t s);
+kc_status radix_sort_u32_i64(uint32_t* k_in, int64_t* v_in, uint32_t* k_out, int64_t* v_out, int64_t n,
+                             int bits, Arena& A, cudaStream_t s);
+
+inline unsigned blocks_for(int64_t n, int per) { return (unsigned)((n + per - 1) / per); }
+
+}  // namespace kc

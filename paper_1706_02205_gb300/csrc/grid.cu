@@ -1,0 +1,151 @@
+#include <cmath>
+
+#include "grid.cuh"
+
+namespace kc {
+
+Grid make_grid(int d, const double* lo, const double* hi, int64_t npts, double want, int64_t max_cells) {
+    Grid g;
+    g.dg = d < 3 ? d : 3;
+    double ext[3] = {0, 0, 0};
+    double vol = 1.0;
+    int nz = 0;
+    for (int t = 0; t < g.dg; ++t) {
+        g.lo[t] = lo[t];
+        ext[t] = hi[t] - lo[t];
+        if (ext[t] > 0) {
+            vol *= ext[t];
+            nz++;
+        }
+    }
+    double emax = 0;
+    for (int t = 0; t < g.dg; ++t) emax = fmax(emax, ext[t]);
+    if (!(emax > 0)) {
+        g.c = 1.0;
+        return g;
+    }
+    if (max_cells < 1) max_cells = 1;
+    // smallest cell size allowed by the cell budget
+    double cmin = nz > 0 ? pow(vol / (double)max_cells, 1.0 / nz) : emax;
+    double c = want > 0 ? want : cmin;
+    if (c < cmin) c = cmin;
+    for (;;) {
+        int64_t tot = 1;
+        bool ok = true;
+        for (int t = 0; t < g.dg; ++t) {
+            double f = floor(ext[t] / c) + 1.0;
+            if (f > 1e6) {
+                ok = false;
+                break;
+            }
+            g.n[t] = (int)f;
+            tot *= g.n[t];
+            if (tot > max_cells) {
+                ok = false;
+                break;
+            }
+        }
+        if (ok) {
+            g.ncells = tot;
+            break;
+        }
+        c *= 1.25;
+    }
+    g.c = c;
+    return g;
+}
+
+__global__ void cell_keys_k(Grid g, const double* __restrict__ x, int d, const int32_t* __restrict__ ids, int64_t n,
+                            uint64_t* __restrict__ key, int64_t* __restrict__ val, int* __restrict__ cnt) {
+    int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q < n) {
+        int64_t id = ids ? ids[q] : q;
+        int64_t c = cell_of(g, x + id * d);
+        key[q] = (uint64_t)c;
+        val[q] = id;
+        atomicAdd(&cnt[c], 1);
+    }
+}
+__global__ void ids_out_k(const int64_t* __restrict__ v, int64_t n, int32_t* __restrict__ out) {
+    int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q < n) out[q] = (int32_t)v[q];
+}
+
+static int bits_of(int64_t v) {
+    int b = 1;
+    while (b < 63 && ((int64_t)1 << b) <= v) ++b;
+    return b;
+}
+
+kc_status grid_build(const Grid& g, const double* x, int d, const int32_t* ids, int64_t n, int32_t* sorted,
+                     int64_t* cell_start, Arena& A, cudaStream_t s) {
+    uint64_t *k0, *k1;
+    int64_t *v0, *v1;
+    int* cnt;
+    KC_TRY(A.get(&k0, n));
+    KC_TRY(A.get(&k1, n));
+    KC_TRY(A.get(&v0, n));
+    KC_TRY(A.get(&v1, n));
+    KC_TRY(A.get(&cnt, g.ncells));
+    KC_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int) * g.ncells, s));
+    if (n > 0) cell_keys_k<<<blocks_for(n, 256), 256, 0, s>>>(g, x, d, ids, n, k0, v0, cnt);
+    KC_CUDA(cudaGetLastError());
+    KC_TRY(exclusive_scan_i32_to_i64(cnt, cell_start, g.ncells, A, s));
+    KC_TRY(radix_sort_u64_i64(k0, v0, k1, v1, n, bits_of(g.ncells), A, s));
+    if (n > 0) ids_out_k<<<blocks_for(n, 256), 256, 0, s>>>(v1, n, sorted);
+    KC_CUDA(cudaGetLastError());
+    return KC_OK;
+}
+
+// per-block min/max over 3 axes, then a single-block fold
+__global__ void bbox_k(const double* __restrict__ x, int64_t N, int d, double* __restrict__ part) {
+    __shared__ double smin[3][256], smax[3][256];
+    int dg = d < 3 ? d : 3;
+    double mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
+        for (int t = 0; t < dg; ++t) {
+            double v = x[i * d + t];
+            mn[t] = fmin(mn[t], v);
+            mx[t] = fmax(mx[t], v);
+        }
+    for (int t = 0; t < 3; ++t) {
+        smin[t][threadIdx.x] = mn[t];
+        smax[t][threadIdx.x] = mx[t];
+    }
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o)
+            for (int t = 0; t < 3; ++t) {
+                smin[t][threadIdx.x] = fmin(smin[t][threadIdx.x], smin[t][threadIdx.x + o]);
+                smax[t][threadIdx.x] = fmax(smax[t][threadIdx.x], smax[t][threadIdx.x + o]);
+            }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0)
+        for (int t = 0; t < 3; ++t) {
+            part[blockIdx.x * 6 + t] = smin[t][0];
+            part[blockIdx.x * 6 + 3 + t] = smax[t][0];
+        }
+}
+
+kc_status bbox(const double* x, int64_t N, int d, double* lo, double* hi, Arena& A, cudaStream_t s) {
+    const int nb = 128;
+    double* part;
+    KC_TRY(A.get(&part, nb * 6));
+    bbox_k<<<nb, 256, 0, s>>>(x, N, d, part);
+    KC_CUDA(cudaGetLastError());
+    double h[nb * 6];
+    KC_CUDA(cudaMemcpyAsync(h, part, sizeof(h), cudaMemcpyDeviceToHost, s));
+    KC_CUDA(cudaStreamSynchronize(s));
+    for (int t = 0; t < 3; ++t) {
+        lo[t] = INFINITY;
+        hi[t] = -INFINITY;
+        for (int b = 0; b < nb; ++b) {
+            lo[t] = fmin(lo[t], h[b * 6 + t]);
+            hi[t] = fmax(hi[t], h[b * 6 + 3 + t]);
+        }
+    }
+    return KC_OK;
+}
+
+}  // namespace kc

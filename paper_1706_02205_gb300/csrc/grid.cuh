@@ -1,0 +1,52 @@
+// Uniform bucketing grid over the first min(d,3) coordinates, used by the
+// ordering and the pattern search.  A point p lies in cell
+// floor((x_p,t - lo_t) / c) (clamped); any point within distance R of p lies
+// in the cells within span = floor(R/c) + 1 of p's cell along each gridded
+// axis, because a coordinate difference never exceeds the distance.
+#pragma once
+#include "common.cuh"
+
+namespace kc {
+
+struct Grid {
+    int dg = 1;           // gridded axes
+    double lo[3] = {0, 0, 0};
+    double c = 1.0;       // cell size
+    int n[3] = {1, 1, 1}; // cells per axis
+    int64_t ncells = 1;
+};
+
+__device__ __forceinline__ int cell_coord(const Grid& g, double v, int t) {
+    double f = (v - g.lo[t]) / g.c;
+    int q = (f <= 0.0) ? 0 : (f >= (double)(g.n[t] - 1) ? g.n[t] - 1 : (int)f);
+    return q;
+}
+__device__ __forceinline__ int64_t cell_of(const Grid& g, const double* x) {
+    int64_t key = 0;
+    for (int t = g.dg - 1; t >= 0; --t) key = key * g.n[t] + cell_coord(g, x[t], t);
+    return key;
+}
+// number of cells to either side covering radius R (R may be +inf)
+__device__ __forceinline__ int span_for(const Grid& g, double R, int t) {
+    if (!(R < 1e300)) return g.n[t];
+    double f = R / g.c;
+    if (f > 4.0e9) return g.n[t];
+    int s = (int)f + 1;
+    return s > g.n[t] ? g.n[t] : s;
+}
+
+// Host: choose a grid for `npts` points in the box [lo, hi] with target cell
+// size `want` (0 = automatic), at most `max_cells` cells.
+Grid make_grid(int d, const double* lo, const double* hi, int64_t npts, double want, int64_t max_cells);
+
+// Build the cell-sorted arrangement of the points `ids` (or 0..n-1 when ids is
+// NULL) with coordinates x (row-major, stride d): outputs
+//   sorted[q]      = the id at sorted position q
+//   cell_start[c]  = first sorted position of cell c, cell_start[ncells] = n
+kc_status grid_build(const Grid& g, const double* x, int d, const int32_t* ids, int64_t n, int32_t* sorted,
+                     int64_t* cell_start, Arena& A, cudaStream_t s);
+
+// Bounding box of x (row-major N x d) over the first min(d,3) axes; host out.
+kc_status bbox(const double* x, int64_t N, int d, double* lo, double* hi, Arena& A, cudaStream_t s);
+
+}  // namespace kc

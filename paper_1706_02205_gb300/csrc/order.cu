@@ -1,0 +1,326 @@
+// a2: the maximin ordering (Section 2.3), exact, on the device.
+//
+// Definition (greedy): the first point is original index 0; each next point
+// is the unselected point with the largest squared distance v(p) to the
+// selected set, ties to the smaller original index; l = sqrt(v at selection).
+// Write key(p) = (v(p), -index).  The l values are non-increasing, so the
+// order is the sort of the points by final key, and each point's final v is
+// what must be found.
+//
+// Parallel rounds.  Keep for every undecided point its v over the points
+// selected so far.  An undecided point q is *dominant* when no undecided
+// point of larger key lies at squared distance < v(q).  Then v(q) is final:
+// no point that ends up before q can come closer than v(q) -- the first such
+// point would have to be selected while q, of larger key, is still
+// available.  All dominant points of a round are selected together.  A
+// selected p then lowers v(q) := min(v(q), d2(p,q)) for undecided q of
+// smaller key; undecided q of larger key are left alone, which is exact: q
+// was within reach of p only if d2(p,q) >= v(p), and if q later falls below
+// p its value is already below d2(p,q).
+//
+// Rounds run in bands of keys: with vmax the largest undecided v, the band
+// holds the undecided points with v >= vmax/4; only band points can dominate
+// band points, so the dominance search uses a grid of band points with cell
+// size sqrt(vmax).  The updates scan a fixed fine grid of all points.
+// Finally the points are sorted by (v descending, index ascending).
+#include <cmath>
+#include <cstring>
+
+#include "grid.cuh"
+
+namespace kc {
+
+__global__ void finite_check_k(const double* __restrict__ x, int64_t n, int* __restrict__ bad) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n && !isfinite(x[i])) atomicExch(bad, 1);
+}
+
+kc_status check_finite(const double* x, int64_t n, Arena& A, cudaStream_t s) {
+    int* bad;
+    KC_TRY(A.get(&bad, 1));
+    KC_CUDA(cudaMemsetAsync(bad, 0, sizeof(int), s));
+    finite_check_k<<<blocks_for(n, 256), 256, 0, s>>>(x, n, bad);
+    KC_CUDA(cudaGetLastError());
+    int h = 0;
+    KC_CUDA(cudaMemcpyAsync(&h, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
+    KC_CUDA(cudaStreamSynchronize(s));
+    if (h) return fail(KC_EINVAL, "points must be finite");
+    return KC_OK;
+}
+
+// state in grid order (gpos): coordinates xg, original index idg, v2, stat
+__global__ void ord_init_k(const double* __restrict__ x, int d, const int32_t* __restrict__ gsorted, int64_t N,
+                           double* __restrict__ xg, int32_t* __restrict__ idg, double* __restrict__ v2,
+                           int* __restrict__ stat) {
+    int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= N) return;
+    int64_t id = gsorted[q];
+    for (int t = 0; t < d; ++t) xg[q * d + t] = x[id * d + t];
+    idg[q] = (int32_t)id;
+    if (id == 0) {
+        v2[q] = INFINITY;
+        stat[q] = 1;
+    } else {
+        v2[q] = dist2_exact(x + id * d, x, d);
+        stat[q] = 0;
+    }
+}
+
+// max of v2 over undecided points and their count
+__global__ void ord_vmax_k(const double* __restrict__ v2, const int* __restrict__ stat, int64_t N,
+                           unsigned long long* __restrict__ vmax_bits, unsigned long long* __restrict__ count) {
+    unsigned long long m = 0, c = 0;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < N; q += (int64_t)gridDim.x * blockDim.x)
+        if (stat[q] == 0) {
+            m = max(m, (unsigned long long)__double_as_longlong(v2[q]));
+            c++;
+        }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+        c += __shfl_xor_sync(0xffffffffu, c, o);
+    }
+    if (lane_id() == 0) {
+        atomicMax(vmax_bits, m);
+        atomicAdd(count, c);
+    }
+}
+
+__global__ void ord_band_k(const double* __restrict__ v2, const int* __restrict__ stat, int64_t N, double T,
+                           int32_t* __restrict__ blist, unsigned long long* __restrict__ nb) {
+    int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q < N && stat[q] == 0 && v2[q] >= T) blist[atomicAdd(nb, 1ULL)] = (int32_t)q;
+}
+
+// one thread per band point: is it dominant?
+__global__ void ord_dominance_k(Grid gb, const int32_t* __restrict__ bsorted, const int64_t* __restrict__ bstart,
+                                int64_t nb, const double* __restrict__ xg, int d, const int32_t* __restrict__ idg,
+                                const double* __restrict__ v2, const int* __restrict__ stat, double T,
+                                int32_t* __restrict__ sel, unsigned long long* __restrict__ nsel,
+                                unsigned long long* __restrict__ nactive) {
+    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= nb) return;
+    const int q = bsorted[e];
+    if (stat[q] != 0) return;
+    const double vq = v2[q];
+    if (!(vq >= T)) return;
+    atomicAdd(nactive, 1ULL);
+    const double* xq = xg + (int64_t)q * d;
+    const int idq = idg[q];
+    const double R = sqrt(vq);
+    int lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+    for (int t = 0; t < gb.dg; ++t) {
+        int cq = cell_coord(gb, xq[t], t);
+        int sp = span_for(gb, R, t);
+        lo[t] = max(0, cq - sp);
+        hi[t] = min(gb.n[t] - 1, cq + sp);
+    }
+    bool dom = true;
+    for (int cz = lo[2]; cz <= hi[2] && dom; ++cz)
+        for (int cy = lo[1]; cy <= hi[1] && dom; ++cy) {
+            int64_t base = ((int64_t)cz * gb.n[1] + cy) * gb.n[0];
+            int64_t f0 = bstart[base + lo[0]], f1 = bstart[base + hi[0] + 1];
+            for (int64_t f = f0; f < f1; ++f) {
+                const int p = bsorted[f];
+                if (p == q || stat[p] != 0) continue;
+                const double vp = v2[p];
+                if (vp > vq || (vp == vq && idg[p] < idq)) {
+                    if (dist2_exact(xg + (int64_t)p * d, xq, d) < vq) {
+                        dom = false;
+                        break;
+                    }
+                }
+            }
+        }
+    if (dom) sel[atomicAdd(nsel, 1ULL)] = q;
+}
+
+__global__ void ord_mark_k(const int32_t* __restrict__ sel, int64_t ns, int* __restrict__ stat) {
+    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < ns) stat[sel[k]] = 1;
+}
+
+// cell-rows of the fine grid covered by the update ball of each selected point
+__device__ __forceinline__ void upd_box(const Grid& g, const double* xp, double R, int* lo, int* hi) {
+    for (int t = 0; t < 3; ++t) {
+        lo[t] = 0;
+        hi[t] = 0;
+    }
+    for (int t = 0; t < g.dg; ++t) {
+        int c = cell_coord(g, xp[t], t);
+        int sp = span_for(g, R, t);
+        lo[t] = max(0, c - sp);
+        hi[t] = min(g.n[t] - 1, c + sp);
+    }
+}
+__global__ void ord_items_k(Grid g, const int32_t* __restrict__ sel, int64_t ns, const double* __restrict__ xg,
+                            int d, const double* __restrict__ v2, int64_t* __restrict__ cnt) {
+    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= ns) return;
+    const int p = sel[k];
+    int lo[3], hi[3];
+    upd_box(g, xg + (int64_t)p * d, sqrt(v2[p]), lo, hi);
+    cnt[k] = (int64_t)(hi[1] - lo[1] + 1) * (hi[2] - lo[2] + 1);
+}
+__global__ void ord_item_fill_k(const int64_t* __restrict__ off, int64_t ns, int32_t* __restrict__ item_sel) {
+    int64_t k = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (k >= ns) return;
+    for (int64_t t = off[k] + lane_id(); t < off[k + 1]; t += 32) item_sel[t] = (int32_t)k;
+}
+
+// one warp per (selected point, cell-row): lower v2 of undecided points of smaller key
+__global__ void ord_update_k(Grid g, const int32_t* __restrict__ sel, const int64_t* __restrict__ off,
+                             const int32_t* __restrict__ item_sel, int64_t nitems, const int64_t* __restrict__ cstart,
+                             const double* __restrict__ xg, int d, const int32_t* __restrict__ idg,
+                             double* __restrict__ v2, const int* __restrict__ stat) {
+    int64_t it = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (it >= nitems) return;
+    const int lane = lane_id();
+    const int k = item_sel[it];
+    const int p = sel[k];
+    const double* xp = xg + (int64_t)p * d;
+    const double vp = v2[p];  // final value of the selected point
+    const int idp = idg[p];
+    int lo[3], hi[3];
+    upd_box(g, xp, sqrt(vp), lo, hi);
+    int64_t r = it - off[k];
+    const int ny = hi[1] - lo[1] + 1;
+    const int cy = lo[1] + (int)(r % ny);
+    const int cz = lo[2] + (int)(r / ny);
+    const int64_t base = ((int64_t)cz * g.n[1] + cy) * g.n[0];
+    const int64_t a = cstart[base + lo[0]], b = cstart[base + hi[0] + 1];
+    unsigned long long* vb = (unsigned long long*)v2;
+    for (int64_t q = a + lane; q < b; q += 32) {
+        if (stat[q] != 0) continue;
+        const double vq = v2[q];
+        if (!(vq < vp || (vq == vp && idg[q] > idp))) continue;
+        const double dd = dist2_exact(xg + q * d, xp, d);
+        if (dd < vq) atomicMin(vb + q, (unsigned long long)__double_as_longlong(dd));
+    }
+}
+
+__global__ void ord_keys_k(const double* __restrict__ v2, const int32_t* __restrict__ idg, int64_t N,
+                           uint64_t* __restrict__ key, int64_t* __restrict__ val) {
+    int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= N) return;
+    int64_t id = idg[q];
+    key[id] = ~(uint64_t)__double_as_longlong(v2[q]);
+    val[id] = id;
+}
+
+__global__ void ord_out_k(const uint64_t* __restrict__ skey, const int64_t* __restrict__ sval, const double* __restrict__ x,
+                          int64_t N, int d, int32_t* __restrict__ perm, double* __restrict__ l,
+                          double* __restrict__ x_ord) {
+    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= N) return;
+    int64_t id = sval[k];
+    perm[k] = (int32_t)id;
+    double v = __longlong_as_double((long long)~skey[k]);
+    l[k] = __dsqrt_rn(v);
+    for (int t = 0; t < d; ++t) x_ord[k * d + t] = x[id * d + t];
+}
+
+kc_status order_impl(const double* x, int64_t N, int d, int32_t* perm, double* l, double* x_ord, cudaStream_t s) {
+    Arena A(s);
+    KC_TRY(check_finite(x, N * d, A, s));
+    double lo[3], hi[3];
+    KC_TRY(bbox(x, N, d, lo, hi, A, s));
+    // fine grid of all points, about two points per cell
+    Grid g0 = make_grid(d, lo, hi, N, 0.0, N / 2 > 1 ? N / 2 : 1);
+    int32_t* gsorted;
+    int64_t* cstart;
+    KC_TRY(A.get(&gsorted, N));
+    KC_TRY(A.get(&cstart, g0.ncells + 1));
+    KC_TRY(grid_build(g0, x, d, nullptr, N, gsorted, cstart, A, s));
+
+    double *xg, *v2;
+    int32_t *idg, *blist, *bsorted, *sel, *item_sel;
+    int* stat;
+    int64_t *bstart, *icnt, *ioff;
+    unsigned long long* ctr;  // [0] vmax bits [1] undecided [2] nb [3] nsel [4] nactive
+    KC_TRY(A.get(&xg, N * d));
+    KC_TRY(A.get(&v2, N));
+    KC_TRY(A.get(&idg, N));
+    KC_TRY(A.get(&stat, N));
+    KC_TRY(A.get(&blist, N));
+    KC_TRY(A.get(&bsorted, N));
+    KC_TRY(A.get(&sel, N));
+    KC_TRY(A.get(&icnt, N));
+    KC_TRY(A.get(&ioff, N + 1));
+    KC_TRY(A.get(&bstart, 2 * N + 2));
+    KC_TRY(A.get(&ctr, 8));
+    ord_init_k<<<blocks_for(N, 256), 256, 0, s>>>(x, d, gsorted, N, xg, idg, v2, stat);
+    KC_CUDA(cudaGetLastError());
+    int64_t item_cap = 0;
+    item_sel = nullptr;
+    const int sms = sm_count();
+    int rounds = 0;
+    for (;;) {
+        KC_CUDA(cudaMemsetAsync(ctr, 0, 2 * sizeof(unsigned long long), s));
+        ord_vmax_k<<<sms * 4, 256, 0, s>>>(v2, stat, N, ctr, ctr + 1);
+        unsigned long long h[2];
+        KC_CUDA(cudaMemcpyAsync(h, ctr, sizeof(h), cudaMemcpyDeviceToHost, s));
+        KC_CUDA(cudaStreamSynchronize(s));
+        if (h[1] == 0) break;
+        double vmax;
+        memcpy(&vmax, &h[0], sizeof(double));
+        const double T = vmax * 0.25;
+        KC_CUDA(cudaMemsetAsync(ctr + 2, 0, sizeof(unsigned long long), s));
+        ord_band_k<<<blocks_for(N, 256), 256, 0, s>>>(v2, stat, N, T, blist, ctr + 2);
+        unsigned long long hnb = 0;
+        KC_CUDA(cudaMemcpyAsync(&hnb, ctr + 2, sizeof(hnb), cudaMemcpyDeviceToHost, s));
+        KC_CUDA(cudaStreamSynchronize(s));
+        const int64_t nb = (int64_t)hnb;
+        Grid gb = make_grid(d, lo, hi, nb, vmax > 0 ? sqrt(vmax) : 0.0, 2 * nb + 1);
+        {
+            Arena B(s);
+            int64_t* bst;
+            KC_TRY(B.get(&bst, gb.ncells + 1));
+            KC_TRY(grid_build(gb, xg, d, blist, nb, bsorted, bst, B, s));
+            KC_CUDA(cudaMemcpyAsync(bstart, bst, sizeof(int64_t) * (gb.ncells + 1), cudaMemcpyDeviceToDevice, s));
+        }
+        for (;;) {
+            if (++rounds > 1000000) return fail(KC_ECUDA, "ordering: too many rounds");
+            KC_CUDA(cudaMemsetAsync(ctr + 3, 0, 2 * sizeof(unsigned long long), s));
+            ord_dominance_k<<<blocks_for(nb, 128), 128, 0, s>>>(gb, bsorted, bstart, nb, xg, d, idg, v2, stat, T, sel,
+                                                                ctr + 3, ctr + 4);
+            unsigned long long hs[2];
+            KC_CUDA(cudaMemcpyAsync(hs, ctr + 3, sizeof(hs), cudaMemcpyDeviceToHost, s));
+            KC_CUDA(cudaStreamSynchronize(s));
+            const int64_t ns = (int64_t)hs[0];
+            if (hs[1] == 0) break;  // band exhausted
+            if (ns == 0) return fail(KC_ECUDA, "ordering: no dominant point in a nonempty band");
+            ord_mark_k<<<blocks_for(ns, 256), 256, 0, s>>>(sel, ns, stat);
+            ord_items_k<<<blocks_for(ns, 256), 256, 0, s>>>(g0, sel, ns, xg, d, v2, icnt);
+            Arena R(s);  // per-round scratch of the scan
+            KC_TRY(exclusive_scan_i64(icnt, ioff, ns, R, s));
+            int64_t nitems = 0;
+            KC_CUDA(cudaMemcpyAsync(&nitems, ioff + ns, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+            KC_CUDA(cudaStreamSynchronize(s));
+            if (nitems > item_cap) {
+                item_cap = nitems * 2;
+                if (item_sel) cudaFreeAsync(item_sel, s);
+                KC_CUDA(cudaMallocAsync(&item_sel, sizeof(int32_t) * item_cap, s));
+            }
+            ord_item_fill_k<<<blocks_for(ns * 32, 256), 256, 0, s>>>(ioff, ns, item_sel);
+            ord_update_k<<<blocks_for(nitems * 32, 256), 256, 0, s>>>(g0, sel, ioff, item_sel, nitems, cstart, xg, d,
+                                                                     idg, v2, stat);
+            KC_CUDA(cudaGetLastError());
+        }
+    }
+    if (item_sel) cudaFreeAsync(item_sel, s);
+    uint64_t *k0, *k1;
+    int64_t *w0, *w1;
+    KC_TRY(A.get(&k0, N));
+    KC_TRY(A.get(&k1, N));
+    KC_TRY(A.get(&w0, N));
+    KC_TRY(A.get(&w1, N));
+    ord_keys_k<<<blocks_for(N, 256), 256, 0, s>>>(v2, idg, N, k0, w0);
+    KC_TRY(radix_sort_u64_i64(k0, w0, k1, w1, N, 64, A, s));
+    ord_out_k<<<blocks_for(N, 256), 256, 0, s>>>(k1, w1, x, N, d, perm, l, x_ord);
+    KC_CUDA(cudaGetLastError());
+    KC_CUDA(cudaStreamSynchronize(s));
+    return KC_OK;
+}
+
+}  // namespace kc

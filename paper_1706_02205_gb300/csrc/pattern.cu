@@ -1,0 +1,315 @@
+// a3: the sparsity pattern S_rho (Section 2.3) on the device.
+//
+// For positions i < j of the maximin order, (j,i) is in S iff
+//   dist(x_i, x_j) <= rho * l[i]   (max rule: l is non-increasing), or
+//   dist(x_i, x_j) <= rho * l[j]   (min rule),
+// with dist = sqrt(d2) correctly rounded and the product correctly rounded,
+// so membership is bit-identical to a CPU evaluation of the definition.
+// The diagonal is always in S.
+//
+// Column-centric search: column i looks at the points within rho*l[i] of
+// x_i (a superset for the min rule) through a fine grid of all points, one
+// warp per (column, row of grid cells); the points of consecutive cells are
+// contiguous in the cell-sorted order.  A count pass gives the row lengths,
+// a fill pass scatters the column indices with atomics, and a sort of each
+// row (bitonic, in shared memory) restores ascending order.
+#include <cmath>
+
+#include "grid.cuh"
+
+namespace kc {
+
+kc_status check_finite(const double* x, int64_t n, Arena& A, cudaStream_t s);
+
+struct PatArgs {
+    Grid g;
+    const double* xs;      // coordinates in cell-sorted order
+    const int32_t* ps;     // position of each sorted point
+    const int64_t* cstart;
+    const double* xo;      // coordinates by position
+    const double* l;
+    int d;
+    double rho;
+    int rule;
+    const int64_t* off;    // item offsets per column
+    const int32_t* item_col;
+    int64_t nitems;
+};
+
+__device__ __forceinline__ void col_box(const Grid& g, const double* xi, double R, int* lo, int* hi) {
+    for (int t = 0; t < 3; ++t) {
+        lo[t] = 0;
+        hi[t] = 0;
+    }
+    for (int t = 0; t < g.dg; ++t) {
+        int c = cell_coord(g, xi[t], t);
+        int sp = span_for(g, R, t);
+        lo[t] = max(0, c - sp);
+        hi[t] = min(g.n[t] - 1, c + sp);
+    }
+}
+
+__device__ __forceinline__ double col_radius(double rho, double li) {
+    return isinf(li) ? INFINITY : __dmul_rn(rho, li);
+}
+
+// exact membership of (j,i), i < j, given the squared distance
+__device__ __forceinline__ bool in_s(double d2, double R) {
+    if (isinf(R)) return true;
+    const double Rs = R * R;
+    if (d2 > Rs * (1.0 + 1e-12)) return false;
+    if (d2 < Rs * (1.0 - 1e-12)) return true;
+    return __dsqrt_rn(d2) <= R;
+}
+
+__global__ void pat_items_k(Grid g, const double* __restrict__ xo, const double* __restrict__ l, int64_t N, int d,
+                            double rho, int64_t* __restrict__ cnt) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    int lo[3], hi[3];
+    col_box(g, xo + i * d, col_radius(rho, l[i]), lo, hi);
+    cnt[i] = (int64_t)(hi[1] - lo[1] + 1) * (hi[2] - lo[2] + 1);
+}
+__global__ void pat_item_fill_k(const int64_t* __restrict__ off, int64_t N, int32_t* __restrict__ item_col) {
+    int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (i >= N) return;
+    for (int64_t t = off[i] + lane_id(); t < off[i + 1]; t += 32) item_col[t] = (int32_t)i;
+}
+
+template <bool FILL>
+__global__ void pat_scan_k(PatArgs P, int* __restrict__ cnt, const int64_t* __restrict__ rowptr,
+                           int32_t* __restrict__ col) {
+    int64_t it = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (it >= P.nitems) return;
+    const int lane = lane_id();
+    const int i = P.item_col[it];
+    const double* xi = P.xo + (int64_t)i * P.d;
+    const double li = P.l[i];
+    const double R = col_radius(P.rho, li);
+    int lo[3], hi[3];
+    col_box(P.g, xi, R, lo, hi);
+    const int64_t r = it - P.off[i];
+    const int ny = hi[1] - lo[1] + 1;
+    const int cy = lo[1] + (int)(r % ny);
+    const int cz = lo[2] + (int)(r / ny);
+    const int64_t base = ((int64_t)cz * P.g.n[1] + cy) * P.g.n[0];
+    const int64_t a = P.cstart[base + lo[0]], b = P.cstart[base + hi[0] + 1];
+    for (int64_t q = a + lane; q < b; q += 32) {
+        const int j = P.ps[q];
+        if (j <= i) continue;
+        const double d2 = dist2_exact(P.xs + q * P.d, xi, P.d);
+        const double Rj = P.rule == KC_RULE_MIN ? col_radius(P.rho, P.l[j]) : R;
+        if (!in_s(d2, Rj)) continue;
+        if (!FILL) {
+            atomicAdd(&cnt[j], 1);
+        } else {
+            const int slot = atomicAdd(&cnt[j], 1);
+            col[rowptr[j] + slot] = i;
+        }
+    }
+}
+
+__global__ void pat_gather_k(const double* __restrict__ xo, const int32_t* __restrict__ gs, int64_t N, int d,
+                             double* __restrict__ xs) {
+    int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q < N)
+        for (int t = 0; t < d; ++t) xs[q * d + t] = xo[(int64_t)gs[q] * d + t];
+}
+__global__ void plus_one_k(const int* __restrict__ c, int64_t N, int32_t* __restrict__ out) {
+    int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < N) out[j] = c[j] + 1;
+}
+
+// Shared setup of both passes: grid, cell-sorted coordinates, work items.
+struct PatSetup {
+    Grid g;
+    int32_t* gs;
+    int64_t* cstart;
+    double* xs;
+    int64_t* off;
+    int32_t* item_col;
+    int64_t nitems;
+};
+
+static kc_status pat_setup(const double* xo, const double* l, int64_t N, int d, double rho, PatSetup& S, Arena& A,
+                           cudaStream_t s) {
+    KC_TRY(check_finite(xo, N * d, A, s));
+    double lo[3], hi[3];
+    KC_TRY(bbox(xo, N, d, lo, hi, A, s));
+    S.g = make_grid(d, lo, hi, N, 0.0, N / 2 > 1 ? N / 2 : 1);
+    KC_TRY(A.get(&S.gs, N));
+    KC_TRY(A.get(&S.cstart, S.g.ncells + 1));
+    KC_TRY(grid_build(S.g, xo, d, nullptr, N, S.gs, S.cstart, A, s));
+    KC_TRY(A.get(&S.xs, N * d));
+    pat_gather_k<<<blocks_for(N, 256), 256, 0, s>>>(xo, S.gs, N, d, S.xs);
+    int64_t* cnt;
+    KC_TRY(A.get(&cnt, N));
+    KC_TRY(A.get(&S.off, N + 1));
+    pat_items_k<<<blocks_for(N, 256), 256, 0, s>>>(S.g, xo, l, N, d, rho, cnt);
+    KC_CUDA(cudaGetLastError());
+    KC_TRY(exclusive_scan_i64(cnt, S.off, N, A, s));
+    KC_CUDA(cudaMemcpyAsync(&S.nitems, S.off + N, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    KC_CUDA(cudaStreamSynchronize(s));
+    KC_TRY(A.get(&S.item_col, S.nitems));
+    pat_item_fill_k<<<blocks_for(N * 32, 256), 256, 0, s>>>(S.off, N, S.item_col);
+    KC_CUDA(cudaGetLastError());
+    return KC_OK;
+}
+
+static PatArgs pat_args(const PatSetup& S, const double* xo, const double* l, int d, double rho, int rule) {
+    PatArgs P;
+    P.g = S.g;
+    P.xs = S.xs;
+    P.ps = S.gs;
+    P.cstart = S.cstart;
+    P.xo = xo;
+    P.l = l;
+    P.d = d;
+    P.rho = rho;
+    P.rule = rule;
+    P.off = S.off;
+    P.item_col = S.item_col;
+    P.nitems = S.nitems;
+    return P;
+}
+
+kc_status pattern_count_impl(const double* xo, const double* l, int64_t N, int d, double rho, int rule,
+                             int64_t* rowptr, int64_t* nnz_out, cudaStream_t s) {
+    Arena A(s);
+    PatSetup S;
+    KC_TRY(pat_setup(xo, l, N, d, rho, S, A, s));
+    int* cnt;
+    int32_t* len;
+    KC_TRY(A.get(&cnt, N));
+    KC_TRY(A.get(&len, N));
+    KC_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int) * N, s));
+    PatArgs P = pat_args(S, xo, l, d, rho, rule);
+    if (S.nitems > 0) pat_scan_k<false><<<blocks_for(S.nitems * 32, 256), 256, 0, s>>>(P, cnt, nullptr, nullptr);
+    plus_one_k<<<blocks_for(N, 256), 256, 0, s>>>(cnt, N, len);
+    KC_CUDA(cudaGetLastError());
+    KC_TRY(exclusive_scan_i32_to_i64(len, rowptr, N, A, s));
+    int64_t nnz = 0;
+    KC_CUDA(cudaMemcpyAsync(&nnz, rowptr + N, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    KC_CUDA(cudaStreamSynchronize(s));
+    if (nnz_out) *nnz_out = nnz;
+    return KC_OK;
+}
+
+// ---- per-row sort (ascending), the diagonal appended last
+constexpr int SORT_WARP_CAP = 1024;
+constexpr int SORT_BLOCK_CAP = 16384;
+
+__global__ void row_sort_warp_k(const int64_t* __restrict__ rowptr, int64_t N, int32_t* __restrict__ col,
+                                int32_t* __restrict__ long_rows, unsigned long long* __restrict__ nlong) {
+    __shared__ int buf[8][SORT_WARP_CAP];
+    const int w = threadIdx.x >> 5, lane = lane_id();
+    const int64_t j = (int64_t)blockIdx.x * 8 + w;
+    if (j >= N) return;
+    const int64_t a = rowptr[j], b = rowptr[j + 1] - 1;  // off-diagonal part [a, b)
+    col[b] = (int32_t)j;
+    const int L = (int)(b - a);
+    if (L <= 1) return;
+    if (L > SORT_WARP_CAP) {
+        if (lane == 0) long_rows[atomicAdd(nlong, 1ULL)] = (int32_t)j;
+        return;
+    }
+    int P = 1;
+    while (P < L) P <<= 1;
+    int* s = buf[w];
+    for (int t = lane; t < P; t += 32) s[t] = t < L ? col[a + t] : INT_MAX;
+    __syncwarp();
+    for (int k = 2; k <= P; k <<= 1)
+        for (int jj = k >> 1; jj > 0; jj >>= 1) {
+            for (int t = lane; t < P; t += 32) {
+                int u = t ^ jj;
+                if (u > t) {
+                    int x0 = s[t], x1 = s[u];
+                    bool up = (t & k) == 0;
+                    if ((x0 > x1) == up) {
+                        s[t] = x1;
+                        s[u] = x0;
+                    }
+                }
+            }
+            __syncwarp();
+        }
+    for (int t = lane; t < L; t += 32) col[a + t] = s[t];
+}
+
+__global__ void row_sort_block_k(const int64_t* __restrict__ rowptr, int32_t* __restrict__ col,
+                                 const int32_t* __restrict__ long_rows) {
+    extern __shared__ int sb[];
+    const int64_t j = long_rows[blockIdx.x];
+    const int64_t a = rowptr[j], b = rowptr[j + 1] - 1;
+    const int L = (int)(b - a);
+    int P = 1;
+    while (P < L) P <<= 1;
+    for (int t = threadIdx.x; t < P; t += blockDim.x) sb[t] = t < L ? col[a + t] : INT_MAX;
+    __syncthreads();
+    for (int k = 2; k <= P; k <<= 1)
+        for (int jj = k >> 1; jj > 0; jj >>= 1) {
+            for (int t = threadIdx.x; t < P; t += blockDim.x) {
+                int u = t ^ jj;
+                if (u > t) {
+                    int x0 = sb[t], x1 = sb[u];
+                    bool up = (t & k) == 0;
+                    if ((x0 > x1) == up) {
+                        sb[t] = x1;
+                        sb[u] = x0;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    for (int t = threadIdx.x; t < L; t += blockDim.x) col[a + t] = sb[t];
+}
+
+__global__ void max_len_k(const int64_t* __restrict__ rowptr, int64_t N, int* __restrict__ out) {
+    int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int m = 0;
+    if (j < N) m = (int)(rowptr[j + 1] - rowptr[j] - 1);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (lane_id() == 0) atomicMax(out, m);
+}
+
+kc_status pattern_fill_impl(const double* xo, const double* l, int64_t N, int d, double rho, int rule,
+                            const int64_t* rowptr, int32_t* col, cudaStream_t s) {
+    Arena A(s);
+    int* mx;
+    KC_TRY(A.get(&mx, 1));
+    KC_CUDA(cudaMemsetAsync(mx, 0, sizeof(int), s));
+    max_len_k<<<blocks_for(N, 256), 256, 0, s>>>(rowptr, N, mx);
+    int hmx = 0;
+    KC_CUDA(cudaMemcpyAsync(&hmx, mx, sizeof(int), cudaMemcpyDeviceToHost, s));
+    KC_CUDA(cudaStreamSynchronize(s));
+    if (hmx > SORT_BLOCK_CAP) return fail(KC_EINVAL, "pattern row longer than 16384 entries");
+    PatSetup S;
+    KC_TRY(pat_setup(xo, l, N, d, rho, S, A, s));
+    int* cnt;
+    KC_TRY(A.get(&cnt, N));
+    KC_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int) * N, s));
+    PatArgs P = pat_args(S, xo, l, d, rho, rule);
+    if (S.nitems > 0) pat_scan_k<true><<<blocks_for(S.nitems * 32, 256), 256, 0, s>>>(P, cnt, rowptr, col);
+    KC_CUDA(cudaGetLastError());
+    int32_t* long_rows;
+    unsigned long long* nlong;
+    KC_TRY(A.get(&long_rows, N));
+    KC_TRY(A.get(&nlong, 1));
+    KC_CUDA(cudaMemsetAsync(nlong, 0, sizeof(unsigned long long), s));
+    row_sort_warp_k<<<blocks_for(N, 8), 256, 0, s>>>(rowptr, N, col, long_rows, nlong);
+    KC_CUDA(cudaGetLastError());
+    unsigned long long hl = 0;
+    KC_CUDA(cudaMemcpyAsync(&hl, nlong, sizeof(hl), cudaMemcpyDeviceToHost, s));
+    KC_CUDA(cudaStreamSynchronize(s));
+    if (hl > 0) {
+        size_t sm = sizeof(int) * SORT_BLOCK_CAP;
+        KC_CUDA(cudaFuncSetAttribute(row_sort_block_k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        row_sort_block_k<<<(unsigned)hl, 1024, sm, s>>>(rowptr, col, long_rows);
+        KC_CUDA(cudaGetLastError());
+    }
+    KC_CUDA(cudaStreamSynchronize(s));
+    return KC_OK;
+}
+
+}  // namespace kc

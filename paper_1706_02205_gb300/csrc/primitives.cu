@@ -1,0 +1,270 @@
+// Scan and stable radix sort used by the ordering, pattern and schedule
+// steps, plus error reporting.  Written for sm_103a; no library kernels.
+#include <cstdio>
+#include <cmath>
+#include <mutex>
+
+#include "common.cuh"
+
+namespace kc {
+
+static thread_local std::string g_last_error;
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+const char* last_error_cstr() { return g_last_error.c_str(); }
+kc_status fail(kc_status st, const std::string& msg) {
+    g_last_error = msg;
+    return st;
+}
+kc_status cuda_fail(cudaError_t e, const char* what) {
+    g_last_error = std::string(what) + ": " + cudaGetErrorString(e);
+    return e == cudaErrorMemoryAllocation ? KC_ENOMEM : KC_ECUDA;
+}
+
+int sm_count() {
+    int dev = 0, n = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    return n > 0 ? n : 1;
+}
+
+kc_status kernel_params(const kc_kernel* k, KernelParams* out) {
+    if (!k) return fail(KC_EINVAL, "kernel parameters are NULL");
+    if (!(k->ell > 0.0) || !(k->sigma2 > 0.0) || !(k->nugget >= 0.0))
+        return fail(KC_EINVAL, "kernel needs ell > 0, sigma2 > 0, nugget >= 0");
+    if (k->nu == 0.5) out->nu_code = 0;
+    else if (k->nu == 1.5) out->nu_code = 1;
+    else if (k->nu == 2.5) out->nu_code = 2;
+    else return fail(KC_EINVAL, "nu must be 0.5, 1.5 or 2.5");
+    out->scale = sqrt(2.0 * k->nu) / k->ell;
+    out->sigma2 = k->sigma2;
+    out->nugget = k->nugget;
+    return KC_OK;
+}
+
+// ------------------------------------------------------------------ scan
+constexpr int SCAN_THREADS = 256;
+constexpr int SCAN_ITEMS = 8;
+constexpr int SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;
+
+template <typename Tin>
+__global__ void scan_reduce_k(const Tin* __restrict__ in, int64_t n, int64_t* __restrict__ bsum) {
+    __shared__ int64_t red[SCAN_THREADS / 32];
+    int64_t base = (int64_t)blockIdx.x * SCAN_TILE;
+    int64_t s = 0;
+    for (int it = 0; it < SCAN_ITEMS; ++it) {
+        int64_t i = base + (int64_t)it * SCAN_THREADS + threadIdx.x;
+        if (i < n) s += (int64_t)in[i];
+    }
+    s = warp_sum(s);
+    if (lane_id() == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        int64_t v = threadIdx.x < SCAN_THREADS / 32 ? red[threadIdx.x] : 0;
+        v = warp_sum(v);
+        if (threadIdx.x == 0) bsum[blockIdx.x] = v;
+    }
+}
+
+// Each block scans its tile (blocked arrangement) and adds its block offset.
+template <typename Tin>
+__global__ void scan_tile_k(const Tin* __restrict__ in, int64_t n, const int64_t* __restrict__ boff,
+                            int64_t* __restrict__ out) {
+    __shared__ int64_t wsum[SCAN_THREADS / 32];
+    int64_t base = (int64_t)blockIdx.x * SCAN_TILE + (int64_t)threadIdx.x * SCAN_ITEMS;
+    int64_t v[SCAN_ITEMS];
+    int64_t t = 0;
+#pragma unroll
+    for (int it = 0; it < SCAN_ITEMS; ++it) {
+        int64_t i = base + it;
+        v[it] = i < n ? (int64_t)in[i] : 0;
+        t += v[it];
+    }
+    // inclusive warp scan of thread totals
+    int lane = lane_id(), w = threadIdx.x >> 5;
+    int64_t incl = t;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int64_t y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) wsum[w] = incl;
+    __syncthreads();
+    int64_t woff = 0;
+    for (int q = 0; q < w; ++q) woff += wsum[q];
+    int64_t run = boff[blockIdx.x] + woff + incl - t;
+#pragma unroll
+    for (int it = 0; it < SCAN_ITEMS; ++it) {
+        int64_t i = base + it;
+        if (i < n) out[i] = run;
+        run += v[it];
+    }
+    // total goes to out[n] from the last block's last thread
+    if (blockIdx.x == gridDim.x - 1 && threadIdx.x == SCAN_THREADS - 1) out[n] = run;
+}
+
+__global__ void scan_single_k(const int64_t* __restrict__ in, int64_t n, int64_t* __restrict__ out) {
+    // one block, sequential over chunks of 1024 (used for short arrays)
+    __shared__ int64_t carry;
+    __shared__ int64_t wsum[32];
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int64_t base = 0; base < n; base += blockDim.x) {
+        int64_t i = base + threadIdx.x;
+        int64_t v = i < n ? in[i] : 0;
+        int lane = lane_id(), w = threadIdx.x >> 5;
+        int64_t incl = v;
+        for (int o = 1; o < 32; o <<= 1) {
+            int64_t y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        if (lane == 31) wsum[w] = incl;
+        __syncthreads();
+        int64_t woff = 0;
+        for (int q = 0; q < w; ++q) woff += wsum[q];
+        int64_t c = carry;
+        if (i < n) out[i] = c + woff + incl - v;
+        __syncthreads();
+        if (threadIdx.x == blockDim.x - 1) carry = c + woff + incl;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[n] = carry;
+}
+
+template <typename Tin>
+static kc_status scan_impl(const Tin* in, int64_t* out, int64_t n, Arena& A, cudaStream_t s) {
+    if (n <= 0) {
+        KC_CUDA(cudaMemsetAsync(out, 0, sizeof(int64_t), s));
+        return KC_OK;
+    }
+    int64_t nb = (n + SCAN_TILE - 1) / SCAN_TILE;
+    int64_t* bsum;
+    int64_t* boff;
+    KC_TRY(A.get(&bsum, nb));
+    KC_TRY(A.get(&boff, nb + 1));
+    scan_reduce_k<Tin><<<(unsigned)nb, SCAN_THREADS, 0, s>>>(in, n, bsum);
+    if (nb <= 8192) scan_single_k<<<1, 1024, 0, s>>>(bsum, nb, boff);
+    else KC_TRY(scan_impl<int64_t>(bsum, boff, nb, A, s));
+    scan_tile_k<Tin><<<(unsigned)nb, SCAN_THREADS, 0, s>>>(in, n, boff, out);
+    KC_CUDA(cudaGetLastError());
+    return KC_OK;
+}
+
+kc_status exclusive_scan_i64(const int64_t* in, int64_t* out, int64_t n, Arena& A, cudaStream_t s) {
+    return scan_impl<int64_t>(in, out, n, A, s);
+}
+kc_status exclusive_scan_i32_to_i64(const int32_t* in, int64_t* out, int64_t n, Arena& A, cudaStream_t s) {
+    return scan_impl<int32_t>(in, out, n, A, s);
+}
+
+// ------------------------------------------------------------ radix sort
+// Tile of one block = 8 warps x 16 rounds x 32 lanes = 4096 elements, each
+// warp owning 512 consecutive elements processed in order, so the scatter
+// is stable.  Histograms are digit-major: hist[digit * ntiles + tile].
+constexpr int RS_WARPS = 8;
+constexpr int RS_ROUNDS = 16;
+constexpr int RS_TILE = RS_WARPS * RS_ROUNDS * 32;
+
+template <typename K>
+__global__ void rs_hist_k(const K* __restrict__ key, int64_t n, int shift, int64_t ntiles,
+                          int64_t* __restrict__ hist) {
+    __shared__ int cnt[256];
+    for (int i = threadIdx.x; i < 256; i += blockDim.x) cnt[i] = 0;
+    __syncthreads();
+    int64_t base = (int64_t)blockIdx.x * RS_TILE;
+    for (int i = threadIdx.x; i < RS_TILE; i += blockDim.x) {
+        int64_t e = base + i;
+        if (e < n) atomicAdd(&cnt[(int)((key[e] >> shift) & 0xFF)], 1);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < 256; i += blockDim.x) hist[(int64_t)i * ntiles + blockIdx.x] = cnt[i];
+}
+
+template <typename K>
+__global__ void rs_scatter_k(const K* __restrict__ kin, const int64_t* __restrict__ vin, int64_t n, int shift,
+                             int64_t ntiles, const int64_t* __restrict__ goff, K* __restrict__ kout,
+                             int64_t* __restrict__ vout) {
+    __shared__ long long cnt[RS_WARPS][256];
+    int lane = lane_id(), w = threadIdx.x >> 5;
+    for (int i = lane; i < 256; i += 32) cnt[w][i] = 0;
+    __syncwarp();
+    int64_t wbase = (int64_t)blockIdx.x * RS_TILE + (int64_t)w * RS_ROUNDS * 32;
+    const unsigned lt = (1u << lane) - 1u;
+    for (int r = 0; r < RS_ROUNDS; ++r) {
+        int64_t e = wbase + r * 32 + lane;
+        int dg = e < n ? (int)((kin[e] >> shift) & 0xFF) : 256 + lane;
+        unsigned peers = __match_any_sync(0xffffffffu, dg);
+        int leader = 31 - __clz(peers);
+        if (e < n && lane == leader) cnt[w][dg] += __popc(peers);
+        __syncwarp();
+    }
+    __syncthreads();
+    for (int dgt = threadIdx.x; dgt < 256; dgt += blockDim.x) {
+        long long run = goff[(int64_t)dgt * ntiles + blockIdx.x];
+        for (int q = 0; q < RS_WARPS; ++q) {
+            long long t = cnt[q][dgt];
+            cnt[q][dgt] = run;
+            run += t;
+        }
+    }
+    __syncthreads();
+    for (int r = 0; r < RS_ROUNDS; ++r) {
+        int64_t e = wbase + r * 32 + lane;
+        bool ok = e < n;
+        K kv = ok ? kin[e] : (K)0;
+        int dg = ok ? (int)((kv >> shift) & 0xFF) : 256 + lane;
+        unsigned peers = __match_any_sync(0xffffffffu, dg);
+        int leader = 31 - __clz(peers);
+        if (ok) {
+            long long pos = cnt[w][dg] + __popc(peers & lt);
+            kout[pos] = kv;
+            vout[pos] = vin[e];
+        }
+        __syncwarp();
+        if (ok && lane == leader) cnt[w][dg] += __popc(peers);
+        __syncwarp();
+    }
+}
+
+template <typename K>
+static kc_status radix_impl(K* k_in, int64_t* v_in, K* k_out, int64_t* v_out, int64_t n, int bits, Arena& A,
+                            cudaStream_t s) {
+    if (n <= 0) return KC_OK;
+    int passes = (bits + 7) / 8;
+    if (passes < 1) passes = 1;
+    int64_t ntiles = (n + RS_TILE - 1) / RS_TILE;
+    int64_t* hist;
+    int64_t* goff;
+    KC_TRY(A.get(&hist, 256 * ntiles));
+    KC_TRY(A.get(&goff, 256 * ntiles + 1));
+    K* ka = k_in;
+    int64_t* va = v_in;
+    K* kb = k_out;
+    int64_t* vb = v_out;
+    for (int p = 0; p < passes; ++p) {
+        int shift = 8 * p;
+        rs_hist_k<K><<<(unsigned)ntiles, 256, 0, s>>>(ka, n, shift, ntiles, hist);
+        KC_TRY(exclusive_scan_i64(hist, goff, 256 * ntiles, A, s));
+        rs_scatter_k<K><<<(unsigned)ntiles, RS_WARPS * 32, 0, s>>>(ka, va, n, shift, ntiles, goff, kb, vb);
+        KC_CUDA(cudaGetLastError());
+        K* tk = ka; ka = kb; kb = tk;
+        int64_t* tv = va; va = vb; vb = tv;
+    }
+    // after an odd number of passes the result is in the *_out buffers
+    if (ka != k_out) {
+        KC_CUDA(cudaMemcpyAsync(k_out, ka, sizeof(K) * n, cudaMemcpyDeviceToDevice, s));
+        KC_CUDA(cudaMemcpyAsync(v_out, va, sizeof(int64_t) * n, cudaMemcpyDeviceToDevice, s));
+    }
+    return KC_OK;
+}
+
+kc_status radix_sort_u64_i64(uint64_t* k_in, int64_t* v_in, uint64_t* k_out, int64_t* v_out, int64_t n, int bits,
+                             Arena& A, cudaStream_t s) {
+    return radix_impl<uint64_t>(k_in, v_in, k_out, v_out, n, bits, A, s);
+}
+kc_status radix_sort_u32_i64(uint32_t* k_in, int64_t* v_in, uint32_t* k_out, int64_t* v_out, int64_t n, int bits,
+                             Arena& A, cudaStream_t s) {
+    return radix_impl<uint32_t>(k_in, v_in, k_out, v_out, n, bits, A, s);
+}
+
+}  // namespace kc

@@ -1,0 +1,163 @@
+// a4: the dependency schedule of the factorisation.
+//
+// Column i of the left-looking ICHOL(0) (Algorithm 2) needs every column k in
+// row i of L (k in R_i) to be complete, so the columns form a DAG whose
+// levels are level(i) = 1 + max_{k in R_i} level(k).  This file builds, on the
+// device: the CSC view of L (rows of each column ascending, with the CSR slot
+// of every entry), the levels (a sync-free kernel over rows in index order),
+// and the columns sorted by (level, index) with a stable radix sort.
+#include "common.cuh"
+
+namespace kc {
+
+// rowof[e] = row of CSR entry e
+__global__ void row_of_k(const int64_t* __restrict__ rowptr, int64_t N, int32_t* __restrict__ rowof) {
+    int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int lane = lane_id();
+    int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t j = warp; j < N; j += nw) {
+        int64_t a = rowptr[j], b = rowptr[j + 1];
+        for (int64_t e = a + lane; e < b; e += 32) rowof[e] = (int32_t)j;
+    }
+}
+
+__global__ void col_keys_k(const int32_t* __restrict__ col, int64_t nnz, uint32_t* __restrict__ key,
+                           int64_t* __restrict__ val) {
+    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < nnz) {
+        key[e] = (uint32_t)col[e];
+        val[e] = e;
+    }
+}
+
+// After the stable sort by column: slot[q] = CSR position, rowidx[q] = its row,
+// colptr[c] = first q of column c (every column holds its diagonal).
+__global__ void csc_finish_k(const uint32_t* __restrict__ skey, const int64_t* __restrict__ sval, int64_t nnz,
+                             const int32_t* __restrict__ rowof, int64_t N, int64_t* __restrict__ colptr,
+                             int32_t* __restrict__ rowidx, int64_t* __restrict__ slot) {
+    int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q < nnz) {
+        int64_t e = sval[q];
+        slot[q] = e;
+        rowidx[q] = rowof[e];
+        uint32_t c = skey[q];
+        if (q == 0 || skey[q - 1] != c) colptr[c] = q;
+    }
+    if (q == 0) colptr[N] = nnz;
+}
+
+// level[j] = 1 + max level over row j; rows claimed in index order, so a row
+// waits only on rows with smaller index that were claimed before it.
+__global__ void levels_k(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col, int64_t N,
+                         int* __restrict__ level, unsigned long long* __restrict__ ticket, int* __restrict__ depth,
+                         int* __restrict__ status, long long spin_limit) {
+    int lane = lane_id();
+    for (;;) {
+        unsigned long long t = 0;
+        if (lane == 0) t = atomicAdd(ticket, 1ULL);
+        t = __shfl_sync(0xffffffffu, t, 0);
+        if ((int64_t)t >= N) return;
+        if (ld_volatile_s32(status) != 0) return;
+        int64_t j = (int64_t)t;
+        int64_t a = rowptr[j], b = rowptr[j + 1] - 1;
+        int m = 0;
+        bool ok = true;
+        for (int64_t e = a + lane; e < b && ok; e += 32) {
+            int k = __ldg(&col[e]);
+            int v = ld_acquire_s32(&level[k]);
+            if (v == 0) {
+                long long t0 = clock64();
+                while ((v = ld_acquire_s32(&level[k])) == 0) {
+                    if (clock64() - t0 > spin_limit || ld_volatile_s32(status) != 0) {
+                        ok = false;
+                        break;
+                    }
+                }
+            }
+            m = max(m, v);
+        }
+        if (!__all_sync(0xffffffffu, ok)) {
+            if (lane == 0) atomicCAS(status, 0, DEV_TIMEOUT);
+            return;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+        if (lane == 0) {
+            st_release_s32(&level[j], m + 1);
+            atomicMax(depth, m + 1);
+        }
+    }
+}
+
+__global__ void level_keys_k(const int* __restrict__ level, int64_t N, uint32_t* __restrict__ key,
+                             int64_t* __restrict__ val) {
+    int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < N) {
+        key[j] = (uint32_t)level[j];
+        val[j] = j;
+    }
+}
+
+__global__ void order_out_k(const int64_t* __restrict__ sval, int64_t N, int32_t* __restrict__ order) {
+    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p < N) order[p] = (int32_t)sval[p];
+}
+
+static int bits_for(int64_t v) {
+    int b = 1;
+    while (b < 63 && ((int64_t)1 << b) <= v) ++b;
+    return b;
+}
+
+kc_status schedule_impl(int64_t N, const int64_t* rowptr, const int32_t* col, int64_t nnz, int64_t* colptr,
+                        int32_t* rowidx, int64_t* slot, int32_t* level, int32_t* order, int32_t* depth_out,
+                        cudaStream_t s) {
+    Arena A(s);
+    // CSC by a stable sort of the CSR entries by column
+    int32_t* rowof;
+    uint32_t *k0, *k1;
+    int64_t *v0, *v1;
+    KC_TRY(A.get(&rowof, nnz));
+    KC_TRY(A.get(&k0, nnz));
+    KC_TRY(A.get(&k1, nnz));
+    KC_TRY(A.get(&v0, nnz));
+    KC_TRY(A.get(&v1, nnz));
+    int sms = sm_count();
+    row_of_k<<<sms * 8, 256, 0, s>>>(rowptr, N, rowof);
+    col_keys_k<<<blocks_for(nnz, 256), 256, 0, s>>>(col, nnz, k0, v0);
+    KC_CUDA(cudaGetLastError());
+    KC_TRY(radix_sort_u32_i64(k0, v0, k1, v1, nnz, bits_for(N), A, s));
+    csc_finish_k<<<blocks_for(nnz, 256), 256, 0, s>>>(k1, v1, nnz, rowof, N, colptr, rowidx, slot);
+    KC_CUDA(cudaGetLastError());
+
+    // levels
+    unsigned long long* ticket;
+    int* dev_depth;
+    int* status;
+    KC_TRY(A.get(&ticket, 1));
+    KC_TRY(A.get(&dev_depth, 1));
+    KC_TRY(A.get(&status, 1));
+    KC_CUDA(cudaMemsetAsync(ticket, 0, sizeof(unsigned long long), s));
+    KC_CUDA(cudaMemsetAsync(dev_depth, 0, sizeof(int), s));
+    KC_CUDA(cudaMemsetAsync(status, 0, sizeof(int), s));
+    KC_CUDA(cudaMemsetAsync(level, 0, sizeof(int) * N, s));
+    levels_k<<<sms * 8, 256, 0, s>>>(rowptr, col, N, level, ticket, dev_depth, status, 4000000000LL);
+    KC_CUDA(cudaGetLastError());
+    int h_depth = 0, h_status = 0;
+    KC_CUDA(cudaMemcpyAsync(&h_depth, dev_depth, sizeof(int), cudaMemcpyDeviceToHost, s));
+    KC_CUDA(cudaMemcpyAsync(&h_status, status, sizeof(int), cudaMemcpyDeviceToHost, s));
+    KC_CUDA(cudaStreamSynchronize(s));
+    if (h_status != 0) return fail(KC_ETIMEOUT, "level computation: a dependency wait ran out");
+
+    // columns sorted by (level, index)
+    level_keys_k<<<blocks_for(N, 256), 256, 0, s>>>(level, N, k0, v0);
+    KC_CUDA(cudaGetLastError());
+    KC_TRY(radix_sort_u32_i64(k0, v0, k1, v1, N, bits_for(h_depth), A, s));
+    order_out_k<<<blocks_for(N, 256), 256, 0, s>>>(v1, N, order);
+    KC_CUDA(cudaGetLastError());
+    KC_CUDA(cudaStreamSynchronize(s));
+    if (depth_out) *depth_out = h_depth;
+    return KC_OK;
+}
+
+}  // namespace kc

@@ -1,0 +1,276 @@
+"""Thin Python binding of libkchol (include/kchol.h).
+
+Argument marshalling only: every step runs in the library's sm_103a kernels.
+PyTorch supplies device memory (tensors) and the CUDA stream; no torch type
+crosses the C ABI.  There is no CPU fallback: if the shared library is
+missing, importing the binding's functions raises.
+
+Function names follow the C entry points without the ``kc_`` prefix.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libkchol.so")
+
+KC_OK, KC_EINVAL, KC_ENOMEM, KC_ECUDA, KC_ETIMEOUT, KC_ENOTCONV, KC_ERANKDEF, KC_EINDEF = range(8)
+RULE_MAX, RULE_MIN = 0, 1
+FP64, FP32_FORM = 0, 1
+_STATUS = {0: "KC_OK", 1: "KC_EINVAL", 2: "KC_ENOMEM", 3: "KC_ECUDA", 4: "KC_ETIMEOUT",
+           5: "KC_ENOTCONV", 6: "KC_ERANKDEF", 7: "KC_EINDEF"}
+
+
+class KcError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class kc_kernel(C.Structure):
+    _fields_ = [("nu", C.c_double), ("ell", C.c_double), ("sigma2", C.c_double), ("nugget", C.c_double)]
+
+
+class kc_pattern(C.Structure):
+    _fields_ = [("N", C.c_int64), ("nnz", C.c_int64), ("rowptr", C.c_void_p), ("col", C.c_void_p),
+                ("colptr", C.c_void_p), ("rowidx", C.c_void_p), ("slot", C.c_void_p), ("order", C.c_void_p),
+                ("depth", C.c_int32)]
+
+
+class kc_opts(C.Structure):
+    _fields_ = [("spin_limit_cycles", C.c_int64), ("rows_per_task", C.c_int32), ("ctas_per_sm", C.c_int32),
+                ("warps_per_cta", C.c_int32), ("test_hold_column", C.c_int32)]
+
+
+_lib = None
+
+
+def lib():
+    """Load libkchol.so (built by ``build()``); raises if it is missing."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"libkchol.so not built ({LIB_PATH}); run __graft_entry__.build()")
+        L = C.CDLL(LIB_PATH)
+        vp, i64, i32, dbl = C.c_void_p, C.c_int64, C.c_int32, C.c_double
+        P = C.POINTER
+        L.kc_last_error.restype = C.c_char_p
+        L.kc_abi_version.restype = i32
+        sigs = {
+            "kc_order_points": [vp, i64, i32, vp, vp, vp, vp],
+            "kc_pattern_count": [vp, vp, i64, i32, dbl, i32, vp, P(C.c_int64), vp],
+            "kc_pattern_fill": [vp, vp, i64, i32, dbl, i32, vp, vp, vp],
+            "kc_schedule": [i64, vp, vp, vp, vp, vp, vp, vp, P(C.c_int32), vp],
+            "kc_factor": [P(kc_pattern), vp, i32, P(kc_kernel), i32, vp, vp, P(C.c_int64), P(kc_opts), vp],
+            "kc_solve": [P(kc_pattern), i32, vp, vp, P(kc_kernel), vp, vp, i32, vp, P(kc_opts), vp],
+            "kc_refine": [P(kc_pattern), vp, i32, P(kc_kernel), i32, vp, vp, vp, vp, i32, dbl, i32, vp,
+                          P(C.c_int32), P(C.c_double), P(kc_opts), vp],
+            "kc_pca_truncate": [P(kc_pattern), i32, vp, vp, i32, vp, vp],
+            "kc_pca_error": [vp, i64, i32, P(kc_kernel), i32, vp, vp, i32, P(C.c_double), vp],
+        }
+        for name, args in sigs.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = C.c_int
+        _lib = L
+    return _lib
+
+
+EXPORTED = ("kc_last_error", "kc_abi_version", "kc_order_points", "kc_pattern_count", "kc_pattern_fill",
+            "kc_schedule", "kc_factor", "kc_solve", "kc_refine", "kc_pca_truncate", "kc_pca_error")
+
+
+def _check(st: int):
+    if st != KC_OK:
+        raise KcError(st, lib().kc_last_error().decode(errors="replace"))
+
+
+def _ptr(t: torch.Tensor | None):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def _dev(t: torch.Tensor, dtype, name):
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise ValueError(f"{name} must be {dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return t
+
+
+@dataclass
+class Kernel:
+    """Matern covariance: nu in {0.5, 1.5, 2.5}, length scale ell, variance
+    sigma2, nugget on the diagonal."""
+    nu: float = 1.5
+    ell: float = 0.2
+    sigma2: float = 1.0
+    nugget: float = 0.0
+
+    def c(self):
+        return kc_kernel(self.nu, self.ell, self.sigma2, self.nugget)
+
+
+def make_opts(spin_limit_cycles=0, rows_per_task=0, ctas_per_sm=0, warps_per_cta=0, test_hold_column=-1):
+    return kc_opts(spin_limit_cycles, rows_per_task, ctas_per_sm, warps_per_cta, test_hold_column + 1)
+
+
+# ----------------------------------------------------------------- a2, a3, a4
+
+def order_points(x: torch.Tensor, stream=None):
+    """Maximin ordering of x (N, d) float64 on the GPU -> (perm int32, l float64, x_ord float64)."""
+    _dev(x, torch.float64, "x")
+    N, d = x.shape
+    perm = torch.empty(N, dtype=torch.int32, device=x.device)
+    l = torch.empty(N, dtype=torch.float64, device=x.device)
+    xo = torch.empty_like(x)
+    _check(lib().kc_order_points(_ptr(x), N, d, _ptr(perm), _ptr(l), _ptr(xo), _stream(stream)))
+    return perm, l, xo
+
+
+def pattern_count(x_ord, l, rho, rule=RULE_MAX, stream=None):
+    _dev(x_ord, torch.float64, "x_ord")
+    _dev(l, torch.float64, "l")
+    N, d = x_ord.shape
+    rowptr = torch.empty(N + 1, dtype=torch.int64, device=x_ord.device)
+    nnz = C.c_int64(0)
+    _check(lib().kc_pattern_count(_ptr(x_ord), _ptr(l), N, d, float(rho), int(rule), _ptr(rowptr),
+                                  C.byref(nnz), _stream(stream)))
+    return rowptr, int(nnz.value)
+
+
+def pattern_fill(x_ord, l, rho, rowptr, nnz, rule=RULE_MAX, stream=None):
+    N, d = x_ord.shape
+    _dev(rowptr, torch.int64, "rowptr")
+    col = torch.empty(nnz, dtype=torch.int32, device=x_ord.device)
+    _check(lib().kc_pattern_fill(_ptr(x_ord), _ptr(l), N, d, float(rho), int(rule), _ptr(rowptr), _ptr(col),
+                                 _stream(stream)))
+    return col
+
+
+class Pattern:
+    """Device CSR/CSC pattern of L plus its dependency schedule."""
+
+    def __init__(self, rowptr, col, colptr, rowidx, slot, level, order, depth):
+        self.rowptr, self.col, self.colptr, self.rowidx, self.slot = rowptr, col, colptr, rowidx, slot
+        self.level, self.order, self.depth = level, order, depth
+        self.N = rowptr.numel() - 1
+        self.nnz = col.numel()
+        self._c = kc_pattern(self.N, self.nnz, rowptr.data_ptr(), col.data_ptr(), colptr.data_ptr(),
+                             rowidx.data_ptr(), slot.data_ptr(), order.data_ptr(), depth)
+
+    def c(self):
+        return C.byref(self._c)
+
+
+def schedule(rowptr, col, stream=None) -> Pattern:
+    _dev(rowptr, torch.int64, "rowptr")
+    _dev(col, torch.int32, "col")
+    N = rowptr.numel() - 1
+    nnz = col.numel()
+    dev = rowptr.device
+    colptr = torch.empty(N + 1, dtype=torch.int64, device=dev)
+    rowidx = torch.empty(nnz, dtype=torch.int32, device=dev)
+    slot = torch.empty(nnz, dtype=torch.int64, device=dev)
+    level = torch.empty(N, dtype=torch.int32, device=dev)
+    order = torch.empty(N, dtype=torch.int32, device=dev)
+    depth = C.c_int32(0)
+    _check(lib().kc_schedule(N, _ptr(rowptr), _ptr(col), _ptr(colptr), _ptr(rowidx), _ptr(slot), _ptr(level),
+                             _ptr(order), C.byref(depth), _stream(stream)))
+    return Pattern(rowptr, col, colptr, rowidx, slot, level, order, int(depth.value))
+
+
+# ------------------------------------------------------------------ a5, a6
+
+def factor(pat: Pattern, x_ord, kern: Kernel, prec=FP32_FORM, opts: kc_opts | None = None, val=None, diag=None,
+           stream=None):
+    """ICHOL(0) -> (val [nnz] float64|float32, diag [N] float64, zero_pivots)."""
+    _dev(x_ord, torch.float64, "x_ord")
+    d = x_ord.shape[1]
+    dt = torch.float64 if prec == FP64 else torch.float32
+    if val is None:
+        val = torch.empty(pat.nnz, dtype=dt, device=x_ord.device)
+    if diag is None:
+        diag = torch.empty(pat.N, dtype=torch.float64, device=x_ord.device)
+    zp = C.c_int64(0)
+    k = kern.c()
+    _check(lib().kc_factor(pat.c(), _ptr(x_ord), d, C.byref(k), int(prec), _ptr(val), _ptr(diag), C.byref(zp),
+                           C.byref(opts) if opts is not None else None, _stream(stream)))
+    return val, diag, int(zp.value)
+
+
+# ------------------------------------------------------------- a7, a8, a9
+
+def solve(pat: Pattern, prec, val, diag, kern: Kernel, perm, b, opts=None, stream=None):
+    """x = (L L^T)^{-1} b; b is (nrhs, N) float64 in original order (row r = rhs r)."""
+    _dev(b, torch.float64, "b")
+    if b.dim() == 1:
+        b = b[None]
+    nrhs = b.shape[0]
+    x = torch.empty_like(b)
+    k = kern.c()
+    _check(lib().kc_solve(pat.c(), int(prec), _ptr(val), _ptr(diag), C.byref(k), _ptr(perm), _ptr(b), nrhs,
+                          _ptr(x), C.byref(opts) if opts is not None else None, _stream(stream)))
+    return x
+
+
+def refine(pat: Pattern, x_ord, kern: Kernel, prec, val, diag, perm, b, rtol=1e-10, maxit=200, opts=None,
+           stream=None):
+    """CG on the dense Theta preconditioned by L L^T -> (x, iters, relres per rhs, status)."""
+    _dev(b, torch.float64, "b")
+    if b.dim() == 1:
+        b = b[None]
+    nrhs = b.shape[0]
+    x = torch.empty_like(b)
+    it = C.c_int32(0)
+    rr = (C.c_double * nrhs)()
+    k = kern.c()
+    st = lib().kc_refine(pat.c(), _ptr(x_ord), x_ord.shape[1], C.byref(k), int(prec), _ptr(val), _ptr(diag),
+                         _ptr(perm), _ptr(b), nrhs, float(rtol), int(maxit), _ptr(x), C.byref(it), rr,
+                         C.byref(opts) if opts is not None else None, _stream(stream))
+    if st not in (KC_OK, KC_ENOTCONV, KC_EINDEF):
+        _check(st)
+    return x, int(it.value), [rr[i] for i in range(nrhs)], st
+
+
+def pca_truncate(pat: Pattern, prec, val, perm, k, stream=None):
+    """First k columns of L, rows in original order -> (k, N) float32."""
+    Lk = torch.empty((k, pat.N), dtype=torch.float32, device=val.device)
+    _check(lib().kc_pca_truncate(pat.c(), int(prec), _ptr(val), _ptr(perm), int(k), _ptr(Lk), _stream(stream)))
+    return Lk
+
+
+def pca_error(x, kern: Kernel, Lk, v0, iters=50, stream=None):
+    """Power-iteration estimate of ||Theta - Lk^T Lk||_2 (x in original order)."""
+    N, d = x.shape
+    est = C.c_double(0.0)
+    kk = kern.c()
+    _check(lib().kc_pca_error(_ptr(x), N, d, C.byref(kk), Lk.shape[0], _ptr(Lk), _ptr(v0), int(iters),
+                              C.byref(est), _stream(stream)))
+    return float(est.value)
+
+
+# ------------------------------------------------------------------ the path
+
+def build_pattern(x_ord, l, rho, rule=RULE_MAX, stream=None) -> Pattern:
+    rowptr, nnz = pattern_count(x_ord, l, rho, rule, stream)
+    col = pattern_fill(x_ord, l, rho, rowptr, nnz, rule, stream)
+    return schedule(rowptr, col, stream)
+
+
+def pipeline(x, rho, kern: Kernel, prec=FP32_FORM, rule=RULE_MAX, opts=None, stream=None):
+    """order -> pattern -> schedule -> factor, all on the device."""
+    perm, l, xo = order_points(x, stream)
+    pat = build_pattern(xo, l, rho, rule, stream)
+    val, diag, zp = factor(pat, xo, kern, prec, opts, stream=stream)
+    return dict(perm=perm, l=l, x_ord=xo, pat=pat, val=val, diag=diag, zero_pivots=zp)
