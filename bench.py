@@ -1,0 +1,351 @@
+#!/usr/bin/env python
+"""Benchmark of the hot path on synthetic inputs shaped like the paper's runs.
+
+Workload (default): N = 2^20 points on a 1024 x 1024 jittered grid in [0,1]^2
+(+-0.25 cell), Matern-3/2 with l = 0.1, rho = 3, 16 right-hand sides.
+One step = maximin ordering -> pattern S_rho -> schedule -> ICHOL(0) in the
+FP32 form -> solve L L^T x = b for the 16 right-hand sides, all on the GPU
+with inputs already resident.  The FP64 factor (+ solve) is timed on the same
+pattern for comparison.  Metric: nnz(L) per second of a whole step (and of
+the factor alone, the paper's t_ICHOL).
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+
+Prints one JSON line (rank 0).  With N > 1 (torchrun) every rank runs an
+independent replica of the workload on its own GPU ("replicas only": a single
+factor does not shard); value = nnz of all ranks / max over ranks of the time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1706_02205_gb300 import inputs  # noqa: E402
+
+METRIC = "ICHOL(0) nnz(L)/s at N=2^20 d=2 rho=3, FP32-form vs FP64; serve p50/p99 ms"
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        j = json.load(open(p))
+        return float(j["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def bytes_op(rowptr: np.ndarray, N: int, d: int, s: int) -> int:
+    """Operand bytes of the left-looking factor with value size s:
+    the pivot row staged once per column, the prefix of row j below i and x_j
+    for every entry (j,i), the pattern read and L written once, the points
+    read once.  sum over (j,i) of |R_j cap [0,i)| = sum_j |R_j|(|R_j|-1)/2."""
+    r = np.diff(rowptr).astype(np.int64) - 1
+    rsum = int(r.sum())
+    pre = int((r * (r - 1) // 2).sum())
+    nnz = int(rowptr[-1])
+    return rsum * (4 + s) + pre * (4 + s) + (nnz - N) * 8 * d + nnz * (4 + s) + N * d * 8
+
+
+class Clocks:
+    """nvidia-smi samples during the timed region."""
+
+    def __init__(self, dev_index: int):
+        self.f = tempfile.NamedTemporaryFile(prefix="clk", suffix=".csv", delete=False)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(dev_index), f"--query-gpu={q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.f.name):
+            c = [v.strip() for v in line.split(",")]
+            if len(c) < 9:
+                continue
+            try:
+                sm.append(float(c[1]))
+                mx.append(float(c[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, c[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.f.name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ---------------------------------------------------------------- our arm
+
+def run_ours(args, rank, world):
+    import torch
+
+    from paper_1706_02205_gb300 import kchol as kc
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream()
+    x_h = inputs.jittered_grid(args.n_side, seed=inputs.seed_for(2, rank))
+    N, d = x_h.shape
+    b_h = inputs.rhs(N, args.nrhs, seed=inputs.seed_for(2, 100 + rank))
+    kern = kc.Kernel(args.nu, args.ell, 1.0, 0.0)
+    x = torch.from_numpy(x_h).to(dev)
+    b = torch.from_numpy(b_h).to(dev)
+    flush = torch.empty(256 * 2**20 // 4, dtype=torch.float32, device=dev)  # 256 MB > L2
+
+    def step(prec=kc.FP32_FORM, ev=None):
+        if ev:
+            ev[0].record(stream)
+        perm, l, xo = kc.order_points(x)
+        if ev:
+            ev[1].record(stream)
+        rowptr, nnz = kc.pattern_count(xo, l, args.rho)
+        col = kc.pattern_fill(xo, l, args.rho, rowptr, nnz)
+        if ev:
+            ev[2].record(stream)
+        pat = kc.schedule(rowptr, col)
+        if ev:
+            ev[3].record(stream)
+        val, diag, zp = kc.factor(pat, xo, kern, prec)
+        if ev:
+            ev[4].record(stream)
+        xs = kc.solve(pat, prec, val, diag, kern, perm, b)
+        if ev:
+            ev[5].record(stream)
+        return dict(perm=perm, xo=xo, pat=pat, val=val, diag=diag, zp=zp, xs=xs)
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        r = step()
+    torch.cuda.synchronize()
+    pat = r["pat"]
+    nnz = pat.nnz
+    rowptr_h = pat.rowptr.cpu().numpy()
+
+    names = ["order", "pattern", "schedule", "factor", "solve"]
+    phase = {n: [] for n in names}
+    step_ms, fk_ms = [], []
+    launches0 = kc.launch_count()
+    clk = Clocks(dev.index) if rank == 0 else None
+    barrier()
+    torch.cuda.synchronize()
+    for _ in range(args.steps):
+        flush.zero_()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
+        r = step(kc.FP32_FORM, ev)
+        torch.cuda.synchronize()
+        fk_ms.append(kc.last_factor_kernel_ms())
+        for k, n in enumerate(names):
+            phase[n].append(ev[k].elapsed_time(ev[k + 1]))
+        step_ms.append(ev[0].elapsed_time(ev[5]))
+    torch.cuda.synchronize()
+    barrier()
+    launches = kc.launch_count() - launches0
+    clocks = clk.stop() if clk else None
+
+    # FP64 factor + solve on the same pattern (plain-method comparison)
+    pat, xo, perm = r["pat"], r["xo"], r["perm"]
+    f64_ms, f64_k, s64_ms = [], [], []
+    for it in range(args.warmup + args.steps):
+        flush.zero_()
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        e[0].record(stream)
+        v64, d64, zp64 = kc.factor(pat, xo, kern, kc.FP64)
+        e[1].record(stream)
+        kc.solve(pat, kc.FP64, v64, d64, kern, perm, b)
+        e[2].record(stream)
+        torch.cuda.synchronize()
+        if it >= args.warmup:
+            f64_ms.append(e[0].elapsed_time(e[1]))
+            s64_ms.append(e[1].elapsed_time(e[2]))
+            f64_k.append(kc.last_factor_kernel_ms())
+
+    # end to end through the public calls from pinned host buffers
+    xp = torch.from_numpy(x_h).pin_memory()
+    bp = torch.from_numpy(b_h).pin_memory()
+    out = torch.empty((args.nrhs, N), dtype=torch.float64).pin_memory()
+    e2e_ms = []
+    for _ in range(max(1, args.steps)):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        xd = xp.to(dev, non_blocking=True)
+        bd = bp.to(dev, non_blocking=True)
+        perm_, l_, xo_ = kc.order_points(xd)
+        pat_ = kc.build_pattern(xo_, l_, args.rho)
+        val_, diag_, _ = kc.factor(pat_, xo_, kern, kc.FP32_FORM)
+        xs_ = kc.solve(pat_, kc.FP32_FORM, val_, diag_, kern, perm_, bd)
+        out.copy_(xs_, non_blocking=True)
+        torch.cuda.synchronize()
+        e2e_ms.append((time.perf_counter() - t0) * 1e3)
+        del pat_, val_, diag_, xs_
+
+    # max over ranks
+    tot_ms = sum(step_ms)
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([tot_ms, sum(e2e_ms)], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        tot_ms, e2e_tot = float(t[0]), float(t[1])
+    else:
+        e2e_tot = sum(e2e_ms)
+
+    if rank != 0:
+        return None
+    hbm, peak_kind = peaks()
+    bop = bytes_op(rowptr_h, N, d, 4)
+    fk = statistics.mean(fk_ms)
+    achieved = bop / (fk * 1e-3) / 1e9
+    value = world * nnz * args.steps / (tot_ms * 1e-3)
+    line = {
+        "metric": METRIC,
+        "value": value,
+        "unit": "nnz(L)/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": tot_ms / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32 values + f64 pivots (FP32 form)",
+        "data": "synthetic",
+        "config": {"workload": f"jittered grid {args.n_side}x{args.n_side} (N={N}) in [0,1]^2, Matern-{args.nu} "
+                               f"l={args.ell}, rho={args.rho}, {args.nrhs} rhs; step = order+pattern+schedule+"
+                               f"factor(FP32 form)+solve",
+                   "N": N, "d": d, "nnz": nnz, "nnz_per_row": nnz / N, "depth": pat.depth,
+                   "zero_pivots": r["zp"], "l2": "working set > L2 (GBs); 256 MB L2 flush between steps",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "phases_ms": {n: statistics.mean(v) for n, v in phase.items()},
+        "factor_fp32_form": {"nnz_per_s": nnz / (statistics.mean(phase["factor"]) * 1e-3),
+                             "kernel_ms": fk, "kernel_nnz_per_s": nnz / (fk * 1e-3)},
+        "factor_fp64": {"nnz_per_s": nnz / (statistics.mean(f64_ms) * 1e-3), "call_ms": statistics.mean(f64_ms),
+                        "kernel_ms": statistics.mean(f64_k), "solve_ms": statistics.mean(s64_ms)},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                     "traffic": args.traffic, "peak_kind": f"{peak_kind} hbm_gbs (burst)",
+                     "kernel": "ichol_persistent_k<float>", "algorithmic_bytes": bop},
+        "e2e": {"value": world * nnz * max(1, args.steps) / (e2e_tot * 1e-3), "unit": "nnz(L)/s",
+                "ms_per_step": e2e_tot / max(1, args.steps),
+                "h2d_bytes_per_step": int(x_h.nbytes + b_h.nbytes), "d2h_bytes_per_step": int(out.numel() * 8)},
+        "gpu_launches": launches,
+        "clocks": clocks,
+    }
+    if args.cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args)
+    return line
+
+
+# ------------------------------------------------------- oracle (CPU) arm
+
+def oracle_step(n_side, args):
+    """One pass of the path in the FP64 oracle on a jittered grid n_side^2."""
+    import oracle
+    x = inputs.jittered_grid(n_side, seed=inputs.seed_for(2, 50))
+    N = x.shape[0]
+    b = inputs.rhs(N, args.nrhs, seed=inputs.seed_for(2, 51))
+    t0 = time.perf_counter()
+    perm, l, rp, col = oracle.sortsparse(x, args.rho)
+    xo = x[perm]
+    kern = oracle.Kernel(args.nu, args.ell)
+    val, zc = oracle.ichol(xo, rp, col, kern)
+    dg = oracle.solve_diag(xo, rp, val, kern)
+    for r in range(args.nrhs):
+        y = oracle.solve_lower(rp, col, val, dg, b[r][perm])
+        oracle.solve_upper(rp, col, val, dg, y)
+    dt = time.perf_counter() - t0
+    return int(rp[-1]), dt, N
+
+
+def cpu_baseline(args):
+    nnz, dt, N = oracle_step(args.cpu_side, args)
+    return {"value": nnz / dt, "unit": "nnz(L)/s", "cores": 1, "kind": "oracle",
+            "sample": f"jittered grid {args.cpu_side}x{args.cpu_side} (N={N}), same kernel/rho/{args.nrhs} rhs; "
+                      f"one full step (order+pattern+factor+solve) single-threaded FP64 C, {dt:.1f} s"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return None
+    for _ in range(args.warmup):
+        oracle_step(args.cpu_side, args)
+    tot, nnz_tot, N = 0.0, 0, 0
+    for _ in range(args.steps):
+        nnz, dt, N = oracle_step(args.cpu_side, args)
+        tot += dt
+        nnz_tot += nnz
+    v = nnz_tot / tot
+    return {"impl": "reference", "metric": METRIC, "value": v, "unit": "nnz(L)/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot * 1e3 / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"jittered grid {args.cpu_side}x{args.cpu_side} (N={N}) sample of the "
+                                   f"{args.n_side}x{args.n_side} workload, Matern-{args.nu} l={args.ell}, "
+                                   f"rho={args.rho}, {args.nrhs} rhs"},
+            "cpu_baseline": {"value": v, "unit": "nnz(L)/s", "cores": 1, "kind": "oracle",
+                             "sample": f"jittered grid {args.cpu_side}^2 per step"},
+            "e2e": {"value": v, "unit": "nnz(L)/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n-side", type=int, default=1024)
+    ap.add_argument("--nu", type=float, default=1.5)
+    ap.add_argument("--ell", type=float, default=0.1)
+    ap.add_argument("--rho", type=float, default=3.0)
+    ap.add_argument("--nrhs", type=int, default=16)
+    ap.add_argument("--cpu-side", type=int, default=320)
+    ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    ap.add_argument("--traffic", type=float, default=None, help="ncu DRAM bytes per factor launch, if measured")
+    args = ap.parse_args()
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if world > 1 and args.impl == "ours":
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+        dist.init_process_group("nccl")
+    if args.impl == "reference":
+        line = run_reference(args, rank, world)
+    else:
+        line = run_ours(args, rank, world)
+    if line is not None:
+        print(json.dumps(line), flush=True)
+    if world > 1 and args.impl == "ours":
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -99,6 +99,15 @@ typedef struct {
 const char* kc_last_error(void);
 int32_t kc_abi_version(void);
 
+/* Number of kernels this library has launched in the process so far
+ * (monotone; take differences around a region of interest). */
+int64_t kc_launch_count(void);
+
+/* Device time in ms of the persistent factor kernel of the calling thread's
+ * last kc_factor, measured with CUDA events on the launching stream (the
+ * task-list build before it is excluded). */
+double kc_last_factor_kernel_ms(void);
+
 /* ---- a2: maximin ordering (Section 2.3) -------------------------------- *
  * x: device double[N*d].  Outputs (device): perm int32[N] (position ->
  * original index), l double[N] (l[0] = +inf; first point = original index 0;

@@ -369,12 +369,14 @@ void ko_csr_to_csc(i64 N, const i64* rowptr, const i32* col, i64* colptr, i32* r
 /* where R_i = {k < i : (i,k) in S} and C_i = {j > i : (j,i) in S}.  In       */
 /* exact arithmetic this is the same as the algorithm's right-looking update  */
 /* A_kj -= A_ki A_ji / A_ii applied iff (i,j),(k,i),(k,j) in S.              */
-/* Sums run in ascending k.  val[] follows the CSR layout.  Returns the       */
-/* number of zeroed columns.                                                 */
+/* Sums run in ascending k (rev=1: descending, the same arithmetic in the   */
+/* other order, used only to measure how much FP64 rounding order moves the */
+/* result).  val[] follows the CSR layout; piv (optional) receives every     */
+/* pivot p before the test.  Returns the number of zeroed columns.          */
 /* ------------------------------------------------------------------------ */
 
 i64 ko_ichol(const double* xo, i64 N, i32 d, double nu, double ell, double sigma2, double nugget,
-             const i64* rowptr, const i32* col, double* val, char* zero_col) {
+             const i64* rowptr, const i32* col, double* val, char* zero_col, i32 rev, double* piv) {
     ko_kernel K = {nu, ell, sigma2, nugget};
     i64 nnz = rowptr[N];
     i64* colptr = (i64*)malloc(sizeof(i64) * ((size_t)N + 1));
@@ -386,7 +388,9 @@ i64 ko_ichol(const double* xo, i64 N, i32 d, double nu, double ell, double sigma
     for (i64 i = 0; i < N; ++i) {
         i64 a0 = rowptr[i], a1 = rowptr[i + 1] - 1; /* row i without its diagonal: [a0, a1) */
         double p = theta_pos(xo, d, i, i, &K);
-        for (i64 e = a0; e < a1; ++e) p -= val[e] * val[e];
+        if (!rev) for (i64 e = a0; e < a1; ++e) p -= val[e] * val[e];
+        else for (i64 e = a1 - 1; e >= a0; --e) p -= val[e] * val[e];
+        if (piv) piv[i] = p;
         if (!(p > 0.0)) {
             zero_col[i] = 1; zeroed++;
             continue; /* column stays zero, diagonal included */
@@ -400,12 +404,22 @@ i64 ko_ichol(const double* xo, i64 N, i32 d, double nu, double ell, double sigma
             i64 bij = slot[q];                 /* position of (j,i) in row j */
             /* merge row j (k < i) with row i (k < i) */
             double s = theta_pos(xo, d, j, i, &K);
-            i64 u = a0, v = b0;
-            while (u < a1 && v < bij) {
-                i32 ku = col[u], kv = col[v];
-                if (ku == kv) { s -= val[v] * val[u]; ++u; ++v; }
-                else if (ku < kv) ++u;
-                else ++v;
+            if (!rev) {
+                i64 u = a0, v = b0;
+                while (u < a1 && v < bij) {
+                    i32 ku = col[u], kv = col[v];
+                    if (ku == kv) { s -= val[v] * val[u]; ++u; ++v; }
+                    else if (ku < kv) ++u;
+                    else ++v;
+                }
+            } else {
+                i64 u = a1 - 1, v = bij - 1;
+                while (u >= a0 && v >= b0) {
+                    i32 ku = col[u], kv = col[v];
+                    if (ku == kv) { s -= val[v] * val[u]; --u; --v; }
+                    else if (ku > kv) --u;
+                    else --v;
+                }
             }
             val[bij] = s / Lii;
         }

@@ -50,6 +50,10 @@ const char* kc_last_error(void) { return last_error_cstr(); }
 
 int32_t kc_abi_version(void) { return 1; }
 
+int64_t kc_launch_count(void) { return launch_count(); }
+
+double kc_last_factor_kernel_ms(void) { return factor_kernel_ms(); }
+
 kc_status kc_order_points(const double* x, int64_t N, int32_t d, int32_t* perm, double* l, double* x_ord,
                           void* stream) {
     KC_TRY(check_points(x, N, d));

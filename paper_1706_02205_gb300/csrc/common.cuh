@@ -58,6 +58,14 @@ struct Arena {
 
 int sm_count();
 
+// Every kernel launch of the library goes through note_launch() (a process-wide
+// counter, read by kc_launch_count) so callers can see how much device work ran.
+void note_launch();
+int64_t launch_count();
+// Device time of the last persistent factor kernel (CUDA events on its stream).
+void set_factor_kernel_ms(double ms);
+double factor_kernel_ms();
+
 // ------------------------------------------------------ device helpers
 __device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }
 

@@ -280,10 +280,10 @@ kc_status build_tasks(const kc_pattern* P, int rpt, Arena& A, cudaStream_t s, in
     KC_TRY(A.get(&cnt, N));
     KC_TRY(A.get(&toff, N + 1));
     KC_TRY(A.get(&mr, 1));
-    task_count_k<<<blocks_for(N, 256), 256, 0, s>>>(P->order, P->colptr, N, rpt, cnt);
+    ::kc::note_launch(), task_count_k<<<blocks_for(N, 256), 256, 0, s>>>(P->order, P->colptr, N, rpt, cnt);
     KC_TRY(exclusive_scan_i64(cnt, toff, N, A, s));
     KC_CUDA(cudaMemsetAsync(mr, 0, sizeof(int), s));
-    max_row_k<<<blocks_for(N, 256), 256, 0, s>>>(P->rowptr, N, mr);
+    ::kc::note_launch(), max_row_k<<<blocks_for(N, 256), 256, 0, s>>>(P->rowptr, N, mr);
     KC_CUDA(cudaGetLastError());
     int64_t nt = 0;
     int hmr = 0;
@@ -292,7 +292,7 @@ kc_status build_tasks(const kc_pattern* P, int rpt, Arena& A, cudaStream_t s, in
     KC_CUDA(cudaStreamSynchronize(s));
     int2* tasks;
     KC_TRY(A.get(&tasks, nt));
-    task_fill_k<<<blocks_for(N * 32, 256), 256, 0, s>>>(P->order, toff, N, tasks);
+    ::kc::note_launch(), task_fill_k<<<blocks_for(N * 32, 256), 256, 0, s>>>(P->order, toff, N, tasks);
     KC_CUDA(cudaGetLastError());
     *tasks_out = tasks;
     *ntasks_out = nt;
@@ -356,13 +356,23 @@ static kc_status factor_run(const kc_pattern* P, const double* x, int d, const K
     if (o && o->ctas_per_sm > 0 && o->ctas_per_sm < per_sm) per_sm = o->ctas_per_sm;
     if (per_sm < 1) per_sm = 1;
     int grid = sm_count() * per_sm;
-    ichol_persistent_k<T><<<grid, warps * 32, smem, s>>>(a);
+    cudaEvent_t e0, e1;
+    KC_CUDA(cudaEventCreate(&e0));
+    KC_CUDA(cudaEventCreate(&e1));
+    KC_CUDA(cudaEventRecord(e0, s));
+    ::kc::note_launch(), ichol_persistent_k<T><<<grid, warps * 32, smem, s>>>(a);
     KC_CUDA(cudaGetLastError());
+    KC_CUDA(cudaEventRecord(e1, s));
     int h_status = 0;
     unsigned long long h_zp = 0;
     KC_CUDA(cudaMemcpyAsync(&h_status, status, sizeof(int), cudaMemcpyDeviceToHost, s));
     KC_CUDA(cudaMemcpyAsync(&h_zp, zp, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
     KC_CUDA(cudaStreamSynchronize(s));
+    float ms = 0.f;
+    KC_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    set_factor_kernel_ms(ms);
     if (zero_out) *zero_out = (int64_t)h_zp;
     if (h_status == DEV_TIMEOUT) return fail(KC_ETIMEOUT, "factor: a dependency wait ran out");
     if (h_status != 0) return fail(KC_ECUDA, "factor: device status " + std::to_string(h_status));

@@ -88,11 +88,11 @@ kc_status grid_build(const Grid& g, const double* x, int d, const int32_t* ids, 
     KC_TRY(A.get(&v1, n));
     KC_TRY(A.get(&cnt, g.ncells));
     KC_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int) * g.ncells, s));
-    if (n > 0) cell_keys_k<<<blocks_for(n, 256), 256, 0, s>>>(g, x, d, ids, n, k0, v0, cnt);
+    if (n > 0) ::kc::note_launch(), cell_keys_k<<<blocks_for(n, 256), 256, 0, s>>>(g, x, d, ids, n, k0, v0, cnt);
     KC_CUDA(cudaGetLastError());
     KC_TRY(exclusive_scan_i32_to_i64(cnt, cell_start, g.ncells, A, s));
     KC_TRY(radix_sort_u64_i64(k0, v0, k1, v1, n, bits_of(g.ncells), A, s));
-    if (n > 0) ids_out_k<<<blocks_for(n, 256), 256, 0, s>>>(v1, n, sorted);
+    if (n > 0) ::kc::note_launch(), ids_out_k<<<blocks_for(n, 256), 256, 0, s>>>(v1, n, sorted);
     KC_CUDA(cudaGetLastError());
     return KC_OK;
 }
@@ -132,7 +132,7 @@ kc_status bbox(const double* x, int64_t N, int d, double* lo, double* hi, Arena&
     const int nb = 128;
     double* part;
     KC_TRY(A.get(&part, nb * 6));
-    bbox_k<<<nb, 256, 0, s>>>(x, N, d, part);
+    ::kc::note_launch(), bbox_k<<<nb, 256, 0, s>>>(x, N, d, part);
     KC_CUDA(cudaGetLastError());
     double h[nb * 6];
     KC_CUDA(cudaMemcpyAsync(h, part, sizeof(h), cudaMemcpyDeviceToHost, s));

@@ -39,7 +39,7 @@ kc_status check_finite(const double* x, int64_t n, Arena& A, cudaStream_t s) {
     int* bad;
     KC_TRY(A.get(&bad, 1));
     KC_CUDA(cudaMemsetAsync(bad, 0, sizeof(int), s));
-    finite_check_k<<<blocks_for(n, 256), 256, 0, s>>>(x, n, bad);
+    ::kc::note_launch(), finite_check_k<<<blocks_for(n, 256), 256, 0, s>>>(x, n, bad);
     KC_CUDA(cudaGetLastError());
     int h = 0;
     KC_CUDA(cudaMemcpyAsync(&h, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -249,7 +249,7 @@ kc_status order_impl(const double* x, int64_t N, int d, int32_t* perm, double* l
     KC_TRY(A.get(&ioff, N + 1));
     KC_TRY(A.get(&bstart, 2 * N + 2));
     KC_TRY(A.get(&ctr, 8));
-    ord_init_k<<<blocks_for(N, 256), 256, 0, s>>>(x, d, gsorted, N, xg, idg, v2, stat);
+    ::kc::note_launch(), ord_init_k<<<blocks_for(N, 256), 256, 0, s>>>(x, d, gsorted, N, xg, idg, v2, stat);
     KC_CUDA(cudaGetLastError());
     int64_t item_cap = 0;
     item_sel = nullptr;
@@ -257,7 +257,7 @@ kc_status order_impl(const double* x, int64_t N, int d, int32_t* perm, double* l
     int rounds = 0;
     for (;;) {
         KC_CUDA(cudaMemsetAsync(ctr, 0, 2 * sizeof(unsigned long long), s));
-        ord_vmax_k<<<sms * 4, 256, 0, s>>>(v2, stat, N, ctr, ctr + 1);
+        ::kc::note_launch(), ord_vmax_k<<<sms * 4, 256, 0, s>>>(v2, stat, N, ctr, ctr + 1);
         unsigned long long h[2];
         KC_CUDA(cudaMemcpyAsync(h, ctr, sizeof(h), cudaMemcpyDeviceToHost, s));
         KC_CUDA(cudaStreamSynchronize(s));
@@ -266,7 +266,7 @@ kc_status order_impl(const double* x, int64_t N, int d, int32_t* perm, double* l
         memcpy(&vmax, &h[0], sizeof(double));
         const double T = vmax * 0.25;
         KC_CUDA(cudaMemsetAsync(ctr + 2, 0, sizeof(unsigned long long), s));
-        ord_band_k<<<blocks_for(N, 256), 256, 0, s>>>(v2, stat, N, T, blist, ctr + 2);
+        ::kc::note_launch(), ord_band_k<<<blocks_for(N, 256), 256, 0, s>>>(v2, stat, N, T, blist, ctr + 2);
         unsigned long long hnb = 0;
         KC_CUDA(cudaMemcpyAsync(&hnb, ctr + 2, sizeof(hnb), cudaMemcpyDeviceToHost, s));
         KC_CUDA(cudaStreamSynchronize(s));
@@ -282,7 +282,7 @@ kc_status order_impl(const double* x, int64_t N, int d, int32_t* perm, double* l
         for (;;) {
             if (++rounds > 1000000) return fail(KC_ECUDA, "ordering: too many rounds");
             KC_CUDA(cudaMemsetAsync(ctr + 3, 0, 2 * sizeof(unsigned long long), s));
-            ord_dominance_k<<<blocks_for(nb, 128), 128, 0, s>>>(gb, bsorted, bstart, nb, xg, d, idg, v2, stat, T, sel,
+            ::kc::note_launch(), ord_dominance_k<<<blocks_for(nb, 128), 128, 0, s>>>(gb, bsorted, bstart, nb, xg, d, idg, v2, stat, T, sel,
                                                                 ctr + 3, ctr + 4);
             unsigned long long hs[2];
             KC_CUDA(cudaMemcpyAsync(hs, ctr + 3, sizeof(hs), cudaMemcpyDeviceToHost, s));
@@ -290,8 +290,8 @@ kc_status order_impl(const double* x, int64_t N, int d, int32_t* perm, double* l
             const int64_t ns = (int64_t)hs[0];
             if (hs[1] == 0) break;  // band exhausted
             if (ns == 0) return fail(KC_ECUDA, "ordering: no dominant point in a nonempty band");
-            ord_mark_k<<<blocks_for(ns, 256), 256, 0, s>>>(sel, ns, stat);
-            ord_items_k<<<blocks_for(ns, 256), 256, 0, s>>>(g0, sel, ns, xg, d, v2, icnt);
+            ::kc::note_launch(), ord_mark_k<<<blocks_for(ns, 256), 256, 0, s>>>(sel, ns, stat);
+            ::kc::note_launch(), ord_items_k<<<blocks_for(ns, 256), 256, 0, s>>>(g0, sel, ns, xg, d, v2, icnt);
             Arena R(s);  // per-round scratch of the scan
             KC_TRY(exclusive_scan_i64(icnt, ioff, ns, R, s));
             int64_t nitems = 0;
@@ -302,8 +302,8 @@ kc_status order_impl(const double* x, int64_t N, int d, int32_t* perm, double* l
                 if (item_sel) cudaFreeAsync(item_sel, s);
                 KC_CUDA(cudaMallocAsync(&item_sel, sizeof(int32_t) * item_cap, s));
             }
-            ord_item_fill_k<<<blocks_for(ns * 32, 256), 256, 0, s>>>(ioff, ns, item_sel);
-            ord_update_k<<<blocks_for(nitems * 32, 256), 256, 0, s>>>(g0, sel, ioff, item_sel, nitems, cstart, xg, d,
+            ::kc::note_launch(), ord_item_fill_k<<<blocks_for(ns * 32, 256), 256, 0, s>>>(ioff, ns, item_sel);
+            ::kc::note_launch(), ord_update_k<<<blocks_for(nitems * 32, 256), 256, 0, s>>>(g0, sel, ioff, item_sel, nitems, cstart, xg, d,
                                                                      idg, v2, stat);
             KC_CUDA(cudaGetLastError());
         }
@@ -315,9 +315,9 @@ kc_status order_impl(const double* x, int64_t N, int d, int32_t* perm, double* l
     KC_TRY(A.get(&k1, N));
     KC_TRY(A.get(&w0, N));
     KC_TRY(A.get(&w1, N));
-    ord_keys_k<<<blocks_for(N, 256), 256, 0, s>>>(v2, idg, N, k0, w0);
+    ::kc::note_launch(), ord_keys_k<<<blocks_for(N, 256), 256, 0, s>>>(v2, idg, N, k0, w0);
     KC_TRY(radix_sort_u64_i64(k0, w0, k1, w1, N, 64, A, s));
-    ord_out_k<<<blocks_for(N, 256), 256, 0, s>>>(k1, w1, x, N, d, perm, l, x_ord);
+    ::kc::note_launch(), ord_out_k<<<blocks_for(N, 256), 256, 0, s>>>(k1, w1, x, N, d, perm, l, x_ord);
     KC_CUDA(cudaGetLastError());
     KC_CUDA(cudaStreamSynchronize(s));
     return KC_OK;

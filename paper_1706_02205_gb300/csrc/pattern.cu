@@ -141,17 +141,17 @@ static kc_status pat_setup(const double* xo, const double* l, int64_t N, int d, 
     KC_TRY(A.get(&S.cstart, S.g.ncells + 1));
     KC_TRY(grid_build(S.g, xo, d, nullptr, N, S.gs, S.cstart, A, s));
     KC_TRY(A.get(&S.xs, N * d));
-    pat_gather_k<<<blocks_for(N, 256), 256, 0, s>>>(xo, S.gs, N, d, S.xs);
+    ::kc::note_launch(), pat_gather_k<<<blocks_for(N, 256), 256, 0, s>>>(xo, S.gs, N, d, S.xs);
     int64_t* cnt;
     KC_TRY(A.get(&cnt, N));
     KC_TRY(A.get(&S.off, N + 1));
-    pat_items_k<<<blocks_for(N, 256), 256, 0, s>>>(S.g, xo, l, N, d, rho, cnt);
+    ::kc::note_launch(), pat_items_k<<<blocks_for(N, 256), 256, 0, s>>>(S.g, xo, l, N, d, rho, cnt);
     KC_CUDA(cudaGetLastError());
     KC_TRY(exclusive_scan_i64(cnt, S.off, N, A, s));
     KC_CUDA(cudaMemcpyAsync(&S.nitems, S.off + N, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     KC_CUDA(cudaStreamSynchronize(s));
     KC_TRY(A.get(&S.item_col, S.nitems));
-    pat_item_fill_k<<<blocks_for(N * 32, 256), 256, 0, s>>>(S.off, N, S.item_col);
+    ::kc::note_launch(), pat_item_fill_k<<<blocks_for(N * 32, 256), 256, 0, s>>>(S.off, N, S.item_col);
     KC_CUDA(cudaGetLastError());
     return KC_OK;
 }
@@ -184,8 +184,8 @@ kc_status pattern_count_impl(const double* xo, const double* l, int64_t N, int d
     KC_TRY(A.get(&len, N));
     KC_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int) * N, s));
     PatArgs P = pat_args(S, xo, l, d, rho, rule);
-    if (S.nitems > 0) pat_scan_k<false><<<blocks_for(S.nitems * 32, 256), 256, 0, s>>>(P, cnt, nullptr, nullptr);
-    plus_one_k<<<blocks_for(N, 256), 256, 0, s>>>(cnt, N, len);
+    if (S.nitems > 0) ::kc::note_launch(), pat_scan_k<false><<<blocks_for(S.nitems * 32, 256), 256, 0, s>>>(P, cnt, nullptr, nullptr);
+    ::kc::note_launch(), plus_one_k<<<blocks_for(N, 256), 256, 0, s>>>(cnt, N, len);
     KC_CUDA(cudaGetLastError());
     KC_TRY(exclusive_scan_i32_to_i64(len, rowptr, N, A, s));
     int64_t nnz = 0;
@@ -279,7 +279,7 @@ kc_status pattern_fill_impl(const double* xo, const double* l, int64_t N, int d,
     int* mx;
     KC_TRY(A.get(&mx, 1));
     KC_CUDA(cudaMemsetAsync(mx, 0, sizeof(int), s));
-    max_len_k<<<blocks_for(N, 256), 256, 0, s>>>(rowptr, N, mx);
+    ::kc::note_launch(), max_len_k<<<blocks_for(N, 256), 256, 0, s>>>(rowptr, N, mx);
     int hmx = 0;
     KC_CUDA(cudaMemcpyAsync(&hmx, mx, sizeof(int), cudaMemcpyDeviceToHost, s));
     KC_CUDA(cudaStreamSynchronize(s));
@@ -290,14 +290,14 @@ kc_status pattern_fill_impl(const double* xo, const double* l, int64_t N, int d,
     KC_TRY(A.get(&cnt, N));
     KC_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int) * N, s));
     PatArgs P = pat_args(S, xo, l, d, rho, rule);
-    if (S.nitems > 0) pat_scan_k<true><<<blocks_for(S.nitems * 32, 256), 256, 0, s>>>(P, cnt, rowptr, col);
+    if (S.nitems > 0) ::kc::note_launch(), pat_scan_k<true><<<blocks_for(S.nitems * 32, 256), 256, 0, s>>>(P, cnt, rowptr, col);
     KC_CUDA(cudaGetLastError());
     int32_t* long_rows;
     unsigned long long* nlong;
     KC_TRY(A.get(&long_rows, N));
     KC_TRY(A.get(&nlong, 1));
     KC_CUDA(cudaMemsetAsync(nlong, 0, sizeof(unsigned long long), s));
-    row_sort_warp_k<<<blocks_for(N, 8), 256, 0, s>>>(rowptr, N, col, long_rows, nlong);
+    ::kc::note_launch(), row_sort_warp_k<<<blocks_for(N, 8), 256, 0, s>>>(rowptr, N, col, long_rows, nlong);
     KC_CUDA(cudaGetLastError());
     unsigned long long hl = 0;
     KC_CUDA(cudaMemcpyAsync(&hl, nlong, sizeof(hl), cudaMemcpyDeviceToHost, s));
@@ -305,7 +305,7 @@ kc_status pattern_fill_impl(const double* xo, const double* l, int64_t N, int d,
     if (hl > 0) {
         size_t sm = sizeof(int) * SORT_BLOCK_CAP;
         KC_CUDA(cudaFuncSetAttribute(row_sort_block_k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-        row_sort_block_k<<<(unsigned)hl, 1024, sm, s>>>(rowptr, col, long_rows);
+        ::kc::note_launch(), row_sort_block_k<<<(unsigned)hl, 1024, sm, s>>>(rowptr, col, long_rows);
         KC_CUDA(cudaGetLastError());
     }
     KC_CUDA(cudaStreamSynchronize(s));

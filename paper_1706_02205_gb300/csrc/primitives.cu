@@ -2,7 +2,7 @@
 // steps, plus error reporting.  Written for sm_103a; no library kernels.
 #include <cstdio>
 #include <cmath>
-#include <mutex>
+#include <atomic>
 
 #include "common.cuh"
 
@@ -20,6 +20,13 @@ kc_status cuda_fail(cudaError_t e, const char* what) {
     g_last_error = std::string(what) + ": " + cudaGetErrorString(e);
     return e == cudaErrorMemoryAllocation ? KC_ENOMEM : KC_ECUDA;
 }
+
+static std::atomic<int64_t> g_launches{0};
+static thread_local double g_factor_ms = 0.0;
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+int64_t launch_count() { return g_launches.load(std::memory_order_relaxed); }
+void set_factor_kernel_ms(double ms) { g_factor_ms = ms; }
+double factor_kernel_ms() { return g_factor_ms; }
 
 int sm_count() {
     int dev = 0, n = 0;
@@ -142,10 +149,10 @@ static kc_status scan_impl(const Tin* in, int64_t* out, int64_t n, Arena& A, cud
     int64_t* boff;
     KC_TRY(A.get(&bsum, nb));
     KC_TRY(A.get(&boff, nb + 1));
-    scan_reduce_k<Tin><<<(unsigned)nb, SCAN_THREADS, 0, s>>>(in, n, bsum);
-    if (nb <= 8192) scan_single_k<<<1, 1024, 0, s>>>(bsum, nb, boff);
+    ::kc::note_launch(), scan_reduce_k<Tin><<<(unsigned)nb, SCAN_THREADS, 0, s>>>(in, n, bsum);
+    if (nb <= 8192) ::kc::note_launch(), scan_single_k<<<1, 1024, 0, s>>>(bsum, nb, boff);
     else KC_TRY(scan_impl<int64_t>(bsum, boff, nb, A, s));
-    scan_tile_k<Tin><<<(unsigned)nb, SCAN_THREADS, 0, s>>>(in, n, boff, out);
+    ::kc::note_launch(), scan_tile_k<Tin><<<(unsigned)nb, SCAN_THREADS, 0, s>>>(in, n, boff, out);
     KC_CUDA(cudaGetLastError());
     return KC_OK;
 }
@@ -243,9 +250,9 @@ static kc_status radix_impl(K* k_in, int64_t* v_in, K* k_out, int64_t* v_out, in
     int64_t* vb = v_out;
     for (int p = 0; p < passes; ++p) {
         int shift = 8 * p;
-        rs_hist_k<K><<<(unsigned)ntiles, 256, 0, s>>>(ka, n, shift, ntiles, hist);
+        ::kc::note_launch(), rs_hist_k<K><<<(unsigned)ntiles, 256, 0, s>>>(ka, n, shift, ntiles, hist);
         KC_TRY(exclusive_scan_i64(hist, goff, 256 * ntiles, A, s));
-        rs_scatter_k<K><<<(unsigned)ntiles, RS_WARPS * 32, 0, s>>>(ka, va, n, shift, ntiles, goff, kb, vb);
+        ::kc::note_launch(), rs_scatter_k<K><<<(unsigned)ntiles, RS_WARPS * 32, 0, s>>>(ka, va, n, shift, ntiles, goff, kb, vb);
         KC_CUDA(cudaGetLastError());
         K* tk = ka; ka = kb; kb = tk;
         int64_t* tv = va; va = vb; vb = tv;

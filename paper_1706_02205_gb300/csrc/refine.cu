@@ -64,7 +64,7 @@ static kc_status dense_f64_launch(const double* x, int64_t N, int d, const Kerne
                                   double* y, cudaStream_t s) {
     size_t sm = sizeof(double) * DM_THREADS * (d + NRHS);
     KC_CUDA(cudaFuncSetAttribute(dense_theta_f64_k<NRHS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    dense_theta_f64_k<NRHS><<<blocks_for(N, DM_THREADS), DM_THREADS, sm, s>>>(x, N, d, kp, v, y);
+    ::kc::note_launch(), dense_theta_f64_k<NRHS><<<blocks_for(N, DM_THREADS), DM_THREADS, sm, s>>>(x, N, d, kp, v, y);
     KC_CUDA(cudaGetLastError());
     return KC_OK;
 }
@@ -115,8 +115,8 @@ __global__ void dots_final_k(const double* __restrict__ partial, int nb, int nrh
 
 static kc_status dots(const double* a, const double* c, int64_t N, int nrhs, double* partial, double* out,
                       cudaStream_t s) {
-    dots_k<<<RED_BLOCKS, 256, 0, s>>>(a, c, N, nrhs, partial);
-    dots_final_k<<<1, 32, 0, s>>>(partial, RED_BLOCKS, nrhs, out);
+    ::kc::note_launch(), dots_k<<<RED_BLOCKS, 256, 0, s>>>(a, c, N, nrhs, partial);
+    ::kc::note_launch(), dots_final_k<<<1, 32, 0, s>>>(partial, RED_BLOCKS, nrhs, out);
     KC_CUDA(cudaGetLastError());
     return KC_OK;
 }
@@ -203,10 +203,10 @@ kc_status refine_impl(const kc_pattern* P, const double* x_ord, int d, const kc_
         return solver_apply<float>(S, (const float*)val, diag, fb, in, out, ns, s);
     };
     const unsigned gb = blocks_for(n, 256);
-    copy_k<<<gb, 256, 0, s>>>(r, bp, n);
+    ::kc::note_launch(), copy_k<<<gb, 256, 0, s>>>(r, bp, n);
     KC_TRY(dots(bp, bp, N, ns, partial, bb, s));
     KC_TRY(precond(r, z));
-    copy_k<<<gb, 256, 0, s>>>(p, z, n);
+    ::kc::note_launch(), copy_k<<<gb, 256, 0, s>>>(p, z, n);
     KC_TRY(dots(r, z, N, ns, partial, rz, s));
     double h_bb[16], h_rr[16], h_pq[16];
     int h_active[16];
@@ -241,18 +241,18 @@ kc_status refine_impl(const kc_pattern* P, const double* x_ord, int d, const kc_
                 h_active[c] = 0;
             }
         if (result == KC_EINDEF) break;
-        cg_update_xr_k<<<gb, 256, 0, s>>>(xs, r, p, q, rz, pq, active, N, ns);
+        ::kc::note_launch(), cg_update_xr_k<<<gb, 256, 0, s>>>(xs, r, p, q, rz, pq, active, N, ns);
         KC_TRY(precond(r, z));
         KC_TRY(dots(r, z, N, ns, partial, rzn, s));
-        cg_update_p_k<<<gb, 256, 0, s>>>(p, z, rz, rzn, active, N, ns);
-        copy_k<<<1, 32, 0, s>>>(rz, rzn, ns);
+        ::kc::note_launch(), cg_update_p_k<<<gb, 256, 0, s>>>(p, z, rz, rzn, active, N, ns);
+        ::kc::note_launch(), copy_k<<<1, 32, 0, s>>>(rz, rzn, ns);
         KC_CUDA(cudaGetLastError());
         ++it;
     }
     KC_TRY(solver_check(S, s));
     // true residual b - Theta x
     KC_TRY(dense_theta_f64(x_ord, N, d, kp, xs, q, ns, s));
-    sub_k<<<gb, 256, 0, s>>>(r, bp, q, n);
+    ::kc::note_launch(), sub_k<<<gb, 256, 0, s>>>(r, bp, q, n);
     KC_TRY(dots(r, r, N, ns, partial, rr, s));
     KC_CUDA(cudaMemcpyAsync(h_rr, rr, sizeof(double) * ns, cudaMemcpyDeviceToHost, s));
     {
@@ -294,7 +294,7 @@ kc_status pca_truncate_impl(const kc_pattern* P, int prec, const void* val, cons
     if (prec != KC_FP64 && prec != KC_FP32_FORM) return fail(KC_EINVAL, "bad prec");
     KC_CUDA(cudaMemsetAsync(Lk, 0, sizeof(float) * P->N * (size_t)k, s));
     if (k == 0) return KC_OK;
-    pca_scatter_k<<<blocks_for(P->N * 32, 256), 256, 0, s>>>(P->rowptr, P->col, P->N, k, val, prec == KC_FP32_FORM,
+    ::kc::note_launch(), pca_scatter_k<<<blocks_for(P->N * 32, 256), 256, 0, s>>>(P->rowptr, P->col, P->N, k, val, prec == KC_FP32_FORM,
                                                              perm, Lk);
     KC_CUDA(cudaGetLastError());
     return KC_OK;
@@ -387,14 +387,14 @@ kc_status pca_error_impl(const double* x, int64_t N, int d, const kc_kernel* ker
     KC_TRY(A.get(&sc, 2));
     KC_CUDA(cudaMemcpyAsync(v, v0, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
     for (int it = 0; it < iters; ++it) {
-        dense_theta_f32_k<<<blocks_for(N, DM_THREADS), DM_THREADS, 0, s>>>(x, N, d, kp, v, w);
+        ::kc::note_launch(), dense_theta_f32_k<<<blocks_for(N, DM_THREADS), DM_THREADS, 0, s>>>(x, N, d, kp, v, w);
         if (k > 0) {
-            lkt_v_k<<<k, 256, 0, s>>>(Lk, v, N, c);
-            w_minus_lk_c_k<<<blocks_for(N, 256), 256, 0, s>>>(Lk, c, k, N, w);
+            ::kc::note_launch(), lkt_v_k<<<k, 256, 0, s>>>(Lk, v, N, c);
+            ::kc::note_launch(), w_minus_lk_c_k<<<blocks_for(N, 256), 256, 0, s>>>(Lk, c, k, N, w);
         }
         KC_TRY(dots(v, w, N, 1, partial, sc, s));
         KC_TRY(dots(w, w, N, 1, partial, sc + 1, s));
-        scale_k<<<blocks_for(N, 256), 256, 0, s>>>(w, sc + 1, N, v);
+        ::kc::note_launch(), scale_k<<<blocks_for(N, 256), 256, 0, s>>>(w, sc + 1, N, v);
         KC_CUDA(cudaGetLastError());
     }
     double h[2] = {0, 0};

@@ -123,11 +123,11 @@ kc_status schedule_impl(int64_t N, const int64_t* rowptr, const int32_t* col, in
     KC_TRY(A.get(&v0, nnz));
     KC_TRY(A.get(&v1, nnz));
     int sms = sm_count();
-    row_of_k<<<sms * 8, 256, 0, s>>>(rowptr, N, rowof);
-    col_keys_k<<<blocks_for(nnz, 256), 256, 0, s>>>(col, nnz, k0, v0);
+    ::kc::note_launch(), row_of_k<<<sms * 8, 256, 0, s>>>(rowptr, N, rowof);
+    ::kc::note_launch(), col_keys_k<<<blocks_for(nnz, 256), 256, 0, s>>>(col, nnz, k0, v0);
     KC_CUDA(cudaGetLastError());
     KC_TRY(radix_sort_u32_i64(k0, v0, k1, v1, nnz, bits_for(N), A, s));
-    csc_finish_k<<<blocks_for(nnz, 256), 256, 0, s>>>(k1, v1, nnz, rowof, N, colptr, rowidx, slot);
+    ::kc::note_launch(), csc_finish_k<<<blocks_for(nnz, 256), 256, 0, s>>>(k1, v1, nnz, rowof, N, colptr, rowidx, slot);
     KC_CUDA(cudaGetLastError());
 
     // levels
@@ -141,7 +141,7 @@ kc_status schedule_impl(int64_t N, const int64_t* rowptr, const int32_t* col, in
     KC_CUDA(cudaMemsetAsync(dev_depth, 0, sizeof(int), s));
     KC_CUDA(cudaMemsetAsync(status, 0, sizeof(int), s));
     KC_CUDA(cudaMemsetAsync(level, 0, sizeof(int) * N, s));
-    levels_k<<<sms * 8, 256, 0, s>>>(rowptr, col, N, level, ticket, dev_depth, status, 4000000000LL);
+    ::kc::note_launch(), levels_k<<<sms * 8, 256, 0, s>>>(rowptr, col, N, level, ticket, dev_depth, status, 4000000000LL);
     KC_CUDA(cudaGetLastError());
     int h_depth = 0, h_status = 0;
     KC_CUDA(cudaMemcpyAsync(&h_depth, dev_depth, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -150,10 +150,10 @@ kc_status schedule_impl(int64_t N, const int64_t* rowptr, const int32_t* col, in
     if (h_status != 0) return fail(KC_ETIMEOUT, "level computation: a dependency wait ran out");
 
     // columns sorted by (level, index)
-    level_keys_k<<<blocks_for(N, 256), 256, 0, s>>>(level, N, k0, v0);
+    ::kc::note_launch(), level_keys_k<<<blocks_for(N, 256), 256, 0, s>>>(level, N, k0, v0);
     KC_CUDA(cudaGetLastError());
     KC_TRY(radix_sort_u32_i64(k0, v0, k1, v1, N, bits_for(h_depth), A, s));
-    order_out_k<<<blocks_for(N, 256), 256, 0, s>>>(v1, N, order);
+    ::kc::note_launch(), order_out_k<<<blocks_for(N, 256), 256, 0, s>>>(v1, N, order);
     KC_CUDA(cudaGetLastError());
     KC_CUDA(cudaStreamSynchronize(s));
     if (depth_out) *depth_out = h_depth;

@@ -225,13 +225,13 @@ kc_status solver_apply(Solver& S, const T* val, const double* diag, double diag_
     KC_CUDA(cudaMemsetAsync(S.ticket, 0, 2 * sizeof(unsigned long long), s));
     KC_CUDA(cudaMemsetAsync(S.status, 0, sizeof(int), s));
     a.ticket = S.ticket;
-    fwd_solve_k<T><<<grid, 256, 0, s>>>(a);
+    ::kc::note_launch(), fwd_solve_k<T><<<grid, 256, 0, s>>>(a);
     KC_CUDA(cudaGetLastError());
     KC_CUDA(cudaMemsetAsync(S.ready, 0, sizeof(int) * P->N, s));
     KC_CUDA(cudaMemsetAsync(S.cnt, 0, sizeof(unsigned) * P->N, s));
     KC_CUDA(cudaMemsetAsync(S.acc, 0, sizeof(double) * P->N * nrhs, s));
     a.ticket = S.ticket + 1;
-    bwd_solve_k<T><<<grid, 256, 0, s>>>(a);
+    ::kc::note_launch(), bwd_solve_k<T><<<grid, 256, 0, s>>>(a);
     KC_CUDA(cudaGetLastError());
     return KC_OK;
 }
@@ -250,12 +250,12 @@ kc_status solver_check(Solver& S, cudaStream_t s) {
 }
 
 kc_status to_point_major(const double* b, const int32_t* perm, int64_t N, int nrhs, double* out, cudaStream_t s) {
-    to_point_major_k<<<blocks_for(N * nrhs, 256), 256, 0, s>>>(b, perm, N, nrhs, out);
+    ::kc::note_launch(), to_point_major_k<<<blocks_for(N * nrhs, 256), 256, 0, s>>>(b, perm, N, nrhs, out);
     KC_CUDA(cudaGetLastError());
     return KC_OK;
 }
 kc_status from_point_major(const double* xp, const int32_t* perm, int64_t N, int nrhs, double* x, cudaStream_t s) {
-    from_point_major_k<<<blocks_for(N * nrhs, 256), 256, 0, s>>>(xp, perm, N, nrhs, x);
+    ::kc::note_launch(), from_point_major_k<<<blocks_for(N * nrhs, 256), 256, 0, s>>>(xp, perm, N, nrhs, x);
     KC_CUDA(cudaGetLastError());
     return KC_OK;
 }

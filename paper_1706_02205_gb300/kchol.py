@@ -60,6 +60,8 @@ def lib():
         P = C.POINTER
         L.kc_last_error.restype = C.c_char_p
         L.kc_abi_version.restype = i32
+        L.kc_launch_count.restype = i64
+        L.kc_last_factor_kernel_ms.restype = dbl
         sigs = {
             "kc_order_points": [vp, i64, i32, vp, vp, vp, vp],
             "kc_pattern_count": [vp, vp, i64, i32, dbl, i32, vp, P(C.c_int64), vp],
@@ -80,8 +82,18 @@ def lib():
     return _lib
 
 
-EXPORTED = ("kc_last_error", "kc_abi_version", "kc_order_points", "kc_pattern_count", "kc_pattern_fill",
+EXPORTED = ("kc_last_error", "kc_abi_version", "kc_launch_count", "kc_last_factor_kernel_ms", "kc_order_points", "kc_pattern_count", "kc_pattern_fill",
             "kc_schedule", "kc_factor", "kc_solve", "kc_refine", "kc_pca_truncate", "kc_pca_error")
+
+
+def launch_count() -> int:
+    """Kernels launched by libkchol in this process so far."""
+    return int(lib().kc_launch_count())
+
+
+def last_factor_kernel_ms() -> float:
+    """Device time of the last persistent factor kernel (CUDA events)."""
+    return float(lib().kc_last_factor_kernel_ms())
 
 
 def _check(st: int):
