@@ -2,7 +2,8 @@
 """Benchmark of the hot path on synthetic inputs shaped like the paper's runs.
 
 Workload (default): N = 2^20 points on a 1024 x 1024 jittered grid in [0,1]^2
-(+-0.25 cell), Matern-3/2 with l = 0.1, rho = 3, 16 right-hand sides.
+(+-0.25 cell), Matern-1/2 with l = 0.1 (the paper's Table 1 kernel), rho = 3,
+16 right-hand sides; Matern-3/2 is factored on the same pattern as well.
 One step = maximin ordering -> pattern S_rho -> schedule -> ICHOL(0) in the
 FP32 form -> solve L L^T x = b for the 16 right-hand sides, all on the GPU
 with inputs already resident.  The FP64 factor (+ solve) is timed on the same
@@ -188,6 +189,25 @@ def run_ours(args, rank, world):
             s64_ms.append(e[1].elapsed_time(e[2]))
             f64_k.append(kc.last_factor_kernel_ms())
 
+    # the other kernel of the workload on the same pattern (the pattern does not
+    # depend on the kernel): factor only, both precisions
+    other = {}
+    for nu2 in args.other_nu:
+        k2 = kc.Kernel(nu2, args.ell, 1.0, 0.0)
+        res = {}
+        for pname, pr in (("fp32_form", kc.FP32_FORM), ("fp64", kc.FP64)):
+            ks, zps = [], []
+            for it in range(1 + args.steps):
+                flush.zero_()
+                _, _, zz = kc.factor(pat, xo, k2, pr)
+                torch.cuda.synchronize()
+                if it >= 1:
+                    ks.append(kc.last_factor_kernel_ms())
+                    zps.append(zz)
+            res[pname] = {"kernel_ms": statistics.mean(ks), "kernel_nnz_per_s": nnz / (statistics.mean(ks) * 1e-3),
+                          "zero_pivots": zps[-1]}
+        other[f"matern_nu{nu2}"] = res
+
     # end to end through the public calls from pinned host buffers
     xp = torch.from_numpy(x_h).pin_memory()
     bp = torch.from_numpy(b_h).pin_memory()
@@ -255,6 +275,7 @@ def run_ours(args, rank, world):
         "e2e": {"value": world * nnz * max(1, args.steps) / (e2e_tot * 1e-3), "unit": "nnz(L)/s",
                 "ms_per_step": e2e_tot / max(1, args.steps),
                 "h2d_bytes_per_step": int(x_h.nbytes + b_h.nbytes), "d2h_bytes_per_step": int(out.numel() * 8)},
+        "other_kernels_same_pattern": other,
         "gpu_launches": launches,
         "clocks": clocks,
     }
@@ -320,7 +341,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n-side", type=int, default=1024)
-    ap.add_argument("--nu", type=float, default=1.5)
+    ap.add_argument("--nu", type=float, default=0.5)
+    ap.add_argument("--other-nu", type=float, nargs="*", default=[1.5])
     ap.add_argument("--ell", type=float, default=0.1)
     ap.add_argument("--rho", type=float, default=3.0)
     ap.add_argument("--nrhs", type=int, default=16)

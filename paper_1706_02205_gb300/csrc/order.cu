@@ -23,7 +23,10 @@
 // band points, so the dominance search uses a grid of band points with cell
 // size sqrt(vmax).  The updates scan a fixed fine grid of all points.
 // Finally the points are sorted by (v descending, index ascending).
+#include <chrono>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 
 #include "grid.cuh"
@@ -255,6 +258,7 @@ kc_status order_impl(const double* x, int64_t N, int d, int32_t* perm, double* l
     item_sel = nullptr;
     const int sms = sm_count();
     int rounds = 0;
+    const bool stats = getenv("KC_ORDER_STATS") != nullptr;
     for (;;) {
         KC_CUDA(cudaMemsetAsync(ctr, 0, 2 * sizeof(unsigned long long), s));
         ::kc::note_launch(), ord_vmax_k<<<sms * 4, 256, 0, s>>>(v2, stat, N, ctr, ctr + 1);
@@ -279,6 +283,9 @@ kc_status order_impl(const double* x, int64_t N, int d, int32_t* perm, double* l
             KC_TRY(grid_build(gb, xg, d, blist, nb, bsorted, bst, B, s));
             KC_CUDA(cudaMemcpyAsync(bstart, bst, sizeof(int64_t) * (gb.ncells + 1), cudaMemcpyDeviceToDevice, s));
         }
+        const int band_r0 = rounds;
+        const auto band_t0 = std::chrono::steady_clock::now();
+        int64_t band_sel = 0, band_items = 0;
         for (;;) {
             if (++rounds > 1000000) return fail(KC_ECUDA, "ordering: too many rounds");
             KC_CUDA(cudaMemsetAsync(ctr + 3, 0, 2 * sizeof(unsigned long long), s));
@@ -288,7 +295,16 @@ kc_status order_impl(const double* x, int64_t N, int d, int32_t* perm, double* l
             KC_CUDA(cudaMemcpyAsync(hs, ctr + 3, sizeof(hs), cudaMemcpyDeviceToHost, s));
             KC_CUDA(cudaStreamSynchronize(s));
             const int64_t ns = (int64_t)hs[0];
-            if (hs[1] == 0) break;  // band exhausted
+            if (hs[1] == 0) {  // band exhausted
+                if (stats) {
+                    double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - band_t0)
+                                    .count();
+                    fprintf(stderr, "[kc order] vmax=%.3e band=%lld rounds=%d selected=%lld items=%lld ms=%.2f\n", vmax,
+                            (long long)nb, rounds - band_r0 - 1, (long long)band_sel, (long long)band_items, ms);
+                }
+                break;
+            }
+            band_sel += (int64_t)hs[0];
             if (ns == 0) return fail(KC_ECUDA, "ordering: no dominant point in a nonempty band");
             ::kc::note_launch(), ord_mark_k<<<blocks_for(ns, 256), 256, 0, s>>>(sel, ns, stat);
             ::kc::note_launch(), ord_items_k<<<blocks_for(ns, 256), 256, 0, s>>>(g0, sel, ns, xg, d, v2, icnt);
@@ -297,6 +313,7 @@ kc_status order_impl(const double* x, int64_t N, int d, int32_t* perm, double* l
             int64_t nitems = 0;
             KC_CUDA(cudaMemcpyAsync(&nitems, ioff + ns, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
             KC_CUDA(cudaStreamSynchronize(s));
+            band_items += nitems;
             if (nitems > item_cap) {
                 item_cap = nitems * 2;
                 if (item_sel) cudaFreeAsync(item_sel, s);
