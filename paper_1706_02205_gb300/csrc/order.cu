@@ -111,31 +111,150 @@ __global__ void ord_dominance_k(Grid gb, const int32_t* __restrict__ bsorted, co
     const double* xq = xg + (int64_t)q * d;
     const int idq = idg[q];
     const double R = sqrt(vq);
-    int lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
-    for (int t = 0; t < gb.dg; ++t) {
-        int cq = cell_coord(gb, xq[t], t);
-        int sp = span_for(gb, R, t);
-        lo[t] = max(0, cq - sp);
-        hi[t] = min(gb.n[t] - 1, cq + sp);
+    // Scan the band grid ring by ring outward from q's cell, so a dominated
+    // point usually meets a dominator within the first rings; ring r holds no
+    // point closer than (r-1) cells.
+    const int dg = gb.dg;
+    int c[3] = {0, 0, 0};
+    int maxr = 0;
+    for (int t = 0; t < dg; ++t) {
+        c[t] = cell_coord(gb, xq[t], t);
+        maxr = max(maxr, span_for(gb, R, t));
     }
     bool dom = true;
-    for (int cz = lo[2]; cz <= hi[2] && dom; ++cz)
-        for (int cy = lo[1]; cy <= hi[1] && dom; ++cy) {
-            int64_t base = ((int64_t)cz * gb.n[1] + cy) * gb.n[0];
-            int64_t f0 = bstart[base + lo[0]], f1 = bstart[base + hi[0] + 1];
-            for (int64_t f = f0; f < f1; ++f) {
-                const int p = bsorted[f];
-                if (p == q || stat[p] != 0) continue;
-                const double vp = v2[p];
-                if (vp > vq || (vp == vq && idg[p] < idq)) {
-                    if (dist2_exact(xg + (int64_t)p * d, xq, d) < vq) {
-                        dom = false;
-                        break;
+    for (int r = 0; r <= maxr && dom; ++r) {
+        if (r >= 2 && (double)(r - 1) * gb.c > R) break;
+        const int z0 = dg > 2 ? max(0, c[2] - r) : 0, z1 = dg > 2 ? min(gb.n[2] - 1, c[2] + r) : 0;
+        const int y0 = dg > 1 ? max(0, c[1] - r) : 0, y1 = dg > 1 ? min(gb.n[1] - 1, c[1] + r) : 0;
+        for (int cz = z0; cz <= z1 && dom; ++cz)
+            for (int cy = y0; cy <= y1 && dom; ++cy) {
+                const bool edge = r == 0 || (dg > 2 && abs(cz - c[2]) == r) || (dg > 1 && abs(cy - c[1]) == r);
+                const int64_t base = ((int64_t)cz * gb.n[1] + cy) * gb.n[0];
+                // the cells of this ring in the row: all of [c-r, c+r] on an edge row, else the two ends
+                int seg[2][2];
+                int nseg = 0;
+                if (edge) {
+                    seg[0][0] = max(0, c[0] - r);
+                    seg[0][1] = min(gb.n[0] - 1, c[0] + r);
+                    nseg = 1;
+                } else {
+                    if (c[0] - r >= 0) {
+                        seg[nseg][0] = seg[nseg][1] = c[0] - r;
+                        ++nseg;
+                    }
+                    if (c[0] + r <= gb.n[0] - 1) {
+                        seg[nseg][0] = seg[nseg][1] = c[0] + r;
+                        ++nseg;
+                    }
+                }
+                for (int sg = 0; sg < nseg && dom; ++sg) {
+                    const int64_t f0 = bstart[base + seg[sg][0]], f1 = bstart[base + seg[sg][1] + 1];
+                    for (int64_t f = f0; f < f1; ++f) {
+                        const int p = bsorted[f];
+                        if (p == q || stat[p] != 0) continue;
+                        const double vp = v2[p];
+                        if (vp > vq || (vp == vq && idg[p] < idq)) {
+                            if (dist2_exact(xg + (int64_t)p * d, xq, d) < vq) {
+                                dom = false;
+                                break;
+                            }
+                        }
                     }
                 }
             }
-        }
+    }
     if (dom) sel[atomicAdd(nsel, 1ULL)] = q;
+}
+
+// ---- greedy steps for the coarsest points: one launch selects the argmax of
+// the previous launch's per-block candidates and pushes it to every point.
+constexpr int GREEDY_BLOCKS_PER_SM = 4;
+constexpr int64_t GREEDY_STEPS = 512;
+
+__device__ __forceinline__ bool key_above(double va, int ia, double vb, int ib) {
+    return va > vb || (va == vb && ia < ib);
+}
+
+// per-block best (v2 desc, original index asc) over undecided points; cand_g = -1 if none
+__device__ void block_best(double v, int id, int g, double* sv, int* si, int* sg, double* out_v, int* out_i,
+                           int* out_g) {
+    for (int o = 16; o > 0; o >>= 1) {
+        double v2o = __shfl_xor_sync(0xffffffffu, v, o);
+        int i2 = __shfl_xor_sync(0xffffffffu, id, o);
+        int g2 = __shfl_xor_sync(0xffffffffu, g, o);
+        if (g2 >= 0 && (g < 0 || key_above(v2o, i2, v, id))) {
+            v = v2o;
+            id = i2;
+            g = g2;
+        }
+    }
+    const int w = threadIdx.x >> 5;
+    if (lane_id() == 0) {
+        sv[w] = v;
+        si[w] = id;
+        sg[w] = g;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int q = 1; q < (int)(blockDim.x >> 5); ++q)
+            if (sg[q] >= 0 && (g < 0 || key_above(sv[q], si[q], v, id))) {
+                v = sv[q];
+                id = si[q];
+                g = sg[q];
+            }
+        *out_v = v;
+        *out_i = id;
+        *out_g = g;
+    }
+}
+
+__global__ void ord_greedy_k(const double* __restrict__ xg, int d, const int32_t* __restrict__ idg,
+                             double* __restrict__ v2, int* __restrict__ stat, int64_t N,
+                             const double* __restrict__ pv_in, const int* __restrict__ pi_in,
+                             const int* __restrict__ pg_in, int nin, double* __restrict__ pv_out,
+                             int* __restrict__ pi_out, int* __restrict__ pg_out, int apply) {
+    __shared__ double sv[32];
+    __shared__ int si[32], sg[32];
+    __shared__ double s_wv;
+    __shared__ int s_wi, s_wg;
+    // winner of the previous candidates (every block computes the same)
+    {
+        double v = 0;
+        int i = 0, g = -1;
+        if (apply)
+            for (int b = threadIdx.x; b < nin; b += blockDim.x)
+                if (pg_in[b] >= 0 && (g < 0 || key_above(pv_in[b], pi_in[b], v, i))) {
+                    v = pv_in[b];
+                    i = pi_in[b];
+                    g = pg_in[b];
+                }
+        block_best(v, i, g, sv, si, sg, &s_wv, &s_wi, &s_wg);
+    }
+    __syncthreads();
+    const int w = s_wg;
+    if (w >= 0 && blockIdx.x == 0 && threadIdx.x == 0) stat[w] = 1;  // v2[w] keeps its final value l^2
+    double bv = 0;
+    int bi = 0, bg = -1;
+    const double* xw = w >= 0 ? xg + (int64_t)w * d : nullptr;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < N; q += (int64_t)gridDim.x * blockDim.x) {
+        if (q == w || stat[q] != 0) continue;
+        double vq = v2[q];
+        if (w >= 0) {
+            const double dd = dist2_exact(xg + q * d, xw, d);
+            if (dd < vq) {
+                vq = dd;
+                v2[q] = dd;
+            }
+        }
+        const int iq = idg[q];
+        if (bg < 0 || key_above(vq, iq, bv, bi)) {
+            bv = vq;
+            bi = iq;
+            bg = (int)q;
+        }
+    }
+    __syncthreads();  // sv/si/sg are reused
+    block_best(bv, bi, bg, sv, si, sg, &pv_out[blockIdx.x], &pi_out[blockIdx.x], &pg_out[blockIdx.x]);
 }
 
 __global__ void ord_mark_k(const int32_t* __restrict__ sel, int64_t ns, int* __restrict__ stat) {
@@ -257,6 +376,29 @@ kc_status order_impl(const double* x, int64_t N, int d, int32_t* perm, double* l
     int64_t item_cap = 0;
     item_sel = nullptr;
     const int sms = sm_count();
+
+    // Greedy phase: the coarsest points are selected one per launch (each
+    // launch updates every point), because while few points are selected the
+    // update balls cover the whole cloud and the band rounds would be quadratic.
+    {
+        const int nblk = sms * GREEDY_BLOCKS_PER_SM;
+        double* pv[2];
+        int *pi[2], *pg[2];
+        for (int k = 0; k < 2; ++k) {
+            KC_TRY(A.get(&pv[k], nblk));
+            KC_TRY(A.get(&pi[k], nblk));
+            KC_TRY(A.get(&pg[k], nblk));
+        }
+        ::kc::note_launch(), ord_greedy_k<<<nblk, 256, 0, s>>>(xg, d, idg, v2, stat, N, nullptr, nullptr, nullptr, 0,
+                                                              pv[0], pi[0], pg[0], 0);
+        const int64_t steps = N - 1 < GREEDY_STEPS ? N - 1 : GREEDY_STEPS;
+        for (int64_t k = 0; k < steps; ++k) {
+            const int a = (int)(k & 1), b = a ^ 1;
+            ::kc::note_launch(), ord_greedy_k<<<nblk, 256, 0, s>>>(xg, d, idg, v2, stat, N, pv[a], pi[a], pg[a], nblk,
+                                                                  pv[b], pi[b], pg[b], 1);
+        }
+        KC_CUDA(cudaGetLastError());
+    }
     int rounds = 0;
     const bool stats = getenv("KC_ORDER_STATS") != nullptr;
     for (;;) {
@@ -275,7 +417,9 @@ kc_status order_impl(const double* x, int64_t N, int d, int32_t* perm, double* l
         KC_CUDA(cudaMemcpyAsync(&hnb, ctr + 2, sizeof(hnb), cudaMemcpyDeviceToHost, s));
         KC_CUDA(cudaStreamSynchronize(s));
         const int64_t nb = (int64_t)hnb;
-        Grid gb = make_grid(d, lo, hi, nb, vmax > 0 ? sqrt(vmax) : 0.0, 2 * nb + 1);
+        // band cells a quarter of the largest search radius (bounded by the
+        // cell budget), scanned nearest ring first
+        Grid gb = make_grid(d, lo, hi, nb, vmax > 0 ? 0.25 * sqrt(vmax) : 0.0, 2 * nb + 1);
         {
             Arena B(s);
             int64_t* bst;
