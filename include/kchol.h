@@ -94,6 +94,7 @@ typedef struct {
     int32_t warps_per_cta;         /* 0 -> 8 */
     int32_t test_hold_column;      /* test hook: 0 = off; c+1 makes column c never signal
                                       ready, so a wait on it runs out (KC_ETIMEOUT) */
+    int32_t lanes_per_row;         /* factor: lanes merging one row (1,2,4,..,32); 0 -> from |R_i| */
 } kc_opts;
 
 const char* kc_last_error(void);

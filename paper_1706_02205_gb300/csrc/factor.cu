@@ -10,14 +10,19 @@
 //
 // Work units ("tasks") are (column, chunk of up to `rows_per_task` rows of
 // C_i), listed in (level, index) order and handed out by an atomic ticket.  A
-// warp that takes a task waits (bounded spin, acquire loads) until every
-// column k in R_i has published all its tasks, stages row i (indices and
-// values) in shared memory, recomputes the pivot, and then for each row j of
-// its chunk merges the prefix of row j (entries k < i) against the staged
-// row: lanes split into groups of G; each lane walks the prefix with stride G
-// and binary-searches its k in the staged row.  Theta_ji is evaluated from the
-// coordinates in the kernel (entries are never stored).  The task publishes
-// by a release increment of done[i].
+// warp that takes a task waits (bounded spin with backoff, acquire loads)
+// until every column k in R_i has published all its tasks, puts row i
+// (index -> value) into an open-addressing hash table in shared memory,
+// recomputes the pivot, and then merges the prefix of each row j of its chunk
+// (entries k < i) against the table.  Lanes form groups of G; a group owns
+// one row, each lane walks the row with stride G, loading four (col, val)
+// pairs ahead so that enough loads are in flight to cover HBM latency.
+// Theta_ji is evaluated from the coordinates in the kernel (entries are never
+// stored).  The task publishes by a release increment of done[i].
+//
+// FP32 form: values, products and the compensated (Dot2) sums stay in FP32;
+// only the pivot and its square root are FP64 (the FP64 pipe of the GB300 is
+// a small fraction of its FP32 rate).  FP64 form: everything in FP64.
 //
 // Forward progress: a task only waits on columns of lower level, whose tasks
 // have smaller ticket numbers and were claimed by running warps, so the
@@ -49,7 +54,8 @@ struct FactorArgs {
     KernelParams kp;
     long long spin_limit;
     int hold_col;
-    int cap;  // staged entries per warp
+    int hbits;  // hash table of 2^hbits slots per warp
+    int lanes;  // lanes per row, 0 = from |R_i|
 };
 
 __device__ __forceinline__ unsigned n_tasks_of(const int64_t* __restrict__ colptr, int k, int rpt) {
@@ -57,16 +63,20 @@ __device__ __forceinline__ unsigned n_tasks_of(const int64_t* __restrict__ colpt
     return m <= 0 ? 1u : (unsigned)((m + rpt - 1) / rpt);
 }
 
-// position of key k in sorted a[0..n), or -1
-__device__ __forceinline__ int bsearch_smem(const int* a, int n, int k) {
-    int lo = 0, hi = n;
-    while (lo < hi) {
-        int mid = (lo + hi) >> 1;
-        if (a[mid] < k) lo = mid + 1;
-        else hi = mid;
+__device__ __forceinline__ int hslot(int k, int hbits) { return (int)(((unsigned)k * 2654435761u) >> (32 - hbits)); }
+
+// slot of key k in the table, or -1
+__device__ __forceinline__ int hfind(const int* hkey, int hbits, int k) {
+    const int mask = (1 << hbits) - 1;
+    int h = hslot(k, hbits);
+    for (;;) {
+        const int x = hkey[h];
+        if (x == k) return h;
+        if (x < 0) return -1;
+        h = (h + 1) & mask;
     }
-    return (lo < n && a[lo] == k) ? lo : -1;
 }
+
 __device__ __forceinline__ int64_t bsearch_glob(const int32_t* __restrict__ a, int64_t lo, int64_t hi, int k) {
     int64_t end = hi;
     while (lo < hi) {
@@ -77,39 +87,49 @@ __device__ __forceinline__ int64_t bsearch_glob(const int32_t* __restrict__ a, i
     return (lo < end && __ldg(&a[lo]) == k) ? lo : -1;
 }
 
-// Compensated accumulation (Dot2 of Ogita, Rump and Oishi, 2005):
-// TwoProduct by fma, TwoSum of the running sum, errors summed separately.
-struct Dot2 {
-    float s = 0.f, c = 0.f;
-    __device__ __forceinline__ void add(float a, float b) {
-        float p = a * b;
-        float ep = fmaf(a, b, -p);
-        float ns = s + p;
-        float z = ns - s;
-        float es = (s - (ns - z)) + (p - z);
-        s = ns;
-        c += ep + es;
-    }
-    __device__ __forceinline__ double value() const { return (double)s + (double)c; }
-};
-
+// Accumulators.  FP32: compensated dot product Dot2 of Ogita, Rump and Oishi
+// (TwoProduct by fma, TwoSum of the running sum, errors summed apart); FP64:
+// plain fma.
 template <typename T>
 struct Acc;
 template <>
 struct Acc<double> {
     double s = 0.0;
     __device__ __forceinline__ void add(double a, double b) { s = fma(a, b, s); }
-    __device__ __forceinline__ double value() const { return s; }
+    __device__ __forceinline__ void group_reduce(int G) {
+        for (int o = G >> 1; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    }
+    // (theta - sum) / L_ii
+    __device__ __forceinline__ double finish(double th, double Lii, double) const { return (th - s) / Lii; }
 };
 template <>
 struct Acc<float> {
-    Dot2 d;
-    __device__ __forceinline__ void add(float a, float b) { d.add(a, b); }
-    __device__ __forceinline__ double value() const { return d.value(); }
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void add(float a, float b) {
+        const float p = a * b;
+        const float ep = fmaf(a, b, -p);
+        const float ns = s + p;
+        const float z = ns - s;
+        const float es = (s - (ns - z)) + (p - z);
+        s = ns;
+        c += ep + es;
+    }
+    __device__ __forceinline__ void group_reduce(int G) {
+        for (int o = G >> 1; o > 0; o >>= 1) {
+            const float s2 = __shfl_xor_sync(0xffffffffu, s, o);
+            const float c2 = __shfl_xor_sync(0xffffffffu, c, o);
+            const float t = s + s2;
+            const float z = t - s;
+            const float e = (s - (t - z)) + (s2 - z);
+            s = t;
+            c += c2 + e;
+        }
+    }
+    __device__ __forceinline__ float finish(float th, double, float inv) const { return ((th - s) - c) * inv; }
 };
 
 template <typename T>
-__device__ __forceinline__ double theta_off(const FactorArgs<T>& A, const double* xj, const double* xi);
+__device__ __forceinline__ T theta_off(const FactorArgs<T>& A, const double* xj, const double* xi);
 
 template <>
 __device__ __forceinline__ double theta_off<double>(const FactorArgs<double>& A, const double* xj,
@@ -122,13 +142,27 @@ __device__ __forceinline__ double theta_off<double>(const FactorArgs<double>& A,
     return matern_f64(sqrt(s), A.kp.nu_code, A.kp.scale, A.kp.sigma2);
 }
 template <>
-__device__ __forceinline__ double theta_off<float>(const FactorArgs<float>& A, const double* xj, const double* xi) {
+__device__ __forceinline__ float theta_off<float>(const FactorArgs<float>& A, const double* xj, const double* xi) {
     float s = 0.f;
     for (int t = 0; t < A.d; ++t) {
         float u = (float)(xj[t] - xi[t]);
         s = fmaf(u, u, s);
     }
-    return (double)matern_f32(sqrtf(s), A.kp.nu_code, (float)A.kp.scale, (float)A.kp.sigma2);
+    return matern_f32(sqrtf(s), A.kp.nu_code, (float)A.kp.scale, (float)A.kp.sigma2);
+}
+
+// bounded wait until done[k] >= need; false when the budget ran out or the
+// kernel is stopping
+__device__ __forceinline__ bool wait_done(const unsigned* f, unsigned need, const int* status, long long limit) {
+    if (ld_acquire_u32(f) >= need) return true;
+    const long long t0 = clock64();
+    unsigned ns = 32;
+    while (ld_acquire_u32(f) < need) {
+        if (clock64() - t0 > limit || ld_volatile_s32(status) != 0) return false;
+        __nanosleep(ns);
+        if (ns < 512) ns <<= 1;
+    }
+    return true;
 }
 
 template <typename T>
@@ -136,8 +170,9 @@ __global__ void __launch_bounds__(256) ichol_persistent_k(FactorArgs<T> A) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = lane_id();
     const int w = threadIdx.x >> 5;
-    int* s_idx = (int*)(smem + (size_t)w * A.cap * (sizeof(int) + sizeof(T)));
-    T* s_val = (T*)(s_idx + A.cap);
+    const int H = 1 << A.hbits;
+    int* hkey = (int*)(smem + (size_t)w * H * (sizeof(int) + sizeof(T)));
+    T* hval = (T*)(hkey + H);
     const unsigned FULL = 0xffffffffu;
 
     for (;;) {
@@ -155,17 +190,7 @@ __global__ void __launch_bounds__(256) ichol_persistent_k(FactorArgs<T> A) {
         bool ok = true;
         for (int e = lane; e < nr && ok; e += 32) {
             const int k = __ldg(&A.col[a0 + e]);
-            const unsigned need = n_tasks_of(A.colptr, k, A.rpt);
-            const unsigned* f = &A.done[k];
-            if (ld_acquire_u32(f) < need) {
-                long long t0 = clock64();
-                while (ld_acquire_u32(f) < need) {
-                    if (clock64() - t0 > A.spin_limit || ld_volatile_s32(A.status) != 0) {
-                        ok = false;
-                        break;
-                    }
-                }
-            }
+            ok = wait_done(&A.done[k], n_tasks_of(A.colptr, k, A.rpt), A.status, A.spin_limit);
         }
         if (!__all_sync(FULL, ok)) {
             if (lane == 0) atomicCAS(A.status, 0, DEV_TIMEOUT);
@@ -174,22 +199,28 @@ __global__ void __launch_bounds__(256) ichol_persistent_k(FactorArgs<T> A) {
         __threadfence();
         __syncwarp();
 
-        // ---- stage row i, pivot in FP64
-        const bool staged = nr <= A.cap;
+        // ---- row i into the hash table; pivot in FP64
+        const bool staged = 2 * nr <= H;
+        if (staged)
+            for (int s = lane; s < H; s += 32) hkey[s] = -1;
+        __syncwarp();
         double ps = 0.0;
         for (int e = lane; e < nr; e += 32) {
             const T v = ldcg(&A.val[a0 + e]);
             if (staged) {
-                s_idx[e] = __ldg(&A.col[a0 + e]);
-                s_val[e] = v;
+                const int k = __ldg(&A.col[a0 + e]);
+                int h = hslot(k, A.hbits);
+                while (atomicCAS(&hkey[h], -1, k) != -1) h = (h + 1) & (H - 1);
+                hval[h] = v;
             }
-            ps += (double)v * (double)v;
+            ps = fma((double)v, (double)v, ps);
         }
         ps = warp_sum(ps);
         __syncwarp();
         const double p = (A.kp.sigma2 + A.kp.nugget) - ps;
         const bool zero = !(p > 0.0);
         const double Lii = zero ? 0.0 : sqrt(p);
+        const T inv = zero ? (T)0 : (T)(1.0 / Lii);
         if (c == 0 && lane == 0) {
             A.val[a1] = (T)Lii;
             A.diag[i] = Lii;
@@ -197,9 +228,11 @@ __global__ void __launch_bounds__(256) ichol_persistent_k(FactorArgs<T> A) {
         }
         const double* xi = A.x + (int64_t)i * A.d;
 
-        // ---- rows of this chunk
+        // ---- rows of this chunk: groups of G lanes, one row per group
         int G = 1;
-        while (G < 32 && 2 * G <= nr) G <<= 1;
+        if (A.lanes > 0) G = A.lanes;
+        else
+            while (G < 32 && 16 * G <= nr) G <<= 1;
         const int ng = 32 / G, g = lane / G, sub = lane % G;
         const int64_t qs = A.colptr[i] + 1 + (int64_t)c * A.rpt;
         const int64_t qe = min(A.colptr[i + 1], qs + A.rpt);
@@ -212,29 +245,40 @@ __global__ void __launch_bounds__(256) ichol_persistent_k(FactorArgs<T> A) {
             if (act) {
                 j = __ldg(&A.rowidx[q]);
                 bij = __ldg(&A.slot[q]);
-                const int64_t b0 = __ldg(&A.rowptr[j]);
-                if (!zero) {
-                    for (int64_t e = b0 + sub; e < bij; e += G) {
-                        const int k = __ldg(&A.col[e]);
-                        if (staged) {
-                            const int pos = bsearch_smem(s_idx, nr, k);
-                            if (pos >= 0) acc.add(ldcg(&A.val[e]), s_val[pos]);
-                        } else {
-                            const int64_t pos = bsearch_glob(A.col, a0, a1, k);
-                            if (pos >= 0) acc.add(ldcg(&A.val[e]), ldcg(&A.val[pos]));
-                        }
+            }
+            if (act && !zero) {
+                int64_t e = __ldg(&A.rowptr[j]) + sub;
+                if (staged) {
+                    for (; e + 3 * G < bij; e += 4 * G) {
+                        const int k0 = __ldg(&A.col[e]), k1 = __ldg(&A.col[e + G]);
+                        const int k2 = __ldg(&A.col[e + 2 * G]), k3 = __ldg(&A.col[e + 3 * G]);
+                        const T w0 = ldcg(&A.val[e]), w1 = ldcg(&A.val[e + G]);
+                        const T w2 = ldcg(&A.val[e + 2 * G]), w3 = ldcg(&A.val[e + 3 * G]);
+                        const int h0 = hfind(hkey, A.hbits, k0), h1 = hfind(hkey, A.hbits, k1);
+                        const int h2 = hfind(hkey, A.hbits, k2), h3 = hfind(hkey, A.hbits, k3);
+                        if (h0 >= 0) acc.add(w0, hval[h0]);
+                        if (h1 >= 0) acc.add(w1, hval[h1]);
+                        if (h2 >= 0) acc.add(w2, hval[h2]);
+                        if (h3 >= 0) acc.add(w3, hval[h3]);
+                    }
+                    for (; e < bij; e += G) {
+                        const int k0 = __ldg(&A.col[e]);
+                        const T w0 = ldcg(&A.val[e]);
+                        const int h0 = hfind(hkey, A.hbits, k0);
+                        if (h0 >= 0) acc.add(w0, hval[h0]);
+                    }
+                } else {
+                    for (; e < bij; e += G) {
+                        const int64_t pos = bsearch_glob(A.col, a0, a1, __ldg(&A.col[e]));
+                        if (pos >= 0) acc.add(ldcg(&A.val[e]), ldcg(&A.val[pos]));
                     }
                 }
             }
-            double s = acc.value();
-            for (int o = G >> 1; o > 0; o >>= 1) s += __shfl_xor_sync(FULL, s, o);
+            acc.group_reduce(G);
             if (act && sub == 0) {
-                double v = 0.0;
-                if (!zero) {
-                    const double th = theta_off<T>(A, A.x + (int64_t)j * A.d, xi);
-                    v = (th - s) / Lii;
-                }
-                A.val[bij] = (T)v;
+                T v = (T)0;
+                if (!zero) v = acc.finish(theta_off<T>(A, A.x + (int64_t)j * A.d, xi), Lii, inv);
+                A.val[bij] = v;
             }
         }
 
@@ -346,10 +390,17 @@ static kc_status factor_run(const kc_pattern* P, const double* x, int d, const K
     a.kp = kp;
     a.spin_limit = (o && o->spin_limit_cycles > 0) ? o->spin_limit_cycles : 4000000000LL;
     a.hold_col = (o && o->test_hold_column > 0) ? o->test_hold_column - 1 : -1;
-    int cap = 64;
-    while (cap < maxr && cap < 1024) cap *= 2;
-    a.cap = cap;
-    size_t smem = (size_t)warps * cap * (sizeof(int) + sizeof(T));
+    // hash table: at least twice the longest row (load factor <= 1/2), 128..2048 slots
+    int hb = 7;
+    while (hb < 11 && (1 << hb) < 2 * maxr) ++hb;
+    a.hbits = hb;
+    a.lanes = 0;
+    if (o && o->lanes_per_row > 0) {
+        int L = o->lanes_per_row;
+        if (L > 32 || (L & (L - 1))) return fail(KC_EINVAL, "lanes_per_row must be a power of two <= 32");
+        a.lanes = L;
+    }
+    size_t smem = (size_t)warps * (1 << hb) * (sizeof(int) + sizeof(T));
     KC_CUDA(cudaFuncSetAttribute(ichol_persistent_k<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
     KC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ichol_persistent_k<T>, warps * 32, smem));
