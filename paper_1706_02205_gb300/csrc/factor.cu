@@ -232,7 +232,7 @@ __global__ void __launch_bounds__(256) ichol_persistent_k(FactorArgs<T> A) {
         int G = 1;
         if (A.lanes > 0) G = A.lanes;
         else
-            while (G < 32 && 16 * G <= nr) G <<= 1;
+            while (G < 32 && 32 * G <= nr) G <<= 1;  // about 32+ prefix entries per lane-group step
         const int ng = 32 / G, g = lane / G, sub = lane % G;
         const int64_t qs = A.colptr[i] + 1 + (int64_t)c * A.rpt;
         const int64_t qe = min(A.colptr[i + 1], qs + A.rpt);
