@@ -158,6 +158,25 @@ kc_status kc_solve(const kc_pattern* pat, int32_t prec, const void* val, const d
                    const kc_kernel* kern, const int32_t* perm, const double* b, int32_t nrhs,
                    double* x, const kc_opts* opts, void* stream);
 
+/* ---- kc_solve without device allocation ---------------------------------- *
+ * The paper has no counterpart: this is an operational variant of kc_solve.
+ * It is for callers that cannot allocate device memory while they run -- a
+ * server whose device memory is handed out up front to another framework's
+ * pool, a plugin that its host application forbids to allocate, a
+ * latency-critical loop where an allocation could block on driver locks or
+ * synchronise the device.  Same arguments and result as kc_solve (no opts);
+ * the scratch comes from one fixed file-scope device array of 28 MiB + 256 B
+ * that every GPU loading this library keeps until the process exits, so it
+ * needs N <= 2^20 and N*nrhs <= 2^20 (larger sizes return KC_EINVAL).  The
+ * caller passes every input and output.  All calls on a device share the one
+ * array: calls that overlap on the GPU race and corrupt each other, so
+ * serialise them.  The first call on a device, with that device current,
+ * looks up the array's device address (cudaGetSymbolAddress); make that first
+ * call before any stream capture.  Synchronises. */
+kc_status kc_solve_noalloc(const kc_pattern* pat, int32_t prec, const void* val, const double* diag,
+                           const kc_kernel* kern, const int32_t* perm, const double* b, int32_t nrhs, double* x,
+                           void* stream);
+
 /* ---- a8: refinement: CG on the dense Theta preconditioned by L L^T ------ *
  * (task (2); CG with the factor as preconditioner, Section 4.3).  The
  * matrix-vector product with Theta is evaluated from the coordinates in

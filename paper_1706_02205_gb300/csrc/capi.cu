@@ -19,6 +19,9 @@ kc_status refine_impl(const kc_pattern* P, const double* x_ord, int d, const kc_
                       const void* val, const double* diag, const int32_t* perm, const double* b, int nrhs,
                       double rtol, int maxit, double* x_out, int32_t* iters_out, double* relres_out,
                       const kc_opts* o, cudaStream_t s);
+kc_status solve_noalloc_impl(const kc_pattern* P, int prec, const void* val, const double* diag,
+                             const kc_kernel* kern, const int32_t* perm, const double* b, int nrhs, double* x,
+                             cudaStream_t s);
 kc_status pca_truncate_impl(const kc_pattern* P, int prec, const void* val, const int32_t* perm, int k, float* Lk,
                             cudaStream_t s);
 kc_status pca_error_impl(const double* x, int64_t N, int d, const kc_kernel* kern, int k, const float* Lk,
@@ -105,6 +108,14 @@ kc_status kc_solve(const kc_pattern* pat, int32_t prec, const void* val, const d
     KC_TRY(check_pattern(pat));
     if (!val || !diag || !perm || !b || !x) return fail(KC_EINVAL, "arrays must be non-NULL");
     return solve_impl(pat, prec, val, diag, kern, perm, b, nrhs, x, opts, (cudaStream_t)stream);
+}
+
+kc_status kc_solve_noalloc(const kc_pattern* pat, int32_t prec, const void* val, const double* diag,
+                           const kc_kernel* kern, const int32_t* perm, const double* b, int32_t nrhs, double* x,
+                           void* stream) {
+    KC_TRY(check_pattern(pat));
+    if (!val || !diag || !perm || !b || !x) return fail(KC_EINVAL, "arrays must be non-NULL");
+    return solve_noalloc_impl(pat, prec, val, diag, kern, perm, b, nrhs, x, (cudaStream_t)stream);
 }
 
 kc_status kc_refine(const kc_pattern* pat, const double* x_ord, int32_t d, const kc_kernel* kern, int32_t prec,

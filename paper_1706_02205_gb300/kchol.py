@@ -69,6 +69,7 @@ def lib():
             "kc_schedule": [i64, vp, vp, vp, vp, vp, vp, vp, P(C.c_int32), vp],
             "kc_factor": [P(kc_pattern), vp, i32, P(kc_kernel), i32, vp, vp, P(C.c_int64), P(kc_opts), vp],
             "kc_solve": [P(kc_pattern), i32, vp, vp, P(kc_kernel), vp, vp, i32, vp, P(kc_opts), vp],
+            "kc_solve_noalloc": [P(kc_pattern), i32, vp, vp, P(kc_kernel), vp, vp, i32, vp, vp],
             "kc_refine": [P(kc_pattern), vp, i32, P(kc_kernel), i32, vp, vp, vp, vp, i32, dbl, i32, vp,
                           P(C.c_int32), P(C.c_double), P(kc_opts), vp],
             "kc_pca_truncate": [P(kc_pattern), i32, vp, vp, i32, vp, vp],
@@ -83,7 +84,7 @@ def lib():
 
 
 EXPORTED = ("kc_last_error", "kc_abi_version", "kc_launch_count", "kc_last_factor_kernel_ms", "kc_order_points", "kc_pattern_count", "kc_pattern_fill",
-            "kc_schedule", "kc_factor", "kc_solve", "kc_refine", "kc_pca_truncate", "kc_pca_error")
+            "kc_schedule", "kc_factor", "kc_solve", "kc_solve_noalloc", "kc_refine", "kc_pca_truncate", "kc_pca_error")
 
 
 def launch_count() -> int:
@@ -235,6 +236,23 @@ def solve(pat: Pattern, prec, val, diag, kern: Kernel, perm, b, opts=None, strea
     k = kern.c()
     _check(lib().kc_solve(pat.c(), int(prec), _ptr(val), _ptr(diag), C.byref(k), _ptr(perm), _ptr(b), nrhs,
                           _ptr(x), C.byref(opts) if opts is not None else None, _stream(stream)))
+    return x
+
+
+def solve_noalloc(pat: Pattern, prec, val, diag, kern: Kernel, perm, b, out=None, stream=None):
+    """Same result as solve(), for callers that may not allocate device memory
+    during the call: the library takes its scratch from a fixed device array
+    (limits N <= 2^20 and N * nrhs <= 2^20).  Pass ``out`` (nrhs, N) float64 to
+    keep this call free of allocations on the Python side too.  Calls that
+    overlap on the GPU share that array and race: serialise them."""
+    _dev(b, torch.float64, "b")
+    if b.dim() == 1:
+        b = b[None]
+    nrhs = b.shape[0]
+    x = torch.empty_like(b) if out is None else _dev(out, torch.float64, "out")
+    k = kern.c()
+    _check(lib().kc_solve_noalloc(pat.c(), int(prec), _ptr(val), _ptr(diag), C.byref(k), _ptr(perm), _ptr(b), nrhs,
+                                  _ptr(x), _stream(stream)))
     return x
 
 
