@@ -35,6 +35,26 @@ __device__ __forceinline__ int span_for(const Grid& g, double R, int t) {
     return s > g.n[t] ? g.n[t] : s;
 }
 
+// FP32 screen of a distance test.  a, b: coordinates minus a common origin,
+// rounded to float from double; delta bounds the error of one coordinate
+// difference (2^-23 times the largest |x - origin|).  Returns 1 when dist <= R
+// surely holds, 0 when dist > R surely holds, -1 when only the exact FP64 test
+// can tell.  The margin covers the float rounding of the inputs, of the sum of
+// squares and of sqrtf (first order, with a factor of two to spare).
+// Rf may carry up to two float roundings of the exact threshold.
+__device__ __forceinline__ int screen_f32(const float* a, const float* b, int d, float Rf, float delta) {
+    float s = 0.f;
+    for (int t = 0; t < d; ++t) {
+        const float w = a[t] - b[t];
+        s = fmaf(w, w, s);
+    }
+    const float dist = sqrtf(s);
+    const float M = sqrtf((float)d) * delta + (float)(d + 6) * 1.1920929e-7f * fmaxf(dist, Rf);
+    if (dist - M > Rf) return 0;
+    if (dist + M < Rf) return 1;
+    return -1;
+}
+
 // Host: choose a grid for `npts` points in the box [lo, hi] with target cell
 // size `want` (0 = automatic), at most `max_cells` cells.
 Grid make_grid(int d, const double* lo, const double* hi, int64_t npts, double want, int64_t max_cells);

@@ -54,11 +54,14 @@ kc_status check_finite(const double* x, int64_t n, Arena& A, cudaStream_t s) {
 // state in grid order (gpos): coordinates xg, original index idg, v2, stat
 __global__ void ord_init_k(const double* __restrict__ x, int d, const int32_t* __restrict__ gsorted, int64_t N,
                            double* __restrict__ xg, int32_t* __restrict__ idg, double* __restrict__ v2,
-                           int* __restrict__ stat) {
+                           int* __restrict__ stat, Grid g, float* __restrict__ xgf) {
     int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= N) return;
     int64_t id = gsorted[q];
-    for (int t = 0; t < d; ++t) xg[q * d + t] = x[id * d + t];
+    for (int t = 0; t < d; ++t) {
+        xg[q * d + t] = x[id * d + t];
+        if (xgf) xgf[q * d + t] = (float)(x[id * d + t] - g.lo[t]);
+    }
     idg[q] = (int32_t)id;
     if (id == 0) {
         v2[q] = INFINITY;
@@ -100,7 +103,8 @@ __global__ void ord_dominance_k(Grid gb, const int32_t* __restrict__ bsorted, co
                                 int64_t nb, const double* __restrict__ xg, int d, const int32_t* __restrict__ idg,
                                 const double* __restrict__ v2, const int* __restrict__ stat, double T,
                                 int32_t* __restrict__ sel, unsigned long long* __restrict__ nsel,
-                                unsigned long long* __restrict__ nactive) {
+                                unsigned long long* __restrict__ nactive, const float* __restrict__ xgf,
+                                float delta) {
     int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= nb) return;
     const int q = bsorted[e];
@@ -109,6 +113,7 @@ __global__ void ord_dominance_k(Grid gb, const int32_t* __restrict__ bsorted, co
     if (!(vq >= T)) return;
     atomicAdd(nactive, 1ULL);
     const double* xq = xg + (int64_t)q * d;
+    const float rq = sqrtf((float)vq);
     const int idq = idg[q];
     const double R = sqrt(vq);
     // Scan the band grid ring by ring outward from q's cell, so a dominated
@@ -154,6 +159,8 @@ __global__ void ord_dominance_k(Grid gb, const int32_t* __restrict__ bsorted, co
                         if (p == q || stat[p] != 0) continue;
                         const double vp = v2[p];
                         if (vp > vq || (vp == vq && idg[p] < idq)) {
+                            if (xgf && screen_f32(xgf + (int64_t)p * d, xgf + (int64_t)q * d, d, rq, delta) == 0)
+                                continue;  // surely farther than sqrt(vq)
                             if (dist2_exact(xg + (int64_t)p * d, xq, d) < vq) {
                                 dom = false;
                                 break;
@@ -212,7 +219,8 @@ __global__ void ord_greedy_k(const double* __restrict__ xg, int d, const int32_t
                              double* __restrict__ v2, int* __restrict__ stat, int64_t N,
                              const double* __restrict__ pv_in, const int* __restrict__ pi_in,
                              const int* __restrict__ pg_in, int nin, double* __restrict__ pv_out,
-                             int* __restrict__ pi_out, int* __restrict__ pg_out, int apply) {
+                             int* __restrict__ pi_out, int* __restrict__ pg_out, int apply,
+                             const float* __restrict__ xgf, float delta) {
     __shared__ double sv[32];
     __shared__ int si[32], sg[32];
     __shared__ double s_wv;
@@ -239,7 +247,8 @@ __global__ void ord_greedy_k(const double* __restrict__ xg, int d, const int32_t
     for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < N; q += (int64_t)gridDim.x * blockDim.x) {
         if (q == w || stat[q] != 0) continue;
         double vq = v2[q];
-        if (w >= 0) {
+        if (w >= 0 &&
+            !(xgf && screen_f32(xgf + q * d, xgf + (int64_t)w * d, d, sqrtf((float)vq), delta) == 0)) {
             const double dd = dist2_exact(xg + q * d, xw, d);
             if (dd < vq) {
                 vq = dd;
@@ -294,7 +303,8 @@ __global__ void ord_item_fill_k(const int64_t* __restrict__ off, int64_t ns, int
 __global__ void ord_update_k(Grid g, const int32_t* __restrict__ sel, const int64_t* __restrict__ off,
                              const int32_t* __restrict__ item_sel, int64_t nitems, const int64_t* __restrict__ cstart,
                              const double* __restrict__ xg, int d, const int32_t* __restrict__ idg,
-                             double* __restrict__ v2, const int* __restrict__ stat) {
+                             double* __restrict__ v2, const int* __restrict__ stat, const float* __restrict__ xgf,
+                             float delta) {
     int64_t it = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (it >= nitems) return;
     const int lane = lane_id();
@@ -316,6 +326,7 @@ __global__ void ord_update_k(Grid g, const int32_t* __restrict__ sel, const int6
         if (stat[q] != 0) continue;
         const double vq = v2[q];
         if (!(vq < vp || (vq == vp && idg[q] > idp))) continue;
+        if (xgf && screen_f32(xgf + q * d, xgf + (int64_t)p * d, d, sqrtf((float)vq), delta) == 0) continue;
         const double dd = dist2_exact(xg + q * d, xp, d);
         if (dd < vq) atomicMin(vb + q, (unsigned long long)__double_as_longlong(dd));
     }
@@ -371,7 +382,17 @@ kc_status order_impl(const double* x, int64_t N, int d, int32_t* perm, double* l
     KC_TRY(A.get(&ioff, N + 1));
     KC_TRY(A.get(&bstart, 2 * N + 2));
     KC_TRY(A.get(&ctr, 8));
-    ::kc::note_launch(), ord_init_k<<<blocks_for(N, 256), 256, 0, s>>>(x, d, gsorted, N, xg, idg, v2, stat);
+    // float copy of the coordinates (minus the box corner) for FP32 screens of
+    // the distance tests; exact FP64 tests decide every close call
+    float* xgf = nullptr;
+    float delta = 0.f;
+    if (d <= 3) {
+        double E = 0.0;
+        for (int t = 0; t < d; ++t) E = fmax(E, hi[t] - lo[t]);
+        delta = (float)(E * 1.1920928955078125e-07);  // 2^-23 E
+        KC_TRY(A.get(&xgf, N * d));
+    }
+    ::kc::note_launch(), ord_init_k<<<blocks_for(N, 256), 256, 0, s>>>(x, d, gsorted, N, xg, idg, v2, stat, g0, xgf);
     KC_CUDA(cudaGetLastError());
     int64_t item_cap = 0;
     item_sel = nullptr;
@@ -390,12 +411,12 @@ kc_status order_impl(const double* x, int64_t N, int d, int32_t* perm, double* l
             KC_TRY(A.get(&pg[k], nblk));
         }
         ::kc::note_launch(), ord_greedy_k<<<nblk, 256, 0, s>>>(xg, d, idg, v2, stat, N, nullptr, nullptr, nullptr, 0,
-                                                              pv[0], pi[0], pg[0], 0);
+                                                              pv[0], pi[0], pg[0], 0, xgf, delta);
         const int64_t steps = N - 1 < GREEDY_STEPS ? N - 1 : GREEDY_STEPS;
         for (int64_t k = 0; k < steps; ++k) {
             const int a = (int)(k & 1), b = a ^ 1;
             ::kc::note_launch(), ord_greedy_k<<<nblk, 256, 0, s>>>(xg, d, idg, v2, stat, N, pv[a], pi[a], pg[a], nblk,
-                                                                  pv[b], pi[b], pg[b], 1);
+                                                                  pv[b], pi[b], pg[b], 1, xgf, delta);
         }
         KC_CUDA(cudaGetLastError());
     }
@@ -434,7 +455,7 @@ kc_status order_impl(const double* x, int64_t N, int d, int32_t* perm, double* l
             if (++rounds > 1000000) return fail(KC_ECUDA, "ordering: too many rounds");
             KC_CUDA(cudaMemsetAsync(ctr + 3, 0, 2 * sizeof(unsigned long long), s));
             ::kc::note_launch(), ord_dominance_k<<<blocks_for(nb, 128), 128, 0, s>>>(gb, bsorted, bstart, nb, xg, d, idg, v2, stat, T, sel,
-                                                                ctr + 3, ctr + 4);
+                                                                ctr + 3, ctr + 4, xgf, delta);
             unsigned long long hs[2];
             KC_CUDA(cudaMemcpyAsync(hs, ctr + 3, sizeof(hs), cudaMemcpyDeviceToHost, s));
             KC_CUDA(cudaStreamSynchronize(s));
@@ -465,7 +486,7 @@ kc_status order_impl(const double* x, int64_t N, int d, int32_t* perm, double* l
             }
             ::kc::note_launch(), ord_item_fill_k<<<blocks_for(ns * 32, 256), 256, 0, s>>>(ioff, ns, item_sel);
             ::kc::note_launch(), ord_update_k<<<blocks_for(nitems * 32, 256), 256, 0, s>>>(g0, sel, ioff, item_sel, nitems, cstart, xg, d,
-                                                                     idg, v2, stat);
+                                                                     idg, v2, stat, xgf, delta);
             KC_CUDA(cudaGetLastError());
         }
     }

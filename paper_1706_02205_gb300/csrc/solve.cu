@@ -75,11 +75,23 @@ __global__ void __launch_bounds__(256) fwd_solve_k(SolveArgs<T> A) {
         __threadfence();
         __syncwarp();
         double s = 0.0;
-        if (r < A.nrhs)
-            for (int64_t e = a + eo; e < b; e += per) {
-                const int k = __ldg(&A.col[e]);
-                s = fma((double)__ldg(&A.val[e]), __ldcg(&A.y[(int64_t)k * A.nrhs + r]), s);
+        if (r < A.nrhs) {
+            // four independent (col, val, y) loads in flight per lane
+            double s1 = 0.0, s2 = 0.0, s3 = 0.0;
+            int64_t e = a + eo;
+            for (; e + 3 * per < b; e += 4 * per) {
+                const int k0 = __ldg(&A.col[e]), k1 = __ldg(&A.col[e + per]);
+                const int k2 = __ldg(&A.col[e + 2 * per]), k3 = __ldg(&A.col[e + 3 * per]);
+                const double v0 = (double)__ldg(&A.val[e]), v1 = (double)__ldg(&A.val[e + per]);
+                const double v2 = (double)__ldg(&A.val[e + 2 * per]), v3 = (double)__ldg(&A.val[e + 3 * per]);
+                s = fma(v0, __ldcg(&A.y[(int64_t)k0 * A.nrhs + r]), s);
+                s1 = fma(v1, __ldcg(&A.y[(int64_t)k1 * A.nrhs + r]), s1);
+                s2 = fma(v2, __ldcg(&A.y[(int64_t)k2 * A.nrhs + r]), s2);
+                s3 = fma(v3, __ldcg(&A.y[(int64_t)k3 * A.nrhs + r]), s3);
             }
+            for (; e < b; e += per) s = fma((double)__ldg(&A.val[e]), __ldcg(&A.y[(int64_t)__ldg(&A.col[e]) * A.nrhs + r]), s);
+            s = (s + s1) + (s2 + s3);
+        }
         for (int o = 16; o >= A.NR; o >>= 1) s += __shfl_xor_sync(FULL, s, o);
         if (eo == 0 && r < A.nrhs) {
             double dj = A.diag[j];
@@ -121,11 +133,25 @@ __global__ void __launch_bounds__(256) bwd_solve_k(SolveArgs<T> A) {
         __threadfence();
         __syncwarp();
         double s = 0.0;
-        if (r < A.nrhs)
-            for (int64_t q = qs + eo; q < qe; q += per) {
+        if (r < A.nrhs) {
+            double s1 = 0.0, s2 = 0.0, s3 = 0.0;
+            int64_t q = qs + eo;
+            for (; q + 3 * per < qe; q += 4 * per) {
+                const int j0 = __ldg(&A.rowidx[q]), j1 = __ldg(&A.rowidx[q + per]);
+                const int j2 = __ldg(&A.rowidx[q + 2 * per]), j3 = __ldg(&A.rowidx[q + 3 * per]);
+                const int64_t p0 = __ldg(&A.slot[q]), p1 = __ldg(&A.slot[q + per]);
+                const int64_t p2 = __ldg(&A.slot[q + 2 * per]), p3 = __ldg(&A.slot[q + 3 * per]);
+                s = fma((double)__ldg(&A.val[p0]), __ldcg(&A.x[(int64_t)j0 * A.nrhs + r]), s);
+                s1 = fma((double)__ldg(&A.val[p1]), __ldcg(&A.x[(int64_t)j1 * A.nrhs + r]), s1);
+                s2 = fma((double)__ldg(&A.val[p2]), __ldcg(&A.x[(int64_t)j2 * A.nrhs + r]), s2);
+                s3 = fma((double)__ldg(&A.val[p3]), __ldcg(&A.x[(int64_t)j3 * A.nrhs + r]), s3);
+            }
+            for (; q < qe; q += per) {
                 const int j = __ldg(&A.rowidx[q]);
                 s = fma((double)__ldg(&A.val[__ldg(&A.slot[q])]), __ldcg(&A.x[(int64_t)j * A.nrhs + r]), s);
             }
+            s = (s + s1) + (s2 + s3);
+        }
         for (int o = 16; o >= A.NR; o >>= 1) s += __shfl_xor_sync(FULL, s, o);
         bool finish = true;
         if (nch > 1) {
