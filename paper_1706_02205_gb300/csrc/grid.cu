@@ -22,6 +22,7 @@ Grid make_grid(int d, const double* lo, const double* hi, int64_t npts, double w
     for (int t = 0; t < g.dg; ++t) emax = fmax(emax, ext[t]);
     if (!(emax > 0)) {
         g.c = 1.0;
+        g.inv_c = 1.0;
         return g;
     }
     if (max_cells < 1) max_cells = 1;
@@ -52,6 +53,7 @@ Grid make_grid(int d, const double* lo, const double* hi, int64_t npts, double w
         c *= 1.25;
     }
     g.c = c;
+    g.inv_c = 1.0 / c;
     return g;
 }
 

@@ -12,12 +12,13 @@ struct Grid {
     int dg = 1;           // gridded axes
     double lo[3] = {0, 0, 0};
     double c = 1.0;       // cell size
+    double inv_c = 1.0;   // 1 / c (multiplications only on the device)
     int n[3] = {1, 1, 1}; // cells per axis
     int64_t ncells = 1;
 };
 
 __device__ __forceinline__ int cell_coord(const Grid& g, double v, int t) {
-    double f = (v - g.lo[t]) / g.c;
+    double f = (v - g.lo[t]) * g.inv_c;
     int q = (f <= 0.0) ? 0 : (f >= (double)(g.n[t] - 1) ? g.n[t] - 1 : (int)f);
     return q;
 }
@@ -29,10 +30,31 @@ __device__ __forceinline__ int64_t cell_of(const Grid& g, const double* x) {
 // number of cells to either side covering radius R (R may be +inf)
 __device__ __forceinline__ int span_for(const Grid& g, double R, int t) {
     if (!(R < 1e300)) return g.n[t];
-    double f = R / g.c;
+    // a hair of slack so that rounding in R*inv_c or in the cell coordinates
+    // can never drop a cell layer
+    double f = R * g.inv_c * (1.0 + 1e-12) + 1e-9;
     if (f > 4.0e9) return g.n[t];
     int s = (int)f + 1;
     return s > g.n[t] ? g.n[t] : s;
+}
+
+// Search box of a query point x with radius R, packed as (cell x, cell y,
+// cell z, span); computed once per query and expanded by box_range.
+__device__ __forceinline__ int4 query_box(const Grid& g, const double* x, double R) {
+    int c[3] = {0, 0, 0};
+    int sp = 0;
+    for (int t = 0; t < g.dg; ++t) {
+        c[t] = cell_coord(g, x[t], t);
+        sp = max(sp, span_for(g, R, t));
+    }
+    return make_int4(c[0], c[1], c[2], sp);
+}
+__device__ __forceinline__ void box_range(const Grid& g, int4 b, int* lo, int* hi) {
+    const int c[3] = {b.x, b.y, b.z};
+    for (int t = 0; t < 3; ++t) {
+        lo[t] = t < g.dg ? max(0, c[t] - b.w) : 0;
+        hi[t] = t < g.dg ? min(g.n[t] - 1, c[t] + b.w) : 0;
+    }
 }
 
 // FP32 screen of a distance test.  a, b: coordinates minus a common origin,

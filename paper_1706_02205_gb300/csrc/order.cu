@@ -271,26 +271,17 @@ __global__ void ord_mark_k(const int32_t* __restrict__ sel, int64_t ns, int* __r
     if (k < ns) stat[sel[k]] = 1;
 }
 
-// cell-rows of the fine grid covered by the update ball of each selected point
-__device__ __forceinline__ void upd_box(const Grid& g, const double* xp, double R, int* lo, int* hi) {
-    for (int t = 0; t < 3; ++t) {
-        lo[t] = 0;
-        hi[t] = 0;
-    }
-    for (int t = 0; t < g.dg; ++t) {
-        int c = cell_coord(g, xp[t], t);
-        int sp = span_for(g, R, t);
-        lo[t] = max(0, c - sp);
-        hi[t] = min(g.n[t] - 1, c + sp);
-    }
-}
+// cell-rows of the fine grid covered by the update ball of each selected
+// point: the box is computed once per point (query_box) and kept in sbox
 __global__ void ord_items_k(Grid g, const int32_t* __restrict__ sel, int64_t ns, const double* __restrict__ xg,
-                            int d, const double* __restrict__ v2, int64_t* __restrict__ cnt) {
+                            int d, const double* __restrict__ v2, int64_t* __restrict__ cnt, int4* __restrict__ sbox) {
     int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= ns) return;
     const int p = sel[k];
+    const int4 b = query_box(g, xg + (int64_t)p * d, sqrt(v2[p]));
+    sbox[k] = b;
     int lo[3], hi[3];
-    upd_box(g, xg + (int64_t)p * d, sqrt(v2[p]), lo, hi);
+    box_range(g, b, lo, hi);
     cnt[k] = (int64_t)(hi[1] - lo[1] + 1) * (hi[2] - lo[2] + 1);
 }
 __global__ void ord_item_fill_k(const int64_t* __restrict__ off, int64_t ns, int32_t* __restrict__ item_sel) {
@@ -304,7 +295,7 @@ __global__ void ord_update_k(Grid g, const int32_t* __restrict__ sel, const int6
                              const int32_t* __restrict__ item_sel, int64_t nitems, const int64_t* __restrict__ cstart,
                              const double* __restrict__ xg, int d, const int32_t* __restrict__ idg,
                              double* __restrict__ v2, const int* __restrict__ stat, const float* __restrict__ xgf,
-                             float delta) {
+                             float delta, const int4* __restrict__ sbox) {
     int64_t it = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (it >= nitems) return;
     const int lane = lane_id();
@@ -314,7 +305,7 @@ __global__ void ord_update_k(Grid g, const int32_t* __restrict__ sel, const int6
     const double vp = v2[p];  // final value of the selected point
     const int idp = idg[p];
     int lo[3], hi[3];
-    upd_box(g, xp, sqrt(vp), lo, hi);
+    box_range(g, sbox[k], lo, hi);
     int64_t r = it - off[k];
     const int ny = hi[1] - lo[1] + 1;
     const int cy = lo[1] + (int)(r % ny);
@@ -379,6 +370,8 @@ kc_status order_impl(const double* x, int64_t N, int d, int32_t* perm, double* l
     KC_TRY(A.get(&bsorted, N));
     KC_TRY(A.get(&sel, N));
     KC_TRY(A.get(&icnt, N));
+    int4* sbox;
+    KC_TRY(A.get(&sbox, N));
     KC_TRY(A.get(&ioff, N + 1));
     KC_TRY(A.get(&bstart, 2 * N + 2));
     KC_TRY(A.get(&ctr, 8));
@@ -472,7 +465,7 @@ kc_status order_impl(const double* x, int64_t N, int d, int32_t* perm, double* l
             band_sel += (int64_t)hs[0];
             if (ns == 0) return fail(KC_ECUDA, "ordering: no dominant point in a nonempty band");
             ::kc::note_launch(), ord_mark_k<<<blocks_for(ns, 256), 256, 0, s>>>(sel, ns, stat);
-            ::kc::note_launch(), ord_items_k<<<blocks_for(ns, 256), 256, 0, s>>>(g0, sel, ns, xg, d, v2, icnt);
+            ::kc::note_launch(), ord_items_k<<<blocks_for(ns, 256), 256, 0, s>>>(g0, sel, ns, xg, d, v2, icnt, sbox);
             Arena R(s);  // per-round scratch of the scan
             KC_TRY(exclusive_scan_i64(icnt, ioff, ns, R, s));
             int64_t nitems = 0;
@@ -486,7 +479,7 @@ kc_status order_impl(const double* x, int64_t N, int d, int32_t* perm, double* l
             }
             ::kc::note_launch(), ord_item_fill_k<<<blocks_for(ns * 32, 256), 256, 0, s>>>(ioff, ns, item_sel);
             ::kc::note_launch(), ord_update_k<<<blocks_for(nitems * 32, 256), 256, 0, s>>>(g0, sel, ioff, item_sel, nitems, cstart, xg, d,
-                                                                     idg, v2, stat, xgf, delta);
+                                                                     idg, v2, stat, xgf, delta, sbox);
             KC_CUDA(cudaGetLastError());
         }
     }

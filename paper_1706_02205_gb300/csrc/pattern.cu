@@ -36,20 +36,8 @@ struct PatArgs {
     int64_t nitems;
     const float* xsf;      // float copy of xs minus the grid origin (d <= 3), else NULL
     float delta;           // error bound of one float coordinate difference
+    const int4* colbox;    // search box of every column (query_box)
 };
-
-__device__ __forceinline__ void col_box(const Grid& g, const double* xi, double R, int* lo, int* hi) {
-    for (int t = 0; t < 3; ++t) {
-        lo[t] = 0;
-        hi[t] = 0;
-    }
-    for (int t = 0; t < g.dg; ++t) {
-        int c = cell_coord(g, xi[t], t);
-        int sp = span_for(g, R, t);
-        lo[t] = max(0, c - sp);
-        hi[t] = min(g.n[t] - 1, c + sp);
-    }
-}
 
 __device__ __forceinline__ double col_radius(double rho, double li) {
     return isinf(li) ? INFINITY : __dmul_rn(rho, li);
@@ -65,11 +53,13 @@ __device__ __forceinline__ bool in_s(double d2, double R) {
 }
 
 __global__ void pat_items_k(Grid g, const double* __restrict__ xo, const double* __restrict__ l, int64_t N, int d,
-                            double rho, int64_t* __restrict__ cnt) {
+                            double rho, int64_t* __restrict__ cnt, int4* __restrict__ colbox) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
+    const int4 b = query_box(g, xo + i * d, col_radius(rho, l[i]));
+    colbox[i] = b;
     int lo[3], hi[3];
-    col_box(g, xo + i * d, col_radius(rho, l[i]), lo, hi);
+    box_range(g, b, lo, hi);
     cnt[i] = (int64_t)(hi[1] - lo[1] + 1) * (hi[2] - lo[2] + 1);
 }
 __global__ void pat_item_fill_k(const int64_t* __restrict__ off, int64_t N, int32_t* __restrict__ item_col) {
@@ -89,7 +79,7 @@ __global__ void pat_scan_k(PatArgs P, int* __restrict__ cnt, const int64_t* __re
     const double li = P.l[i];
     const double R = col_radius(P.rho, li);
     int lo[3], hi[3];
-    col_box(P.g, xi, R, lo, hi);
+    box_range(P.g, P.colbox[i], lo, hi);
     const int64_t r = it - P.off[i];
     const int ny = hi[1] - lo[1] + 1;
     const int cy = lo[1] + (int)(r % ny);
@@ -142,6 +132,7 @@ struct PatSetup {
     int64_t* off;
     int32_t* item_col;
     int64_t nitems;
+    int4* colbox = nullptr;
     float* xsf = nullptr;
     float delta = 0.f;
 };
@@ -166,7 +157,8 @@ static kc_status pat_setup(const double* xo, const double* l, int64_t N, int d, 
     int64_t* cnt;
     KC_TRY(A.get(&cnt, N));
     KC_TRY(A.get(&S.off, N + 1));
-    ::kc::note_launch(), pat_items_k<<<blocks_for(N, 256), 256, 0, s>>>(S.g, xo, l, N, d, rho, cnt);
+    KC_TRY(A.get(&S.colbox, N));
+    ::kc::note_launch(), pat_items_k<<<blocks_for(N, 256), 256, 0, s>>>(S.g, xo, l, N, d, rho, cnt, S.colbox);
     KC_CUDA(cudaGetLastError());
     KC_TRY(exclusive_scan_i64(cnt, S.off, N, A, s));
     KC_CUDA(cudaMemcpyAsync(&S.nitems, S.off + N, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
@@ -193,6 +185,7 @@ static PatArgs pat_args(const PatSetup& S, const double* xo, const double* l, in
     P.nitems = S.nitems;
     P.xsf = S.xsf;
     P.delta = S.delta;
+    P.colbox = S.colbox;
     return P;
 }
 

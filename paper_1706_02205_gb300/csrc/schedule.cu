@@ -67,11 +67,14 @@ __global__ void levels_k(const int64_t* __restrict__ rowptr, const int32_t* __re
             int v = ld_acquire_s32(&level[k]);
             if (v == 0) {
                 long long t0 = clock64();
+                unsigned ns = 32;
                 while ((v = ld_acquire_s32(&level[k])) == 0) {
                     if (clock64() - t0 > spin_limit || ld_volatile_s32(status) != 0) {
                         ok = false;
                         break;
                     }
+                    __nanosleep(ns);
+                    if (ns < 512) ns <<= 1;
                 }
             }
             m = max(m, v);

@@ -46,8 +46,11 @@ struct SolveArgs {
 __device__ __forceinline__ bool wait_flag(const int* f, const int* status, long long limit) {
     if (ld_acquire_s32(f) != 0) return true;
     long long t0 = clock64();
+    unsigned ns = 32;
     while (ld_acquire_s32(f) == 0) {
         if (clock64() - t0 > limit || ld_volatile_s32(status) != 0) return false;
+        __nanosleep(ns);  // back off so waiting warps do not flood L2 with polls
+        if (ns < 512) ns <<= 1;
     }
     return true;
 }
