@@ -284,6 +284,136 @@ def run_ours(args, rank, world):
     return line
 
 
+# ------------------------------------------------ other workloads (ours)
+
+def run_factor_only(args):
+    """Factor-only probe (the launch profiled by ncu): order + pattern once,
+    then the FP32-form factor `--steps` times on the same pattern."""
+    import torch
+
+    from paper_1706_02205_gb300 import kchol as kc
+    x = torch.from_numpy(inputs.jittered_grid(args.n_side, seed=inputs.seed_for(2))).cuda()
+    kern = kc.Kernel(args.nu, args.ell)
+    perm, l, xo = kc.order_points(x)
+    pat = kc.build_pattern(xo, l, args.rho)
+    prec = kc.FP64 if args.prec == "fp64" else kc.FP32_FORM
+    ms = []
+    for _ in range(args.steps):
+        kc.factor(pat, xo, kern, prec)
+        torch.cuda.synchronize()
+        ms.append(kc.last_factor_kernel_ms())
+    return {"workload": "factor-only", "n_side": args.n_side, "N": pat.N, "nnz": pat.nnz, "prec": args.prec,
+            "kernel_ms": ms, "algorithmic_bytes": bytes_op(pat.rowptr.cpu().numpy(), pat.N, 2,
+                                                            8 if args.prec == "fp64" else 4)}
+
+
+def run_cube3d(args):
+    """N = 2^18 points uniform in [0,1]^3, Matern-5/2, l = 0.3, nugget 1e-6,
+    rho = 4, FP32 form; rank-k PCA for k in {64, 512} with the operator-norm
+    error from 50 power iterations."""
+    import torch
+
+    from paper_1706_02205_gb300 import kchol as kc
+    N = args.n3
+    x_h = inputs.uniform(N, 3, seed=inputs.seed_for(3))
+    x = torch.from_numpy(x_h).cuda()
+    kern = kc.Kernel(2.5, 0.3, 1.0, 1e-6)
+    stream = torch.cuda.current_stream()
+    ph = {k: [] for k in ("order", "pattern", "schedule", "factor", "pca64", "pca512")}
+    for it in range(args.warmup + args.steps):
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(7)]
+        ev[0].record(stream)
+        perm, l, xo = kc.order_points(x)
+        ev[1].record(stream)
+        rowptr, nnz = kc.pattern_count(xo, l, 4.0)
+        col = kc.pattern_fill(xo, l, 4.0, rowptr, nnz)
+        ev[2].record(stream)
+        pat = kc.schedule(rowptr, col)
+        ev[3].record(stream)
+        val, diag, zp = kc.factor(pat, xo, kern, kc.FP32_FORM)
+        ev[4].record(stream)
+        L64 = kc.pca_truncate(pat, kc.FP32_FORM, val, perm, 64)
+        ev[5].record(stream)
+        L512 = kc.pca_truncate(pat, kc.FP32_FORM, val, perm, 512)
+        ev[6].record(stream)
+        torch.cuda.synchronize()
+        if it >= args.warmup:
+            for k, n in enumerate(ph):
+                ph[n].append(ev[k].elapsed_time(ev[k + 1]))
+    v0 = torch.from_numpy(inputs.unit_vector(N, seed=inputs.seed_for(3, 9))).cuda()
+    t0 = time.perf_counter()
+    e64 = kc.pca_error(x, kern, L64, v0, iters=50)
+    t1 = time.perf_counter()
+    e512 = kc.pca_error(x, kern, L512, v0, iters=50)
+    t2 = time.perf_counter()
+    e0 = kc.pca_error(x, kern, L64[:0], v0, iters=50)  # ||Theta||_2 for scale
+    fk = statistics.mean(ph["factor"])
+    return {"workload": f"uniform [0,1]^3, N={N}, Matern-5/2 l=0.3 nugget 1e-6, rho=4, FP32 form",
+            "N": N, "nnz": nnz, "nnz_per_row": nnz / N, "depth": pat.depth, "zero_pivots": zp,
+            "phases_ms": {k: statistics.mean(v) for k, v in ph.items()},
+            "factor_nnz_per_s": nnz / (fk * 1e-3), "factor_kernel_ms": kc.last_factor_kernel_ms(),
+            "pca": {"theta_norm2_est": e0, "err_k64": e64, "err_k512": e512,
+                    "rel_err_k64": e64 / e0, "rel_err_k512": e512 / e0,
+                    "power_iter_s": {"k64": t1 - t0, "k512": t2 - t1}, "iters": 50}}
+
+
+def run_batch(args):
+    """256 independent sets, N_s log-uniform in [2000, 50000], 192 in 2-D and
+    64 in 3-D, Matern-3/2 with l_s ~ U[0.05, 0.3], rho = 3, FP32 form: one
+    persistent launch over all sets, tuned, recorded in a CUDA graph and
+    replayed; plus one solve of every set at once."""
+    import torch
+
+    from paper_1706_02205_gb300 import batch as kb
+    from paper_1706_02205_gb300 import kchol as kc
+    sets = inputs.batch_sets(n_sets=args.n_sets)
+    xs = [torch.from_numpy(s["x"]).cuda() for s in sets]
+    kerns = [kc.Kernel(1.5, s["ell"]) for s in sets]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    B = kb.BatchFactor(xs, kerns, 3.0, kc.FP32_FORM, n_streams=8)
+    torch.cuda.synchronize()
+    t_prep = time.perf_counter() - t0
+    tuned = B.tune()
+    B.capture()
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        B.replay()
+    ms = []
+    for _ in range(args.steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        B.replay()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    zp = B.plan.finish()
+    Ntot = sum(B.Ns)
+    b = torch.from_numpy(inputs.rhs(Ntot, 1, seed=inputs.seed_for(4, 2))).cuda()
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    B.solve(b)
+    torch.cuda.synchronize()
+    t_solve = time.perf_counter() - t1
+    # parity of a few sets against the same sets factored alone
+    worst = 0.0
+    for s in (0, len(sets) // 2, len(sets) - 1):
+        r = kc.pipeline(xs[s], 3.0, kerns[s], kc.FP32_FORM,
+                        opts=kc.make_opts(lanes_per_row=tuned["lanes_per_row"], unroll=tuned["unroll"]))
+        worst = max(worst, float((B.set_values(s) - r["val"]).abs().max()))
+    m = statistics.mean(ms)
+    return {"workload": f"{len(sets)} sets, N_s log-U[2000,50000] (sum N={Ntot}), 2-D/3-D, Matern-3/2 "
+                        f"l_s~U[0.05,0.3], rho=3, FP32 form, one graph-replayed launch",
+            "sets": len(sets), "N_total": Ntot, "nnz": B.pat.nnz, "depth": B.pat.depth, "zero_pivots": zp,
+            "graph_launch_ms": m, "aggregate_nnz_per_s": B.pat.nnz / (m * 1e-3), "tuned": tuned,
+            "prepare_s": t_prep, "solve_all_ms": t_solve * 1e3, "max_abs_diff_vs_alone": worst}
+
+
+def run_serve(args):
+    from paper_1706_02205_gb300 import serve
+    return serve.bench(args)
+
+
 # ------------------------------------------------------- oracle (CPU) arm
 
 def oracle_step(n_side, args):
@@ -349,6 +479,12 @@ def main():
     ap.add_argument("--cpu-side", type=int, default=320)
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--traffic", type=float, default=None, help="ncu DRAM bytes per factor launch, if measured")
+    ap.add_argument("--workload", default="grid2d", choices=["grid2d", "cube3d", "factor", "batch", "serve"],
+                    help="grid2d: the headline step (default); cube3d: 3-D factor + PCA; factor: factor-only "
+                         "probe; batch: many sets in one launch; serve: request stream")
+    ap.add_argument("--n3", type=int, default=2**18)
+    ap.add_argument("--n-sets", type=int, default=256)
+    ap.add_argument("--prec", default="fp32", choices=["fp32", "fp64"])
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -360,6 +496,14 @@ def main():
         dist.init_process_group("nccl")
     if args.impl == "reference":
         line = run_reference(args, rank, world)
+    elif args.workload == "factor":
+        line = run_factor_only(args)
+    elif args.workload == "cube3d":
+        line = run_cube3d(args)
+    elif args.workload == "batch":
+        line = run_batch(args)
+    elif args.workload == "serve":
+        line = run_serve(args)
     else:
         line = run_ours(args, rank, world)
     if line is not None:

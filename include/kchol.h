@@ -95,6 +95,7 @@ typedef struct {
     int32_t test_hold_column;      /* test hook: 0 = off; c+1 makes column c never signal
                                       ready, so a wait on it runs out (KC_ETIMEOUT) */
     int32_t lanes_per_row;         /* factor: lanes merging one row (1,2,4,..,32); 0 -> from |R_i| */
+    int32_t unroll;                /* factor: (col, val) loads staged ahead per lane, 4 or 8; 0 -> 4 */
 } kc_opts;
 
 const char* kc_last_error(void);
@@ -148,6 +149,45 @@ kc_status kc_schedule(int64_t N, const int64_t* rowptr, const int32_t* col, int6
 kc_status kc_factor(const kc_pattern* pat, const double* x_ord, int32_t d, const kc_kernel* kern,
                     int32_t prec, void* val, double* diag, int64_t* zero_pivots_out,
                     const kc_opts* opts, void* stream);
+
+/* ---- factor plans: many point sets in one launch, capturable ------------ *
+ * A plan keeps the task list and counters of one pattern, so that each
+ * factorisation is a single persistent launch with no allocation and no host
+ * synchronisation (it can be recorded in a CUDA graph).  Independent point
+ * sets are factored together by concatenating their patterns
+ * block-diagonally (positions of set s shifted by its offset, coordinates
+ * padded to a common d with zeros): col_set (device int32[N]) gives the set of
+ * every column and kerns[set] (host, nsets entries) its Matern parameters;
+ * with nsets == 1, col_set may be NULL.  x_ord must stay valid while the plan
+ * is used.  kc_factor_plan_finish synchronises and reports a timeout or the
+ * dropped pivots of the last launch.  kc_factor_plan_tune times every
+ * combination of lanes per row {4,8,16,32} and staging depth {4,8} once on the
+ * plan's own problem and keeps the fastest (it overwrites val and diag). */
+typedef struct kc_factor_plan kc_factor_plan;
+kc_status kc_factor_plan_create(const kc_pattern* pat, const double* x_ord, int32_t d, const kc_kernel* kerns,
+                                int32_t nsets, const int32_t* col_set, int32_t prec, const kc_opts* opts,
+                                kc_factor_plan** out, void* stream);
+kc_status kc_factor_plan_launch(kc_factor_plan* plan, void* val, double* diag, void* stream);
+kc_status kc_factor_plan_finish(kc_factor_plan* plan, int64_t* zero_pivots_out, void* stream);
+kc_status kc_factor_plan_tune(kc_factor_plan* plan, void* val, double* diag, int32_t* lanes_out,
+                              int32_t* unroll_out, double* best_ms_out, void* stream);
+void kc_factor_plan_destroy(kc_factor_plan* plan);
+
+/* Concatenate nsets patterns block-diagonally (host arrays of device
+ * pointers): rowptr_out int64[sum N + 1], col_out int32[sum nnz], and
+ * set_out int32[sum N] (set of every position).  Synchronises. */
+kc_status kc_pattern_concat(int32_t nsets, const int64_t* const* rowptrs, const int32_t* const* cols,
+                            const int64_t* Ns, int64_t* rowptr_out, int32_t* col_out, int32_t* set_out, void* stream);
+
+/* Concatenate point arrays (host array of device pointers, set s has Ns[s]
+ * points of dimension ds[s]) into out double[sum N * dout], padding missing
+ * coordinates with 0 (dout >= every ds). */
+kc_status kc_points_concat(int32_t nsets, const double* const* xs, const int64_t* Ns, const int32_t* ds,
+                           int32_t dout, double* out, void* stream);
+
+/* Concatenate index arrays (host array of device pointers) shifting set s by
+ * its offset sum_{t<s} Ns[t]: for permutations of the concatenated sets. */
+kc_status kc_index_concat(int32_t nsets, const int32_t* const* idx, const int64_t* Ns, int32_t* out, void* stream);
 
 /* ---- a7: solve L L^T x = b (task (2) with the factor) ------------------- *
  * b, x: device double[nrhs*N], column-major (rhs r at offset r*N), original

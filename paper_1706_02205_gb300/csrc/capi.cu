@@ -22,6 +22,18 @@ kc_status refine_impl(const kc_pattern* P, const double* x_ord, int d, const kc_
 kc_status solve_noalloc_impl(const kc_pattern* P, int prec, const void* val, const double* diag,
                              const kc_kernel* kern, const int32_t* perm, const double* b, int nrhs, double* x,
                              cudaStream_t s);
+kc_status plan_create_impl(const kc_pattern* P, const double* x, int d, const kc_kernel* kerns, int nsets,
+                           const int32_t* col_set, int prec, const kc_opts* o, kc_factor_plan** out, cudaStream_t s);
+kc_status plan_launch_impl(kc_factor_plan* pl, void* val, double* diag, cudaStream_t s);
+kc_status plan_finish_impl(kc_factor_plan* pl, int64_t* zero_out, cudaStream_t s);
+kc_status plan_tune_impl(kc_factor_plan* pl, void* val, double* diag, int32_t* lanes_out, int32_t* unroll_out,
+                         double* best_ms_out, cudaStream_t s);
+void plan_destroy_impl(kc_factor_plan* pl);
+kc_status pattern_concat_impl(int nsets, const int64_t* const* rowptrs, const int32_t* const* cols, const int64_t* Ns,
+                              int64_t* rowptr_out, int32_t* col_out, int32_t* set_out, cudaStream_t s);
+kc_status points_concat_impl(int nsets, const double* const* xs, const int64_t* Ns, const int32_t* ds, int dout,
+                             double* out, cudaStream_t s);
+kc_status index_concat_impl(int nsets, const int32_t* const* idx, const int64_t* Ns, int32_t* out, cudaStream_t s);
 kc_status pca_truncate_impl(const kc_pattern* P, int prec, const void* val, const int32_t* perm, int k, float* Lk,
                             cudaStream_t s);
 kc_status pca_error_impl(const double* x, int64_t N, int d, const kc_kernel* kern, int k, const float* Lk,
@@ -108,6 +120,50 @@ kc_status kc_solve(const kc_pattern* pat, int32_t prec, const void* val, const d
     KC_TRY(check_pattern(pat));
     if (!val || !diag || !perm || !b || !x) return fail(KC_EINVAL, "arrays must be non-NULL");
     return solve_impl(pat, prec, val, diag, kern, perm, b, nrhs, x, opts, (cudaStream_t)stream);
+}
+
+kc_status kc_factor_plan_create(const kc_pattern* pat, const double* x_ord, int32_t d, const kc_kernel* kerns,
+                                int32_t nsets, const int32_t* col_set, int32_t prec, const kc_opts* opts,
+                                kc_factor_plan** out, void* stream) {
+    KC_TRY(check_pattern(pat));
+    KC_TRY(check_points(x_ord, pat->N, d));
+    if (!kerns || !out) return fail(KC_EINVAL, "kerns and out must be non-NULL");
+    return plan_create_impl(pat, x_ord, d, kerns, nsets, col_set, prec, opts, out, (cudaStream_t)stream);
+}
+
+kc_status kc_factor_plan_launch(kc_factor_plan* plan, void* val, double* diag, void* stream) {
+    if (!plan || !val || !diag) return fail(KC_EINVAL, "plan, val and diag must be non-NULL");
+    return plan_launch_impl(plan, val, diag, (cudaStream_t)stream);
+}
+
+kc_status kc_factor_plan_finish(kc_factor_plan* plan, int64_t* zero_pivots_out, void* stream) {
+    if (!plan) return fail(KC_EINVAL, "plan is NULL");
+    return plan_finish_impl(plan, zero_pivots_out, (cudaStream_t)stream);
+}
+
+kc_status kc_factor_plan_tune(kc_factor_plan* plan, void* val, double* diag, int32_t* lanes_out, int32_t* unroll_out,
+                              double* best_ms_out, void* stream) {
+    if (!plan || !val || !diag) return fail(KC_EINVAL, "plan, val and diag must be non-NULL");
+    return plan_tune_impl(plan, val, diag, lanes_out, unroll_out, best_ms_out, (cudaStream_t)stream);
+}
+
+void kc_factor_plan_destroy(kc_factor_plan* plan) { plan_destroy_impl(plan); }
+
+kc_status kc_pattern_concat(int32_t nsets, const int64_t* const* rowptrs, const int32_t* const* cols, const int64_t* Ns,
+                            int64_t* rowptr_out, int32_t* col_out, int32_t* set_out, void* stream) {
+    if (nsets < 1 || !rowptrs || !cols || !Ns || !rowptr_out || !col_out) return fail(KC_EINVAL, "bad concat arguments");
+    return pattern_concat_impl(nsets, rowptrs, cols, Ns, rowptr_out, col_out, set_out, (cudaStream_t)stream);
+}
+
+kc_status kc_points_concat(int32_t nsets, const double* const* xs, const int64_t* Ns, const int32_t* ds, int32_t dout,
+                           double* out, void* stream) {
+    if (nsets < 1 || !xs || !Ns || !ds || !out || dout < 1) return fail(KC_EINVAL, "bad concat arguments");
+    return points_concat_impl(nsets, xs, Ns, ds, dout, out, (cudaStream_t)stream);
+}
+
+kc_status kc_index_concat(int32_t nsets, const int32_t* const* idx, const int64_t* Ns, int32_t* out, void* stream) {
+    if (nsets < 1 || !idx || !Ns || !out) return fail(KC_EINVAL, "bad concat arguments");
+    return index_concat_impl(nsets, idx, Ns, out, (cudaStream_t)stream);
 }
 
 kc_status kc_solve_noalloc(const kc_pattern* pat, int32_t prec, const void* val, const double* diag,

@@ -15,10 +15,14 @@
 // (index -> value) into an open-addressing hash table in shared memory,
 // recomputes the pivot, and then merges the prefix of each row j of its chunk
 // (entries k < i) against the table.  Lanes form groups of G; a group owns
-// one row, each lane walks the row with stride G, loading four (col, val)
-// pairs ahead so that enough loads are in flight to cover HBM latency.
-// Theta_ji is evaluated from the coordinates in the kernel (entries are never
-// stored).  The task publishes by a release increment of done[i].
+// one row, each lane walks the row with stride G, loading U (col, val) pairs
+// ahead (the staging depth) so that enough loads are in flight to cover HBM
+// latency.  Theta_ji is evaluated from the coordinates in the kernel (entries
+// are never stored).  The task publishes by a release increment of done[i].
+//
+// Several independent point sets can be factored in one launch: their
+// patterns are concatenated block-diagonally and every column names its set,
+// whose Matern parameters the kernel then uses.
 //
 // FP32 form: values, products and the compensated (Dot2) sums stay in FP32;
 // only the pivot and its square root are FP64 (the FP64 pipe of the GB300 is
@@ -28,6 +32,8 @@
 // have smaller ticket numbers and were claimed by running warps, so the
 // earliest unfinished task can always proceed.  Every wait is bounded: when it
 // runs out the kernel records DEV_TIMEOUT in the status word and returns.
+#include <vector>
+
 #include "common.cuh"
 
 namespace kc {
@@ -51,7 +57,9 @@ struct FactorArgs {
     unsigned long long* ticket;
     int* status;
     unsigned long long* zero_piv;
-    KernelParams kp;
+    KernelParams kp;                 // kernel of a single set
+    const int32_t* __restrict__ col_set;  // set of every column (NULL: one set)
+    const KernelParams* __restrict__ kps; // kernels of the sets
     long long spin_limit;
     int hold_col;
     int hbits;  // hash table of 2^hbits slots per warp
@@ -129,26 +137,26 @@ struct Acc<float> {
 };
 
 template <typename T>
-__device__ __forceinline__ T theta_off(const FactorArgs<T>& A, const double* xj, const double* xi);
+__device__ __forceinline__ T theta_off(const KernelParams& kp, int d, const double* xj, const double* xi);
 
 template <>
-__device__ __forceinline__ double theta_off<double>(const FactorArgs<double>& A, const double* xj,
+__device__ __forceinline__ double theta_off<double>(const KernelParams& kp, int d, const double* xj,
                                                     const double* xi) {
     double s = 0.0;
-    for (int t = 0; t < A.d; ++t) {
+    for (int t = 0; t < d; ++t) {
         double u = xj[t] - xi[t];
         s = fma(u, u, s);
     }
-    return matern_f64(sqrt(s), A.kp.nu_code, A.kp.scale, A.kp.sigma2);
+    return matern_f64(sqrt(s), kp.nu_code, kp.scale, kp.sigma2);
 }
 template <>
-__device__ __forceinline__ float theta_off<float>(const FactorArgs<float>& A, const double* xj, const double* xi) {
+__device__ __forceinline__ float theta_off<float>(const KernelParams& kp, int d, const double* xj, const double* xi) {
     float s = 0.f;
-    for (int t = 0; t < A.d; ++t) {
+    for (int t = 0; t < d; ++t) {
         float u = (float)(xj[t] - xi[t]);
         s = fmaf(u, u, s);
     }
-    return matern_f32(sqrtf(s), A.kp.nu_code, (float)A.kp.scale, (float)A.kp.sigma2);
+    return matern_f32(sqrtf(s), kp.nu_code, (float)kp.scale, (float)kp.sigma2);
 }
 
 // bounded wait until done[k] >= need; false when the budget ran out or the
@@ -165,7 +173,7 @@ __device__ __forceinline__ bool wait_done(const unsigned* f, unsigned need, cons
     return true;
 }
 
-template <typename T>
+template <typename T, int U>
 __global__ void __launch_bounds__(256) ichol_persistent_k(FactorArgs<T> A) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = lane_id();
@@ -185,6 +193,7 @@ __global__ void __launch_bounds__(256) ichol_persistent_k(FactorArgs<T> A) {
         const int i = tk.x, c = tk.y;
         const int64_t a0 = A.rowptr[i], a1 = A.rowptr[i + 1] - 1;  // R_i = col[a0..a1)
         const int nr = (int)(a1 - a0);
+        const KernelParams kp = A.col_set ? A.kps[A.col_set[i]] : A.kp;
 
         // ---- wait until every column k in R_i is complete
         bool ok = true;
@@ -217,7 +226,7 @@ __global__ void __launch_bounds__(256) ichol_persistent_k(FactorArgs<T> A) {
         }
         ps = warp_sum(ps);
         __syncwarp();
-        const double p = (A.kp.sigma2 + A.kp.nugget) - ps;
+        const double p = (kp.sigma2 + kp.nugget) - ps;
         const bool zero = !(p > 0.0);
         const double Lii = zero ? 0.0 : sqrt(p);
         const T inv = zero ? (T)0 : (T)(1.0 / Lii);
@@ -249,17 +258,18 @@ __global__ void __launch_bounds__(256) ichol_persistent_k(FactorArgs<T> A) {
             if (act && !zero) {
                 int64_t e = __ldg(&A.rowptr[j]) + sub;
                 if (staged) {
-                    for (; e + 3 * G < bij; e += 4 * G) {
-                        const int k0 = __ldg(&A.col[e]), k1 = __ldg(&A.col[e + G]);
-                        const int k2 = __ldg(&A.col[e + 2 * G]), k3 = __ldg(&A.col[e + 3 * G]);
-                        const T w0 = ldcg(&A.val[e]), w1 = ldcg(&A.val[e + G]);
-                        const T w2 = ldcg(&A.val[e + 2 * G]), w3 = ldcg(&A.val[e + 3 * G]);
-                        const int h0 = hfind(hkey, A.hbits, k0), h1 = hfind(hkey, A.hbits, k1);
-                        const int h2 = hfind(hkey, A.hbits, k2), h3 = hfind(hkey, A.hbits, k3);
-                        if (h0 >= 0) acc.add(w0, hval[h0]);
-                        if (h1 >= 0) acc.add(w1, hval[h1]);
-                        if (h2 >= 0) acc.add(w2, hval[h2]);
-                        if (h3 >= 0) acc.add(w3, hval[h3]);
+                    for (; e + (U - 1) * G < bij; e += U * G) {
+                        int k[U];
+                        T wv[U];
+#pragma unroll
+                        for (int u = 0; u < U; ++u) k[u] = __ldg(&A.col[e + u * G]);
+#pragma unroll
+                        for (int u = 0; u < U; ++u) wv[u] = ldcg(&A.val[e + u * G]);
+#pragma unroll
+                        for (int u = 0; u < U; ++u) {
+                            const int h = hfind(hkey, A.hbits, k[u]);
+                            if (h >= 0) acc.add(wv[u], hval[h]);
+                        }
                     }
                     for (; e < bij; e += G) {
                         const int k0 = __ldg(&A.col[e]);
@@ -277,7 +287,7 @@ __global__ void __launch_bounds__(256) ichol_persistent_k(FactorArgs<T> A) {
             acc.group_reduce(G);
             if (act && sub == 0) {
                 T v = (T)0;
-                if (!zero) v = acc.finish(theta_off<T>(A, A.x + (int64_t)j * A.d, xi), Lii, inv);
+                if (!zero) v = acc.finish(theta_off<T>(kp, A.d, A.x + (int64_t)j * A.d, xi), Lii, inv);
                 A.val[bij] = v;
             }
         }
@@ -344,99 +354,265 @@ kc_status build_tasks(const kc_pattern* P, int rpt, Arena& A, cudaStream_t s, in
     return KC_OK;
 }
 
-template <typename T>
-static kc_status factor_run(const kc_pattern* P, const double* x, int d, const KernelParams& kp, T* val,
-                            double* diag, int64_t* zero_out, const kc_opts* o, cudaStream_t s) {
-    Arena A(s);
-    const int rpt = (o && o->rows_per_task > 0) ? o->rows_per_task : 64;
-    const int warps = (o && o->warps_per_cta > 0) ? o->warps_per_cta : 8;
-    if (warps > 8) return fail(KC_EINVAL, "warps_per_cta must be <= 8");
-    int2* tasks;
-    int64_t nt;
-    int maxr;
-    KC_TRY(build_tasks(P, rpt, A, s, &tasks, &nt, &maxr));
+// ---------------------------------------------------------------- launch core
+// Everything one persistent launch needs.  kc_factor fills it with
+// stream-ordered scratch; a kc_factor_plan keeps it across launches.
+struct FactorCore {
+    kc_pattern P;
+    int prec = KC_FP32_FORM;
+    int d = 2;
+    const double* x = nullptr;
+    int2* tasks = nullptr;
+    int64_t ntasks = 0;
+    int maxr = 0;
+    unsigned* done = nullptr;
+    unsigned long long* ticket = nullptr;
+    unsigned long long* zp = nullptr;
+    int* status = nullptr;
+    KernelParams kp;
+    const int32_t* col_set = nullptr;
+    KernelParams* kps = nullptr;
+    int rpt = 64, lanes = 0, unroll = 4, warps = 8, hbits = 7, ctas = 0;
+    long long spin = 4000000000LL;
+    int hold = -1;
+};
 
-    unsigned* done;
-    unsigned long long* ticket;
-    unsigned long long* zp;
-    int* status;
-    KC_TRY(A.get(&done, P->N));
-    KC_TRY(A.get(&ticket, 1));
-    KC_TRY(A.get(&zp, 1));
-    KC_TRY(A.get(&status, 1));
-    KC_CUDA(cudaMemsetAsync(done, 0, sizeof(unsigned) * P->N, s));
-    KC_CUDA(cudaMemsetAsync(ticket, 0, sizeof(unsigned long long), s));
-    KC_CUDA(cudaMemsetAsync(zp, 0, sizeof(unsigned long long), s));
-    KC_CUDA(cudaMemsetAsync(status, 0, sizeof(int), s));
-
+template <typename T, int U>
+static kc_status launch_core(const FactorCore& F, T* val, double* diag, cudaStream_t s) {
     FactorArgs<T> a;
-    a.N = P->N;
-    a.d = d;
-    a.x = x;
-    a.rowptr = P->rowptr;
-    a.col = P->col;
-    a.colptr = P->colptr;
-    a.rowidx = P->rowidx;
-    a.slot = P->slot;
-    a.tasks = tasks;
-    a.ntasks = nt;
-    a.rpt = rpt;
+    a.N = F.P.N;
+    a.d = F.d;
+    a.x = F.x;
+    a.rowptr = F.P.rowptr;
+    a.col = F.P.col;
+    a.colptr = F.P.colptr;
+    a.rowidx = F.P.rowidx;
+    a.slot = F.P.slot;
+    a.tasks = F.tasks;
+    a.ntasks = F.ntasks;
+    a.rpt = F.rpt;
     a.val = val;
     a.diag = diag;
-    a.done = done;
-    a.ticket = ticket;
-    a.status = status;
-    a.zero_piv = zp;
-    a.kp = kp;
-    a.spin_limit = (o && o->spin_limit_cycles > 0) ? o->spin_limit_cycles : 4000000000LL;
-    a.hold_col = (o && o->test_hold_column > 0) ? o->test_hold_column - 1 : -1;
-    // hash table: at least twice the longest row (load factor <= 1/2), 128..2048 slots
-    int hb = 7;
-    while (hb < 11 && (1 << hb) < 2 * maxr) ++hb;
-    a.hbits = hb;
-    a.lanes = 0;
-    if (o && o->lanes_per_row > 0) {
-        int L = o->lanes_per_row;
-        if (L > 32 || (L & (L - 1))) return fail(KC_EINVAL, "lanes_per_row must be a power of two <= 32");
-        a.lanes = L;
-    }
-    size_t smem = (size_t)warps * (1 << hb) * (sizeof(int) + sizeof(T));
-    KC_CUDA(cudaFuncSetAttribute(ichol_persistent_k<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    a.done = F.done;
+    a.ticket = F.ticket;
+    a.status = F.status;
+    a.zero_piv = F.zp;
+    a.kp = F.kp;
+    a.col_set = F.col_set;
+    a.kps = F.kps;
+    a.spin_limit = F.spin;
+    a.hold_col = F.hold;
+    a.hbits = F.hbits;
+    a.lanes = F.lanes;
+    const size_t smem = (size_t)F.warps * (1 << F.hbits) * (sizeof(int) + sizeof(T));
+    KC_CUDA(cudaFuncSetAttribute(ichol_persistent_k<T, U>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
-    KC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ichol_persistent_k<T>, warps * 32, smem));
-    if (o && o->ctas_per_sm > 0 && o->ctas_per_sm < per_sm) per_sm = o->ctas_per_sm;
+    KC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ichol_persistent_k<T, U>, F.warps * 32, smem));
+    if (F.ctas > 0 && F.ctas < per_sm) per_sm = F.ctas;
     if (per_sm < 1) per_sm = 1;
-    int grid = sm_count() * per_sm;
-    cudaEvent_t e0, e1;
-    KC_CUDA(cudaEventCreate(&e0));
-    KC_CUDA(cudaEventCreate(&e1));
-    KC_CUDA(cudaEventRecord(e0, s));
-    ::kc::note_launch(), ichol_persistent_k<T><<<grid, warps * 32, smem, s>>>(a);
+    KC_CUDA(cudaMemsetAsync(F.done, 0, sizeof(unsigned) * F.P.N, s));
+    KC_CUDA(cudaMemsetAsync(F.ticket, 0, sizeof(unsigned long long), s));
+    KC_CUDA(cudaMemsetAsync(F.zp, 0, sizeof(unsigned long long), s));
+    KC_CUDA(cudaMemsetAsync(F.status, 0, sizeof(int), s));
+    ::kc::note_launch(), ichol_persistent_k<T, U><<<sm_count() * per_sm, F.warps * 32, smem, s>>>(a);
     KC_CUDA(cudaGetLastError());
-    KC_CUDA(cudaEventRecord(e1, s));
+    return KC_OK;
+}
+
+static kc_status launch_any(const FactorCore& F, void* val, double* diag, cudaStream_t s) {
+    if (F.prec == KC_FP64)
+        return F.unroll >= 8 ? launch_core<double, 8>(F, (double*)val, diag, s)
+                             : launch_core<double, 4>(F, (double*)val, diag, s);
+    return F.unroll >= 8 ? launch_core<float, 8>(F, (float*)val, diag, s)
+                         : launch_core<float, 4>(F, (float*)val, diag, s);
+}
+
+static kc_status read_status(const FactorCore& F, int64_t* zero_out, cudaStream_t s) {
     int h_status = 0;
     unsigned long long h_zp = 0;
-    KC_CUDA(cudaMemcpyAsync(&h_status, status, sizeof(int), cudaMemcpyDeviceToHost, s));
-    KC_CUDA(cudaMemcpyAsync(&h_zp, zp, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+    KC_CUDA(cudaMemcpyAsync(&h_status, F.status, sizeof(int), cudaMemcpyDeviceToHost, s));
+    KC_CUDA(cudaMemcpyAsync(&h_zp, F.zp, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
     KC_CUDA(cudaStreamSynchronize(s));
-    float ms = 0.f;
-    KC_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    set_factor_kernel_ms(ms);
     if (zero_out) *zero_out = (int64_t)h_zp;
     if (h_status == DEV_TIMEOUT) return fail(KC_ETIMEOUT, "factor: a dependency wait ran out");
     if (h_status != 0) return fail(KC_ECUDA, "factor: device status " + std::to_string(h_status));
     return KC_OK;
 }
 
+static kc_status apply_opts(FactorCore& F, const kc_opts* o) {
+    F.rpt = (o && o->rows_per_task > 0) ? o->rows_per_task : 64;
+    F.warps = (o && o->warps_per_cta > 0) ? o->warps_per_cta : 8;
+    if (F.warps > 8) return fail(KC_EINVAL, "warps_per_cta must be <= 8");
+    F.spin = (o && o->spin_limit_cycles > 0) ? o->spin_limit_cycles : 4000000000LL;
+    F.ctas = (o && o->ctas_per_sm > 0) ? o->ctas_per_sm : 0;
+    F.hold = (o && o->test_hold_column > 0) ? o->test_hold_column - 1 : -1;
+    F.lanes = 0;
+    if (o && o->lanes_per_row > 0) {
+        int L = o->lanes_per_row;
+        if (L > 32 || (L & (L - 1))) return fail(KC_EINVAL, "lanes_per_row must be a power of two <= 32");
+        F.lanes = L;
+    }
+    F.unroll = (o && o->unroll > 0) ? o->unroll : 4;
+    if (F.unroll != 4 && F.unroll != 8) return fail(KC_EINVAL, "unroll must be 4 or 8");
+    return KC_OK;
+}
+
+static void pick_hash(FactorCore& F) {
+    // hash table: at least twice the longest row (load factor <= 1/2), 128..2048 slots
+    int hb = 7;
+    while (hb < 11 && (1 << hb) < 2 * F.maxr) ++hb;
+    F.hbits = hb;
+}
+
 kc_status factor_impl(const kc_pattern* P, const double* x, int d, const kc_kernel* kern, int prec, void* val,
                       double* diag, int64_t* zero_out, const kc_opts* o, cudaStream_t s) {
-    KernelParams kp;
-    KC_TRY(kernel_params(kern, &kp));
-    if (prec == KC_FP64) return factor_run<double>(P, x, d, kp, (double*)val, diag, zero_out, o, s);
-    if (prec == KC_FP32_FORM) return factor_run<float>(P, x, d, kp, (float*)val, diag, zero_out, o, s);
-    return fail(KC_EINVAL, "prec must be KC_FP64 or KC_FP32_FORM");
+    if (prec != KC_FP64 && prec != KC_FP32_FORM) return fail(KC_EINVAL, "prec must be KC_FP64 or KC_FP32_FORM");
+    FactorCore F;
+    KC_TRY(kernel_params(kern, &F.kp));
+    KC_TRY(apply_opts(F, o));
+    F.P = *P;
+    F.prec = prec;
+    F.d = d;
+    F.x = x;
+    Arena A(s);
+    KC_TRY(build_tasks(P, F.rpt, A, s, &F.tasks, &F.ntasks, &F.maxr));
+    pick_hash(F);
+    KC_TRY(A.get(&F.done, P->N));
+    KC_TRY(A.get(&F.ticket, 1));
+    KC_TRY(A.get(&F.zp, 1));
+    KC_TRY(A.get(&F.status, 1));
+    cudaEvent_t e0, e1;
+    KC_CUDA(cudaEventCreate(&e0));
+    KC_CUDA(cudaEventCreate(&e1));
+    KC_CUDA(cudaEventRecord(e0, s));
+    kc_status st = launch_any(F, val, diag, s);
+    if (st != KC_OK) return st;
+    KC_CUDA(cudaEventRecord(e1, s));
+    st = read_status(F, zero_out, s);
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess) set_factor_kernel_ms(ms);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return st;
+}
+
+}  // namespace kc
+
+// ------------------------------------------------------------------ plans
+// A plan keeps the task list and the counters of one pattern so that the
+// factorisation is a single capturable launch (no allocation, no host sync).
+struct kc_factor_plan {
+    kc::FactorCore F;
+    std::vector<void*> owned;
+};
+
+namespace kc {
+
+static kc_status plan_alloc(kc_factor_plan* pl, void** p, size_t bytes) {
+    cudaError_t e = cudaMalloc(p, bytes ? bytes : 16);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(plan)");
+    pl->owned.push_back(*p);
+    return KC_OK;
+}
+
+kc_status plan_create_impl(const kc_pattern* P, const double* x, int d, const kc_kernel* kerns, int nsets,
+                           const int32_t* col_set, int prec, const kc_opts* o, kc_factor_plan** out, cudaStream_t s) {
+    if (prec != KC_FP64 && prec != KC_FP32_FORM) return fail(KC_EINVAL, "prec must be KC_FP64 or KC_FP32_FORM");
+    if (nsets < 1 || (nsets > 1 && !col_set)) return fail(KC_EINVAL, "nsets >= 1; col_set required when nsets > 1");
+    kc_factor_plan* pl = new kc_factor_plan();
+    FactorCore& F = pl->F;
+    auto bail = [&](kc_status st) {
+        for (void* p : pl->owned) cudaFree(p);
+        delete pl;
+        return st;
+    };
+    kc_status st = kernel_params(&kerns[0], &F.kp);
+    if (st == KC_OK) st = apply_opts(F, o);
+    if (st != KC_OK) return bail(st);
+    F.P = *P;
+    F.prec = prec;
+    F.d = d;
+    F.x = x;
+    F.col_set = nsets > 1 ? col_set : nullptr;
+    {
+        Arena A(s);
+        int2* t;
+        st = build_tasks(P, F.rpt, A, s, &t, &F.ntasks, &F.maxr);
+        if (st != KC_OK) return bail(st);
+        if ((st = plan_alloc(pl, (void**)&F.tasks, sizeof(int2) * F.ntasks)) != KC_OK) return bail(st);
+        if (cudaMemcpyAsync(F.tasks, t, sizeof(int2) * F.ntasks, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+            return bail(fail(KC_ECUDA, "plan: task copy"));
+    }
+    pick_hash(F);
+    if ((st = plan_alloc(pl, (void**)&F.done, sizeof(unsigned) * P->N)) != KC_OK) return bail(st);
+    if ((st = plan_alloc(pl, (void**)&F.ticket, 64)) != KC_OK) return bail(st);
+    if ((st = plan_alloc(pl, (void**)&F.zp, 64)) != KC_OK) return bail(st);
+    if ((st = plan_alloc(pl, (void**)&F.status, 64)) != KC_OK) return bail(st);
+    if (nsets > 1) {
+        std::vector<KernelParams> h(nsets);
+        for (int k = 0; k < nsets; ++k)
+            if ((st = kernel_params(&kerns[k], &h[k])) != KC_OK) return bail(st);
+        if ((st = plan_alloc(pl, (void**)&F.kps, sizeof(KernelParams) * nsets)) != KC_OK) return bail(st);
+        if (cudaMemcpy(F.kps, h.data(), sizeof(KernelParams) * nsets, cudaMemcpyHostToDevice) != cudaSuccess)
+            return bail(fail(KC_ECUDA, "plan: kernel parameter copy"));
+    }
+    if (cudaStreamSynchronize(s) != cudaSuccess) return bail(fail(KC_ECUDA, "plan: synchronize"));
+    *out = pl;
+    return KC_OK;
+}
+
+kc_status plan_launch_impl(kc_factor_plan* pl, void* val, double* diag, cudaStream_t s) {
+    return launch_any(pl->F, val, diag, s);
+}
+
+kc_status plan_finish_impl(kc_factor_plan* pl, int64_t* zero_out, cudaStream_t s) {
+    return read_status(pl->F, zero_out, s);
+}
+
+// Pick lanes per row (the warp share of one row) and the staging depth by
+// timing every combination once on the plan's own problem.
+kc_status plan_tune_impl(kc_factor_plan* pl, void* val, double* diag, int32_t* lanes_out, int32_t* unroll_out,
+                         double* best_ms_out, cudaStream_t s) {
+    FactorCore& F = pl->F;
+    const int lanes_c[] = {4, 8, 16, 32};
+    const int unroll_c[] = {4, 8};
+    cudaEvent_t e0, e1;
+    KC_CUDA(cudaEventCreate(&e0));
+    KC_CUDA(cudaEventCreate(&e1));
+    double best = 1e300;
+    int bl = F.lanes, bu = F.unroll;
+    KC_TRY(launch_any(F, val, diag, s));  // warm-up
+    KC_TRY(read_status(F, nullptr, s));
+    for (int L : lanes_c)
+        for (int U : unroll_c) {
+            F.lanes = L;
+            F.unroll = U;
+            KC_CUDA(cudaEventRecord(e0, s));
+            KC_TRY(launch_any(F, val, diag, s));
+            KC_CUDA(cudaEventRecord(e1, s));
+            KC_TRY(read_status(F, nullptr, s));
+            float ms = 0.f;
+            KC_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+            if (ms < best) {
+                best = ms;
+                bl = L;
+                bu = U;
+            }
+        }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    F.lanes = bl;
+    F.unroll = bu;
+    if (lanes_out) *lanes_out = bl;
+    if (unroll_out) *unroll_out = bu;
+    if (best_ms_out) *best_ms_out = best;
+    return KC_OK;
+}
+
+void plan_destroy_impl(kc_factor_plan* pl) {
+    if (!pl) return;
+    for (void* p : pl->owned) cudaFree(p);
+    delete pl;
 }
 
 }  // namespace kc

@@ -43,7 +43,8 @@ class kc_pattern(C.Structure):
 
 class kc_opts(C.Structure):
     _fields_ = [("spin_limit_cycles", C.c_int64), ("rows_per_task", C.c_int32), ("ctas_per_sm", C.c_int32),
-                ("warps_per_cta", C.c_int32), ("test_hold_column", C.c_int32), ("lanes_per_row", C.c_int32)]
+                ("warps_per_cta", C.c_int32), ("test_hold_column", C.c_int32), ("lanes_per_row", C.c_int32),
+                ("unroll", C.c_int32)]
 
 
 _lib = None
@@ -74,17 +75,29 @@ def lib():
                           P(C.c_int32), P(C.c_double), P(kc_opts), vp],
             "kc_pca_truncate": [P(kc_pattern), i32, vp, vp, i32, vp, vp],
             "kc_pca_error": [vp, i64, i32, P(kc_kernel), i32, vp, vp, i32, P(C.c_double), vp],
+            "kc_factor_plan_create": [P(kc_pattern), vp, i32, P(kc_kernel), i32, vp, i32, P(kc_opts),
+                                      P(vp), vp],
+            "kc_factor_plan_launch": [vp, vp, vp, vp],
+            "kc_factor_plan_finish": [vp, P(C.c_int64), vp],
+            "kc_factor_plan_tune": [vp, vp, vp, P(C.c_int32), P(C.c_int32), P(C.c_double), vp],
+            "kc_pattern_concat": [i32, P(vp), P(vp), P(C.c_int64), vp, vp, vp, vp],
+            "kc_points_concat": [i32, P(vp), P(C.c_int64), P(C.c_int32), i32, vp, vp],
+            "kc_index_concat": [i32, P(vp), P(C.c_int64), vp, vp],
         }
         for name, args in sigs.items():
             f = getattr(L, name)
             f.argtypes = args
             f.restype = C.c_int
+        L.kc_factor_plan_destroy.argtypes = [vp]
+        L.kc_factor_plan_destroy.restype = None
         _lib = L
     return _lib
 
 
 EXPORTED = ("kc_last_error", "kc_abi_version", "kc_launch_count", "kc_last_factor_kernel_ms", "kc_order_points", "kc_pattern_count", "kc_pattern_fill",
-            "kc_schedule", "kc_factor", "kc_solve", "kc_solve_noalloc", "kc_refine", "kc_pca_truncate", "kc_pca_error")
+            "kc_schedule", "kc_factor", "kc_solve", "kc_solve_noalloc", "kc_refine", "kc_pca_truncate", "kc_pca_error",
+            "kc_factor_plan_create", "kc_factor_plan_launch", "kc_factor_plan_finish", "kc_factor_plan_tune",
+            "kc_factor_plan_destroy", "kc_pattern_concat", "kc_points_concat", "kc_index_concat")
 
 
 def launch_count() -> int:
@@ -135,9 +148,9 @@ class Kernel:
 
 
 def make_opts(spin_limit_cycles=0, rows_per_task=0, ctas_per_sm=0, warps_per_cta=0, test_hold_column=-1,
-              lanes_per_row=0):
+              lanes_per_row=0, unroll=0):
     return kc_opts(spin_limit_cycles, rows_per_task, ctas_per_sm, warps_per_cta, test_hold_column + 1,
-                   lanes_per_row)
+                   lanes_per_row, unroll)
 
 
 # ----------------------------------------------------------------- a2, a3, a4
@@ -306,3 +319,84 @@ def pipeline(x, rho, kern: Kernel, prec=FP32_FORM, rule=RULE_MAX, opts=None, str
     pat = build_pattern(xo, l, rho, rule, stream)
     val, diag, zp = factor(pat, xo, kern, prec, opts, stream=stream)
     return dict(perm=perm, l=l, x_ord=xo, pat=pat, val=val, diag=diag, zero_pivots=zp)
+
+
+# ------------------------------------------------------ plans and batching
+
+class FactorPlan:
+    """A factorisation plan: task list and counters of one pattern kept on the
+    device, so that each factorisation is one persistent launch with no
+    allocation and no host synchronisation (it can be recorded in a CUDA
+    graph).  ``kerns`` has one Kernel per set and ``col_set`` (int32[N]) the
+    set of every column when several sets are concatenated."""
+
+    def __init__(self, pat: Pattern, x_ord, kerns, col_set=None, prec=FP32_FORM, opts=None, stream=None):
+        _dev(x_ord, torch.float64, "x_ord")
+        kerns = list(kerns)
+        arr = (kc_kernel * len(kerns))(*[k.c() for k in kerns])
+        h = C.c_void_p()
+        self._keep = (pat, x_ord, col_set)
+        self.prec = prec
+        _check(lib().kc_factor_plan_create(pat.c(), _ptr(x_ord), x_ord.shape[1], arr, len(kerns), _ptr(col_set),
+                                           int(prec), C.byref(opts) if opts is not None else None, C.byref(h),
+                                           _stream(stream)))
+        self._h = h
+
+    def launch(self, val, diag, stream=None):
+        _check(lib().kc_factor_plan_launch(self._h, _ptr(val), _ptr(diag), _stream(stream)))
+
+    def finish(self, stream=None) -> int:
+        zp = C.c_int64(0)
+        _check(lib().kc_factor_plan_finish(self._h, C.byref(zp), _stream(stream)))
+        return int(zp.value)
+
+    def tune(self, val, diag, stream=None):
+        """Time lanes-per-row x staging-depth once each and keep the fastest."""
+        L, U, ms = C.c_int32(0), C.c_int32(0), C.c_double(0)
+        _check(lib().kc_factor_plan_tune(self._h, _ptr(val), _ptr(diag), C.byref(L), C.byref(U), C.byref(ms),
+                                         _stream(stream)))
+        return {"lanes_per_row": L.value, "unroll": U.value, "ms": ms.value}
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and _lib is not None:
+            _lib.kc_factor_plan_destroy(h)
+            self._h = None
+
+
+def _ptr_array(ts):
+    return (C.c_void_p * len(ts))(*[t.data_ptr() for t in ts])
+
+
+def pattern_concat(rowptrs, cols, stream=None):
+    """Block-diagonal concatenation -> (rowptr int64, col int32, set int32 per position)."""
+    Ns = [r.numel() - 1 for r in rowptrs]
+    tot = sum(Ns)
+    nnz = sum(c.numel() for c in cols)
+    dev = rowptrs[0].device
+    rowptr = torch.empty(tot + 1, dtype=torch.int64, device=dev)
+    col = torch.empty(nnz, dtype=torch.int32, device=dev)
+    sets = torch.empty(tot, dtype=torch.int32, device=dev)
+    _check(lib().kc_pattern_concat(len(Ns), _ptr_array(rowptrs), _ptr_array(cols), (C.c_int64 * len(Ns))(*Ns),
+                                   _ptr(rowptr), _ptr(col), _ptr(sets), _stream(stream)))
+    return rowptr, col, sets
+
+
+def points_concat(xs, dout=None, stream=None):
+    """Concatenate (N_s, d_s) float64 point sets, zero-padded to dout columns."""
+    Ns = [x.shape[0] for x in xs]
+    ds = [x.shape[1] for x in xs]
+    dout = dout or max(ds)
+    out = torch.empty((sum(Ns), dout), dtype=torch.float64, device=xs[0].device)
+    _check(lib().kc_points_concat(len(xs), _ptr_array(xs), (C.c_int64 * len(Ns))(*Ns), (C.c_int32 * len(ds))(*ds),
+                                  dout, _ptr(out), _stream(stream)))
+    return out
+
+
+def index_concat(idxs, stream=None):
+    """Concatenate int32 index arrays, shifting set s by the sizes before it."""
+    Ns = [t.numel() for t in idxs]
+    out = torch.empty(sum(Ns), dtype=torch.int32, device=idxs[0].device)
+    _check(lib().kc_index_concat(len(idxs), _ptr_array(idxs), (C.c_int64 * len(Ns))(*Ns), _ptr(out),
+                                 _stream(stream)))
+    return out

@@ -11,7 +11,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 def _declared():
     txt = open(os.path.join(ROOT, "include", "kchol.h")).read()
-    return sorted(set(re.findall(r"^\s*(?:const\s+char\s*\*|kc_status|int32_t|int64_t|double)\s+(kc_\w+)\s*\(", txt, re.M)))
+    return sorted(set(re.findall(r"^\s*(?:const\s+char\s*\*|kc_status|int32_t|int64_t|double|void)\s+(kc_\w+)\s*\(", txt, re.M)))
 
 
 @pytest.fixture(scope="module")
