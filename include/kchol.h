@@ -84,6 +84,9 @@ typedef struct {
     const int64_t* slot;     /* [nnz] CSR position of each CSC entry */
     const int32_t* order;    /* [N]   columns sorted by (dependency level, index) */
     int32_t depth;           /* number of dependency levels */
+    const int32_t* level;    /* [N]   dependency level of every column, or NULL.  When given, the
+                                factor runs each level's columns in spatial (Morton) order of
+                                their points, so tasks that read the same rows run close in time */
 } kc_pattern;
 
 /* Options of the persistent kernels (zero-initialise for defaults). */

@@ -34,7 +34,7 @@
 // runs out the kernel records DEV_TIMEOUT in the status word and returns.
 #include <vector>
 
-#include "common.cuh"
+#include "grid.cuh"
 
 namespace kc {
 
@@ -159,13 +159,16 @@ __device__ __forceinline__ float theta_off<float>(const KernelParams& kp, int d,
     return matern_f32(sqrtf(s), kp.nu_code, (float)kp.scale, (float)kp.sigma2);
 }
 
-// bounded wait until done[k] >= need; false when the budget ran out or the
-// kernel is stopping
-__device__ __forceinline__ bool wait_done(const unsigned* f, unsigned need, const int* status, long long limit) {
-    if (ld_acquire_u32(f) >= need) return true;
+// done[k] starts at minus the number of tasks of column k and every finished
+// task adds one, so column k is complete exactly when done[k] >= 0: one load
+// per dependency.  Bounded wait; false when the budget ran out or the kernel
+// is stopping.
+__device__ __forceinline__ bool done_ready(const unsigned* f) { return (int)ld_acquire_u32(f) >= 0; }
+__device__ __forceinline__ bool wait_done(const unsigned* f, const int* status, long long limit) {
+    if (done_ready(f)) return true;
     const long long t0 = clock64();
     unsigned ns = 32;
-    while (ld_acquire_u32(f) < need) {
+    while (!done_ready(f)) {
         if (clock64() - t0 > limit || ld_volatile_s32(status) != 0) return false;
         __nanosleep(ns);
         if (ns < 512) ns <<= 1;
@@ -199,7 +202,7 @@ __global__ void __launch_bounds__(256) ichol_persistent_k(FactorArgs<T> A) {
         bool ok = true;
         for (int e = lane; e < nr && ok; e += 32) {
             const int k = __ldg(&A.col[a0 + e]);
-            ok = wait_done(&A.done[k], n_tasks_of(A.colptr, k, A.rpt), A.status, A.spin_limit);
+            ok = wait_done(&A.done[k], A.status, A.spin_limit);
         }
         if (!__all_sync(FULL, ok)) {
             if (lane == 0) atomicCAS(A.status, 0, DEV_TIMEOUT);
@@ -299,6 +302,12 @@ __global__ void __launch_bounds__(256) ichol_persistent_k(FactorArgs<T> A) {
     }
 }
 
+// done[k] = -(tasks of column k), as an unsigned word
+__global__ void done_init_k(const int64_t* __restrict__ colptr, int64_t N, int rpt, unsigned* __restrict__ done) {
+    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < N) done[k] = 0u - n_tasks_of(colptr, (int)k, rpt);
+}
+
 // tasks of column order[p]: n_tasks_of(order[p])
 __global__ void task_count_k(const int32_t* __restrict__ order, const int64_t* __restrict__ colptr, int64_t N,
                              int rpt, int64_t* __restrict__ cnt) {
@@ -324,9 +333,46 @@ __global__ void max_row_k(const int64_t* __restrict__ rowptr, int64_t N, int* __
     if (lane_id() == 0) atomicMax(out, m);
 }
 
+// Morton code of the first min(d,3) coordinates, quantised in the box [lo, hi]
+__device__ __forceinline__ uint32_t morton_of(const double* x, int d, const double* lo, const double* inv) {
+    const int dg = d < 3 ? d : 3;
+    const int bits = dg <= 2 ? 16 : 10;
+    uint32_t q[3] = {0, 0, 0};
+    for (int t = 0; t < dg; ++t) {
+        double f = (x[t] - lo[t]) * inv[t];
+        f = f < 0.0 ? 0.0 : (f > 1.0 ? 1.0 : f);
+        q[t] = (uint32_t)(f * (double)((1u << bits) - 1));
+    }
+    uint32_t m = 0;
+    for (int b = bits - 1; b >= 0; --b)
+        for (int t = 0; t < dg; ++t) m = (m << 1) | ((q[t] >> b) & 1u);
+    return m;
+}
+struct Box3 {
+    double lo[3], inv[3];
+};
+__global__ void level_morton_keys_k(const int32_t* __restrict__ order, const int32_t* __restrict__ level,
+                                    const double* __restrict__ x, int d, Box3 box, int64_t N,
+                                    uint64_t* __restrict__ key, int64_t* __restrict__ val) {
+    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p < N) {
+        const int i = order[p];
+        key[p] = ((uint64_t)(uint32_t)level[i] << 32) | morton_of(x + (int64_t)i * d, d, box.lo, box.inv);
+        val[p] = i;
+    }
+}
+__global__ void i64_to_i32_k(const int64_t* __restrict__ v, int64_t n, int32_t* __restrict__ out) {
+    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p < n) out[p] = (int32_t)v[p];
+}
+
 // Build the task list (level order) of a pattern; returns count on the host.
+// With points x and the pattern's levels, the columns of each level are put
+// in Morton order of their points: consecutive tasks then merge rows of
+// neighbouring points, which share most of their entries, so the row
+// prefixes they read are often still in L2.
 kc_status build_tasks(const kc_pattern* P, int rpt, Arena& A, cudaStream_t s, int2** tasks_out, int64_t* ntasks_out,
-                      int* max_row_out) {
+                      int* max_row_out, const double* x, int d) {
     int64_t N = P->N;
     int64_t* cnt;
     int64_t* toff;
@@ -334,7 +380,34 @@ kc_status build_tasks(const kc_pattern* P, int rpt, Arena& A, cudaStream_t s, in
     KC_TRY(A.get(&cnt, N));
     KC_TRY(A.get(&toff, N + 1));
     KC_TRY(A.get(&mr, 1));
-    ::kc::note_launch(), task_count_k<<<blocks_for(N, 256), 256, 0, s>>>(P->order, P->colptr, N, rpt, cnt);
+    const int32_t* order = P->order;
+    if (x && P->level) {
+        double lo[3], hi[3];
+        KC_TRY(bbox(x, N, d, lo, hi, A, s));
+        Box3 box;
+        for (int t = 0; t < 3; ++t) {
+            box.lo[t] = t < d ? lo[t] : 0.0;
+            const double e = t < d ? hi[t] - lo[t] : 0.0;
+            box.inv[t] = e > 0 ? 1.0 / e : 0.0;
+        }
+        uint64_t *k0, *k1;
+        int64_t *v0, *v1;
+        int32_t* ord2;
+        KC_TRY(A.get(&k0, N));
+        KC_TRY(A.get(&k1, N));
+        KC_TRY(A.get(&v0, N));
+        KC_TRY(A.get(&v1, N));
+        KC_TRY(A.get(&ord2, N));
+        ::kc::note_launch(), level_morton_keys_k<<<blocks_for(N, 256), 256, 0, s>>>(P->order, P->level, x, d, box, N,
+                                                                                   k0, v0);
+        int lb = 1;
+        while (lb < 31 && (1 << lb) <= P->depth) ++lb;
+        KC_TRY(radix_sort_u64_i64(k0, v0, k1, v1, N, 32 + lb, A, s));
+        ::kc::note_launch(), i64_to_i32_k<<<blocks_for(N, 256), 256, 0, s>>>(v1, N, ord2);
+        KC_CUDA(cudaGetLastError());
+        order = ord2;
+    }
+    ::kc::note_launch(), task_count_k<<<blocks_for(N, 256), 256, 0, s>>>(order, P->colptr, N, rpt, cnt);
     KC_TRY(exclusive_scan_i64(cnt, toff, N, A, s));
     KC_CUDA(cudaMemsetAsync(mr, 0, sizeof(int), s));
     ::kc::note_launch(), max_row_k<<<blocks_for(N, 256), 256, 0, s>>>(P->rowptr, N, mr);
@@ -346,7 +419,7 @@ kc_status build_tasks(const kc_pattern* P, int rpt, Arena& A, cudaStream_t s, in
     KC_CUDA(cudaStreamSynchronize(s));
     int2* tasks;
     KC_TRY(A.get(&tasks, nt));
-    ::kc::note_launch(), task_fill_k<<<blocks_for(N * 32, 256), 256, 0, s>>>(P->order, toff, N, tasks);
+    ::kc::note_launch(), task_fill_k<<<blocks_for(N * 32, 256), 256, 0, s>>>(order, toff, N, tasks);
     KC_CUDA(cudaGetLastError());
     *tasks_out = tasks;
     *ntasks_out = nt;
@@ -410,7 +483,7 @@ static kc_status launch_core(const FactorCore& F, T* val, double* diag, cudaStre
     KC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ichol_persistent_k<T, U>, F.warps * 32, smem));
     if (F.ctas > 0 && F.ctas < per_sm) per_sm = F.ctas;
     if (per_sm < 1) per_sm = 1;
-    KC_CUDA(cudaMemsetAsync(F.done, 0, sizeof(unsigned) * F.P.N, s));
+    ::kc::note_launch(), done_init_k<<<blocks_for(F.P.N, 256), 256, 0, s>>>(F.P.colptr, F.P.N, F.rpt, F.done);
     KC_CUDA(cudaMemsetAsync(F.ticket, 0, sizeof(unsigned long long), s));
     KC_CUDA(cudaMemsetAsync(F.zp, 0, sizeof(unsigned long long), s));
     KC_CUDA(cudaMemsetAsync(F.status, 0, sizeof(int), s));
@@ -475,7 +548,7 @@ kc_status factor_impl(const kc_pattern* P, const double* x, int d, const kc_kern
     F.d = d;
     F.x = x;
     Arena A(s);
-    KC_TRY(build_tasks(P, F.rpt, A, s, &F.tasks, &F.ntasks, &F.maxr));
+    KC_TRY(build_tasks(P, F.rpt, A, s, &F.tasks, &F.ntasks, &F.maxr, x, d));
     pick_hash(F);
     KC_TRY(A.get(&F.done, P->N));
     KC_TRY(A.get(&F.ticket, 1));
@@ -537,7 +610,7 @@ kc_status plan_create_impl(const kc_pattern* P, const double* x, int d, const kc
     {
         Arena A(s);
         int2* t;
-        st = build_tasks(P, F.rpt, A, s, &t, &F.ntasks, &F.maxr);
+        st = build_tasks(P, F.rpt, A, s, &t, &F.ntasks, &F.maxr, x, d);
         if (st != KC_OK) return bail(st);
         if ((st = plan_alloc(pl, (void**)&F.tasks, sizeof(int2) * F.ntasks)) != KC_OK) return bail(st);
         if (cudaMemcpyAsync(F.tasks, t, sizeof(int2) * F.ntasks, cudaMemcpyDeviceToDevice, s) != cudaSuccess)

@@ -38,7 +38,7 @@ class kc_kernel(C.Structure):
 class kc_pattern(C.Structure):
     _fields_ = [("N", C.c_int64), ("nnz", C.c_int64), ("rowptr", C.c_void_p), ("col", C.c_void_p),
                 ("colptr", C.c_void_p), ("rowidx", C.c_void_p), ("slot", C.c_void_p), ("order", C.c_void_p),
-                ("depth", C.c_int32)]
+                ("depth", C.c_int32), ("level", C.c_void_p)]
 
 
 class kc_opts(C.Structure):
@@ -195,7 +195,7 @@ class Pattern:
         self.N = rowptr.numel() - 1
         self.nnz = col.numel()
         self._c = kc_pattern(self.N, self.nnz, rowptr.data_ptr(), col.data_ptr(), colptr.data_ptr(),
-                             rowidx.data_ptr(), slot.data_ptr(), order.data_ptr(), depth)
+                             rowidx.data_ptr(), slot.data_ptr(), order.data_ptr(), depth, level.data_ptr())
 
     def c(self):
         return C.byref(self._c)
