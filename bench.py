@@ -484,6 +484,9 @@ def main():
                          "probe; batch: many sets in one launch; serve: request stream")
     ap.add_argument("--n3", type=int, default=2**18)
     ap.add_argument("--n-sets", type=int, default=256)
+    ap.add_argument("--n-req", type=int, default=40)
+    ap.add_argument("--slots", type=int, default=4)
+    ap.add_argument("--serve-n-max", type=int, default=1_000_000)
     ap.add_argument("--prec", default="fp32", choices=["fp32", "fp64"])
     args = ap.parse_args()
 
