@@ -409,6 +409,37 @@ def run_batch(args):
             "prepare_s": t_prep, "solve_all_ms": t_solve * 1e3, "max_abs_diff_vs_alone": worst}
 
 
+def run_refine(args):
+    """Time to a refined solve: factor (FP32 form or FP64) + CG on the dense
+    Theta preconditioned by the factor, 16 right-hand sides to relative
+    residual 1e-10, on a jittered grid small enough for O(N^2) products."""
+    import torch
+
+    from paper_1706_02205_gb300 import kchol as kc
+    n = args.refine_side
+    x = torch.from_numpy(inputs.jittered_grid(n, seed=inputs.seed_for(2, 30))).cuda()
+    b = torch.from_numpy(inputs.rhs(n * n, args.nrhs, seed=inputs.seed_for(2, 31))).cuda()
+    kern = kc.Kernel(args.nu, args.ell)
+    perm, l, xo = kc.order_points(x)
+    pat = kc.build_pattern(xo, l, args.rho)
+    out = {"workload": f"jittered grid {n}x{n} (N={n * n}), Matern-{args.nu} l={args.ell}, rho={args.rho}, "
+                       f"{args.nrhs} rhs, CG on dense Theta to 1e-10", "N": n * n, "nnz": pat.nnz}
+    for name, prec in (("fp32_form", kc.FP32_FORM), ("fp64", kc.FP64)):
+        kc.factor(pat, xo, kern, prec)  # warm-up
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        val, diag, zp = kc.factor(pat, xo, kern, prec)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        xs, it, rr, st = kc.refine(pat, xo, kern, prec, val, diag, perm, b, rtol=1e-10, maxit=500)
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        out[name] = {"factor_ms": (t1 - t0) * 1e3, "refine_ms": (t2 - t1) * 1e3, "total_ms": (t2 - t0) * 1e3,
+                     "iterations": it, "max_true_relres": max(rr), "status": st, "zero_pivots": zp,
+                     "ms_per_iteration": (t2 - t1) * 1e3 / max(1, it)}
+    return out
+
+
 def run_serve(args):
     from paper_1706_02205_gb300 import serve
     return serve.bench(args)
@@ -479,12 +510,13 @@ def main():
     ap.add_argument("--cpu-side", type=int, default=320)
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--traffic", type=float, default=None, help="ncu DRAM bytes per factor launch, if measured")
-    ap.add_argument("--workload", default="grid2d", choices=["grid2d", "cube3d", "factor", "batch", "serve"],
+    ap.add_argument("--workload", default="grid2d", choices=["grid2d", "cube3d", "factor", "batch", "serve", "refine"],
                     help="grid2d: the headline step (default); cube3d: 3-D factor + PCA; factor: factor-only "
                          "probe; batch: many sets in one launch; serve: request stream")
     ap.add_argument("--n3", type=int, default=2**18)
     ap.add_argument("--n-sets", type=int, default=256)
     ap.add_argument("--n-req", type=int, default=40)
+    ap.add_argument("--refine-side", type=int, default=128)
     ap.add_argument("--slots", type=int, default=4)
     ap.add_argument("--serve-n-max", type=int, default=1_000_000)
     ap.add_argument("--prec", default="fp32", choices=["fp32", "fp64"])
@@ -507,6 +539,8 @@ def main():
         line = run_batch(args)
     elif args.workload == "serve":
         line = run_serve(args)
+    elif args.workload == "refine":
+        line = run_refine(args)
     else:
         line = run_ours(args, rank, world)
     if line is not None:

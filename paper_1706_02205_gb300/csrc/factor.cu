@@ -66,9 +66,19 @@ struct FactorArgs {
     int lanes;  // lanes per row, 0 = from |R_i|
 };
 
-__device__ __forceinline__ unsigned n_tasks_of(const int64_t* __restrict__ colptr, int k, int rpt) {
-    int64_t m = colptr[k + 1] - colptr[k] - 1;  // rows below the diagonal
-    return m <= 0 ? 1u : (unsigned)((m + rpt - 1) / rpt);
+// Rows of column k handled by one task.  Adaptive (the factor): at least a
+// quarter of |R_k|, because every task re-stages row k, so a long row should
+// not be staged again for every few rows below it.
+__device__ __forceinline__ int rows_of_task(const int64_t* __restrict__ rowptr, int k, int rpt, int adaptive) {
+    if (!adaptive) return rpt;
+    const int nr = (int)(rowptr[k + 1] - rowptr[k] - 1);
+    return max(rpt, nr >> 2);
+}
+__device__ __forceinline__ unsigned n_tasks_of(const int64_t* __restrict__ colptr, const int64_t* __restrict__ rowptr,
+                                               int k, int rpt, int adaptive) {
+    const int64_t m = colptr[k + 1] - colptr[k] - 1;  // rows below the diagonal
+    const int r = rows_of_task(rowptr, k, rpt, adaptive);
+    return m <= 0 ? 1u : (unsigned)((m + r - 1) / r);
 }
 
 __device__ __forceinline__ int hslot(int k, int hbits) { return (int)(((unsigned)k * 2654435761u) >> (32 - hbits)); }
@@ -212,7 +222,7 @@ __global__ void __launch_bounds__(256) ichol_persistent_k(FactorArgs<T> A) {
         __syncwarp();
 
         // ---- row i into the hash table; pivot in FP64
-        const bool staged = 2 * nr <= H;
+        const bool staged = 4 * nr <= 3 * H;  // load factor <= 3/4
         if (staged)
             for (int s = lane; s < H; s += 32) hkey[s] = -1;
         __syncwarp();
@@ -246,8 +256,9 @@ __global__ void __launch_bounds__(256) ichol_persistent_k(FactorArgs<T> A) {
         else
             while (G < 32 && 32 * G <= nr) G <<= 1;  // about 32+ prefix entries per lane-group step
         const int ng = 32 / G, g = lane / G, sub = lane % G;
-        const int64_t qs = A.colptr[i] + 1 + (int64_t)c * A.rpt;
-        const int64_t qe = min(A.colptr[i + 1], qs + A.rpt);
+        const int rows = rows_of_task(A.rowptr, i, A.rpt, 1);
+        const int64_t qs = A.colptr[i] + 1 + (int64_t)c * rows;
+        const int64_t qe = min(A.colptr[i + 1], qs + rows);
         for (int64_t q0 = qs; q0 < qe; q0 += ng) {
             const int64_t q = q0 + g;
             const bool act = q < qe;
@@ -303,16 +314,18 @@ __global__ void __launch_bounds__(256) ichol_persistent_k(FactorArgs<T> A) {
 }
 
 // done[k] = -(tasks of column k), as an unsigned word
-__global__ void done_init_k(const int64_t* __restrict__ colptr, int64_t N, int rpt, unsigned* __restrict__ done) {
+__global__ void done_init_k(const int64_t* __restrict__ colptr, const int64_t* __restrict__ rowptr, int64_t N, int rpt,
+                            unsigned* __restrict__ done) {
     int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k < N) done[k] = 0u - n_tasks_of(colptr, (int)k, rpt);
+    if (k < N) done[k] = 0u - n_tasks_of(colptr, rowptr, (int)k, rpt, 1);
 }
 
 // tasks of column order[p]: n_tasks_of(order[p])
-__global__ void task_count_k(const int32_t* __restrict__ order, const int64_t* __restrict__ colptr, int64_t N,
-                             int rpt, int64_t* __restrict__ cnt) {
+__global__ void task_count_k(const int32_t* __restrict__ order, const int64_t* __restrict__ colptr,
+                             const int64_t* __restrict__ rowptr, int64_t N, int rpt, int adaptive,
+                             int64_t* __restrict__ cnt) {
     int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p < N) cnt[p] = n_tasks_of(colptr, order[p], rpt);
+    if (p < N) cnt[p] = n_tasks_of(colptr, rowptr, order[p], rpt, adaptive);
 }
 __global__ void task_fill_k(const int32_t* __restrict__ order, const int64_t* __restrict__ toff, int64_t N,
                             int2* __restrict__ tasks) {
@@ -372,7 +385,7 @@ __global__ void i64_to_i32_k(const int64_t* __restrict__ v, int64_t n, int32_t* 
 // neighbouring points, which share most of their entries, so the row
 // prefixes they read are often still in L2.
 kc_status build_tasks(const kc_pattern* P, int rpt, Arena& A, cudaStream_t s, int2** tasks_out, int64_t* ntasks_out,
-                      int* max_row_out, const double* x, int d) {
+                      int* max_row_out, const double* x, int d, bool adaptive) {
     int64_t N = P->N;
     int64_t* cnt;
     int64_t* toff;
@@ -407,7 +420,8 @@ kc_status build_tasks(const kc_pattern* P, int rpt, Arena& A, cudaStream_t s, in
         KC_CUDA(cudaGetLastError());
         order = ord2;
     }
-    ::kc::note_launch(), task_count_k<<<blocks_for(N, 256), 256, 0, s>>>(order, P->colptr, N, rpt, cnt);
+    ::kc::note_launch(), task_count_k<<<blocks_for(N, 256), 256, 0, s>>>(order, P->colptr, P->rowptr, N, rpt,
+                                                                            adaptive ? 1 : 0, cnt);
     KC_TRY(exclusive_scan_i64(cnt, toff, N, A, s));
     KC_CUDA(cudaMemsetAsync(mr, 0, sizeof(int), s));
     ::kc::note_launch(), max_row_k<<<blocks_for(N, 256), 256, 0, s>>>(P->rowptr, N, mr);
@@ -483,7 +497,8 @@ static kc_status launch_core(const FactorCore& F, T* val, double* diag, cudaStre
     KC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ichol_persistent_k<T, U>, F.warps * 32, smem));
     if (F.ctas > 0 && F.ctas < per_sm) per_sm = F.ctas;
     if (per_sm < 1) per_sm = 1;
-    ::kc::note_launch(), done_init_k<<<blocks_for(F.P.N, 256), 256, 0, s>>>(F.P.colptr, F.P.N, F.rpt, F.done);
+    ::kc::note_launch(), done_init_k<<<blocks_for(F.P.N, 256), 256, 0, s>>>(F.P.colptr, F.P.rowptr, F.P.N, F.rpt,
+                                                                           F.done);
     KC_CUDA(cudaMemsetAsync(F.ticket, 0, sizeof(unsigned long long), s));
     KC_CUDA(cudaMemsetAsync(F.zp, 0, sizeof(unsigned long long), s));
     KC_CUDA(cudaMemsetAsync(F.status, 0, sizeof(int), s));
@@ -531,9 +546,10 @@ static kc_status apply_opts(FactorCore& F, const kc_opts* o) {
 }
 
 static void pick_hash(FactorCore& F) {
-    // hash table: at least twice the longest row (load factor <= 1/2), 128..2048 slots
+    // hash table: at least 4/3 of the longest row (load factor <= 3/4), 128..2048 slots;
+    // longer rows fall back to binary search in global memory
     int hb = 7;
-    while (hb < 11 && (1 << hb) < 2 * F.maxr) ++hb;
+    while (hb < 11 && 3 * (1 << hb) < 4 * F.maxr) ++hb;
     F.hbits = hb;
 }
 
@@ -548,7 +564,7 @@ kc_status factor_impl(const kc_pattern* P, const double* x, int d, const kc_kern
     F.d = d;
     F.x = x;
     Arena A(s);
-    KC_TRY(build_tasks(P, F.rpt, A, s, &F.tasks, &F.ntasks, &F.maxr, x, d));
+    KC_TRY(build_tasks(P, F.rpt, A, s, &F.tasks, &F.ntasks, &F.maxr, x, d, true));
     pick_hash(F);
     KC_TRY(A.get(&F.done, P->N));
     KC_TRY(A.get(&F.ticket, 1));
@@ -610,7 +626,7 @@ kc_status plan_create_impl(const kc_pattern* P, const double* x, int d, const kc
     {
         Arena A(s);
         int2* t;
-        st = build_tasks(P, F.rpt, A, s, &t, &F.ntasks, &F.maxr, x, d);
+        st = build_tasks(P, F.rpt, A, s, &t, &F.ntasks, &F.maxr, x, d, true);
         if (st != KC_OK) return bail(st);
         if ((st = plan_alloc(pl, (void**)&F.tasks, sizeof(int2) * F.ntasks)) != KC_OK) return bail(st);
         if (cudaMemcpyAsync(F.tasks, t, sizeof(int2) * F.ntasks, cudaMemcpyDeviceToDevice, s) != cudaSuccess)

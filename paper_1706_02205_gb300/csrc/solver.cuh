@@ -21,7 +21,7 @@ struct Solver {
 };
 
 kc_status build_tasks(const kc_pattern* P, int rpt, Arena& A, cudaStream_t s, int2** tasks_out, int64_t* ntasks_out,
-                      int* max_row_out, const double* x = nullptr, int d = 0);
+                      int* max_row_out, const double* x = nullptr, int d = 0, bool adaptive = false);
 kc_status solver_init(Solver& S, const kc_pattern* P, int nrhs_cap, const kc_opts* o, Arena& A, cudaStream_t s);
 template <typename T>
 kc_status solver_apply(Solver& S, const T* val, const double* diag, double diag_fallback, const double* rhs,
