@@ -292,19 +292,31 @@ def run_factor_only(args):
     import torch
 
     from paper_1706_02205_gb300 import kchol as kc
-    x = torch.from_numpy(inputs.jittered_grid(args.n_side, seed=inputs.seed_for(2))).cuda()
-    kern = kc.Kernel(args.nu, args.ell)
+    if args.geom == "cube3d":  # the 3-D configuration: 2^18 uniform points, Matern-5/2 l=0.3, nugget, rho=4
+        x = torch.from_numpy(inputs.uniform(args.n3, 3, seed=inputs.seed_for(3))).cuda()
+        kern, rho = kc.Kernel(2.5, 0.3, 1.0, 1e-6), 4.0
+    else:
+        x = torch.from_numpy(inputs.jittered_grid(args.n_side, seed=inputs.seed_for(2))).cuda()
+        kern, rho = kc.Kernel(args.nu, args.ell), args.rho
     perm, l, xo = kc.order_points(x)
-    pat = kc.build_pattern(xo, l, args.rho)
+    pat = kc.build_pattern(xo, l, rho)
     prec = kc.FP64 if args.prec == "fp64" else kc.FP32_FORM
-    ms = []
-    for _ in range(args.steps):
-        kc.factor(pat, xo, kern, prec)
-        torch.cuda.synchronize()
-        ms.append(kc.last_factor_kernel_ms())
-    return {"workload": "factor-only", "n_side": args.n_side, "N": pat.N, "nnz": pat.nnz, "prec": args.prec,
-            "kernel_ms": ms, "algorithmic_bytes": bytes_op(pat.rowptr.cpu().numpy(), pat.N, 2,
-                                                            8 if args.prec == "fp64" else 4)}
+    out = {"workload": f"factor-only {args.geom}", "N": pat.N, "nnz": pat.nnz, "depth": pat.depth, "prec": args.prec,
+           "algorithmic_bytes": bytes_op(pat.rowptr.cpu().numpy(), pat.N, x.shape[1], 8 if args.prec == "fp64" else 4),
+           "runs": []}
+    for rpt in args.rpt:
+        for lanes in args.lanes:
+            for unroll in args.unroll:
+                for adapt in args.adaptive:
+                    o = kc.make_opts(rows_per_task=rpt, lanes_per_row=lanes, unroll=unroll, adaptive_chunks=adapt)
+                    ms = []
+                    for _ in range(args.steps):
+                        _, _, zp = kc.factor(pat, xo, kern, prec, o)
+                        torch.cuda.synchronize()
+                        ms.append(kc.last_factor_kernel_ms())
+                    out["runs"].append({"rpt": rpt, "lanes": lanes, "unroll": unroll, "adaptive": adapt,
+                                        "kernel_ms": min(ms), "zero_pivots": zp})
+    return out
 
 
 def run_cube3d(args):
@@ -515,6 +527,11 @@ def main():
                          "probe; batch: many sets in one launch; serve: request stream")
     ap.add_argument("--n3", type=int, default=2**18)
     ap.add_argument("--n-sets", type=int, default=256)
+    ap.add_argument("--geom", default="grid2d", choices=["grid2d", "cube3d"], help="factor-only probe geometry")
+    ap.add_argument("--rpt", type=int, nargs="*", default=[0], help="factor-only: rows per task (0 = default)")
+    ap.add_argument("--lanes", type=int, nargs="*", default=[0], help="factor-only: lanes per row (0 = auto)")
+    ap.add_argument("--unroll", type=int, nargs="*", default=[0], help="factor-only: staging depth (0 = 4)")
+    ap.add_argument("--adaptive", type=int, nargs="*", default=[0], help="factor-only: adaptive chunks")
     ap.add_argument("--n-req", type=int, default=40)
     ap.add_argument("--refine-side", type=int, default=128)
     ap.add_argument("--slots", type=int, default=4)

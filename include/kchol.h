@@ -99,6 +99,7 @@ typedef struct {
                                       ready, so a wait on it runs out (KC_ETIMEOUT) */
     int32_t lanes_per_row;         /* factor: lanes merging one row (1,2,4,..,32); 0 -> from |R_i| */
     int32_t unroll;                /* factor: (col, val) loads staged ahead per lane, 4 or 8; 0 -> 4 */
+    int32_t adaptive_chunks;       /* factor: nonzero -> a task takes at least |R_i|/4 rows */
 } kc_opts;
 
 const char* kc_last_error(void);

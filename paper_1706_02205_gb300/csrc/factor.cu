@@ -64,6 +64,7 @@ struct FactorArgs {
     int hold_col;
     int hbits;  // hash table of 2^hbits slots per warp
     int lanes;  // lanes per row, 0 = from |R_i|
+    int adaptive;  // chunk of at least |R_i|/4 rows
 };
 
 // Rows of column k handled by one task.  Adaptive (the factor): at least a
@@ -222,7 +223,7 @@ __global__ void __launch_bounds__(256) ichol_persistent_k(FactorArgs<T> A) {
         __syncwarp();
 
         // ---- row i into the hash table; pivot in FP64
-        const bool staged = 4 * nr <= 3 * H;  // load factor <= 3/4
+        const bool staged = 2 * nr <= H;  // load factor <= 1/2 (linear-probing misses stay short)
         if (staged)
             for (int s = lane; s < H; s += 32) hkey[s] = -1;
         __syncwarp();
@@ -256,7 +257,7 @@ __global__ void __launch_bounds__(256) ichol_persistent_k(FactorArgs<T> A) {
         else
             while (G < 32 && 32 * G <= nr) G <<= 1;  // about 32+ prefix entries per lane-group step
         const int ng = 32 / G, g = lane / G, sub = lane % G;
-        const int rows = rows_of_task(A.rowptr, i, A.rpt, 1);
+        const int rows = rows_of_task(A.rowptr, i, A.rpt, A.adaptive);
         const int64_t qs = A.colptr[i] + 1 + (int64_t)c * rows;
         const int64_t qe = min(A.colptr[i + 1], qs + rows);
         for (int64_t q0 = qs; q0 < qe; q0 += ng) {
@@ -315,9 +316,9 @@ __global__ void __launch_bounds__(256) ichol_persistent_k(FactorArgs<T> A) {
 
 // done[k] = -(tasks of column k), as an unsigned word
 __global__ void done_init_k(const int64_t* __restrict__ colptr, const int64_t* __restrict__ rowptr, int64_t N, int rpt,
-                            unsigned* __restrict__ done) {
+                            int adaptive, unsigned* __restrict__ done) {
     int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k < N) done[k] = 0u - n_tasks_of(colptr, rowptr, (int)k, rpt, 1);
+    if (k < N) done[k] = 0u - n_tasks_of(colptr, rowptr, (int)k, rpt, adaptive);
 }
 
 // tasks of column order[p]: n_tasks_of(order[p])
@@ -459,7 +460,7 @@ struct FactorCore {
     KernelParams kp;
     const int32_t* col_set = nullptr;
     KernelParams* kps = nullptr;
-    int rpt = 64, lanes = 0, unroll = 4, warps = 8, hbits = 7, ctas = 0;
+    int rpt = 64, lanes = 0, unroll = 4, warps = 8, hbits = 7, ctas = 0, adaptive = 0;
     long long spin = 4000000000LL;
     int hold = -1;
 };
@@ -491,6 +492,7 @@ static kc_status launch_core(const FactorCore& F, T* val, double* diag, cudaStre
     a.hold_col = F.hold;
     a.hbits = F.hbits;
     a.lanes = F.lanes;
+    a.adaptive = F.adaptive;
     const size_t smem = (size_t)F.warps * (1 << F.hbits) * (sizeof(int) + sizeof(T));
     KC_CUDA(cudaFuncSetAttribute(ichol_persistent_k<T, U>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
@@ -498,7 +500,7 @@ static kc_status launch_core(const FactorCore& F, T* val, double* diag, cudaStre
     if (F.ctas > 0 && F.ctas < per_sm) per_sm = F.ctas;
     if (per_sm < 1) per_sm = 1;
     ::kc::note_launch(), done_init_k<<<blocks_for(F.P.N, 256), 256, 0, s>>>(F.P.colptr, F.P.rowptr, F.P.N, F.rpt,
-                                                                           F.done);
+                                                                           F.adaptive, F.done);
     KC_CUDA(cudaMemsetAsync(F.ticket, 0, sizeof(unsigned long long), s));
     KC_CUDA(cudaMemsetAsync(F.zp, 0, sizeof(unsigned long long), s));
     KC_CUDA(cudaMemsetAsync(F.status, 0, sizeof(int), s));
@@ -541,15 +543,16 @@ static kc_status apply_opts(FactorCore& F, const kc_opts* o) {
         F.lanes = L;
     }
     F.unroll = (o && o->unroll > 0) ? o->unroll : 4;
+    F.adaptive = (o && o->adaptive_chunks) ? 1 : 0;
     if (F.unroll != 4 && F.unroll != 8) return fail(KC_EINVAL, "unroll must be 4 or 8");
     return KC_OK;
 }
 
 static void pick_hash(FactorCore& F) {
-    // hash table: at least 4/3 of the longest row (load factor <= 3/4), 128..2048 slots;
+    // hash table: at least twice the longest row (load factor <= 1/2), 128..2048 slots;
     // longer rows fall back to binary search in global memory
     int hb = 7;
-    while (hb < 11 && 3 * (1 << hb) < 4 * F.maxr) ++hb;
+    while (hb < 11 && (1 << hb) < 2 * F.maxr) ++hb;
     F.hbits = hb;
 }
 
@@ -564,7 +567,7 @@ kc_status factor_impl(const kc_pattern* P, const double* x, int d, const kc_kern
     F.d = d;
     F.x = x;
     Arena A(s);
-    KC_TRY(build_tasks(P, F.rpt, A, s, &F.tasks, &F.ntasks, &F.maxr, x, d, true));
+    KC_TRY(build_tasks(P, F.rpt, A, s, &F.tasks, &F.ntasks, &F.maxr, x, d, F.adaptive != 0));
     pick_hash(F);
     KC_TRY(A.get(&F.done, P->N));
     KC_TRY(A.get(&F.ticket, 1));
@@ -626,7 +629,7 @@ kc_status plan_create_impl(const kc_pattern* P, const double* x, int d, const kc
     {
         Arena A(s);
         int2* t;
-        st = build_tasks(P, F.rpt, A, s, &t, &F.ntasks, &F.maxr, x, d, true);
+        st = build_tasks(P, F.rpt, A, s, &t, &F.ntasks, &F.maxr, x, d, F.adaptive != 0);
         if (st != KC_OK) return bail(st);
         if ((st = plan_alloc(pl, (void**)&F.tasks, sizeof(int2) * F.ntasks)) != KC_OK) return bail(st);
         if (cudaMemcpyAsync(F.tasks, t, sizeof(int2) * F.ntasks, cudaMemcpyDeviceToDevice, s) != cudaSuccess)

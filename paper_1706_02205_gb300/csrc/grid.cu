@@ -150,4 +150,60 @@ kc_status bbox(const double* x, int64_t N, int d, double* lo, double* hi, Arena&
     return KC_OK;
 }
 
+// per-block min and max of every coordinate
+__global__ void bbox_all_k(const double* __restrict__ x, int64_t N, int d, double* __restrict__ part) {
+    __shared__ double smin[8], smax[8];
+    for (int t = 0; t < d; ++t) {
+        double mn = INFINITY, mx = -INFINITY;
+        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+            const double v = x[i * d + t];
+            mn = fmin(mn, v);
+            mx = fmax(mx, v);
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            mn = fmin(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+            mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        }
+        if (lane_id() == 0) {
+            smin[threadIdx.x >> 5] = mn;
+            smax[threadIdx.x >> 5] = mx;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
+                mn = fmin(mn, smin[w]);
+                mx = fmax(mx, smax[w]);
+            }
+            part[(blockIdx.x * d + t) * 2] = mn;
+            part[(blockIdx.x * d + t) * 2 + 1] = mx;
+        }
+        __syncthreads();
+    }
+}
+
+kc_status bbox_all(const double* x, int64_t N, int d, Origin* lo, double* E, Arena& A, cudaStream_t s) {
+    if (d > MAXD) return fail(KC_EINVAL, "d must be <= 32");
+    const int nb = 64;
+    double* part;
+    KC_TRY(A.get(&part, (size_t)nb * d * 2));
+    ::kc::note_launch(), bbox_all_k<<<nb, 256, 0, s>>>(x, N, d, part);
+    KC_CUDA(cudaGetLastError());
+    double h[nb * MAXD * 2];
+    KC_CUDA(cudaMemcpyAsync(h, part, sizeof(double) * nb * d * 2, cudaMemcpyDeviceToHost, s));
+    KC_CUDA(cudaStreamSynchronize(s));
+    double e = 0.0;
+    for (int t = 0; t < MAXD; ++t) lo->lo[t] = 0.0;
+    for (int t = 0; t < d; ++t) {
+        double mn = INFINITY, mx = -INFINITY;
+        for (int b = 0; b < nb; ++b) {
+            mn = fmin(mn, h[(b * d + t) * 2]);
+            mx = fmax(mx, h[(b * d + t) * 2 + 1]);
+        }
+        lo->lo[t] = mn;
+        e = fmax(e, mx - mn);
+    }
+    *E = e;
+    return KC_OK;
+}
+
 }  // namespace kc

@@ -91,4 +91,12 @@ kc_status grid_build(const Grid& g, const double* x, int d, const int32_t* ids, 
 // Bounding box of x (row-major N x d) over the first min(d,3) axes; host out.
 kc_status bbox(const double* x, int64_t N, int d, double* lo, double* hi, Arena& A, cudaStream_t s);
 
+// Bounding box over all d <= 32 axes (host out), for the float copies used by
+// the FP32 distance screens; E = the largest extent.
+constexpr int MAXD = 32;
+struct Origin {
+    double lo[MAXD];
+};
+kc_status bbox_all(const double* x, int64_t N, int d, Origin* lo, double* E, Arena& A, cudaStream_t s);
+
 }  // namespace kc

@@ -54,13 +54,13 @@ kc_status check_finite(const double* x, int64_t n, Arena& A, cudaStream_t s) {
 // state in grid order (gpos): coordinates xg, original index idg, v2, stat
 __global__ void ord_init_k(const double* __restrict__ x, int d, const int32_t* __restrict__ gsorted, int64_t N,
                            double* __restrict__ xg, int32_t* __restrict__ idg, double* __restrict__ v2,
-                           int* __restrict__ stat, Grid g, float* __restrict__ xgf) {
+                           int* __restrict__ stat, Origin org, float* __restrict__ xgf) {
     int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= N) return;
     int64_t id = gsorted[q];
     for (int t = 0; t < d; ++t) {
         xg[q * d + t] = x[id * d + t];
-        if (xgf) xgf[q * d + t] = (float)(x[id * d + t] - g.lo[t]);
+        if (xgf) xgf[q * d + t] = (float)(x[id * d + t] - org.lo[t]);
     }
     idg[q] = (int32_t)id;
     if (id == 0) {
@@ -378,14 +378,12 @@ kc_status order_impl(const double* x, int64_t N, int d, int32_t* perm, double* l
     // float copy of the coordinates (minus the box corner) for FP32 screens of
     // the distance tests; exact FP64 tests decide every close call
     float* xgf = nullptr;
-    float delta = 0.f;
-    if (d <= 3) {
-        double E = 0.0;
-        for (int t = 0; t < d; ++t) E = fmax(E, hi[t] - lo[t]);
-        delta = (float)(E * 1.1920928955078125e-07);  // 2^-23 E
-        KC_TRY(A.get(&xgf, N * d));
-    }
-    ::kc::note_launch(), ord_init_k<<<blocks_for(N, 256), 256, 0, s>>>(x, d, gsorted, N, xg, idg, v2, stat, g0, xgf);
+    Origin org;
+    double E = 0.0;
+    KC_TRY(bbox_all(x, N, d, &org, &E, A, s));
+    const float delta = (float)(E * 1.1920928955078125e-07);  // 2^-23 E
+    KC_TRY(A.get(&xgf, N * d));
+    ::kc::note_launch(), ord_init_k<<<blocks_for(N, 256), 256, 0, s>>>(x, d, gsorted, N, xg, idg, v2, stat, org, xgf);
     KC_CUDA(cudaGetLastError());
     int64_t item_cap = 0;
     item_sel = nullptr;

@@ -34,7 +34,8 @@ struct PatArgs {
     const int64_t* off;    // item offsets per column
     const int32_t* item_col;
     int64_t nitems;
-    const float* xsf;      // float copy of xs minus the grid origin (d <= 3), else NULL
+    const float* xsf;      // float copy of xs minus the box corner
+    const float* xof;      // the same by position
     float delta;           // error bound of one float coordinate difference
     const int4* colbox;    // search box of every column (query_box)
 };
@@ -86,16 +87,14 @@ __global__ void pat_scan_k(PatArgs P, int* __restrict__ cnt, const int64_t* __re
     const int cz = lo[2] + (int)(r / ny);
     const int64_t base = ((int64_t)cz * P.g.n[1] + cy) * P.g.n[0];
     const int64_t a = P.cstart[base + lo[0]], b = P.cstart[base + hi[0] + 1];
-    float xif[3] = {0.f, 0.f, 0.f};
-    if (P.xsf)
-        for (int t = 0; t < P.d; ++t) xif[t] = (float)(xi[t] - P.g.lo[t]);
+    const float* xif = P.xof + (int64_t)i * P.d;
     for (int64_t q = a + lane; q < b; q += 32) {
         const int j = P.ps[q];
         if (j <= i) continue;
         const double Rj = P.rule == KC_RULE_MIN ? col_radius(P.rho, P.l[j]) : R;
         if (!isinf(Rj)) {
             // FP32 screen first; the exact FP64 test only near the boundary
-            const int sc = P.xsf ? screen_f32(P.xsf + q * P.d, xif, P.d, (float)Rj, P.delta) : -1;
+            const int sc = screen_f32(P.xsf + q * P.d, xif, P.d, (float)Rj, P.delta);
             if (sc == 0) continue;
             if (sc < 0 && !in_s(dist2_exact(P.xs + q * P.d, xi, P.d), Rj)) continue;
         }
@@ -109,13 +108,14 @@ __global__ void pat_scan_k(PatArgs P, int* __restrict__ cnt, const int64_t* __re
 }
 
 __global__ void pat_gather_k(const double* __restrict__ xo, const int32_t* __restrict__ gs, int64_t N, int d,
-                             Grid g, double* __restrict__ xs, float* __restrict__ xsf) {
+                             Origin org, double* __restrict__ xs, float* __restrict__ xsf, float* __restrict__ xof) {
     int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (q < N)
         for (int t = 0; t < d; ++t) {
             const double v = xo[(int64_t)gs[q] * d + t];
             xs[q * d + t] = v;
-            if (xsf) xsf[q * d + t] = (float)(v - g.lo[t]);
+            xsf[q * d + t] = (float)(v - org.lo[t]);
+            xof[q * d + t] = (float)(xo[q * d + t] - org.lo[t]);
         }
 }
 __global__ void plus_one_k(const int* __restrict__ c, int64_t N, int32_t* __restrict__ out) {
@@ -134,6 +134,7 @@ struct PatSetup {
     int64_t nitems;
     int4* colbox = nullptr;
     float* xsf = nullptr;
+    float* xof = nullptr;
     float delta = 0.f;
 };
 
@@ -143,17 +144,17 @@ static kc_status pat_setup(const double* xo, const double* l, int64_t N, int d, 
     double lo[3], hi[3];
     KC_TRY(bbox(xo, N, d, lo, hi, A, s));
     S.g = make_grid(d, lo, hi, N, 0.0, N / 2 > 1 ? N / 2 : 1);
-    if (d <= 3) {
-        double E = 0.0;
-        for (int t = 0; t < d; ++t) E = fmax(E, hi[t] - lo[t]);
-        S.delta = (float)(E * 1.1920928955078125e-07);  // 2^-23 E
-        KC_TRY(A.get(&S.xsf, N * d));
-    }
+    Origin org;
+    double E = 0.0;
+    KC_TRY(bbox_all(xo, N, d, &org, &E, A, s));
+    S.delta = (float)(E * 1.1920928955078125e-07);  // 2^-23 E
+    KC_TRY(A.get(&S.xsf, N * d));
+    KC_TRY(A.get(&S.xof, N * d));
     KC_TRY(A.get(&S.gs, N));
     KC_TRY(A.get(&S.cstart, S.g.ncells + 1));
     KC_TRY(grid_build(S.g, xo, d, nullptr, N, S.gs, S.cstart, A, s));
     KC_TRY(A.get(&S.xs, N * d));
-    ::kc::note_launch(), pat_gather_k<<<blocks_for(N, 256), 256, 0, s>>>(xo, S.gs, N, d, S.g, S.xs, S.xsf);
+    ::kc::note_launch(), pat_gather_k<<<blocks_for(N, 256), 256, 0, s>>>(xo, S.gs, N, d, org, S.xs, S.xsf, S.xof);
     int64_t* cnt;
     KC_TRY(A.get(&cnt, N));
     KC_TRY(A.get(&S.off, N + 1));
@@ -184,6 +185,7 @@ static PatArgs pat_args(const PatSetup& S, const double* xo, const double* l, in
     P.item_col = S.item_col;
     P.nitems = S.nitems;
     P.xsf = S.xsf;
+    P.xof = S.xof;
     P.delta = S.delta;
     P.colbox = S.colbox;
     return P;

@@ -83,6 +83,18 @@ def test_pattern_bit_exact(N, d, rho, rule):
     assert np.array_equal(H(col), col_ref)
 
 
+@pytest.mark.parametrize("rho,rule", [(3.0, 0), (4.0, 1)])
+def test_pattern_bit_exact_swiss_roll_r20(rho, rule):
+    """Ambient dimension 20: the grid uses three coordinates, distances all 20."""
+    x = inputs.swiss_roll(1500, seed=61)
+    p_ref, l_ref = oracle.maximin_brute(x)
+    xo = x[p_ref]
+    rp_ref, col_ref = oracle.pattern(xo, l_ref, rho, rule)
+    rowptr, nnz = kc.pattern_count(T(xo), T(l_ref), rho, rule)
+    col = kc.pattern_fill(T(xo), T(l_ref), rho, rowptr, nnz, rule)
+    assert np.array_equal(H(rowptr), rp_ref) and np.array_equal(H(col), col_ref)
+
+
 def test_pattern_duplicates_and_ties():
     g = np.stack(np.meshgrid(np.arange(23.0), np.arange(19.0), indexing="ij"), -1).reshape(-1, 2)
     g = np.concatenate([g, g[:40]])
