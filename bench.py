@@ -530,7 +530,7 @@ def main():
     ap.add_argument("--geom", default="grid2d", choices=["grid2d", "cube3d"], help="factor-only probe geometry")
     ap.add_argument("--rpt", type=int, nargs="*", default=[0], help="factor-only: rows per task (0 = default)")
     ap.add_argument("--lanes", type=int, nargs="*", default=[0], help="factor-only: lanes per row (0 = auto)")
-    ap.add_argument("--unroll", type=int, nargs="*", default=[0], help="factor-only: staging depth (0 = 4)")
+    ap.add_argument("--unroll", type=int, nargs="*", default=[0], help="factor-only: staging depth (0 = 8)")
     ap.add_argument("--adaptive", type=int, nargs="*", default=[0], help="factor-only: adaptive chunks")
     ap.add_argument("--n-req", type=int, default=40)
     ap.add_argument("--refine-side", type=int, default=128)

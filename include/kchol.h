@@ -98,7 +98,7 @@ typedef struct {
     int32_t test_hold_column;      /* test hook: 0 = off; c+1 makes column c never signal
                                       ready, so a wait on it runs out (KC_ETIMEOUT) */
     int32_t lanes_per_row;         /* factor: lanes merging one row (1,2,4,..,32); 0 -> from |R_i| */
-    int32_t unroll;                /* factor: (col, val) loads staged ahead per lane, 4 or 8; 0 -> 4 */
+    int32_t unroll;                /* factor: (col, val) loads staged ahead per lane, 4 or 8; 0 -> 8 */
     int32_t adaptive_chunks;       /* factor: nonzero -> a task takes at least |R_i|/4 rows */
 } kc_opts;
 

@@ -43,6 +43,8 @@ class BatchFactor:
 
     def __init__(self, xs, kerns, rho, prec=kc.FP32_FORM, opts=None, n_streams=8, prepared=None):
         self.kerns = list(kerns)
+        if len({(k.sigma2, k.nugget) for k in self.kerns}) > 1:
+            raise ValueError("the sets of a batch share sigma2 and nugget (nu and ell may differ)")
         self.prec = prec
         self.sets = prepared if prepared is not None else prepare_sets(xs, rho, n_streams)
         self.Ns = [s["perm"].numel() for s in self.sets]
@@ -90,5 +92,6 @@ class BatchFactor:
 
     def solve(self, b):
         """Solve every set at once: b is (nrhs, sum N) in the concatenated
-        original order."""
+        original order.  A dropped pivot is replaced by sqrt(sigma2 + nugget),
+        which the sets share (they may differ in nu and ell)."""
         return kc.solve(self.pat, self.prec, self.val, self.diag, self.kerns[0], self.perm, b)

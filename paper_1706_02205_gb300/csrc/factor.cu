@@ -84,17 +84,73 @@ __device__ __forceinline__ unsigned n_tasks_of(const int64_t* __restrict__ colpt
 
 __device__ __forceinline__ int hslot(int k, int hbits) { return (int)(((unsigned)k * 2654435761u) >> (32 - hbits)); }
 
-// slot of key k in the table, or -1
-__device__ __forceinline__ int hfind(const int* hkey, int hbits, int k) {
-    const int mask = (1 << hbits) - 1;
-    int h = hslot(k, hbits);
-    for (;;) {
-        const int x = hkey[h];
-        if (x == k) return h;
-        if (x < 0) return -1;
-        h = (h + 1) & mask;
+// Open-addressing table (linear probing) of one row i in shared memory: key
+// k in R_i -> L_ik.  FP32: one 8-byte slot per key (key in the low word, the
+// value's bits in the high word), so a probe is a single shared load.  FP64:
+// an array of values followed by an array of keys.  Empty slots have key -1.
+template <typename T>
+struct RowTable;
+template <>
+struct RowTable<float> {
+    unsigned long long* s;
+    int hbits;  // 2^hbits slots
+    __device__ __forceinline__ RowTable(unsigned char* base, int hb) : s((unsigned long long*)base), hbits(hb) {}
+    __device__ __forceinline__ void clear(int lane) {
+        uint4* q = (uint4*)s;
+        for (int h = lane; h < (1 << (hbits - 1)); h += 32) q[h] = make_uint4(~0u, ~0u, ~0u, ~0u);
     }
-}
+    __device__ __forceinline__ void insert(int k, float v) {
+        const int mask = (1 << hbits) - 1;
+        const unsigned long long w = ((unsigned long long)__float_as_uint(v) << 32) | (unsigned)k;
+        int h = hslot(k, hbits);
+        while (atomicCAS(&s[h], ~0ull, w) != ~0ull) h = (h + 1) & mask;
+    }
+    __device__ __forceinline__ bool find(int k, float& v) const {
+        const int mask = (1 << hbits) - 1;
+        int h = hslot(k, hbits);
+        for (;;) {
+            const unsigned long long w = s[h];
+            const int key = (int)(unsigned)w;
+            if (key == k) {
+                v = __uint_as_float((unsigned)(w >> 32));
+                return true;
+            }
+            if (key < 0) return false;
+            h = (h + 1) & mask;
+        }
+    }
+};
+template <>
+struct RowTable<double> {
+    double* val;
+    int* key;
+    int hbits;
+    __device__ __forceinline__ RowTable(unsigned char* base, int hb)
+        : val((double*)base), key((int*)(val + (1 << hb))), hbits(hb) {}
+    __device__ __forceinline__ void clear(int lane) {
+        int4* q = (int4*)key;
+        for (int h = lane; h < (1 << (hbits - 2)); h += 32) q[h] = make_int4(-1, -1, -1, -1);
+    }
+    __device__ __forceinline__ void insert(int k, double v) {
+        const int mask = (1 << hbits) - 1;
+        int h = hslot(k, hbits);
+        while (atomicCAS(&key[h], -1, k) != -1) h = (h + 1) & mask;
+        val[h] = v;
+    }
+    __device__ __forceinline__ bool find(int k, double& v) const {
+        const int mask = (1 << hbits) - 1;
+        int h = hslot(k, hbits);
+        for (;;) {
+            const int x = key[h];
+            if (x == k) {
+                v = val[h];
+                return true;
+            }
+            if (x < 0) return false;
+            h = (h + 1) & mask;
+        }
+    }
+};
 
 __device__ __forceinline__ int64_t bsearch_glob(const int32_t* __restrict__ a, int64_t lo, int64_t hi, int k) {
     int64_t end = hi;
@@ -187,14 +243,18 @@ __device__ __forceinline__ bool wait_done(const unsigned* f, const int* status, 
     return true;
 }
 
+// Resident CTAs of 8 warps per SM that the register budget is cut for.
+#ifndef KC_FACTOR_MIN_BLOCKS
+#define KC_FACTOR_MIN_BLOCKS 4
+#endif
+
 template <typename T, int U>
-__global__ void __launch_bounds__(256) ichol_persistent_k(FactorArgs<T> A) {
+__global__ void __launch_bounds__(256, KC_FACTOR_MIN_BLOCKS) ichol_persistent_k(FactorArgs<T> A) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = lane_id();
     const int w = threadIdx.x >> 5;
     const int H = 1 << A.hbits;
-    int* hkey = (int*)(smem + (size_t)w * H * (sizeof(int) + sizeof(T)));
-    T* hval = (T*)(hkey + H);
+    RowTable<T> tab(smem + (size_t)w * H * (sizeof(int) + sizeof(T)), A.hbits);
     const unsigned FULL = 0xffffffffu;
 
     for (;;) {
@@ -222,20 +282,14 @@ __global__ void __launch_bounds__(256) ichol_persistent_k(FactorArgs<T> A) {
         __threadfence();
         __syncwarp();
 
-        // ---- row i into the hash table; pivot in FP64
+        // ---- row i into the table; pivot in FP64
         const bool staged = 2 * nr <= H;  // load factor <= 1/2 (linear-probing misses stay short)
-        if (staged)
-            for (int s = lane; s < H; s += 32) hkey[s] = -1;
+        if (staged) tab.clear(lane);
         __syncwarp();
         double ps = 0.0;
         for (int e = lane; e < nr; e += 32) {
             const T v = ldcg(&A.val[a0 + e]);
-            if (staged) {
-                const int k = __ldg(&A.col[a0 + e]);
-                int h = hslot(k, A.hbits);
-                while (atomicCAS(&hkey[h], -1, k) != -1) h = (h + 1) & (H - 1);
-                hval[h] = v;
-            }
+            if (staged) tab.insert(__ldg(&A.col[a0 + e]), v);
             ps = fma((double)v, (double)v, ps);
         }
         ps = warp_sum(ps);
@@ -251,7 +305,10 @@ __global__ void __launch_bounds__(256) ichol_persistent_k(FactorArgs<T> A) {
         }
         const double* xi = A.x + (int64_t)i * A.d;
 
-        // ---- rows of this chunk: groups of G lanes, one row per group
+        // ---- rows j of this chunk, in batches of 32.  First every lane fetches
+        // one row's bookkeeping (j, the slot of L_ji, the start of row j) and
+        // evaluates its Theta_ji, so these dependent loads and the exponential
+        // overlap across the batch; then groups of G lanes merge one row each.
         int G = 1;
         if (A.lanes > 0) G = A.lanes;
         else
@@ -260,50 +317,55 @@ __global__ void __launch_bounds__(256) ichol_persistent_k(FactorArgs<T> A) {
         const int rows = rows_of_task(A.rowptr, i, A.rpt, A.adaptive);
         const int64_t qs = A.colptr[i] + 1 + (int64_t)c * rows;
         const int64_t qe = min(A.colptr[i + 1], qs + rows);
-        for (int64_t q0 = qs; q0 < qe; q0 += ng) {
-            const int64_t q = q0 + g;
-            const bool act = q < qe;
-            Acc<T> acc;
-            int j = 0;
-            int64_t bij = 0;
-            if (act) {
-                j = __ldg(&A.rowidx[q]);
-                bij = __ldg(&A.slot[q]);
+        for (int64_t b0 = qs; b0 < qe; b0 += 32) {
+            const int nb = (int)min((int64_t)32, qe - b0);
+            int64_t my_e0 = 0, my_b = 0;
+            T my_th = (T)0;
+            if (lane < nb) {
+                const int j = __ldg(&A.rowidx[b0 + lane]);
+                my_b = __ldg(&A.slot[b0 + lane]);
+                my_e0 = __ldg(&A.rowptr[j]);
+                if (!zero) my_th = theta_off<T>(kp, A.d, A.x + (int64_t)j * A.d, xi);
             }
-            if (act && !zero) {
-                int64_t e = __ldg(&A.rowptr[j]) + sub;
-                if (staged) {
-                    for (; e + (U - 1) * G < bij; e += U * G) {
-                        int k[U];
-                        T wv[U];
+            for (int r0 = 0; r0 < nb; r0 += ng) {
+                const int r = r0 + g;
+                const bool act = r < nb;
+                const int src = act ? r : 0;
+                const int64_t es = __shfl_sync(FULL, my_e0, src);
+                const int64_t be = __shfl_sync(FULL, my_b, src);  // L_ji lives at be; the prefix is [es, be)
+                const T th = __shfl_sync(FULL, my_th, src);
+                Acc<T> acc;
+                if (act && !zero) {
+                    if (staged) {
+                        // U pairs per lane in flight; the ragged end is masked, not looped
+                        for (int64_t e = es + sub; e < be; e += U * G) {
+                            int k[U];
+                            T wv[U];
 #pragma unroll
-                        for (int u = 0; u < U; ++u) k[u] = __ldg(&A.col[e + u * G]);
+                            for (int u = 0; u < U; ++u) {
+                                const int64_t q = e + u * G;
+                                k[u] = q < be ? __ldg(&A.col[q]) : -1;
+                            }
 #pragma unroll
-                        for (int u = 0; u < U; ++u) wv[u] = ldcg(&A.val[e + u * G]);
+                            for (int u = 0; u < U; ++u) {
+                                const int64_t q = e + u * G;
+                                wv[u] = q < be ? ldcg(&A.val[q]) : (T)0;
+                            }
 #pragma unroll
-                        for (int u = 0; u < U; ++u) {
-                            const int h = hfind(hkey, A.hbits, k[u]);
-                            if (h >= 0) acc.add(wv[u], hval[h]);
+                            for (int u = 0; u < U; ++u) {
+                                T hv;
+                                if (k[u] >= 0 && tab.find(k[u], hv)) acc.add(wv[u], hv);
+                            }
+                        }
+                    } else {
+                        for (int64_t e = es + sub; e < be; e += G) {
+                            const int64_t pos = bsearch_glob(A.col, a0, a1, __ldg(&A.col[e]));
+                            if (pos >= 0) acc.add(ldcg(&A.val[e]), ldcg(&A.val[pos]));
                         }
                     }
-                    for (; e < bij; e += G) {
-                        const int k0 = __ldg(&A.col[e]);
-                        const T w0 = ldcg(&A.val[e]);
-                        const int h0 = hfind(hkey, A.hbits, k0);
-                        if (h0 >= 0) acc.add(w0, hval[h0]);
-                    }
-                } else {
-                    for (; e < bij; e += G) {
-                        const int64_t pos = bsearch_glob(A.col, a0, a1, __ldg(&A.col[e]));
-                        if (pos >= 0) acc.add(ldcg(&A.val[e]), ldcg(&A.val[pos]));
-                    }
                 }
-            }
-            acc.group_reduce(G);
-            if (act && sub == 0) {
-                T v = (T)0;
-                if (!zero) v = acc.finish(theta_off<T>(kp, A.d, A.x + (int64_t)j * A.d, xi), Lii, inv);
-                A.val[bij] = v;
+                acc.group_reduce(G);
+                if (act && sub == 0) A.val[be] = zero ? (T)0 : acc.finish(th, Lii, inv);
             }
         }
 
@@ -460,7 +522,7 @@ struct FactorCore {
     KernelParams kp;
     const int32_t* col_set = nullptr;
     KernelParams* kps = nullptr;
-    int rpt = 64, lanes = 0, unroll = 4, warps = 8, hbits = 7, ctas = 0, adaptive = 0;
+    int rpt = 64, lanes = 0, unroll = 8, warps = 8, hbits = 7, ctas = 0, adaptive = 0;
     long long spin = 4000000000LL;
     int hold = -1;
 };
@@ -542,7 +604,7 @@ static kc_status apply_opts(FactorCore& F, const kc_opts* o) {
         if (L > 32 || (L & (L - 1))) return fail(KC_EINVAL, "lanes_per_row must be a power of two <= 32");
         F.lanes = L;
     }
-    F.unroll = (o && o->unroll > 0) ? o->unroll : 4;
+    F.unroll = (o && o->unroll > 0) ? o->unroll : 8;
     F.adaptive = (o && o->adaptive_chunks) ? 1 : 0;
     if (F.unroll != 4 && F.unroll != 8) return fail(KC_EINVAL, "unroll must be 4 or 8");
     return KC_OK;
