@@ -19,6 +19,7 @@ factor does not shard); value = nnz of all ranks / max over ranks of the time.
 from __future__ import annotations
 
 import argparse
+import itertools
 import json
 import os
 import statistics
@@ -304,18 +305,17 @@ def run_factor_only(args):
     out = {"workload": f"factor-only {args.geom}", "N": pat.N, "nnz": pat.nnz, "depth": pat.depth, "prec": args.prec,
            "algorithmic_bytes": bytes_op(pat.rowptr.cpu().numpy(), pat.N, x.shape[1], 8 if args.prec == "fp64" else 4),
            "runs": []}
-    for rpt in args.rpt:
-        for lanes in args.lanes:
-            for unroll in args.unroll:
-                for adapt in args.adaptive:
-                    o = kc.make_opts(rows_per_task=rpt, lanes_per_row=lanes, unroll=unroll, adaptive_chunks=adapt)
-                    ms = []
-                    for _ in range(args.steps):
-                        _, _, zp = kc.factor(pat, xo, kern, prec, o)
-                        torch.cuda.synchronize()
-                        ms.append(kc.last_factor_kernel_ms())
-                    out["runs"].append({"rpt": rpt, "lanes": lanes, "unroll": unroll, "adaptive": adapt,
-                                        "kernel_ms": min(ms), "zero_pivots": zp})
+    for rpt, lanes, unroll, adapt, stage, warps in itertools.product(args.rpt, args.lanes, args.unroll, args.adaptive,
+                                                                     args.stage, args.warps):
+        o = kc.make_opts(rows_per_task=rpt, lanes_per_row=lanes, unroll=unroll, adaptive_chunks=adapt,
+                         stage_bytes=stage, warps_per_cta=warps)
+        ms = []
+        for _ in range(args.steps):
+            _, _, zp = kc.factor(pat, xo, kern, prec, o)
+            torch.cuda.synchronize()
+            ms.append(kc.last_factor_kernel_ms())
+        out["runs"].append({"rpt": rpt, "lanes": lanes, "unroll": unroll, "adaptive": adapt, "stage": stage,
+                            "warps": warps, "kernel_ms": min(ms), "zero_pivots": zp})
     return out
 
 
@@ -532,6 +532,9 @@ def main():
     ap.add_argument("--lanes", type=int, nargs="*", default=[0], help="factor-only: lanes per row (0 = auto)")
     ap.add_argument("--unroll", type=int, nargs="*", default=[0], help="factor-only: staging depth (0 = 8)")
     ap.add_argument("--adaptive", type=int, nargs="*", default=[0], help="factor-only: adaptive chunks")
+    ap.add_argument("--stage", type=int, nargs="*", default=[0],
+                    help="factor-only: stage-buffer bytes (0 = automatic, -1 = register form)")
+    ap.add_argument("--warps", type=int, nargs="*", default=[0], help="factor-only: warps per CTA (0 = default)")
     ap.add_argument("--n-req", type=int, default=40)
     ap.add_argument("--refine-side", type=int, default=128)
     ap.add_argument("--slots", type=int, default=4)

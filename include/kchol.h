@@ -92,14 +92,21 @@ typedef struct {
 /* Options of the persistent kernels (zero-initialise for defaults). */
 typedef struct {
     int64_t spin_limit_cycles;     /* bound of every device wait; 0 -> ~4e9 cycles */
-    int32_t rows_per_task;         /* rows of a column per task; 0 -> 64 */
+    int32_t rows_per_task;         /* rows of a column per task; 0 -> about (nnz - N) / (depth x resident
+                                      warps), a power of two in 16..128 */
     int32_t ctas_per_sm;           /* persistent grid = SMs x this; 0 -> occupancy */
     int32_t warps_per_cta;         /* 0 -> 8 */
     int32_t test_hold_column;      /* test hook: 0 = off; c+1 makes column c never signal
                                       ready, so a wait on it runs out (KC_ETIMEOUT) */
-    int32_t lanes_per_row;         /* factor: lanes merging one row (1,2,4,..,32); 0 -> from |R_i| */
-    int32_t unroll;                /* factor: (col, val) loads staged ahead per lane, 4 or 8; 0 -> 8 */
+    int32_t lanes_per_row;         /* factor: lanes merging one row (1,2,4,..,32); 0 -> 8 (FP32 form) or
+                                      4 (FP64): one 32-byte sector of values per group load */
+    int32_t unroll;                /* factor: (col, val) loads staged ahead per lane, 4, 8 or 16 (16: FP32
+                                      form only; FP64 takes 8); 0 -> FP32 form: 16 when the mean row
+                                      holds >= 400 entries, else 8; FP64: 4 */
     int32_t adaptive_chunks;       /* factor: nonzero -> a task takes at least |R_i|/4 rows */
+    int32_t stage_bytes;           /* factor: <= 0 -> row prefixes loaded into registers (the default);
+                                      > 0 -> bulk form: each warp fills two shared-memory stage buffers of
+                                      this many bytes (<= 65536) with bulk (TMA) copies of row prefixes */
 } kc_opts;
 
 const char* kc_last_error(void);
@@ -165,7 +172,7 @@ kc_status kc_factor(const kc_pattern* pat, const double* x_ord, int32_t d, const
  * with nsets == 1, col_set may be NULL.  x_ord must stay valid while the plan
  * is used.  kc_factor_plan_finish synchronises and reports a timeout or the
  * dropped pivots of the last launch.  kc_factor_plan_tune times every
- * combination of lanes per row {4,8,16,32} and staging depth {4,8} once on the
+ * combination of lanes per row {2,4,8,16} and staging depth {8,16} once on the
  * plan's own problem and keeps the fastest (it overwrites val and diag). */
 typedef struct kc_factor_plan kc_factor_plan;
 kc_status kc_factor_plan_create(const kc_pattern* pat, const double* x_ord, int32_t d, const kc_kernel* kerns,

@@ -111,12 +111,15 @@ __device__ __forceinline__ double matern_f64(double r, int nu_code, double scale
     if (nu_code == 1) return sigma2 * (1.0 + t) * e;
     return sigma2 * (1.0 + t + t * t * (1.0 / 3.0)) * e;
 }
+// roundings pinned with the _rn intrinsics (never contracted), so that every
+// inlined copy gives the same bits
 __device__ __forceinline__ float matern_f32(float r, int nu_code, float scale, float sigma2) {
-    float t = r * scale;
-    float e = expf(-t);
-    if (nu_code == 0) return sigma2 * e;
-    if (nu_code == 1) return sigma2 * (1.0f + t) * e;
-    return sigma2 * (1.0f + t + t * t * (1.0f / 3.0f)) * e;
+    const float t = __fmul_rn(r, scale);
+    const float e = expf(-t);
+    if (nu_code == 0) return __fmul_rn(sigma2, e);
+    if (nu_code == 1) return __fmul_rn(__fmul_rn(sigma2, __fadd_rn(1.0f, t)), e);
+    const float poly = fmaf(__fmul_rn(t, 1.0f / 3.0f), t, __fadd_rn(1.0f, t));
+    return __fmul_rn(__fmul_rn(sigma2, poly), e);
 }
 
 struct KernelParams {

@@ -14,11 +14,21 @@
 // until every column k in R_i has published all its tasks, puts row i
 // (index -> value) into an open-addressing hash table in shared memory,
 // recomputes the pivot, and then merges the prefix of each row j of its chunk
-// (entries k < i) against the table.  Lanes form groups of G; a group owns
-// one row, each lane walks the row with stride G, loading U (col, val) pairs
+// (entries k < i) against the table.  The rows of the chunk go in batches of
+// 32: each lane first fetches one row's bookkeeping and evaluates its
+// Theta_ji from the coordinates (entries are never stored), then lanes form
+// groups of G (one 32-byte sector of values per group load); a group owns one
+// row, each lane walks the row with stride G, loading U (col, val) pairs
 // ahead (the staging depth) so that enough loads are in flight to cover HBM
-// latency.  Theta_ji is evaluated from the coordinates in the kernel (entries
-// are never stored).  The task publishes by a release increment of done[i].
+// latency.  The task publishes by a release increment of done[i].
+//
+// A second form, on request, stages the row prefixes of a batch in shared
+// memory with bulk (TMA) copies into two buffers per warp completing on
+// mbarriers, and merges from there; each lane merges the same entries in the
+// same order as in the first form, so both give the same bits.  On the GB300
+// the per-copy cost of the bulk engine for prefixes of a few hundred bytes
+// makes it the slower form, which is why loads into registers are the
+// default.
 //
 // Several independent point sets can be factored in one launch: their
 // patterns are concatenated block-diagonally and every column names its set,
@@ -32,6 +42,7 @@
 // have smaller ticket numbers and were claimed by running warps, so the
 // earliest unfinished task can always proceed.  Every wait is bounded: when it
 // runs out the kernel records DEV_TIMEOUT in the status word and returns.
+#include <algorithm>
 #include <vector>
 
 #include "grid.cuh"
@@ -65,6 +76,8 @@ struct FactorArgs {
     int hbits;  // hash table of 2^hbits slots per warp
     int lanes;  // lanes per row, 0 = from |R_i|
     int adaptive;  // chunk of at least |R_i|/4 rows
+    int warp_smem;    // shared-memory bytes of one warp (table, then the bulk form's buffers and barriers)
+    int stage_bytes;  // bulk form: bytes of each of the two stage buffers
 };
 
 // Rows of column k handled by one task.  Adaptive (the factor): at least a
@@ -176,31 +189,41 @@ struct Acc<double> {
     }
     // (theta - sum) / L_ii
     __device__ __forceinline__ double finish(double th, double Lii, double) const { return (th - s) / Lii; }
+    __device__ __forceinline__ double total() const { return s; }
+    __device__ __forceinline__ static double recip(double) { return 0.0; }  // finish divides
 };
 template <>
 struct Acc<float> {
+    // every operation rounded on its own (the _rn intrinsics are never
+    // contracted into an FMA): the error-free transformations rely on it, and
+    // every inlined copy then rounds the same way
     float s = 0.f, c = 0.f;
     __device__ __forceinline__ void add(float a, float b) {
-        const float p = a * b;
+        const float p = __fmul_rn(a, b);
         const float ep = fmaf(a, b, -p);
-        const float ns = s + p;
-        const float z = ns - s;
-        const float es = (s - (ns - z)) + (p - z);
+        const float ns = __fadd_rn(s, p);
+        const float z = __fsub_rn(ns, s);
+        const float es = __fadd_rn(__fsub_rn(s, __fsub_rn(ns, z)), __fsub_rn(p, z));
         s = ns;
-        c += ep + es;
+        c = __fadd_rn(c, __fadd_rn(ep, es));
     }
     __device__ __forceinline__ void group_reduce(int G) {
         for (int o = G >> 1; o > 0; o >>= 1) {
             const float s2 = __shfl_xor_sync(0xffffffffu, s, o);
             const float c2 = __shfl_xor_sync(0xffffffffu, c, o);
-            const float t = s + s2;
-            const float z = t - s;
-            const float e = (s - (t - z)) + (s2 - z);
+            const float t = __fadd_rn(s, s2);
+            const float z = __fsub_rn(t, s);
+            const float e = __fadd_rn(__fsub_rn(s, __fsub_rn(t, z)), __fsub_rn(s2, z));
             s = t;
-            c += c2 + e;
+            c = __fadd_rn(c, __fadd_rn(c2, e));
         }
     }
-    __device__ __forceinline__ float finish(float th, double, float inv) const { return ((th - s) - c) * inv; }
+    __device__ __forceinline__ float finish(float th, double, float inv) const {
+        return __fmul_rn(__fsub_rn(__fsub_rn(th, s), c), inv);
+    }
+    // both parts in FP64: the compensated sum to about FP64 accuracy
+    __device__ __forceinline__ double total() const { return (double)s + (double)c; }
+    __device__ __forceinline__ static float recip(double Lii) { return __frcp_rn((float)Lii); }
 };
 
 template <typename T>
@@ -243,90 +266,190 @@ __device__ __forceinline__ bool wait_done(const unsigned* f, const int* status, 
     return true;
 }
 
+// Everything a task knows after its prologue.
+template <typename T>
+struct TaskCtx {
+    int i, c, nr;
+    int64_t a0, a1;  // R_i = col[a0..a1), L_ii at a1
+    KernelParams kp;
+    bool zero;       // dropped pivot: the whole column is zero
+    bool staged;     // row i is in the table (else binary search in global memory)
+    double Lii;
+    T inv;
+};
+
+// Claim the next task and run its prologue: wait until every column k in
+// R_i is complete, put row i into the table, form the pivot in FP64.
+// Returns 0 (task ready), 1 (no tasks left), 2 (stop: a wait ran out or the
+// kernel is stopping).
+template <typename T>
+__device__ __forceinline__ int task_begin(const FactorArgs<T>& A, RowTable<T>& tab, int lane, TaskCtx<T>& X) {
+    const unsigned FULL = 0xffffffffu;
+    unsigned long long t = 0;
+    if (lane == 0) t = atomicAdd(A.ticket, 1ULL);
+    t = __shfl_sync(FULL, t, 0);
+    if ((int64_t)t >= A.ntasks) return 1;
+    if (ld_volatile_s32(A.status) != 0) return 2;
+    const int2 tk = A.tasks[t];
+    X.i = tk.x;
+    X.c = tk.y;
+    X.a0 = A.rowptr[X.i];
+    X.a1 = A.rowptr[X.i + 1] - 1;
+    X.nr = (int)(X.a1 - X.a0);
+    X.kp = A.col_set ? A.kps[A.col_set[X.i]] : A.kp;
+
+    bool ok = true;
+    for (int e = lane; e < X.nr && ok; e += 32) {
+        const int k = __ldg(&A.col[X.a0 + e]);
+        ok = wait_done(&A.done[k], A.status, A.spin_limit);
+    }
+    if (!__all_sync(FULL, ok)) {
+        if (lane == 0) atomicCAS(A.status, 0, DEV_TIMEOUT);
+        return 2;
+    }
+    __threadfence();
+    __syncwarp();
+
+    X.staged = 2 * X.nr <= (1 << A.hbits);  // load factor <= 1/2 (linear-probing misses stay short)
+    if (X.staged) tab.clear(lane);
+    __syncwarp();
+    // sum of squares of row i with the accumulator of the merges (FP32 form:
+    // compensated, its two parts added in FP64); the update and its square
+    // root in FP64
+    Acc<T> sq;
+    for (int e = lane; e < X.nr; e += 32) {
+        const T v = ldcg(&A.val[X.a0 + e]);
+        if (X.staged) tab.insert(__ldg(&A.col[X.a0 + e]), v);
+        sq.add(v, v);
+    }
+    sq.group_reduce(32);
+    // Lane 0 forms the pivot and every lane takes its values: one pivot for the
+    // whole task whichever lane writes a row (after a butterfly the partners'
+    // compensations c + (c2 + e) and c2 + (c + e) may round apart), and the FP64
+    // work runs on one lane.
+    double Lii = 0.0;
+    T inv = (T)0;
+    int zero = 0;
+    if (lane == 0) {
+        const double p = (X.kp.sigma2 + X.kp.nugget) - sq.total();
+        zero = !(p > 0.0);
+        Lii = zero ? 0.0 : sqrt(p);
+        inv = zero ? (T)0 : Acc<T>::recip(Lii);
+        if (X.c == 0) {
+            A.val[X.a1] = (T)Lii;
+            A.diag[X.i] = Lii;
+            if (zero) atomicAdd(A.zero_piv, 1ULL);
+        }
+    }
+    X.Lii = __shfl_sync(FULL, Lii, 0);
+    X.inv = __shfl_sync(FULL, inv, 0);
+    X.zero = __shfl_sync(FULL, zero, 0) != 0;
+    __syncwarp();  // the table's inserts are visible to every lane
+    return 0;
+}
+
+// Publish one finished task of column i.
+template <typename T>
+__device__ __forceinline__ void task_end(const FactorArgs<T>& A, int i, int lane) {
+    __threadfence();
+    __syncwarp();
+    if (lane == 0 && i != A.hold_col) red_release_add_u32(&A.done[i], 1u);
+}
+
+// Lanes per row: one 32-byte sector of values per group load (8 lanes in
+// FP32, 4 in FP64), unless set.
+template <typename T>
+__device__ __forceinline__ int lanes_per_row(int lanes) {
+    return lanes > 0 ? lanes : (int)(32 / sizeof(T));
+}
+
+// Merge of the prefix [es, be) of row j, read from global memory, against
+// row i: U (col, val) pairs per lane in flight; the ragged end is masked.
+template <typename T, int U>
+__device__ __forceinline__ void merge_global(const FactorArgs<T>& A, const RowTable<T>& tab, const TaskCtx<T>& X,
+                                             int64_t es, int64_t be, int sub, int G, Acc<T>& acc) {
+    if (X.staged) {
+        const int n = (int)(be - es);
+        const int32_t* cp = A.col + es;
+        const T* vp = A.val + es;
+        int t = sub;
+        for (; t + (U - 1) * G < n; t += U * G) {  // full rounds
+            int k[U];
+            T wv[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) k[u] = __ldg(cp + t + u * G);
+#pragma unroll
+            for (int u = 0; u < U; ++u) wv[u] = ldcg(vp + t + u * G);
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                T hv;
+                if (tab.find(k[u], hv)) acc.add(wv[u], hv);
+            }
+        }
+        if (t < n) {  // the ragged end: one masked round
+            int k[U];
+            T wv[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) k[u] = t + u * G < n ? __ldg(cp + t + u * G) : -1;
+#pragma unroll
+            for (int u = 0; u < U; ++u) wv[u] = t + u * G < n ? ldcg(vp + t + u * G) : (T)0;
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                T hv;
+                if (k[u] >= 0 && tab.find(k[u], hv)) acc.add(wv[u], hv);
+            }
+        }
+    } else {
+        for (int64_t e = es + sub; e < be; e += G) {
+            const int64_t pos = bsearch_glob(A.col, X.a0, X.a1, __ldg(&A.col[e]));
+            if (pos >= 0) acc.add(ldcg(&A.val[e]), ldcg(&A.val[pos]));
+        }
+    }
+}
+
+// Row-j bookkeeping of the rows b0+lane of a batch: the slot of L_ji, the
+// start of row j, and Theta_ji (loads and exponentials overlap across lanes).
+template <typename T>
+__device__ __forceinline__ void batch_rows(const FactorArgs<T>& A, const TaskCtx<T>& X, int64_t b0, int nb, int lane,
+                                           int64_t& my_e0, int64_t& my_b, T& my_th) {
+    my_e0 = 0;
+    my_b = 0;
+    my_th = (T)0;
+    if (lane < nb) {
+        const int j = __ldg(&A.rowidx[b0 + lane]);
+        my_b = __ldg(&A.slot[b0 + lane]);
+        my_e0 = __ldg(&A.rowptr[j]);
+        if (!X.zero) my_th = theta_off<T>(X.kp, A.d, A.x + (int64_t)j * A.d, A.x + (int64_t)X.i * A.d);
+    }
+}
+
+// ----------------------------------------------------------- register form
+// Each lane keeps U (col, val) loads of its row prefix in flight in registers.
 // Resident CTAs of 8 warps per SM that the register budget is cut for.
 #ifndef KC_FACTOR_MIN_BLOCKS
 #define KC_FACTOR_MIN_BLOCKS 4
 #endif
 
 template <typename T, int U>
-__global__ void __launch_bounds__(256, KC_FACTOR_MIN_BLOCKS) ichol_persistent_k(FactorArgs<T> A) {
+__global__ void __launch_bounds__(256, U >= 16 ? 3 : KC_FACTOR_MIN_BLOCKS) ichol_persistent_k(FactorArgs<T> A) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = lane_id();
     const int w = threadIdx.x >> 5;
-    const int H = 1 << A.hbits;
-    RowTable<T> tab(smem + (size_t)w * H * (sizeof(int) + sizeof(T)), A.hbits);
+    RowTable<T> tab(smem + (size_t)w * A.warp_smem, A.hbits);
     const unsigned FULL = 0xffffffffu;
-
+    TaskCtx<T> X;
     for (;;) {
-        unsigned long long t = 0;
-        if (lane == 0) t = atomicAdd(A.ticket, 1ULL);
-        t = __shfl_sync(FULL, t, 0);
-        if ((int64_t)t >= A.ntasks) return;
-        if (ld_volatile_s32(A.status) != 0) return;
-        const int2 tk = A.tasks[t];
-        const int i = tk.x, c = tk.y;
-        const int64_t a0 = A.rowptr[i], a1 = A.rowptr[i + 1] - 1;  // R_i = col[a0..a1)
-        const int nr = (int)(a1 - a0);
-        const KernelParams kp = A.col_set ? A.kps[A.col_set[i]] : A.kp;
-
-        // ---- wait until every column k in R_i is complete
-        bool ok = true;
-        for (int e = lane; e < nr && ok; e += 32) {
-            const int k = __ldg(&A.col[a0 + e]);
-            ok = wait_done(&A.done[k], A.status, A.spin_limit);
-        }
-        if (!__all_sync(FULL, ok)) {
-            if (lane == 0) atomicCAS(A.status, 0, DEV_TIMEOUT);
-            return;
-        }
-        __threadfence();
-        __syncwarp();
-
-        // ---- row i into the table; pivot in FP64
-        const bool staged = 2 * nr <= H;  // load factor <= 1/2 (linear-probing misses stay short)
-        if (staged) tab.clear(lane);
-        __syncwarp();
-        double ps = 0.0;
-        for (int e = lane; e < nr; e += 32) {
-            const T v = ldcg(&A.val[a0 + e]);
-            if (staged) tab.insert(__ldg(&A.col[a0 + e]), v);
-            ps = fma((double)v, (double)v, ps);
-        }
-        ps = warp_sum(ps);
-        __syncwarp();
-        const double p = (kp.sigma2 + kp.nugget) - ps;
-        const bool zero = !(p > 0.0);
-        const double Lii = zero ? 0.0 : sqrt(p);
-        const T inv = zero ? (T)0 : (T)(1.0 / Lii);
-        if (c == 0 && lane == 0) {
-            A.val[a1] = (T)Lii;
-            A.diag[i] = Lii;
-            if (zero) atomicAdd(A.zero_piv, 1ULL);
-        }
-        const double* xi = A.x + (int64_t)i * A.d;
-
-        // ---- rows j of this chunk, in batches of 32.  First every lane fetches
-        // one row's bookkeeping (j, the slot of L_ji, the start of row j) and
-        // evaluates its Theta_ji, so these dependent loads and the exponential
-        // overlap across the batch; then groups of G lanes merge one row each.
-        int G = 1;
-        if (A.lanes > 0) G = A.lanes;
-        else
-            while (G < 32 && 32 * G <= nr) G <<= 1;  // about 32+ prefix entries per lane-group step
+        if (task_begin(A, tab, lane, X) != 0) return;
+        const int G = lanes_per_row<T>(A.lanes);
         const int ng = 32 / G, g = lane / G, sub = lane % G;
-        const int rows = rows_of_task(A.rowptr, i, A.rpt, A.adaptive);
-        const int64_t qs = A.colptr[i] + 1 + (int64_t)c * rows;
-        const int64_t qe = min(A.colptr[i + 1], qs + rows);
+        const int rows = rows_of_task(A.rowptr, X.i, A.rpt, A.adaptive);
+        const int64_t qs = A.colptr[X.i] + 1 + (int64_t)X.c * rows;
+        const int64_t qe = min(A.colptr[X.i + 1], qs + rows);
         for (int64_t b0 = qs; b0 < qe; b0 += 32) {
             const int nb = (int)min((int64_t)32, qe - b0);
-            int64_t my_e0 = 0, my_b = 0;
-            T my_th = (T)0;
-            if (lane < nb) {
-                const int j = __ldg(&A.rowidx[b0 + lane]);
-                my_b = __ldg(&A.slot[b0 + lane]);
-                my_e0 = __ldg(&A.rowptr[j]);
-                if (!zero) my_th = theta_off<T>(kp, A.d, A.x + (int64_t)j * A.d, xi);
-            }
+            int64_t my_e0, my_b;
+            T my_th;
+            batch_rows(A, X, b0, nb, lane, my_e0, my_b, my_th);
             for (int r0 = 0; r0 < nb; r0 += ng) {
                 const int r = r0 + g;
                 const bool act = r < nb;
@@ -335,44 +458,233 @@ __global__ void __launch_bounds__(256, KC_FACTOR_MIN_BLOCKS) ichol_persistent_k(
                 const int64_t be = __shfl_sync(FULL, my_b, src);  // L_ji lives at be; the prefix is [es, be)
                 const T th = __shfl_sync(FULL, my_th, src);
                 Acc<T> acc;
-                if (act && !zero) {
-                    if (staged) {
-                        // U pairs per lane in flight; the ragged end is masked, not looped
-                        for (int64_t e = es + sub; e < be; e += U * G) {
-                            int k[U];
-                            T wv[U];
-#pragma unroll
-                            for (int u = 0; u < U; ++u) {
-                                const int64_t q = e + u * G;
-                                k[u] = q < be ? __ldg(&A.col[q]) : -1;
-                            }
-#pragma unroll
-                            for (int u = 0; u < U; ++u) {
-                                const int64_t q = e + u * G;
-                                wv[u] = q < be ? ldcg(&A.val[q]) : (T)0;
-                            }
-#pragma unroll
-                            for (int u = 0; u < U; ++u) {
-                                T hv;
-                                if (k[u] >= 0 && tab.find(k[u], hv)) acc.add(wv[u], hv);
-                            }
-                        }
-                    } else {
-                        for (int64_t e = es + sub; e < be; e += G) {
-                            const int64_t pos = bsearch_glob(A.col, a0, a1, __ldg(&A.col[e]));
-                            if (pos >= 0) acc.add(ldcg(&A.val[e]), ldcg(&A.val[pos]));
-                        }
-                    }
-                }
+                if (act && !X.zero) merge_global<T, U>(A, tab, X, es, be, sub, G, acc);
                 acc.group_reduce(G);
-                if (act && sub == 0) A.val[be] = zero ? (T)0 : acc.finish(th, Lii, inv);
+                if (act && sub == 0) A.val[be] = X.zero ? (T)0 : acc.finish(th, X.Lii, X.inv);
             }
         }
+        task_end(A, X.i, lane);
+    }
+}
 
-        // ---- publish
-        __threadfence();
+// --------------------------------------------------------------- bulk form
+// The prefixes of a stage of consecutive rows are copied from global memory
+// into one of two shared-memory buffers of the warp by the bulk-copy (TMA)
+// engine, completing on an mbarrier; the warp merges the previous stage from
+// shared memory meanwhile.  The loads in flight then cost no registers, so a
+// few warps per SM keep enough bytes in flight.  Each row's (col, val)
+// extents are widened to 16-byte boundaries (a bulk copy's rule); a row that
+// alone exceeds a buffer is merged from global memory instead.
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(uint64_t* bar) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(bar)) : "memory");
+}
+__device__ __forceinline__ void mbar_expect(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// bounded wait for the phase with the given parity to complete
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, long long limit) {
+    if (mbar_test(bar, parity)) return true;
+    const long long t0 = clock64();
+    while (!mbar_test(bar, parity))
+        if (clock64() - t0 > limit) return false;
+    return true;
+}
+__device__ __forceinline__ void bulk_copy(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_addr(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_addr(bar))
+                 : "memory");
+}
+
+// A stage: rows [s0, s1) of the current batch, in buffer `buf`; `direct`: one
+// row merged from global memory; `bytes`: the buffer's barrier is armed.
+struct Stage {
+    int s0, s1, buf;
+    bool direct, bytes;
+};
+
+// Issue the copies of the next stage starting at row c0 of the batch into
+// buffer bi.  Each lane owns row lane of the batch: it sizes its widened
+// extents, a warp scan places them, and the rows that fit are copied.
+// my_off / my_meta receive the position of the lane's row in the buffer.
+template <typename T>
+__device__ __forceinline__ Stage stage_issue(const FactorArgs<T>& A, unsigned char* buf, uint64_t* bar, int bi,
+                                             int c0, int nb, int lane, int64_t my_e0, int64_t my_b,
+                                             uint32_t& my_off, uint32_t& my_meta) {
+    const unsigned FULL = 0xffffffffu;
+    uint32_t sz = 0, colB = 0, hc = 0, hv = 0;
+    uintptr_t cl = 0, vl = 0;
+    const bool mine = lane >= c0 && lane < nb;
+    if (mine && my_b > my_e0) {
+        const uintptr_t ca = (uintptr_t)(A.col + my_e0), ce = (uintptr_t)(A.col + my_b);
+        const uintptr_t va = (uintptr_t)(A.val + my_e0), ve = (uintptr_t)(A.val + my_b);
+        cl = ca & ~(uintptr_t)15;
+        vl = va & ~(uintptr_t)15;
+        colB = (uint32_t)(((ce + 15) & ~(uintptr_t)15) - cl);
+        sz = colB + (uint32_t)(((ve + 15) & ~(uintptr_t)15) - vl);
+        hc = (uint32_t)((ca - cl) >> 2);
+        hv = (uint32_t)((va - vl) / sizeof(T));
+    }
+    uint32_t inc = sz;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t n = __shfl_up_sync(FULL, inc, o);
+        if (lane >= o) inc += n;
+    }
+    const bool fits = mine && inc <= (uint32_t)A.stage_bytes;
+    const int cnt = __popc(__ballot_sync(FULL, fits));  // rows c0 .. c0+cnt-1: the scan is monotone
+    Stage S;
+    S.s0 = c0;
+    S.buf = bi;
+    if (cnt == 0) {
+        S.s1 = c0 + 1;
+        S.direct = true;
+        S.bytes = false;
+        return S;
+    }
+    S.s1 = c0 + cnt;
+    S.direct = false;
+    const uint32_t total = __shfl_sync(FULL, inc, c0 + cnt - 1);
+    S.bytes = total > 0;
+    if (fits) {
+        my_off = inc - sz;
+        my_meta = colB | (hc << 24) | (hv << 28);
+    }
+    if (S.bytes) {
+        // the buffer's previous contents were read by this warp's generic loads
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        if (lane == 0) mbar_expect(bar, total);
         __syncwarp();
-        if (lane == 0 && i != A.hold_col) red_release_add_u32(&A.done[i], 1u);
+        if (fits && sz > 0) {
+            bulk_copy(buf + (inc - sz), (const void*)cl, colB, bar);
+            bulk_copy(buf + (inc - sz) + colB, (const void*)vl, sz - colB, bar);
+        }
+    }
+    return S;
+}
+
+// Merge of a prefix of n entries held in shared memory.
+template <typename T, int U>
+__device__ __forceinline__ void merge_smem(const RowTable<T>& tab, const int* cs, const T* vs, int n, int sub, int G,
+                                           Acc<T>& acc) {
+    for (int t = sub; t < n; t += U * G) {
+        int k[U];
+        T wv[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int q = t + u * G;
+            k[u] = q < n ? cs[q] : -1;
+            wv[u] = q < n ? vs[q] : (T)0;
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            T hv;
+            if (k[u] >= 0 && tab.find(k[u], hv)) acc.add(wv[u], hv);
+        }
+    }
+}
+
+template <typename T, int U>
+__global__ void __launch_bounds__(128) ichol_bulk_k(FactorArgs<T> A) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int lane = lane_id();
+    const int w = threadIdx.x >> 5;
+    unsigned char* base = smem + (size_t)w * A.warp_smem;
+    const int H = 1 << A.hbits;
+    RowTable<T> tab(base, A.hbits);
+    unsigned char* bufs = base + (size_t)H * (sizeof(int) + sizeof(T));
+    uint64_t* bars = (uint64_t*)(bufs + 2 * (size_t)A.stage_bytes);
+    const unsigned FULL = 0xffffffffu;
+    if (lane == 0) {
+        mbar_init(&bars[0]);
+        mbar_init(&bars[1]);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    __syncwarp();
+    uint32_t phase = 0;  // bit b: parity of the next phase of barrier b
+    TaskCtx<T> X;
+    for (;;) {
+        if (task_begin(A, tab, lane, X) != 0) return;
+        // values of finished columns were written by other SMs through the generic
+        // proxy and acquired above; the bulk copies read them through the async proxy
+        asm volatile("fence.proxy.async.global;" ::: "memory");
+        const int G = lanes_per_row<T>(A.lanes);
+        const int ng = 32 / G, g = lane / G, sub = lane % G;
+        const int rows = rows_of_task(A.rowptr, X.i, A.rpt, A.adaptive);
+        const int64_t qs = A.colptr[X.i] + 1 + (int64_t)X.c * rows;
+        const int64_t qe = min(A.colptr[X.i + 1], qs + rows);
+        const bool bulk = X.staged && !X.zero;
+        for (int64_t b0 = qs; b0 < qe; b0 += 32) {
+            const int nb = (int)min((int64_t)32, qe - b0);
+            int64_t my_e0, my_b;
+            T my_th;
+            batch_rows(A, X, b0, nb, lane, my_e0, my_b, my_th);
+            uint32_t off0 = 0, meta0 = 0, off1 = 0, meta1 = 0;  // the lane's row in buffer 0 / 1
+            Stage cur;
+            if (bulk) cur = stage_issue(A, bufs, &bars[0], 0, 0, nb, lane, my_e0, my_b, off0, meta0);
+            else cur = Stage{0, nb, 0, true, false};
+            while (cur.s0 < nb) {
+                Stage nxt{nb, nb, 0, true, false};
+                if (bulk && cur.s1 < nb) {
+                    if (cur.buf == 0)
+                        nxt = stage_issue(A, bufs + A.stage_bytes, &bars[1], 1, cur.s1, nb, lane, my_e0, my_b, off1,
+                                          meta1);
+                    else
+                        nxt = stage_issue(A, bufs, &bars[0], 0, cur.s1, nb, lane, my_e0, my_b, off0, meta0);
+                }
+                if (cur.bytes) {
+                    const bool ok = mbar_wait(&bars[cur.buf], (phase >> cur.buf) & 1u, A.spin_limit);
+                    phase ^= 1u << cur.buf;
+                    if (!__all_sync(FULL, ok)) {
+                        // give the copies still in flight a bounded chance to land, then stop
+                        if (nxt.bytes) mbar_wait(&bars[nxt.buf], (phase >> nxt.buf) & 1u, A.spin_limit);
+                        if (lane == 0) atomicCAS(A.status, 0, DEV_TIMEOUT);
+                        return;
+                    }
+                }
+                const unsigned char* sb = bufs + (size_t)cur.buf * A.stage_bytes;
+                const uint32_t my_off = cur.buf ? off1 : off0, my_meta = cur.buf ? meta1 : meta0;
+                for (int r0 = cur.s0; r0 < cur.s1; r0 += ng) {
+                    const int r = r0 + g;
+                    const bool act = r < cur.s1;
+                    const int src = act ? r : cur.s0;
+                    const int64_t es = __shfl_sync(FULL, my_e0, src);
+                    const int64_t be = __shfl_sync(FULL, my_b, src);
+                    const T th = __shfl_sync(FULL, my_th, src);
+                    const uint32_t ro = __shfl_sync(FULL, my_off, src);
+                    const uint32_t rm = __shfl_sync(FULL, my_meta, src);
+                    Acc<T> acc;
+                    if (act && !X.zero) {
+                        if (cur.direct) {
+                            merge_global<T, U>(A, tab, X, es, be, sub, G, acc);
+                        } else {
+                            const uint32_t colB = rm & 0xffffffu;
+                            const int* cs = (const int*)(sb + ro) + (rm >> 24 & 15u);
+                            const T* vs = (const T*)(sb + ro + colB) + (rm >> 28);
+                            merge_smem<T, U>(tab, cs, vs, (int)(be - es), sub, G, acc);
+                        }
+                    }
+                    acc.group_reduce(G);
+                    if (act && sub == 0) A.val[be] = X.zero ? (T)0 : acc.finish(th, X.Lii, X.inv);
+                }
+                __syncwarp();
+                cur = nxt;
+            }
+        }
+        task_end(A, X.i, lane);
     }
 }
 
@@ -522,7 +834,10 @@ struct FactorCore {
     KernelParams kp;
     const int32_t* col_set = nullptr;
     KernelParams* kps = nullptr;
-    int rpt = 64, lanes = 0, unroll = 8, warps = 8, hbits = 7, ctas = 0, adaptive = 0;
+    int rpt = 128, lanes = 0, unroll = 8, warps = 8, hbits = 7, ctas = 0, adaptive = 0;
+    int stage_req = 0;    // requested stage-buffer bytes: 0 automatic, < 0 register form
+    int stage_bytes = 0;  // chosen (0: register form)
+    int bulk_warps = 4;
     long long spin = 4000000000LL;
     int hold = -1;
 };
@@ -555,18 +870,32 @@ static kc_status launch_core(const FactorCore& F, T* val, double* diag, cudaStre
     a.hbits = F.hbits;
     a.lanes = F.lanes;
     a.adaptive = F.adaptive;
-    const size_t smem = (size_t)F.warps * (1 << F.hbits) * (sizeof(int) + sizeof(T));
-    KC_CUDA(cudaFuncSetAttribute(ichol_persistent_k<T, U>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    a.stage_bytes = F.stage_bytes;
+    const size_t table = (size_t)(1 << F.hbits) * (sizeof(int) + sizeof(T));
+    const bool bulk = F.stage_bytes > 0;
+    // bulk form: table, two stage buffers, two mbarriers per warp (128-byte aligned)
+    a.warp_smem = (int)(bulk ? (table + 2 * (size_t)F.stage_bytes + 16 + 127) / 128 * 128 : table);
+    int warps = bulk ? F.bulk_warps : F.warps;
+    if (bulk) {
+        int dev = 0, optin = 0;
+        KC_CUDA(cudaGetDevice(&dev));
+        KC_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+        warps = std::min(warps, optin / a.warp_smem);
+        if (warps < 1) return fail(KC_EINVAL, "factor: stage_bytes too large for one warp's shared memory");
+    }
+    const size_t smem = (size_t)warps * a.warp_smem;
+    auto kfn = bulk ? ichol_bulk_k<T, U> : ichol_persistent_k<T, U>;
+    KC_CUDA(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
-    KC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ichol_persistent_k<T, U>, F.warps * 32, smem));
+    KC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, warps * 32, smem));
     if (F.ctas > 0 && F.ctas < per_sm) per_sm = F.ctas;
-    if (per_sm < 1) per_sm = 1;
+    if (per_sm < 1) return fail(KC_EINVAL, "factor: shared memory of one CTA exceeds the SM (stage_bytes too large?)");
     ::kc::note_launch(), done_init_k<<<blocks_for(F.P.N, 256), 256, 0, s>>>(F.P.colptr, F.P.rowptr, F.P.N, F.rpt,
                                                                            F.adaptive, F.done);
     KC_CUDA(cudaMemsetAsync(F.ticket, 0, sizeof(unsigned long long), s));
     KC_CUDA(cudaMemsetAsync(F.zp, 0, sizeof(unsigned long long), s));
     KC_CUDA(cudaMemsetAsync(F.status, 0, sizeof(int), s));
-    ::kc::note_launch(), ichol_persistent_k<T, U><<<sm_count() * per_sm, F.warps * 32, smem, s>>>(a);
+    ::kc::note_launch(), kfn<<<sm_count() * per_sm, warps * 32, smem, s>>>(a);
     KC_CUDA(cudaGetLastError());
     return KC_OK;
 }
@@ -575,6 +904,7 @@ static kc_status launch_any(const FactorCore& F, void* val, double* diag, cudaSt
     if (F.prec == KC_FP64)
         return F.unroll >= 8 ? launch_core<double, 8>(F, (double*)val, diag, s)
                              : launch_core<double, 4>(F, (double*)val, diag, s);
+    if (F.unroll >= 16) return launch_core<float, 16>(F, (float*)val, diag, s);
     return F.unroll >= 8 ? launch_core<float, 8>(F, (float*)val, diag, s)
                          : launch_core<float, 4>(F, (float*)val, diag, s);
 }
@@ -592,7 +922,7 @@ static kc_status read_status(const FactorCore& F, int64_t* zero_out, cudaStream_
 }
 
 static kc_status apply_opts(FactorCore& F, const kc_opts* o) {
-    F.rpt = (o && o->rows_per_task > 0) ? o->rows_per_task : 64;
+    F.rpt = (o && o->rows_per_task > 0) ? o->rows_per_task : 0;  // 0: from the level width (auto_rows)
     F.warps = (o && o->warps_per_cta > 0) ? o->warps_per_cta : 8;
     if (F.warps > 8) return fail(KC_EINVAL, "warps_per_cta must be <= 8");
     F.spin = (o && o->spin_limit_cycles > 0) ? o->spin_limit_cycles : 4000000000LL;
@@ -604,9 +934,12 @@ static kc_status apply_opts(FactorCore& F, const kc_opts* o) {
         if (L > 32 || (L & (L - 1))) return fail(KC_EINVAL, "lanes_per_row must be a power of two <= 32");
         F.lanes = L;
     }
-    F.unroll = (o && o->unroll > 0) ? o->unroll : 8;
+    F.unroll = (o && o->unroll > 0) ? o->unroll : 0;  // 0: from the mean row length (pick_hash)
+    F.stage_req = o ? o->stage_bytes : 0;
+    if (F.stage_req > 65536) return fail(KC_EINVAL, "stage_bytes must be <= 65536");
     F.adaptive = (o && o->adaptive_chunks) ? 1 : 0;
-    if (F.unroll != 4 && F.unroll != 8) return fail(KC_EINVAL, "unroll must be 4 or 8");
+    if (F.unroll != 0 && F.unroll != 4 && F.unroll != 8 && F.unroll != 16)
+        return fail(KC_EINVAL, "unroll must be 4, 8 or 16");
     return KC_OK;
 }
 
@@ -616,6 +949,25 @@ static void pick_hash(FactorCore& F) {
     int hb = 7;
     while (hb < 11 && (1 << hb) < 2 * F.maxr) ++hb;
     F.hbits = hb;
+    // staging depth: 16 loads per lane in flight for long rows (FP32 form),
+    // else 8; the FP64 form takes at most 8
+    if (F.unroll == 0) F.unroll = F.prec == KC_FP64 ? 4 : (F.P.nnz >= 400 * F.P.N ? 16 : 8);
+    // bulk form (on request): stage buffers of the requested size; a row
+    // prefix longer than a buffer is merged from global memory
+    F.stage_bytes = F.stage_req <= 0 ? 0 : std::max(64, (F.stage_req + 15) / 16 * 16);
+    F.bulk_warps = F.warps < 4 ? F.warps : 4;
+}
+
+// Rows per task, unless set: about one task per resident warp per level,
+// (nnz - N) / (depth * warps), as a power of two in 16..128.  Smaller tasks
+// keep narrow levels busy; larger ones stage each pivot row fewer times.
+static void auto_rows(FactorCore& F) {
+    if (F.rpt > 0) return;
+    const double warps = (double)sm_count() * 32.0;
+    const double per = (double)(F.P.nnz - F.P.N) / ((double)std::max(1, F.P.depth) * warps);
+    int r = 16;
+    while (r < 128 && per > r * 1.41421356) r <<= 1;
+    F.rpt = r;
 }
 
 kc_status factor_impl(const kc_pattern* P, const double* x, int d, const kc_kernel* kern, int prec, void* val,
@@ -628,6 +980,7 @@ kc_status factor_impl(const kc_pattern* P, const double* x, int d, const kc_kern
     F.prec = prec;
     F.d = d;
     F.x = x;
+    auto_rows(F);
     Arena A(s);
     KC_TRY(build_tasks(P, F.rpt, A, s, &F.tasks, &F.ntasks, &F.maxr, x, d, F.adaptive != 0));
     pick_hash(F);
@@ -688,6 +1041,7 @@ kc_status plan_create_impl(const kc_pattern* P, const double* x, int d, const kc
     F.d = d;
     F.x = x;
     F.col_set = nsets > 1 ? col_set : nullptr;
+    auto_rows(F);
     {
         Arena A(s);
         int2* t;
@@ -728,8 +1082,8 @@ kc_status plan_finish_impl(kc_factor_plan* pl, int64_t* zero_out, cudaStream_t s
 kc_status plan_tune_impl(kc_factor_plan* pl, void* val, double* diag, int32_t* lanes_out, int32_t* unroll_out,
                          double* best_ms_out, cudaStream_t s) {
     FactorCore& F = pl->F;
-    const int lanes_c[] = {4, 8, 16, 32};
-    const int unroll_c[] = {4, 8};
+    const int lanes_c[] = {2, 4, 8, 16};
+    const int unroll_c[] = {8, 16};
     cudaEvent_t e0, e1;
     KC_CUDA(cudaEventCreate(&e0));
     KC_CUDA(cudaEventCreate(&e1));

@@ -44,7 +44,7 @@ class kc_pattern(C.Structure):
 class kc_opts(C.Structure):
     _fields_ = [("spin_limit_cycles", C.c_int64), ("rows_per_task", C.c_int32), ("ctas_per_sm", C.c_int32),
                 ("warps_per_cta", C.c_int32), ("test_hold_column", C.c_int32), ("lanes_per_row", C.c_int32),
-                ("unroll", C.c_int32), ("adaptive_chunks", C.c_int32)]
+                ("unroll", C.c_int32), ("adaptive_chunks", C.c_int32), ("stage_bytes", C.c_int32)]
 
 
 _lib = None
@@ -148,9 +148,9 @@ class Kernel:
 
 
 def make_opts(spin_limit_cycles=0, rows_per_task=0, ctas_per_sm=0, warps_per_cta=0, test_hold_column=-1,
-              lanes_per_row=0, unroll=0, adaptive_chunks=0):
+              lanes_per_row=0, unroll=0, adaptive_chunks=0, stage_bytes=0):
     return kc_opts(spin_limit_cycles, rows_per_task, ctas_per_sm, warps_per_cta, test_hold_column + 1,
-                   lanes_per_row, unroll, adaptive_chunks)
+                   lanes_per_row, unroll, adaptive_chunks, stage_bytes)
 
 
 # ----------------------------------------------------------------- a2, a3, a4

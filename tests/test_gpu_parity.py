@@ -214,6 +214,52 @@ def test_factor_fp32_form_parity(nu, ell, rho, nugget):
     assert identity_residual(rp, col, H(val), xo, ko, 3000) < 1e-6
 
 
+# The factor kernel has two forms: row prefixes staged in shared memory by bulk
+# (TMA) copies, or loaded into registers.  Each lane merges the same entries in
+# the same order in both, so the results are the same bits; tiny stage buffers
+# force many stages and rows merged from global memory.
+
+@pytest.mark.parametrize("prec", [kc.FP64, kc.FP32_FORM])
+@pytest.mark.parametrize("lanes", [0, 4, 32])
+def test_factor_forms_same_bits(prec, lanes):
+    x, perm, l, xo, rp, col = _ref_pattern(N=3000, rho=3.0, seed=33)
+    kg, _ = ok_kern(1.5, 0.2)
+    pat = kc.schedule(T(rp), T(col))
+    ref = None
+    for stage in (0, 4096, 256, 64):
+        val, diag, zp = kc.factor(pat, T(xo), kg, prec, kc.make_opts(lanes_per_row=lanes, stage_bytes=stage))
+        if ref is None:
+            ref = (val, diag, zp)
+        else:
+            assert torch.equal(val, ref[0]) and torch.equal(diag, ref[1]) and zp == ref[2], stage
+
+
+def test_factor_deterministic_across_runs():
+    x, perm, l, xo, rp, col = _ref_pattern(N=3000, rho=3.0, seed=34)
+    kg, _ = ok_kern(0.5, 0.2)
+    pat = kc.schedule(T(rp), T(col))
+    a = kc.factor(pat, T(xo), kg, kc.FP32_FORM)[0]
+    for _ in range(3):
+        assert torch.equal(kc.factor(pat, T(xo), kg, kc.FP32_FORM)[0], a)
+
+
+@pytest.mark.parametrize("stage", [-1, 0])
+def test_factor_dependency_wait_times_out(stage):
+    """A column that never publishes (test hook): every wait on it runs out
+    after the spin limit, the kernel reports KC_ETIMEOUT and returns, and the
+    context stays usable for the next factorisation."""
+    x, perm, l, xo, rp, col = _ref_pattern(N=2000, rho=3.0, seed=35)
+    kg, ko = ok_kern(0.5, 0.2)
+    pat = kc.schedule(T(rp), T(col))
+    with pytest.raises(kc.KcError) as ei:
+        kc.factor(pat, T(xo), kg, kc.FP32_FORM,
+                  kc.make_opts(spin_limit_cycles=2_000_000, test_hold_column=5, stage_bytes=stage))
+    assert ei.value.status == kc.KC_ETIMEOUT
+    val, diag, zp = kc.factor(pat, T(xo), kg, kc.FP64, kc.make_opts(stage_bytes=stage))
+    val_ref, _ = oracle.ichol(xo, rp, col, ko)
+    assert row_rel(H(val), val_ref, rp) < 1e-12
+
+
 # --------------------------------------------------------------------- solve
 
 @pytest.mark.parametrize("prec", [0, 1])
