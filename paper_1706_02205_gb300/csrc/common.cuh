@@ -86,6 +86,12 @@ __device__ __forceinline__ void red_release_add_u32(unsigned* p, unsigned v) {
     asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 __device__ __forceinline__ int ld_volatile_s32(const int* p) { return *(volatile const int*)p; }
+// relaxed load at GPU scope: an acquire fence after it completes the synchronisation
+__device__ __forceinline__ unsigned ld_relaxed_u32(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
 
 // Loads that bypass L1 (values written by other SMs during the same launch).
 __device__ __forceinline__ double ldcg(const double* p) { return __ldcg(p); }

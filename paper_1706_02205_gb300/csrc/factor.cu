@@ -251,14 +251,14 @@ __device__ __forceinline__ float theta_off<float>(const KernelParams& kp, int d,
 
 // done[k] starts at minus the number of tasks of column k and every finished
 // task adds one, so column k is complete exactly when done[k] >= 0: one load
-// per dependency.  Bounded wait; false when the budget ran out or the kernel
-// is stopping.
-__device__ __forceinline__ bool done_ready(const unsigned* f) { return (int)ld_acquire_u32(f) >= 0; }
-__device__ __forceinline__ bool wait_done(const unsigned* f, const int* status, long long limit) {
-    if (done_ready(f)) return true;
+// per dependency.  The loads are relaxed so that a lane's checks all go out
+// at once; an acquire fence after them orders the value loads that follow.
+// spin_done: bounded wait (backoff) on a column not yet complete; false when
+// the budget ran out or the kernel is stopping.
+__device__ __forceinline__ bool spin_done(const unsigned* f, const int* status, long long limit) {
     const long long t0 = clock64();
     unsigned ns = 32;
-    while (!done_ready(f)) {
+    while ((int)ld_relaxed_u32(f) < 0) {
         if (clock64() - t0 > limit || ld_volatile_s32(status) != 0) return false;
         __nanosleep(ns);
         if (ns < 512) ns <<= 1;
@@ -298,29 +298,47 @@ __device__ __forceinline__ int task_begin(const FactorArgs<T>& A, RowTable<T>& t
     X.nr = (int)(X.a1 - X.a0);
     X.kp = A.col_set ? A.kps[A.col_set[X.i]] : A.kp;
 
-    bool ok = true;
-    for (int e = lane; e < X.nr && ok; e += 32) {
-        const int k = __ldg(&A.col[X.a0 + e]);
-        ok = wait_done(&A.done[k], A.status, A.spin_limit);
-    }
-    if (!__all_sync(FULL, ok)) {
-        if (lane == 0) atomicCAS(A.status, 0, DEV_TIMEOUT);
-        return 2;
-    }
-    __threadfence();
-    __syncwarp();
-
     X.staged = 2 * X.nr <= (1 << A.hbits);  // load factor <= 1/2 (linear-probing misses stay short)
     if (X.staged) tab.clear(lane);
     __syncwarp();
-    // sum of squares of row i with the accumulator of the merges (FP32 form:
-    // compensated, its two parts added in FP64); the update and its square
-    // root in FP64
+    // R_i in rounds of DEPS entries per lane: the column indices, the completion
+    // counters of those columns (relaxed loads, all in flight together; a
+    // bounded spin only on columns not yet complete), one acquire fence, then
+    // the values into the table and the sum of squares (the accumulator of the
+    // merges: FP32 form compensated, its two parts added in FP64 below).  Each
+    // lane reads only the values of the columns it checked itself; the other
+    // lanes' columns are ordered by the warp barrier at the end.
+    constexpr int DEPS = 8;
     Acc<T> sq;
-    for (int e = lane; e < X.nr; e += 32) {
-        const T v = ldcg(&A.val[X.a0 + e]);
-        if (X.staged) tab.insert(__ldg(&A.col[X.a0 + e]), v);
-        sq.add(v, v);
+    for (int e0 = 0; e0 < X.nr; e0 += 32 * DEPS) {
+        int kk[DEPS];
+#pragma unroll
+        for (int u = 0; u < DEPS; ++u) {
+            const int e = e0 + lane + 32 * u;
+            kk[u] = e < X.nr ? __ldg(&A.col[X.a0 + e]) : -1;
+        }
+        unsigned pend = 0;
+#pragma unroll
+        for (int u = 0; u < DEPS; ++u)
+            if (kk[u] >= 0 && (int)ld_relaxed_u32(&A.done[kk[u]]) < 0) pend |= 1u << u;
+        bool ok = true;
+#pragma unroll
+        for (int u = 0; u < DEPS; ++u)
+            if (ok && ((pend >> u) & 1u)) ok = spin_done(&A.done[kk[u]], A.status, A.spin_limit);
+        if (!__all_sync(FULL, ok)) {
+            if (lane == 0) atomicCAS(A.status, 0, DEV_TIMEOUT);
+            return 2;
+        }
+        __threadfence();  // acquire: the columns' values are visible from here on
+        T vv[DEPS];
+#pragma unroll
+        for (int u = 0; u < DEPS; ++u) vv[u] = kk[u] >= 0 ? ldcg(&A.val[X.a0 + e0 + lane + 32 * u]) : (T)0;
+#pragma unroll
+        for (int u = 0; u < DEPS; ++u)
+            if (kk[u] >= 0) {
+                if (X.staged) tab.insert(kk[u], vv[u]);
+                sq.add(vv[u], vv[u]);
+            }
     }
     sq.group_reduce(32);
     // Lane 0 forms the pivot and every lane takes its values: one pivot for the
