@@ -129,7 +129,7 @@ def run_ours(args, rank, world):
         col = kc.pattern_fill(xo, l, args.rho, rowptr, nnz)
         if ev:
             ev[2].record(stream)
-        pat = kc.schedule(rowptr, col)
+        pat = kc.schedule(rowptr, col, xo)
         if ev:
             ev[3].record(stream)
         val, diag, zp = kc.factor(pat, xo, kern, prec)
@@ -340,7 +340,7 @@ def run_cube3d(args):
         rowptr, nnz = kc.pattern_count(xo, l, 4.0)
         col = kc.pattern_fill(xo, l, 4.0, rowptr, nnz)
         ev[2].record(stream)
-        pat = kc.schedule(rowptr, col)
+        pat = kc.schedule(rowptr, col, xo)
         ev[3].record(stream)
         val, diag, zp = kc.factor(pat, xo, kern, kc.FP32_FORM)
         ev[4].record(stream)

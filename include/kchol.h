@@ -82,11 +82,10 @@ typedef struct {
     const int64_t* colptr;   /* [N+1] CSC columns of L (from kc_schedule) */
     const int32_t* rowidx;   /* [nnz] rows of each column, ascending, diagonal first */
     const int64_t* slot;     /* [nnz] CSR position of each CSC entry */
-    const int32_t* order;    /* [N]   columns sorted by (dependency level, index) */
+    const int32_t* order;    /* [N]   columns sorted by dependency level (kc_schedule): the order
+                                the factor and the solves take them in */
     int32_t depth;           /* number of dependency levels */
-    const int32_t* level;    /* [N]   dependency level of every column, or NULL.  When given, the
-                                factor runs each level's columns in spatial (Morton) order of
-                                their points, so tasks that read the same rows run close in time */
+    const int32_t* level;    /* [N]   dependency level of every column (informational; may be NULL) */
 } kc_pattern;
 
 /* Options of the persistent kernels (zero-initialise for defaults). */
@@ -142,10 +141,14 @@ kc_status kc_pattern_fill(const double* x_ord, const double* l, int64_t N, int32
 /* ---- a4: schedule ------------------------------------------------------ *
  * From the CSR rows: CSC (colptr int64[N+1], rowidx int32[nnz], slot
  * int64[nnz]), dependency levels level int32[N] with level(i) = 1 + max over
- * k in row i of level(k), and order int32[N] = columns sorted by (level,
- * index).  depth_out (host) = number of levels.  Synchronises. */
-kc_status kc_schedule(int64_t N, const int64_t* rowptr, const int32_t* col, int64_t* colptr,
-                      int32_t* rowidx, int64_t* slot, int32_t* level, int32_t* order,
+ * k in row i of level(k), and order int32[N] = the columns sorted by level;
+ * within a level by index, or, when x_ord (device double[N*d], the points in
+ * the pattern's order; may be NULL) is given, by the Morton code of each
+ * column's point, so that the factor's and the solves' consecutive work items
+ * touch neighbouring points (better L2 reuse).  depth_out (host) = number of
+ * levels.  Synchronises. */
+kc_status kc_schedule(int64_t N, const int64_t* rowptr, const int32_t* col, const double* x_ord, int32_t d,
+                      int64_t* colptr, int32_t* rowidx, int64_t* slot, int32_t* level, int32_t* order,
                       int32_t* depth_out, void* stream);
 
 /* ---- a5+a6: ICHOL(0) factor (Algorithm 2, left-looking form) ------------ *

@@ -55,7 +55,7 @@ class BatchFactor:
                                                       [s["col"] for s in self.sets])
         self.x_ord = kc.points_concat([s["x_ord"] for s in self.sets])
         self.perm = kc.index_concat([s["perm"] for s in self.sets])
-        self.pat = kc.schedule(rowptr, col)
+        self.pat = kc.schedule(rowptr, col, self.x_ord)
         self.nnz_offsets = [int(v) for v in rowptr[self.offsets].cpu()]
         self.plan = kc.FactorPlan(self.pat, self.x_ord, self.kerns, self.col_set if len(self.kerns) > 1 else None,
                                   prec, opts)

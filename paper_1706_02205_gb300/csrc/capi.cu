@@ -8,9 +8,9 @@ kc_status pattern_count_impl(const double* x_ord, const double* l, int64_t N, in
                              int64_t* rowptr, int64_t* nnz_out, cudaStream_t s);
 kc_status pattern_fill_impl(const double* x_ord, const double* l, int64_t N, int d, double rho, int rule,
                             const int64_t* rowptr, int32_t* col, cudaStream_t s);
-kc_status schedule_impl(int64_t N, const int64_t* rowptr, const int32_t* col, int64_t nnz, int64_t* colptr,
-                        int32_t* rowidx, int64_t* slot, int32_t* level, int32_t* order, int32_t* depth_out,
-                        cudaStream_t s);
+kc_status schedule_impl(int64_t N, const int64_t* rowptr, const int32_t* col, int64_t nnz, const double* x, int d,
+                        int64_t* colptr, int32_t* rowidx, int64_t* slot, int32_t* level, int32_t* order,
+                        int32_t* depth_out, cudaStream_t s);
 kc_status factor_impl(const kc_pattern* P, const double* x, int d, const kc_kernel* kern, int prec, void* val,
                       double* diag, int64_t* zero_out, const kc_opts* o, cudaStream_t s);
 kc_status solve_impl(const kc_pattern* P, int prec, const void* val, const double* diag, const kc_kernel* kern,
@@ -94,17 +94,19 @@ kc_status kc_pattern_fill(const double* x_ord, const double* l, int64_t N, int32
     return pattern_fill_impl(x_ord, l, N, d, rho, rule, rowptr, col, (cudaStream_t)stream);
 }
 
-kc_status kc_schedule(int64_t N, const int64_t* rowptr, const int32_t* col, int64_t* colptr, int32_t* rowidx,
-                      int64_t* slot, int32_t* level, int32_t* order, int32_t* depth_out, void* stream) {
+kc_status kc_schedule(int64_t N, const int64_t* rowptr, const int32_t* col, const double* x_ord, int32_t d,
+                      int64_t* colptr, int32_t* rowidx, int64_t* slot, int32_t* level, int32_t* order,
+                      int32_t* depth_out, void* stream) {
     if (N < 1 || N > INT32_MAX) return fail(KC_EINVAL, "N must be in 1..2^31-1");
     if (!rowptr || !col || !colptr || !rowidx || !slot || !level || !order)
         return fail(KC_EINVAL, "arrays must be non-NULL");
+    if (x_ord && d < 1) return fail(KC_EINVAL, "d must be >= 1 when x_ord is given");
     cudaStream_t s = (cudaStream_t)stream;
     int64_t nnz = 0;
     KC_CUDA(cudaMemcpyAsync(&nnz, rowptr + N, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     KC_CUDA(cudaStreamSynchronize(s));
     if (nnz < N) return fail(KC_EINVAL, "rowptr[N] must be >= N");
-    return schedule_impl(N, rowptr, col, nnz, colptr, rowidx, slot, level, order, depth_out, s);
+    return schedule_impl(N, rowptr, col, nnz, x_ord, d, colptr, rowidx, slot, level, order, depth_out, s);
 }
 
 kc_status kc_factor(const kc_pattern* pat, const double* x_ord, int32_t d, const kc_kernel* kern, int32_t prec,

@@ -739,46 +739,12 @@ __global__ void max_row_k(const int64_t* __restrict__ rowptr, int64_t N, int* __
     if (lane_id() == 0) atomicMax(out, m);
 }
 
-// Morton code of the first min(d,3) coordinates, quantised in the box [lo, hi]
-__device__ __forceinline__ uint32_t morton_of(const double* x, int d, const double* lo, const double* inv) {
-    const int dg = d < 3 ? d : 3;
-    const int bits = dg <= 2 ? 16 : 10;
-    uint32_t q[3] = {0, 0, 0};
-    for (int t = 0; t < dg; ++t) {
-        double f = (x[t] - lo[t]) * inv[t];
-        f = f < 0.0 ? 0.0 : (f > 1.0 ? 1.0 : f);
-        q[t] = (uint32_t)(f * (double)((1u << bits) - 1));
-    }
-    uint32_t m = 0;
-    for (int b = bits - 1; b >= 0; --b)
-        for (int t = 0; t < dg; ++t) m = (m << 1) | ((q[t] >> b) & 1u);
-    return m;
-}
-struct Box3 {
-    double lo[3], inv[3];
-};
-__global__ void level_morton_keys_k(const int32_t* __restrict__ order, const int32_t* __restrict__ level,
-                                    const double* __restrict__ x, int d, Box3 box, int64_t N,
-                                    uint64_t* __restrict__ key, int64_t* __restrict__ val) {
-    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p < N) {
-        const int i = order[p];
-        key[p] = ((uint64_t)(uint32_t)level[i] << 32) | morton_of(x + (int64_t)i * d, d, box.lo, box.inv);
-        val[p] = i;
-    }
-}
-__global__ void i64_to_i32_k(const int64_t* __restrict__ v, int64_t n, int32_t* __restrict__ out) {
-    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p < n) out[p] = (int32_t)v[p];
-}
-
-// Build the task list (level order) of a pattern; returns count on the host.
-// With points x and the pattern's levels, the columns of each level are put
-// in Morton order of their points: consecutive tasks then merge rows of
-// neighbouring points, which share most of their entries, so the row
-// prefixes they read are often still in L2.
+// Build the task list of a pattern (its columns in the schedule's order:
+// by level, within a level in space-filling-curve order when the schedule was
+// given the points, so that consecutive tasks merge rows of neighbouring
+// points, which share most of their entries); returns the count on the host.
 kc_status build_tasks(const kc_pattern* P, int rpt, Arena& A, cudaStream_t s, int2** tasks_out, int64_t* ntasks_out,
-                      int* max_row_out, const double* x, int d, bool adaptive) {
+                      int* max_row_out, bool adaptive) {
     int64_t N = P->N;
     int64_t* cnt;
     int64_t* toff;
@@ -787,32 +753,6 @@ kc_status build_tasks(const kc_pattern* P, int rpt, Arena& A, cudaStream_t s, in
     KC_TRY(A.get(&toff, N + 1));
     KC_TRY(A.get(&mr, 1));
     const int32_t* order = P->order;
-    if (x && P->level) {
-        double lo[3], hi[3];
-        KC_TRY(bbox(x, N, d, lo, hi, A, s));
-        Box3 box;
-        for (int t = 0; t < 3; ++t) {
-            box.lo[t] = t < d ? lo[t] : 0.0;
-            const double e = t < d ? hi[t] - lo[t] : 0.0;
-            box.inv[t] = e > 0 ? 1.0 / e : 0.0;
-        }
-        uint64_t *k0, *k1;
-        int64_t *v0, *v1;
-        int32_t* ord2;
-        KC_TRY(A.get(&k0, N));
-        KC_TRY(A.get(&k1, N));
-        KC_TRY(A.get(&v0, N));
-        KC_TRY(A.get(&v1, N));
-        KC_TRY(A.get(&ord2, N));
-        ::kc::note_launch(), level_morton_keys_k<<<blocks_for(N, 256), 256, 0, s>>>(P->order, P->level, x, d, box, N,
-                                                                                   k0, v0);
-        int lb = 1;
-        while (lb < 31 && (1 << lb) <= P->depth) ++lb;
-        KC_TRY(radix_sort_u64_i64(k0, v0, k1, v1, N, 32 + lb, A, s));
-        ::kc::note_launch(), i64_to_i32_k<<<blocks_for(N, 256), 256, 0, s>>>(v1, N, ord2);
-        KC_CUDA(cudaGetLastError());
-        order = ord2;
-    }
     ::kc::note_launch(), task_count_k<<<blocks_for(N, 256), 256, 0, s>>>(order, P->colptr, P->rowptr, N, rpt,
                                                                             adaptive ? 1 : 0, cnt);
     KC_TRY(exclusive_scan_i64(cnt, toff, N, A, s));
@@ -1000,7 +940,7 @@ kc_status factor_impl(const kc_pattern* P, const double* x, int d, const kc_kern
     F.x = x;
     auto_rows(F);
     Arena A(s);
-    KC_TRY(build_tasks(P, F.rpt, A, s, &F.tasks, &F.ntasks, &F.maxr, x, d, F.adaptive != 0));
+    KC_TRY(build_tasks(P, F.rpt, A, s, &F.tasks, &F.ntasks, &F.maxr, F.adaptive != 0));
     pick_hash(F);
     KC_TRY(A.get(&F.done, P->N));
     KC_TRY(A.get(&F.ticket, 1));
@@ -1063,7 +1003,7 @@ kc_status plan_create_impl(const kc_pattern* P, const double* x, int d, const kc
     {
         Arena A(s);
         int2* t;
-        st = build_tasks(P, F.rpt, A, s, &t, &F.ntasks, &F.maxr, x, d, F.adaptive != 0);
+        st = build_tasks(P, F.rpt, A, s, &t, &F.ntasks, &F.maxr, F.adaptive != 0);
         if (st != KC_OK) return bail(st);
         if ((st = plan_alloc(pl, (void**)&F.tasks, sizeof(int2) * F.ntasks)) != KC_OK) return bail(st);
         if (cudaMemcpyAsync(F.tasks, t, sizeof(int2) * F.ntasks, cudaMemcpyDeviceToDevice, s) != cudaSuccess)

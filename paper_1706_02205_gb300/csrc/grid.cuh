@@ -77,6 +77,27 @@ __device__ __forceinline__ int screen_f32(const float* a, const float* b, int d,
     return -1;
 }
 
+// Morton code of the first min(d,3) coordinates, quantised in the box
+// [lo, lo + 1/inv] (16 bits per axis in 2-D, 10 in 3-D): points close in
+// space get close codes.
+struct Box3 {
+    double lo[3], inv[3];
+};
+__device__ __forceinline__ uint32_t morton_of(const double* x, int d, const Box3& box) {
+    const int dg = d < 3 ? d : 3;
+    const int bits = dg <= 2 ? 16 : 10;
+    uint32_t q[3] = {0, 0, 0};
+    for (int t = 0; t < dg; ++t) {
+        double f = (x[t] - box.lo[t]) * box.inv[t];
+        f = f < 0.0 ? 0.0 : (f > 1.0 ? 1.0 : f);
+        q[t] = (uint32_t)(f * (double)((1u << bits) - 1));
+    }
+    uint32_t m = 0;
+    for (int b = bits - 1; b >= 0; --b)
+        for (int t = 0; t < dg; ++t) m = (m << 1) | ((q[t] >> b) & 1u);
+    return m;
+}
+
 // Host: choose a grid for `npts` points in the box [lo, hi] with target cell
 // size `want` (0 = automatic), at most `max_cells` cells.
 Grid make_grid(int d, const double* lo, const double* hi, int64_t npts, double want, int64_t max_cells);

@@ -5,8 +5,11 @@
 // levels are level(i) = 1 + max_{k in R_i} level(k).  This file builds, on the
 // device: the CSC view of L (rows of each column ascending, with the CSR slot
 // of every entry), the levels (a sync-free kernel over rows in index order),
-// and the columns sorted by (level, index) with a stable radix sort.
-#include "common.cuh"
+// and the columns sorted by level with a stable radix sort; within a level by
+// index, or, given the points, by the Morton code of each column's point, so
+// that the factor's consecutive tasks and the solves' consecutive rows touch
+// neighbouring points, whose rows share most of their entries (L2 reuse).
+#include "grid.cuh"
 
 namespace kc {
 
@@ -101,6 +104,14 @@ __global__ void level_keys_k(const int* __restrict__ level, int64_t N, uint32_t*
     }
 }
 
+__global__ void level_morton_keys_k(const int* __restrict__ level, const double* __restrict__ x, int d, Box3 box,
+                                    int64_t N, uint64_t* __restrict__ key, int64_t* __restrict__ val) {
+    int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < N) {
+        key[j] = ((uint64_t)(uint32_t)level[j] << 32) | morton_of(x + j * d, d, box);
+        val[j] = j;
+    }
+}
 __global__ void order_out_k(const int64_t* __restrict__ sval, int64_t N, int32_t* __restrict__ order) {
     int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p < N) order[p] = (int32_t)sval[p];
@@ -112,9 +123,9 @@ static int bits_for(int64_t v) {
     return b;
 }
 
-kc_status schedule_impl(int64_t N, const int64_t* rowptr, const int32_t* col, int64_t nnz, int64_t* colptr,
-                        int32_t* rowidx, int64_t* slot, int32_t* level, int32_t* order, int32_t* depth_out,
-                        cudaStream_t s) {
+kc_status schedule_impl(int64_t N, const int64_t* rowptr, const int32_t* col, int64_t nnz, const double* x, int d,
+                        int64_t* colptr, int32_t* rowidx, int64_t* slot, int32_t* level, int32_t* order,
+                        int32_t* depth_out, cudaStream_t s) {
     Arena A(s);
     // CSC by a stable sort of the CSR entries by column
     int32_t* rowof;
@@ -152,10 +163,28 @@ kc_status schedule_impl(int64_t N, const int64_t* rowptr, const int32_t* col, in
     KC_CUDA(cudaStreamSynchronize(s));
     if (h_status != 0) return fail(KC_ETIMEOUT, "level computation: a dependency wait ran out");
 
-    // columns sorted by (level, index)
-    ::kc::note_launch(), level_keys_k<<<blocks_for(N, 256), 256, 0, s>>>(level, N, k0, v0);
-    KC_CUDA(cudaGetLastError());
-    KC_TRY(radix_sort_u32_i64(k0, v0, k1, v1, N, bits_for(h_depth), A, s));
+    if (x) {
+        // columns sorted by (level, Morton code of the point)
+        double lo[3], hi[3];
+        KC_TRY(bbox(x, N, d, lo, hi, A, s));
+        Box3 box;
+        for (int t = 0; t < 3; ++t) {
+            box.lo[t] = t < d ? lo[t] : 0.0;
+            const double e = t < d ? hi[t] - lo[t] : 0.0;
+            box.inv[t] = e > 0 ? 1.0 / e : 0.0;
+        }
+        uint64_t *m0, *m1;
+        KC_TRY(A.get(&m0, N));
+        KC_TRY(A.get(&m1, N));
+        ::kc::note_launch(), level_morton_keys_k<<<blocks_for(N, 256), 256, 0, s>>>(level, x, d, box, N, m0, v0);
+        KC_CUDA(cudaGetLastError());
+        KC_TRY(radix_sort_u64_i64(m0, v0, m1, v1, N, 32 + bits_for(h_depth), A, s));
+    } else {
+        // columns sorted by (level, index)
+        ::kc::note_launch(), level_keys_k<<<blocks_for(N, 256), 256, 0, s>>>(level, N, k0, v0);
+        KC_CUDA(cudaGetLastError());
+        KC_TRY(radix_sort_u32_i64(k0, v0, k1, v1, N, bits_for(h_depth), A, s));
+    }
     ::kc::note_launch(), order_out_k<<<blocks_for(N, 256), 256, 0, s>>>(v1, N, order);
     KC_CUDA(cudaGetLastError());
     KC_CUDA(cudaStreamSynchronize(s));

@@ -6,12 +6,17 @@
 //                     ready flags of its R_j.
 // Backward L^T x = y: x_i = (y_i - sum_{j in C_i} L_ji x_j) / L_ii, over the
 //                     CSC columns in reverse level order; wide columns are cut
-//                     into the same chunks as the factor's tasks, each chunk
-//                     adds its partial sum atomically and the last chunk of a
-//                     column finishes x_i.
-// Vectors are point-major inside (v[k * nrhs + r]) so one entry's right-hand
-// sides are contiguous; lanes map to (entry, rhs) pairs.  Sums are FP64 for
-// both value types.  A dropped pivot (L_ii = 0) uses sqrt(Theta_ii).
+//                     into chunks of rows, each chunk adds its partial sums
+//                     atomically and the last chunk of a column finishes x_i.
+//
+// Vectors are point-major inside with a power-of-two stride NR >= nrhs
+// (v[k * NR + r]), so one point's right-hand sides are one aligned run that a
+// lane gathers with 16-byte loads.  A lane owns entries of the row (or rows of
+// the column): the readiness checks go out as relaxed loads all at once (a
+// bounded spin only on points not yet solved, then one acquire fence), the
+// values and the gathers follow in a few rounds, and the warp reduces its NR
+// partial sums with a reduce-scatter.  Sums are FP64 for both value types.  A
+// dropped pivot (L_ii = 0) uses sqrt(Theta_ii).
 #include "solver.cuh"
 
 namespace kc {
@@ -19,7 +24,6 @@ namespace kc {
 template <typename T>
 struct SolveArgs {
     int64_t N;
-    int nrhs, NR;  // NR = nrhs rounded up to a power of two (<= 16)
     const int64_t* __restrict__ rowptr;
     const int32_t* __restrict__ col;
     const int64_t* __restrict__ colptr;
@@ -43,11 +47,17 @@ struct SolveArgs {
     long long spin_limit;
 };
 
-__device__ __forceinline__ bool wait_flag(const int* f, const int* status, long long limit) {
-    if (ld_acquire_s32(f) != 0) return true;
-    long long t0 = clock64();
+__device__ __forceinline__ int ld_relaxed_s32(const int* p) {
+    int v;
+    asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+// bounded wait (backoff) on a point not yet solved; false when the budget ran
+// out or the kernel is stopping
+__device__ __forceinline__ bool spin_flag(const int* f, const int* status, long long limit) {
+    const long long t0 = clock64();
     unsigned ns = 32;
-    while (ld_acquire_s32(f) == 0) {
+    while (ld_relaxed_s32(f) == 0) {
         if (clock64() - t0 > limit || ld_volatile_s32(status) != 0) return false;
         __nanosleep(ns);  // back off so waiting warps do not flood L2 with polls
         if (ns < 512) ns <<= 1;
@@ -55,12 +65,109 @@ __device__ __forceinline__ bool wait_flag(const int* f, const int* status, long 
     return true;
 }
 
-template <typename T>
+// The NR values of point k (16-byte loads; values written during the launch,
+// so through L2).
+template <int NR>
+__device__ __forceinline__ void gather(const double* v, int k, double* out) {
+    if constexpr (NR == 1) {
+        out[0] = __ldcg(v + k);
+    } else {
+        const double2* p = (const double2*)(v + (int64_t)k * NR);
+#pragma unroll
+        for (int q = 0; q < NR / 2; ++q) {
+            const double2 w = __ldcg(p + q);
+            out[2 * q] = w.x;
+            out[2 * q + 1] = w.y;
+        }
+    }
+}
+
+// Warp reduce-scatter of NR partial sums per lane: each level halves the
+// values a lane keeps (offsets 16, 8, ...), plain sums finish the rest.  The
+// lane ends with the full sum of right-hand side rhs_of_lane<NR>(lane).
+template <int NR>
+__device__ __forceinline__ double reduce_scatter(double (&v)[NR], int lane) {
+    const unsigned FULL = 0xffffffffu;
+#pragma unroll
+    for (int h = NR / 2, o = 16; h >= 1; h >>= 1, o >>= 1) {
+        const bool up = (lane & o) != 0;
+#pragma unroll
+        for (int q = 0; q < h; ++q) {
+            const double send = up ? v[q] : v[q + h];
+            const double keep = up ? v[q + h] : v[q];
+            v[q] = keep + __shfl_xor_sync(FULL, send, o);
+        }
+    }
+    constexpr int L = NR == 1 ? 0 : NR == 2 ? 1 : NR == 4 ? 2 : NR == 8 ? 3 : 4;
+#pragma unroll
+    for (int o = 16 >> L; o >= 1; o >>= 1) v[0] += __shfl_xor_sync(FULL, v[0], o);
+    return v[0];
+}
+template <int NR>
+__device__ __forceinline__ int rhs_of_lane(int lane) {
+    int r = 0;
+#pragma unroll
+    for (int h = NR / 2, o = 16; h >= 1; h >>= 1, o >>= 1)
+        if (lane & o) r += h;
+    return r;
+}
+// one writer per right-hand side: the lanes sharing r differ in the low bits
+template <int NR>
+__device__ __forceinline__ bool rhs_writer(int lane) {
+    return (lane & (32 / NR - 1)) == 0;
+}
+
+// Entries in flight per lane while gathering: at most 32 doubles.
+template <int NR>
+struct Depth {
+    static constexpr int E = NR >= 4 ? 32 / NR : 8;
+};
+
+// Readiness of the points kk[0..D) (negative: none): relaxed loads together,
+// bounded spins on the rest, one acquire fence.  False: a wait ran out.
+template <int D>
+__device__ __forceinline__ bool points_ready(const int* ready, const int (&kk)[D], const int* status, long long lim) {
+    unsigned pend = 0;
+#pragma unroll
+    for (int u = 0; u < D; ++u)
+        if (kk[u] >= 0 && ld_relaxed_s32(&ready[kk[u]]) == 0) pend |= 1u << u;
+    bool ok = true;
+#pragma unroll
+    for (int u = 0; u < D; ++u)
+        if (ok && ((pend >> u) & 1u)) ok = spin_flag(&ready[kk[u]], status, lim);
+    ok = __all_sync(0xffffffffu, ok);
+    __threadfence();  // acquire: the points' values are visible from here on
+    return ok;
+}
+
+// acc[r] += w[u] * v[k[u] * NR + r] for the D entries, E gathers at a time
+template <int NR, int D>
+__device__ __forceinline__ void gather_fma(const double* v, const int (&k)[D], const double (&w)[D],
+                                           double (&acc)[NR]) {
+    constexpr int E = Depth<NR>::E < D ? Depth<NR>::E : D;
+#pragma unroll
+    for (int u0 = 0; u0 < D; u0 += E) {
+        double g[E][NR];
+#pragma unroll
+        for (int q = 0; q < E; ++q) {
+            if (k[u0 + q] >= 0) gather<NR>(v, k[u0 + q], g[q]);
+            else
+#pragma unroll
+                for (int r = 0; r < NR; ++r) g[q][r] = 0.0;
+        }
+#pragma unroll
+        for (int q = 0; q < E; ++q)
+            if (k[u0 + q] >= 0)  // the FP64 pipe is scarce: no products for empty slots
+#pragma unroll
+                for (int r = 0; r < NR; ++r) acc[r] = fma(w[u0 + q], g[q][r], acc[r]);
+    }
+}
+
+template <typename T, int NR>
 __global__ void __launch_bounds__(256) fwd_solve_k(SolveArgs<T> A) {
+    constexpr int D = 8;  // entries of R_j per lane per round
     const int lane = lane_id();
     const unsigned FULL = 0xffffffffu;
-    const int per = 32 / A.NR;  // entries per warp step
-    const int r = lane % A.NR, eo = lane / A.NR;
     for (;;) {
         unsigned long long t = 0;
         if (lane == 0) t = atomicAdd(A.ticket, 1ULL);
@@ -68,38 +175,33 @@ __global__ void __launch_bounds__(256) fwd_solve_k(SolveArgs<T> A) {
         if ((int64_t)t >= A.N) return;
         if (ld_volatile_s32(A.status) != 0) return;
         const int j = A.order[t];
-        const int64_t a = A.rowptr[j], b = A.rowptr[j + 1] - 1;
-        bool ok = true;
-        for (int64_t e = a + lane; e < b && ok; e += 32) ok = wait_flag(&A.ready[__ldg(&A.col[e])], A.status, A.spin_limit);
-        if (!__all_sync(FULL, ok)) {
-            if (lane == 0) atomicCAS(A.status, 0, DEV_TIMEOUT);
-            return;
-        }
-        __threadfence();
-        __syncwarp();
-        double s = 0.0;
-        if (r < A.nrhs) {
-            // four independent (col, val, y) loads in flight per lane
-            double s1 = 0.0, s2 = 0.0, s3 = 0.0;
-            int64_t e = a + eo;
-            for (; e + 3 * per < b; e += 4 * per) {
-                const int k0 = __ldg(&A.col[e]), k1 = __ldg(&A.col[e + per]);
-                const int k2 = __ldg(&A.col[e + 2 * per]), k3 = __ldg(&A.col[e + 3 * per]);
-                const double v0 = (double)__ldg(&A.val[e]), v1 = (double)__ldg(&A.val[e + per]);
-                const double v2 = (double)__ldg(&A.val[e + 2 * per]), v3 = (double)__ldg(&A.val[e + 3 * per]);
-                s = fma(v0, __ldcg(&A.y[(int64_t)k0 * A.nrhs + r]), s);
-                s1 = fma(v1, __ldcg(&A.y[(int64_t)k1 * A.nrhs + r]), s1);
-                s2 = fma(v2, __ldcg(&A.y[(int64_t)k2 * A.nrhs + r]), s2);
-                s3 = fma(v3, __ldcg(&A.y[(int64_t)k3 * A.nrhs + r]), s3);
+        const int64_t a = A.rowptr[j];
+        const int n = (int)(A.rowptr[j + 1] - 1 - a);
+        double acc[NR];
+#pragma unroll
+        for (int r = 0; r < NR; ++r) acc[r] = 0.0;
+        for (int e0 = 0; e0 < n; e0 += 32 * D) {
+            int kk[D];
+#pragma unroll
+            for (int u = 0; u < D; ++u) {
+                const int e = e0 + lane + 32 * u;
+                kk[u] = e < n ? __ldg(&A.col[a + e]) : -1;
             }
-            for (; e < b; e += per) s = fma((double)__ldg(&A.val[e]), __ldcg(&A.y[(int64_t)__ldg(&A.col[e]) * A.nrhs + r]), s);
-            s = (s + s1) + (s2 + s3);
+            if (!points_ready<D>(A.ready, kk, A.status, A.spin_limit)) {
+                if (lane == 0) atomicCAS(A.status, 0, DEV_TIMEOUT);
+                return;
+            }
+            double w[D];
+#pragma unroll
+            for (int u = 0; u < D; ++u) w[u] = kk[u] >= 0 ? (double)__ldg(&A.val[a + e0 + lane + 32 * u]) : 0.0;
+            gather_fma<NR, D>(A.y, kk, w, acc);
         }
-        for (int o = 16; o >= A.NR; o >>= 1) s += __shfl_xor_sync(FULL, s, o);
-        if (eo == 0 && r < A.nrhs) {
+        const double s = reduce_scatter<NR>(acc, lane);
+        if (rhs_writer<NR>(lane)) {
+            const int r = rhs_of_lane<NR>(lane);
             double dj = A.diag[j];
             if (!(dj > 0.0)) dj = A.diag_fallback;
-            A.y[(int64_t)j * A.nrhs + r] = (A.b[(int64_t)j * A.nrhs + r] - s) / dj;
+            A.y[(int64_t)j * NR + r] = (A.b[(int64_t)j * NR + r] - s) / dj;
         }
         __threadfence();
         __syncwarp();
@@ -107,12 +209,11 @@ __global__ void __launch_bounds__(256) fwd_solve_k(SolveArgs<T> A) {
     }
 }
 
-template <typename T>
+template <typename T, int NR>
 __global__ void __launch_bounds__(256) bwd_solve_k(SolveArgs<T> A) {
+    constexpr int D = 4;  // rows of the chunk per lane per round
     const int lane = lane_id();
     const unsigned FULL = 0xffffffffu;
-    const int per = 32 / A.NR;
-    const int r = lane % A.NR, eo = lane / A.NR;
     for (;;) {
         unsigned long long t = 0;
         if (lane == 0) t = atomicAdd(A.ticket, 1ULL);
@@ -125,40 +226,34 @@ __global__ void __launch_bounds__(256) bwd_solve_k(SolveArgs<T> A) {
         const int64_t m = c1 - c0 - 1;
         const unsigned nch = m <= 0 ? 1u : (unsigned)((m + A.rpt - 1) / A.rpt);
         const int64_t qs = c0 + 1 + (int64_t)c * A.rpt;
-        const int64_t qe = min(c1, qs + A.rpt);
-        bool ok = true;
-        for (int64_t q = qs + lane; q < qe && ok; q += 32)
-            ok = wait_flag(&A.ready[__ldg(&A.rowidx[q])], A.status, A.spin_limit);
-        if (!__all_sync(FULL, ok)) {
-            if (lane == 0) atomicCAS(A.status, 0, DEV_TIMEOUT);
-            return;
-        }
-        __threadfence();
-        __syncwarp();
-        double s = 0.0;
-        if (r < A.nrhs) {
-            double s1 = 0.0, s2 = 0.0, s3 = 0.0;
-            int64_t q = qs + eo;
-            for (; q + 3 * per < qe; q += 4 * per) {
-                const int j0 = __ldg(&A.rowidx[q]), j1 = __ldg(&A.rowidx[q + per]);
-                const int j2 = __ldg(&A.rowidx[q + 2 * per]), j3 = __ldg(&A.rowidx[q + 3 * per]);
-                const int64_t p0 = __ldg(&A.slot[q]), p1 = __ldg(&A.slot[q + per]);
-                const int64_t p2 = __ldg(&A.slot[q + 2 * per]), p3 = __ldg(&A.slot[q + 3 * per]);
-                s = fma((double)__ldg(&A.val[p0]), __ldcg(&A.x[(int64_t)j0 * A.nrhs + r]), s);
-                s1 = fma((double)__ldg(&A.val[p1]), __ldcg(&A.x[(int64_t)j1 * A.nrhs + r]), s1);
-                s2 = fma((double)__ldg(&A.val[p2]), __ldcg(&A.x[(int64_t)j2 * A.nrhs + r]), s2);
-                s3 = fma((double)__ldg(&A.val[p3]), __ldcg(&A.x[(int64_t)j3 * A.nrhs + r]), s3);
+        const int nq = (int)(min(c1, qs + A.rpt) - qs);
+        double acc[NR];
+#pragma unroll
+        for (int r = 0; r < NR; ++r) acc[r] = 0.0;
+        for (int q0 = 0; q0 < nq; q0 += 32 * D) {
+            int jj[D];
+            int64_t pp[D];
+#pragma unroll
+            for (int u = 0; u < D; ++u) {
+                const int q = q0 + lane + 32 * u;
+                jj[u] = q < nq ? __ldg(&A.rowidx[qs + q]) : -1;
+                pp[u] = q < nq ? __ldg(&A.slot[qs + q]) : 0;
             }
-            for (; q < qe; q += per) {
-                const int j = __ldg(&A.rowidx[q]);
-                s = fma((double)__ldg(&A.val[__ldg(&A.slot[q])]), __ldcg(&A.x[(int64_t)j * A.nrhs + r]), s);
+            if (!points_ready<D>(A.ready, jj, A.status, A.spin_limit)) {
+                if (lane == 0) atomicCAS(A.status, 0, DEV_TIMEOUT);
+                return;
             }
-            s = (s + s1) + (s2 + s3);
+            double w[D];
+#pragma unroll
+            for (int u = 0; u < D; ++u) w[u] = jj[u] >= 0 ? (double)__ldg(&A.val[pp[u]]) : 0.0;
+            gather_fma<NR, D>(A.x, jj, w, acc);
         }
-        for (int o = 16; o >= A.NR; o >>= 1) s += __shfl_xor_sync(FULL, s, o);
+        double s = reduce_scatter<NR>(acc, lane);
+        const bool wr = rhs_writer<NR>(lane);
+        const int r = rhs_of_lane<NR>(lane);
         bool finish = true;
         if (nch > 1) {
-            if (eo == 0 && r < A.nrhs) atomicAdd(&A.acc[(int64_t)i * A.nrhs + r], s);
+            if (wr) atomicAdd(&A.acc[(int64_t)i * NR + r], s);
             __threadfence();
             __syncwarp();
             unsigned prev = 0;
@@ -167,14 +262,14 @@ __global__ void __launch_bounds__(256) bwd_solve_k(SolveArgs<T> A) {
             finish = (prev == nch - 1);
             if (finish) {
                 __threadfence();
-                s = __ldcg(&A.acc[(int64_t)i * A.nrhs + (r < A.nrhs ? r : 0)]);
+                s = __ldcg(&A.acc[(int64_t)i * NR + r]);
             }
         }
         if (finish) {
-            if (eo == 0 && r < A.nrhs) {
+            if (wr) {
                 double di = A.diag[i];
                 if (!(di > 0.0)) di = A.diag_fallback;
-                A.x[(int64_t)i * A.nrhs + r] = (A.y[(int64_t)i * A.nrhs + r] - s) / di;
+                A.x[(int64_t)i * NR + r] = (A.y[(int64_t)i * NR + r] - s) / di;
             }
             __threadfence();
             __syncwarp();
@@ -183,22 +278,23 @@ __global__ void __launch_bounds__(256) bwd_solve_k(SolveArgs<T> A) {
     }
 }
 
+// out[k * stride + r] = b[r * N + perm[k]] for r < nrhs, 0 for nrhs <= r < stride
 __global__ void to_point_major_k(const double* __restrict__ b, const int32_t* __restrict__ perm, int64_t N, int nrhs,
-                                 double* __restrict__ out) {
+                                 int stride, double* __restrict__ out) {
     int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t < N * nrhs) {
-        int64_t k = t / nrhs;
-        int r = (int)(t % nrhs);
-        out[t] = b[(int64_t)r * N + perm[k]];
+    if (t < N * stride) {
+        int64_t k = t / stride;
+        int r = (int)(t % stride);
+        out[t] = r < nrhs ? b[(int64_t)r * N + perm[k]] : 0.0;
     }
 }
 __global__ void from_point_major_k(const double* __restrict__ xp, const int32_t* __restrict__ perm, int64_t N,
-                                   int nrhs, double* __restrict__ x) {
+                                   int nrhs, int stride, double* __restrict__ x) {
     int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t < N * nrhs) {
         int64_t k = t / nrhs;
         int r = (int)(t % nrhs);
-        x[(int64_t)r * N + perm[k]] = xp[t];
+        x[(int64_t)r * N + perm[k]] = xp[k * stride + r];
     }
 }
 
@@ -219,16 +315,36 @@ kc_status solver_init(Solver& S, const kc_pattern* P, int nrhs_cap, const kc_opt
 
 // z = (L L^T)^{-1} rhs, point-major, positions order.  Does not synchronise;
 // the status word is checked by solver_check.
+template <typename T, int NR>
+static kc_status solve_launch(Solver& S, SolveArgs<T> a, int nrhs, cudaStream_t s) {
+    const kc_pattern* P = S.P;
+    const int grid = sm_count() * 8;
+    KC_CUDA(cudaMemsetAsync(S.ready, 0, sizeof(int) * P->N, s));
+    KC_CUDA(cudaMemsetAsync(S.ticket, 0, 2 * sizeof(unsigned long long), s));
+    KC_CUDA(cudaMemsetAsync(S.status, 0, sizeof(int), s));
+    a.ticket = S.ticket;
+    ::kc::note_launch(), fwd_solve_k<T, NR><<<grid, 256, 0, s>>>(a);
+    KC_CUDA(cudaGetLastError());
+    KC_CUDA(cudaMemsetAsync(S.ready, 0, sizeof(int) * P->N, s));
+    KC_CUDA(cudaMemsetAsync(S.cnt, 0, sizeof(unsigned) * P->N, s));
+    KC_CUDA(cudaMemsetAsync(S.acc, 0, sizeof(double) * P->N * NR, s));
+    a.ticket = S.ticket + 1;
+    ::kc::note_launch(), bwd_solve_k<T, NR><<<grid, 256, 0, s>>>(a);
+    KC_CUDA(cudaGetLastError());
+    return KC_OK;
+}
+
+// z = (L L^T)^{-1} rhs, point-major with stride nrhs (a power of two <= 16),
+// positions order.  Does not synchronise; the status word is checked by
+// solver_check.
 template <typename T>
 kc_status solver_apply(Solver& S, const T* val, const double* diag, double diag_fallback, const double* rhs,
                        double* z, int nrhs, cudaStream_t s) {
     const kc_pattern* P = S.P;
-    int NR = 1;
-    while (NR < nrhs) NR <<= 1;
+    if (nrhs < 1 || nrhs > 16 || (nrhs & (nrhs - 1)) || nrhs > S.nrhs_cap)
+        return fail(KC_EINVAL, "internal: solver stride must be a power of two <= 16");
     SolveArgs<T> a;
     a.N = P->N;
-    a.nrhs = nrhs;
-    a.NR = NR;
     a.rowptr = P->rowptr;
     a.col = P->col;
     a.colptr = P->colptr;
@@ -249,20 +365,13 @@ kc_status solver_apply(Solver& S, const T* val, const double* diag, double diag_
     a.ready = S.ready;
     a.status = S.status;
     a.spin_limit = S.spin;
-    int grid = sm_count() * 8;
-    KC_CUDA(cudaMemsetAsync(S.ready, 0, sizeof(int) * P->N, s));
-    KC_CUDA(cudaMemsetAsync(S.ticket, 0, 2 * sizeof(unsigned long long), s));
-    KC_CUDA(cudaMemsetAsync(S.status, 0, sizeof(int), s));
-    a.ticket = S.ticket;
-    ::kc::note_launch(), fwd_solve_k<T><<<grid, 256, 0, s>>>(a);
-    KC_CUDA(cudaGetLastError());
-    KC_CUDA(cudaMemsetAsync(S.ready, 0, sizeof(int) * P->N, s));
-    KC_CUDA(cudaMemsetAsync(S.cnt, 0, sizeof(unsigned) * P->N, s));
-    KC_CUDA(cudaMemsetAsync(S.acc, 0, sizeof(double) * P->N * nrhs, s));
-    a.ticket = S.ticket + 1;
-    ::kc::note_launch(), bwd_solve_k<T><<<grid, 256, 0, s>>>(a);
-    KC_CUDA(cudaGetLastError());
-    return KC_OK;
+    switch (nrhs) {
+        case 1: return solve_launch<T, 1>(S, a, nrhs, s);
+        case 2: return solve_launch<T, 2>(S, a, nrhs, s);
+        case 4: return solve_launch<T, 4>(S, a, nrhs, s);
+        case 8: return solve_launch<T, 8>(S, a, nrhs, s);
+        default: return solve_launch<T, 16>(S, a, nrhs, s);
+    }
 }
 template kc_status solver_apply<double>(Solver&, const double*, const double*, double, const double*, double*, int,
                                         cudaStream_t);
@@ -278,13 +387,17 @@ kc_status solver_check(Solver& S, cudaStream_t s) {
     return KC_OK;
 }
 
-kc_status to_point_major(const double* b, const int32_t* perm, int64_t N, int nrhs, double* out, cudaStream_t s) {
-    ::kc::note_launch(), to_point_major_k<<<blocks_for(N * nrhs, 256), 256, 0, s>>>(b, perm, N, nrhs, out);
+kc_status to_point_major(const double* b, const int32_t* perm, int64_t N, int nrhs, double* out, cudaStream_t s,
+                         int stride) {
+    if (stride < nrhs) stride = nrhs;
+    ::kc::note_launch(), to_point_major_k<<<blocks_for(N * stride, 256), 256, 0, s>>>(b, perm, N, nrhs, stride, out);
     KC_CUDA(cudaGetLastError());
     return KC_OK;
 }
-kc_status from_point_major(const double* xp, const int32_t* perm, int64_t N, int nrhs, double* x, cudaStream_t s) {
-    ::kc::note_launch(), from_point_major_k<<<blocks_for(N * nrhs, 256), 256, 0, s>>>(xp, perm, N, nrhs, x);
+kc_status from_point_major(const double* xp, const int32_t* perm, int64_t N, int nrhs, double* x, cudaStream_t s,
+                           int stride) {
+    if (stride < nrhs) stride = nrhs;
+    ::kc::note_launch(), from_point_major_k<<<blocks_for(N * nrhs, 256), 256, 0, s>>>(xp, perm, N, nrhs, stride, x);
     KC_CUDA(cudaGetLastError());
     return KC_OK;
 }
@@ -294,18 +407,20 @@ kc_status solve_impl(const kc_pattern* P, int prec, const void* val, const doubl
     KernelParams kp;
     KC_TRY(kernel_params(kern, &kp));
     if (nrhs < 1 || nrhs > 16) return fail(KC_EINVAL, "nrhs must be in 1..16");
+    if (prec != KC_FP64 && prec != KC_FP32_FORM) return fail(KC_EINVAL, "prec must be KC_FP64 or KC_FP32_FORM");
+    int ns = 1;
+    while (ns < nrhs) ns <<= 1;  // padded stride: aligned gathers; the extra columns stay zero
     Arena A(s);
     Solver S;
-    KC_TRY(solver_init(S, P, nrhs, o, A, s));
+    KC_TRY(solver_init(S, P, ns, o, A, s));
     double *bp, *zp;
-    KC_TRY(A.get(&bp, P->N * nrhs));
-    KC_TRY(A.get(&zp, P->N * nrhs));
-    KC_TRY(to_point_major(b, perm, P->N, nrhs, bp, s));
+    KC_TRY(A.get(&bp, P->N * ns));
+    KC_TRY(A.get(&zp, P->N * ns));
+    KC_TRY(to_point_major(b, perm, P->N, nrhs, bp, s, ns));
     double fb = sqrt(kp.sigma2 + kp.nugget);
-    if (prec == KC_FP64) KC_TRY(solver_apply<double>(S, (const double*)val, diag, fb, bp, zp, nrhs, s));
-    else if (prec == KC_FP32_FORM) KC_TRY(solver_apply<float>(S, (const float*)val, diag, fb, bp, zp, nrhs, s));
-    else return fail(KC_EINVAL, "prec must be KC_FP64 or KC_FP32_FORM");
-    KC_TRY(from_point_major(zp, perm, P->N, nrhs, x, s));
+    if (prec == KC_FP64) KC_TRY(solver_apply<double>(S, (const double*)val, diag, fb, bp, zp, ns, s));
+    else KC_TRY(solver_apply<float>(S, (const float*)val, diag, fb, bp, zp, ns, s));
+    KC_TRY(from_point_major(zp, perm, P->N, nrhs, x, s, ns));
     return solver_check(S, s);
 }
 

@@ -67,7 +67,7 @@ def lib():
             "kc_order_points": [vp, i64, i32, vp, vp, vp, vp],
             "kc_pattern_count": [vp, vp, i64, i32, dbl, i32, vp, P(C.c_int64), vp],
             "kc_pattern_fill": [vp, vp, i64, i32, dbl, i32, vp, vp, vp],
-            "kc_schedule": [i64, vp, vp, vp, vp, vp, vp, vp, P(C.c_int32), vp],
+            "kc_schedule": [i64, vp, vp, vp, i32, vp, vp, vp, vp, vp, P(C.c_int32), vp],
             "kc_factor": [P(kc_pattern), vp, i32, P(kc_kernel), i32, vp, vp, P(C.c_int64), P(kc_opts), vp],
             "kc_solve": [P(kc_pattern), i32, vp, vp, P(kc_kernel), vp, vp, i32, vp, P(kc_opts), vp],
             "kc_solve_noalloc": [P(kc_pattern), i32, vp, vp, P(kc_kernel), vp, vp, i32, vp, vp],
@@ -201,9 +201,13 @@ class Pattern:
         return C.byref(self._c)
 
 
-def schedule(rowptr, col, stream=None) -> Pattern:
+def schedule(rowptr, col, x_ord=None, stream=None) -> Pattern:
+    """CSC view, levels and the column order; with the points x_ord (N, d)
+    the columns of each level go in Morton order of their points."""
     _dev(rowptr, torch.int64, "rowptr")
     _dev(col, torch.int32, "col")
+    if x_ord is not None:
+        _dev(x_ord, torch.float64, "x_ord")
     N = rowptr.numel() - 1
     nnz = col.numel()
     dev = rowptr.device
@@ -213,8 +217,10 @@ def schedule(rowptr, col, stream=None) -> Pattern:
     level = torch.empty(N, dtype=torch.int32, device=dev)
     order = torch.empty(N, dtype=torch.int32, device=dev)
     depth = C.c_int32(0)
-    _check(lib().kc_schedule(N, _ptr(rowptr), _ptr(col), _ptr(colptr), _ptr(rowidx), _ptr(slot), _ptr(level),
-                             _ptr(order), C.byref(depth), _stream(stream)))
+    d = int(x_ord.shape[1]) if x_ord is not None else 0
+    _check(lib().kc_schedule(N, _ptr(rowptr), _ptr(col), _ptr(x_ord) if x_ord is not None else None, d,
+                             _ptr(colptr), _ptr(rowidx), _ptr(slot), _ptr(level), _ptr(order), C.byref(depth),
+                             _stream(stream)))
     return Pattern(rowptr, col, colptr, rowidx, slot, level, order, int(depth.value))
 
 
@@ -310,7 +316,7 @@ def pca_error(x, kern: Kernel, Lk, v0, iters=50, stream=None):
 def build_pattern(x_ord, l, rho, rule=RULE_MAX, stream=None) -> Pattern:
     rowptr, nnz = pattern_count(x_ord, l, rho, rule, stream)
     col = pattern_fill(x_ord, l, rho, rowptr, nnz, rule, stream)
-    return schedule(rowptr, col, stream)
+    return schedule(rowptr, col, x_ord, stream)
 
 
 def pipeline(x, rho, kern: Kernel, prec=FP32_FORM, rule=RULE_MAX, opts=None, stream=None):

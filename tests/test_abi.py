@@ -48,5 +48,6 @@ def test_argument_errors_without_gpu(so):
     lib.kc_last_error.restype = ctypes.c_char_p
     st = lib.kc_order_points(None, ctypes.c_int64(10), ctypes.c_int32(2), None, None, None, None)
     assert st == 1 and b"NULL" in lib.kc_last_error()
-    st = lib.kc_schedule(ctypes.c_int64(0), None, None, None, None, None, None, None, None, None)
+    st = lib.kc_schedule(ctypes.c_int64(0), None, None, None, ctypes.c_int32(0), None, None, None, None, None, None,
+                         None)
     assert st == 1

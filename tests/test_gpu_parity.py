@@ -134,6 +134,47 @@ def test_schedule_csc_and_levels():
     assert np.array_equal(order, np.lexsort((np.arange(N), want)))
 
 
+def _morton_np(x):
+    """Morton codes as the schedule defines them (first min(d,3) coordinates,
+    16 bits per axis in 2-D, 10 in 3-D, quantised in the bounding box)."""
+    dg = min(x.shape[1], 3)
+    bits = 16 if dg <= 2 else 10
+    lo, hi = x[:, :dg].min(0), x[:, :dg].max(0)
+    inv = np.where(hi > lo, 1.0 / np.where(hi > lo, hi - lo, 1.0), 0.0)
+    f = np.clip((x[:, :dg] - lo) * inv, 0.0, 1.0)
+    q = (f * float((1 << bits) - 1)).astype(np.uint64)
+    m = np.zeros(len(x), np.uint64)
+    for b in range(bits - 1, -1, -1):
+        for t in range(dg):
+            m = (m << np.uint64(1)) | ((q[:, t] >> np.uint64(b)) & np.uint64(1))
+    return m
+
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_schedule_with_points_orders_levels_spatially(d):
+    """Given the points, the schedule keeps the levels and the CSC, and orders
+    each level's columns by Morton code; the factor does not depend on the
+    order its independent columns run in (same bits), the solve agrees."""
+    x, perm, l, xo, rp, col = _ref_pattern(N=3000, d=d, rho=3.0, seed=23)
+    p0 = kc.schedule(T(rp), T(col))
+    p1 = kc.schedule(T(rp), T(col), T(xo))
+    for a in ("colptr", "rowidx", "slot", "level"):
+        assert torch.equal(getattr(p0, a), getattr(p1, a)), a
+    assert p0.depth == p1.depth
+    order, lev = H(p1.order), H(p1.level)
+    assert np.array_equal(np.sort(order), np.arange(3000))
+    key = lev[order].astype(np.uint64) << np.uint64(32) | _morton_np(xo)[order]
+    assert np.all(np.diff(key.astype(np.float64)) >= 0) and np.all(key[1:] >= key[:-1])
+    kg, ko = ok_kern(1.5, 0.2)
+    v0, g0, _ = kc.factor(p0, T(xo), kg, kc.FP32_FORM)
+    v1, g1, _ = kc.factor(p1, T(xo), kg, kc.FP32_FORM)
+    assert torch.equal(v0, v1) and torch.equal(g0, g1)
+    b = inputs.rhs(3000, 3, seed=24)
+    s0 = H(kc.solve(p0, kc.FP32_FORM, v0, g0, kg, T(perm), T(b)))
+    s1 = H(kc.solve(p1, kc.FP32_FORM, v1, g1, kg, T(perm), T(b)))
+    assert np.linalg.norm(s1 - s0) <= 1e-11 * np.linalg.norm(s0)
+
+
 # -------------------------------------------------------------------- factor
 #
 # FP64 bar: within max(1e-12, 10 x spread) of the row norm, where spread is how
