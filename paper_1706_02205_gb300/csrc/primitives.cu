@@ -187,50 +187,92 @@ __global__ void rs_hist_k(const K* __restrict__ key, int64_t n, int shift, int64
     for (int i = threadIdx.x; i < 256; i += blockDim.x) hist[(int64_t)i * ntiles + blockIdx.x] = cnt[i];
 }
 
+// Scatter of one tile: each warp ranks its elements by digit (match_any, in
+// element order, so the sort is stable), the tile is rearranged in shared
+// memory in digit order, and every digit's run is then written to its global
+// offset with consecutive threads writing consecutive addresses.
 template <typename K>
-__global__ void rs_scatter_k(const K* __restrict__ kin, const int64_t* __restrict__ vin, int64_t n, int shift,
-                             int64_t ntiles, const int64_t* __restrict__ goff, K* __restrict__ kout,
-                             int64_t* __restrict__ vout) {
-    __shared__ long long cnt[RS_WARPS][256];
-    int lane = lane_id(), w = threadIdx.x >> 5;
-    for (int i = lane; i < 256; i += 32) cnt[w][i] = 0;
+__global__ void __launch_bounds__(RS_WARPS * 32) rs_scatter_k(const K* __restrict__ kin, const int64_t* __restrict__ vin,
+                                                               int64_t n, int shift, int64_t ntiles,
+                                                               const int64_t* __restrict__ goff, K* __restrict__ kout,
+                                                               int64_t* __restrict__ vout) {
+    extern __shared__ __align__(16) unsigned char rs_smem[];
+    int64_t* sval = (int64_t*)rs_smem;            // [RS_TILE]
+    K* skey = (K*)(sval + RS_TILE);               // [RS_TILE]
+    __shared__ int wcnt[RS_WARPS][256];           // per-warp digit counts, then offsets in the tile
+    __shared__ int dstart[257];                   // tile-local start of every digit
+    __shared__ long long gbase[256];              // global start of every digit of this tile
+    __shared__ int wsum[RS_WARPS];
+    const int lane = lane_id(), w = threadIdx.x >> 5;
+    for (int i = lane; i < 256; i += 32) wcnt[w][i] = 0;
     __syncwarp();
-    int64_t wbase = (int64_t)blockIdx.x * RS_TILE + (int64_t)w * RS_ROUNDS * 32;
+    const int64_t tbase = (int64_t)blockIdx.x * RS_TILE;
+    const int64_t wbase = tbase + (int64_t)w * RS_ROUNDS * 32;
     const unsigned lt = (1u << lane) - 1u;
     for (int r = 0; r < RS_ROUNDS; ++r) {
-        int64_t e = wbase + r * 32 + lane;
-        int dg = e < n ? (int)((kin[e] >> shift) & 0xFF) : 256 + lane;
-        unsigned peers = __match_any_sync(0xffffffffu, dg);
-        int leader = 31 - __clz(peers);
-        if (e < n && lane == leader) cnt[w][dg] += __popc(peers);
+        const int64_t e = wbase + r * 32 + lane;
+        const int dg = e < n ? (int)((kin[e] >> shift) & 0xFF) : 256 + lane;
+        const unsigned peers = __match_any_sync(0xffffffffu, dg);
+        if (e < n && lane == 31 - __clz(peers)) wcnt[w][dg] += __popc(peers);
         __syncwarp();
     }
     __syncthreads();
-    for (int dgt = threadIdx.x; dgt < 256; dgt += blockDim.x) {
-        long long run = goff[(int64_t)dgt * ntiles + blockIdx.x];
+    // digit totals of the tile, their exclusive scan, and the per-warp offsets
+    {
+        const int dgt = threadIdx.x;  // blockDim == 256
+        int tot = 0;
+        for (int q = 0; q < RS_WARPS; ++q) tot += wcnt[q][dgt];
+        int incl = tot;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        if (lane == 31) wsum[w] = incl;
+        __syncthreads();
+        int off = 0;
+        for (int q = 0; q < w; ++q) off += wsum[q];
+        const int start = off + incl - tot;
+        dstart[dgt] = start;
+        if (dgt == 255) dstart[256] = start + tot;
+        gbase[dgt] = goff[(int64_t)dgt * ntiles + blockIdx.x];
+        int run = start;
         for (int q = 0; q < RS_WARPS; ++q) {
-            long long t = cnt[q][dgt];
-            cnt[q][dgt] = run;
-            run += t;
+            const int c = wcnt[q][dgt];
+            wcnt[q][dgt] = run;
+            run += c;
         }
     }
     __syncthreads();
     for (int r = 0; r < RS_ROUNDS; ++r) {
-        int64_t e = wbase + r * 32 + lane;
-        bool ok = e < n;
-        K kv = ok ? kin[e] : (K)0;
-        int dg = ok ? (int)((kv >> shift) & 0xFF) : 256 + lane;
-        unsigned peers = __match_any_sync(0xffffffffu, dg);
-        int leader = 31 - __clz(peers);
+        const int64_t e = wbase + r * 32 + lane;
+        const bool ok = e < n;
+        const K kv = ok ? kin[e] : (K)0;
+        const int dg = ok ? (int)((kv >> shift) & 0xFF) : 256 + lane;
+        const unsigned peers = __match_any_sync(0xffffffffu, dg);
         if (ok) {
-            long long pos = cnt[w][dg] + __popc(peers & lt);
-            kout[pos] = kv;
-            vout[pos] = vin[e];
+            const int pos = wcnt[w][dg] + __popc(peers & lt);
+            skey[pos] = kv;
+            sval[pos] = vin[e];
         }
         __syncwarp();
-        if (ok && lane == leader) cnt[w][dg] += __popc(peers);
+        if (ok && lane == 31 - __clz(peers)) wcnt[w][dg] += __popc(peers);
         __syncwarp();
     }
+    __syncthreads();
+    const int cnt = (int)min((int64_t)RS_TILE, n - tbase);
+    for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
+        const K kv = skey[i];
+        const int dg = (int)((kv >> shift) & 0xFF);
+        const long long pos = gbase[dg] + (i - dstart[dg]);
+        kout[pos] = kv;
+        vout[pos] = sval[i];
+    }
+}
+
+template <typename K>
+static size_t rs_smem_bytes() {
+    return (size_t)RS_TILE * (sizeof(int64_t) + sizeof(K));
 }
 
 template <typename K>
@@ -239,6 +281,7 @@ static kc_status radix_impl(K* k_in, int64_t* v_in, K* k_out, int64_t* v_out, in
     if (n <= 0) return KC_OK;
     int passes = (bits + 7) / 8;
     if (passes < 1) passes = 1;
+    KC_CUDA(cudaFuncSetAttribute(rs_scatter_k<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rs_smem_bytes<K>()));
     int64_t ntiles = (n + RS_TILE - 1) / RS_TILE;
     int64_t* hist;
     int64_t* goff;
@@ -252,7 +295,8 @@ static kc_status radix_impl(K* k_in, int64_t* v_in, K* k_out, int64_t* v_out, in
         int shift = 8 * p;
         ::kc::note_launch(), rs_hist_k<K><<<(unsigned)ntiles, 256, 0, s>>>(ka, n, shift, ntiles, hist);
         KC_TRY(exclusive_scan_i64(hist, goff, 256 * ntiles, A, s));
-        ::kc::note_launch(), rs_scatter_k<K><<<(unsigned)ntiles, RS_WARPS * 32, 0, s>>>(ka, va, n, shift, ntiles, goff, kb, vb);
+        ::kc::note_launch(), rs_scatter_k<K><<<(unsigned)ntiles, RS_WARPS * 32, rs_smem_bytes<K>(), s>>>(
+            ka, va, n, shift, ntiles, goff, kb, vb);
         KC_CUDA(cudaGetLastError());
         K* tk = ka; ka = kb; kb = tk;
         int64_t* tv = va; va = vb; vb = tv;
