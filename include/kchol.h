@@ -94,7 +94,7 @@ typedef struct {
     int32_t rows_per_task;         /* rows of a column per task; 0 -> about (nnz - N) / (depth x resident
                                       warps), a power of two in 16..128 */
     int32_t ctas_per_sm;           /* persistent grid = SMs x this; 0 -> occupancy */
-    int32_t warps_per_cta;         /* 0 -> 8 */
+    int32_t warps_per_cta;         /* 0 -> the CTA size (8, 4, 2 or 1 warps) with the most resident warps */
     int32_t test_hold_column;      /* test hook: 0 = off; c+1 makes column c never signal
                                       ready, so a wait on it runs out (KC_ETIMEOUT) */
     int32_t lanes_per_row;         /* factor: lanes merging one row (1,2,4,..,32); 0 -> 8 (FP32 form) or

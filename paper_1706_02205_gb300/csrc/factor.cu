@@ -796,6 +796,7 @@ struct FactorCore {
     int stage_req = 0;    // requested stage-buffer bytes: 0 automatic, < 0 register form
     int stage_bytes = 0;  // chosen (0: register form)
     int bulk_warps = 4;
+    bool warps_auto = true;  // register form: CTA size from the occupancy of the row tables
     long long spin = 4000000000LL;
     int hold = -1;
 };
@@ -841,10 +842,27 @@ static kc_status launch_core(const FactorCore& F, T* val, double* diag, cudaStre
         warps = std::min(warps, optin / a.warp_smem);
         if (warps < 1) return fail(KC_EINVAL, "factor: stage_bytes too large for one warp's shared memory");
     }
-    const size_t smem = (size_t)warps * a.warp_smem;
     auto kfn = bulk ? ichol_bulk_k<T, U> : ichol_persistent_k<T, U>;
-    KC_CUDA(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
+    if (!bulk && F.warps_auto) {
+        // CTA size with the most resident warps: a large row table (long rows)
+        // fits one 8-warp CTA per SM where several smaller CTAs fit more warps.
+        // A smaller CTA must win by over 20%: filling the shared memory to the
+        // last CTA leaves the L1 cache (which the column index loads use) too small.
+        int best = 0;
+        for (int w = 8; w >= 1; w >>= 1) {
+            const size_t sm_w = (size_t)w * a.warp_smem;
+            KC_CUDA(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_w));
+            int n = 0;
+            KC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kfn, w * 32, sm_w));
+            if (n * w * 5 > best * 6) {
+                best = n * w;
+                warps = w;
+            }
+        }
+    }
+    const size_t smem = (size_t)warps * a.warp_smem;
+    KC_CUDA(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     KC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, warps * 32, smem));
     if (F.ctas > 0 && F.ctas < per_sm) per_sm = F.ctas;
     if (per_sm < 1) return fail(KC_EINVAL, "factor: shared memory of one CTA exceeds the SM (stage_bytes too large?)");
@@ -882,6 +900,7 @@ static kc_status read_status(const FactorCore& F, int64_t* zero_out, cudaStream_
 static kc_status apply_opts(FactorCore& F, const kc_opts* o) {
     F.rpt = (o && o->rows_per_task > 0) ? o->rows_per_task : 0;  // 0: from the level width (auto_rows)
     F.warps = (o && o->warps_per_cta > 0) ? o->warps_per_cta : 8;
+    F.warps_auto = !(o && o->warps_per_cta > 0);
     if (F.warps > 8) return fail(KC_EINVAL, "warps_per_cta must be <= 8");
     F.spin = (o && o->spin_limit_cycles > 0) ? o->spin_limit_cycles : 4000000000LL;
     F.ctas = (o && o->ctas_per_sm > 0) ? o->ctas_per_sm : 0;
