@@ -128,6 +128,21 @@ __device__ __forceinline__ float matern_f32(float r, int nu_code, float scale, f
     return __fmul_rn(__fmul_rn(sigma2, poly), e);
 }
 
+// Let a kernel take as much dynamic shared memory as the device allows
+// beside its static shared memory.  Every caller sets the same value, so
+// host threads launching the kernel concurrently (each with its own size)
+// never lower the limit under one another.
+template <typename F>
+inline kc_status allow_dynamic_smem(F* func) {
+    int dev = 0, optin = 0;
+    KC_CUDA(cudaGetDevice(&dev));
+    KC_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    cudaFuncAttributes fa;
+    KC_CUDA(cudaFuncGetAttributes(&fa, func));
+    KC_CUDA(cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes));
+    return KC_OK;
+}
+
 struct KernelParams {
     int nu_code;
     double scale;   // sqrt(2 nu) / ell

@@ -844,6 +844,7 @@ static kc_status launch_core(const FactorCore& F, T* val, double* diag, cudaStre
     }
     auto kfn = bulk ? ichol_bulk_k<T, U> : ichol_persistent_k<T, U>;
     int per_sm = 0;
+    KC_TRY(allow_dynamic_smem(kfn));
     if (!bulk && F.warps_auto) {
         // CTA size with the most resident warps: a large row table (long rows)
         // fits one 8-warp CTA per SM where several smaller CTAs fit more warps.
@@ -852,7 +853,6 @@ static kc_status launch_core(const FactorCore& F, T* val, double* diag, cudaStre
         int best = 0;
         for (int w = 8; w >= 1; w >>= 1) {
             const size_t sm_w = (size_t)w * a.warp_smem;
-            KC_CUDA(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_w));
             int n = 0;
             KC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kfn, w * 32, sm_w));
             if (n * w * 5 > best * 6) {
@@ -862,7 +862,6 @@ static kc_status launch_core(const FactorCore& F, T* val, double* diag, cudaStre
         }
     }
     const size_t smem = (size_t)warps * a.warp_smem;
-    KC_CUDA(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     KC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, warps * 32, smem));
     if (F.ctas > 0 && F.ctas < per_sm) per_sm = F.ctas;
     if (per_sm < 1) return fail(KC_EINVAL, "factor: shared memory of one CTA exceeds the SM (stage_bytes too large?)");

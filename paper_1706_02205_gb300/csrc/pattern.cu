@@ -322,7 +322,7 @@ kc_status pattern_fill_impl(const double* xo, const double* l, int64_t N, int d,
     KC_CUDA(cudaStreamSynchronize(s));
     if (hl > 0) {
         size_t sm = sizeof(int) * SORT_BLOCK_CAP;
-        KC_CUDA(cudaFuncSetAttribute(row_sort_block_k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        KC_TRY(allow_dynamic_smem(row_sort_block_k));
         ::kc::note_launch(), row_sort_block_k<<<(unsigned)hl, 1024, sm, s>>>(rowptr, col, long_rows);
         KC_CUDA(cudaGetLastError());
     }

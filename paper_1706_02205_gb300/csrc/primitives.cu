@@ -281,7 +281,7 @@ static kc_status radix_impl(K* k_in, int64_t* v_in, K* k_out, int64_t* v_out, in
     if (n <= 0) return KC_OK;
     int passes = (bits + 7) / 8;
     if (passes < 1) passes = 1;
-    KC_CUDA(cudaFuncSetAttribute(rs_scatter_k<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rs_smem_bytes<K>()));
+    KC_TRY(allow_dynamic_smem(rs_scatter_k<K>));
     int64_t ntiles = (n + RS_TILE - 1) / RS_TILE;
     int64_t* hist;
     int64_t* goff;

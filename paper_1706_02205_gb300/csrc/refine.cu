@@ -63,7 +63,7 @@ template <int NRHS>
 static kc_status dense_f64_launch(const double* x, int64_t N, int d, const KernelParams& kp, const double* v,
                                   double* y, cudaStream_t s) {
     size_t sm = sizeof(double) * DM_THREADS * (d + NRHS);
-    KC_CUDA(cudaFuncSetAttribute(dense_theta_f64_k<NRHS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    KC_TRY(allow_dynamic_smem(dense_theta_f64_k<NRHS>));
     ::kc::note_launch(), dense_theta_f64_k<NRHS><<<blocks_for(N, DM_THREADS), DM_THREADS, sm, s>>>(x, N, d, kp, v, y);
     KC_CUDA(cudaGetLastError());
     return KC_OK;

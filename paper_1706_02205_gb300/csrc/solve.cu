@@ -15,8 +15,19 @@
 // the column): the readiness checks go out as relaxed loads all at once (a
 // bounded spin only on points not yet solved, then one acquire fence), the
 // values and the gathers follow in a few rounds, and the warp reduces its NR
-// partial sums with a reduce-scatter.  Sums are FP64 for both value types.  A
-// dropped pivot (L_ii = 0) uses sqrt(Theta_ii).
+// partial sums with a reduce-scatter.  A dropped pivot (L_ii = 0) uses
+// sqrt(Theta_ii).
+//
+// Arithmetic.  FP64 form: vectors, products and sums in FP64.  FP32 form (L in
+// FP32): the GB300's FP64 pipe is a small fraction of its FP32 rate, so the
+// vectors are kept as pairs of floats (hi, lo) with hi + lo the FP64 value to
+// about 2^-48, every product L_jk (hi + lo) is formed with TwoProduct (fmaf)
+// plus the small L_jk lo term, and the sums are compensated (TwoSum, the
+// scheme of Ogita, Rump and Oishi's Dot2); each row's result is formed in
+// FP64 and split back into a pair.  The solution is about 2^-45 accurate
+// relative to the sums' magnitudes, where FP64 gives 2^-53.
+#include <type_traits>
+
 #include "solver.cuh"
 
 namespace kc {
@@ -37,8 +48,10 @@ struct SolveArgs {
     const double* __restrict__ diag;
     double diag_fallback;
     const double* b;  // point-major input
-    double* y;        // point-major output of the forward solve / input of backward
+    double* y;        // point-major output of the forward solve / input of backward (FP64 form)
     double* x;        // point-major output of the backward solve
+    float2* yf;       // FP32 form: y as (hi, lo) pairs
+    float2* xf;       // FP32 form: x as (hi, lo) pairs (gathered by later columns; x above gets FP64)
     double* acc;      // point-major partial sums of wide columns
     unsigned* cnt;    // finished chunks per column (backward)
     int* ready;       // per point flag
@@ -278,6 +291,212 @@ __global__ void __launch_bounds__(256) bwd_solve_k(SolveArgs<T> A) {
     }
 }
 
+// ------------------------------------------------ FP32 form: float pairs
+template <int NR>
+__device__ __forceinline__ void gather_pair(const float2* v, int k, float* hi, float* lo) {
+    if constexpr (NR == 1) {
+        const float2 w = __ldcg(v + k);
+        hi[0] = w.x;
+        lo[0] = w.y;
+    } else {
+        const float4* p = (const float4*)(v + (int64_t)k * NR);
+#pragma unroll
+        for (int q = 0; q < NR / 2; ++q) {
+            const float4 w = __ldcg(p + q);
+            hi[2 * q] = w.x;
+            lo[2 * q] = w.y;
+            hi[2 * q + 1] = w.z;
+            lo[2 * q + 1] = w.w;
+        }
+    }
+}
+// (s, c) += w (hi + lo): TwoProduct of w hi, TwoSum into s, small terms into c.
+// The _rn intrinsics keep every rounding where the error-free steps need it.
+__device__ __forceinline__ void pair_add(float& s, float& c, float w, float hi, float lo) {
+    const float p = __fmul_rn(w, hi);
+    const float e = fmaf(w, hi, -p);
+    const float ns = __fadd_rn(s, p);
+    const float z = __fsub_rn(ns, s);
+    const float er = __fadd_rn(__fsub_rn(s, __fsub_rn(ns, z)), __fsub_rn(p, z));
+    s = ns;
+    c = fmaf(w, lo, __fadd_rn(c, __fadd_rn(er, e)));
+}
+__device__ __forceinline__ void pair_merge(float& s, float& c, float s2, float c2) {
+    const float t = __fadd_rn(s, s2);
+    const float z = __fsub_rn(t, s);
+    const float er = __fadd_rn(__fsub_rn(s, __fsub_rn(t, z)), __fsub_rn(s2, z));
+    s = t;
+    c = __fadd_rn(c, __fadd_rn(c2, er));
+}
+__device__ __forceinline__ float2 pair_of(double v) {
+    const float hi = __double2float_rn(v);
+    return make_float2(hi, __double2float_rn(v - (double)hi));
+}
+__device__ __forceinline__ double value_of(float2 p) { return (double)p.x + (double)p.y; }
+
+// reduce-scatter of NR (s, c) pairs (as reduce_scatter); returns the FP64 sum
+template <int NR>
+__device__ __forceinline__ double reduce_scatter_pair(float (&s)[NR], float (&c)[NR], int lane) {
+    const unsigned FULL = 0xffffffffu;
+#pragma unroll
+    for (int h = NR / 2, o = 16; h >= 1; h >>= 1, o >>= 1) {
+        const bool up = (lane & o) != 0;
+#pragma unroll
+        for (int q = 0; q < h; ++q) {
+            const float ss = up ? s[q] : s[q + h], sc = up ? c[q] : c[q + h];
+            const float ks = up ? s[q + h] : s[q], kc = up ? c[q + h] : c[q];
+            const float rs = __shfl_xor_sync(FULL, ss, o), rc = __shfl_xor_sync(FULL, sc, o);
+            s[q] = ks;
+            c[q] = kc;
+            pair_merge(s[q], c[q], rs, rc);
+        }
+    }
+    constexpr int L = NR == 1 ? 0 : NR == 2 ? 1 : NR == 4 ? 2 : NR == 8 ? 3 : 4;
+#pragma unroll
+    for (int o = 16 >> L; o >= 1; o >>= 1) {
+        const float rs = __shfl_xor_sync(FULL, s[0], o), rc = __shfl_xor_sync(FULL, c[0], o);
+        pair_merge(s[0], c[0], rs, rc);
+    }
+    return (double)s[0] + (double)c[0];
+}
+
+// (s, c)[r] += w[u] * v[k[u]][r], E gathers at a time, nothing for empty slots
+template <int NR, int D>
+__device__ __forceinline__ void gather_pair_add(const float2* v, const int (&k)[D], const float (&w)[D],
+                                                float (&s)[NR], float (&c)[NR]) {
+    constexpr int E0 = NR >= 2 ? 16 / NR : 8;  // at most 16 pairs in flight per lane
+    constexpr int E = E0 < D ? E0 : D;
+#pragma unroll
+    for (int u0 = 0; u0 < D; u0 += E) {
+        float hi[E][NR], lo[E][NR];
+#pragma unroll
+        for (int q = 0; q < E; ++q)
+            if (k[u0 + q] >= 0) gather_pair<NR>(v, k[u0 + q], hi[q], lo[q]);
+#pragma unroll
+        for (int q = 0; q < E; ++q)
+            if (k[u0 + q] >= 0)
+#pragma unroll
+                for (int r = 0; r < NR; ++r) pair_add(s[r], c[r], w[u0 + q], hi[q][r], lo[q][r]);
+    }
+}
+
+template <int NR>
+__global__ void __launch_bounds__(256) fwd_solve_pair_k(SolveArgs<float> A) {
+    constexpr int D = 8;
+    const int lane = lane_id();
+    const unsigned FULL = 0xffffffffu;
+    for (;;) {
+        unsigned long long t = 0;
+        if (lane == 0) t = atomicAdd(A.ticket, 1ULL);
+        t = __shfl_sync(FULL, t, 0);
+        if ((int64_t)t >= A.N) return;
+        if (ld_volatile_s32(A.status) != 0) return;
+        const int j = A.order[t];
+        const int64_t a = A.rowptr[j];
+        const int n = (int)(A.rowptr[j + 1] - 1 - a);
+        float s[NR], c[NR];
+#pragma unroll
+        for (int r = 0; r < NR; ++r) s[r] = c[r] = 0.f;
+        for (int e0 = 0; e0 < n; e0 += 32 * D) {
+            int kk[D];
+#pragma unroll
+            for (int u = 0; u < D; ++u) {
+                const int e = e0 + lane + 32 * u;
+                kk[u] = e < n ? __ldg(&A.col[a + e]) : -1;
+            }
+            if (!points_ready<D>(A.ready, kk, A.status, A.spin_limit)) {
+                if (lane == 0) atomicCAS(A.status, 0, DEV_TIMEOUT);
+                return;
+            }
+            float w[D];
+#pragma unroll
+            for (int u = 0; u < D; ++u) w[u] = kk[u] >= 0 ? __ldg(&A.val[a + e0 + lane + 32 * u]) : 0.f;
+            gather_pair_add<NR, D>(A.yf, kk, w, s, c);
+        }
+        const double sum = reduce_scatter_pair<NR>(s, c, lane);
+        if (rhs_writer<NR>(lane)) {
+            const int r = rhs_of_lane<NR>(lane);
+            double dj = A.diag[j];
+            if (!(dj > 0.0)) dj = A.diag_fallback;
+            A.yf[(int64_t)j * NR + r] = pair_of((A.b[(int64_t)j * NR + r] - sum) / dj);
+        }
+        __threadfence();
+        __syncwarp();
+        if (lane == 0) st_release_s32(&A.ready[j], 1);
+    }
+}
+
+template <int NR>
+__global__ void __launch_bounds__(256) bwd_solve_pair_k(SolveArgs<float> A) {
+    constexpr int D = 4;
+    const int lane = lane_id();
+    const unsigned FULL = 0xffffffffu;
+    for (;;) {
+        unsigned long long t = 0;
+        if (lane == 0) t = atomicAdd(A.ticket, 1ULL);
+        t = __shfl_sync(FULL, t, 0);
+        if ((int64_t)t >= A.ntasks) return;
+        if (ld_volatile_s32(A.status) != 0) return;
+        const int2 tk = A.tasks[A.ntasks - 1 - (int64_t)t];
+        const int i = tk.x, ch = tk.y;
+        const int64_t c0 = A.colptr[i], c1 = A.colptr[i + 1];
+        const int64_t m = c1 - c0 - 1;
+        const unsigned nch = m <= 0 ? 1u : (unsigned)((m + A.rpt - 1) / A.rpt);
+        const int64_t qs = c0 + 1 + (int64_t)ch * A.rpt;
+        const int nq = (int)(min(c1, qs + A.rpt) - qs);
+        float s[NR], c[NR];
+#pragma unroll
+        for (int r = 0; r < NR; ++r) s[r] = c[r] = 0.f;
+        for (int q0 = 0; q0 < nq; q0 += 32 * D) {
+            int jj[D];
+            int64_t pp[D];
+#pragma unroll
+            for (int u = 0; u < D; ++u) {
+                const int q = q0 + lane + 32 * u;
+                jj[u] = q < nq ? __ldg(&A.rowidx[qs + q]) : -1;
+                pp[u] = q < nq ? __ldg(&A.slot[qs + q]) : 0;
+            }
+            if (!points_ready<D>(A.ready, jj, A.status, A.spin_limit)) {
+                if (lane == 0) atomicCAS(A.status, 0, DEV_TIMEOUT);
+                return;
+            }
+            float w[D];
+#pragma unroll
+            for (int u = 0; u < D; ++u) w[u] = jj[u] >= 0 ? __ldg(&A.val[pp[u]]) : 0.f;
+            gather_pair_add<NR, D>(A.xf, jj, w, s, c);
+        }
+        double sum = reduce_scatter_pair<NR>(s, c, lane);
+        const bool wr = rhs_writer<NR>(lane);
+        const int r = rhs_of_lane<NR>(lane);
+        bool finish = true;
+        if (nch > 1) {
+            if (wr) atomicAdd(&A.acc[(int64_t)i * NR + r], sum);
+            __threadfence();
+            __syncwarp();
+            unsigned prev = 0;
+            if (lane == 0) prev = atomicAdd(&A.cnt[i], 1u);
+            prev = __shfl_sync(FULL, prev, 0);
+            finish = (prev == nch - 1);
+            if (finish) {
+                __threadfence();
+                sum = __ldcg(&A.acc[(int64_t)i * NR + r]);
+            }
+        }
+        if (finish) {
+            if (wr) {
+                double di = A.diag[i];
+                if (!(di > 0.0)) di = A.diag_fallback;
+                const double xi = (value_of(A.yf[(int64_t)i * NR + r]) - sum) / di;
+                A.xf[(int64_t)i * NR + r] = pair_of(xi);
+                A.x[(int64_t)i * NR + r] = xi;
+            }
+            __threadfence();
+            __syncwarp();
+            if (lane == 0) st_release_s32(&A.ready[i], 1);
+        }
+    }
+}
+
 // out[k * stride + r] = b[r * N + perm[k]] for r < nrhs, 0 for nrhs <= r < stride
 __global__ void to_point_major_k(const double* __restrict__ b, const int32_t* __restrict__ perm, int64_t N, int nrhs,
                                  int stride, double* __restrict__ out) {
@@ -310,6 +529,7 @@ kc_status solver_init(Solver& S, const kc_pattern* P, int nrhs_cap, const kc_opt
     KC_TRY(A.get(&S.ticket, 2));
     KC_TRY(A.get(&S.status, 1));
     KC_TRY(A.get(&S.y, P->N * nrhs_cap));
+    KC_TRY(A.get(&S.xf, P->N * nrhs_cap));
     return KC_OK;
 }
 
@@ -323,13 +543,15 @@ static kc_status solve_launch(Solver& S, SolveArgs<T> a, int nrhs, cudaStream_t 
     KC_CUDA(cudaMemsetAsync(S.ticket, 0, 2 * sizeof(unsigned long long), s));
     KC_CUDA(cudaMemsetAsync(S.status, 0, sizeof(int), s));
     a.ticket = S.ticket;
-    ::kc::note_launch(), fwd_solve_k<T, NR><<<grid, 256, 0, s>>>(a);
+    if constexpr (std::is_same<T, float>::value) ::kc::note_launch(), fwd_solve_pair_k<NR><<<grid, 256, 0, s>>>(a);
+    else ::kc::note_launch(), fwd_solve_k<T, NR><<<grid, 256, 0, s>>>(a);
     KC_CUDA(cudaGetLastError());
     KC_CUDA(cudaMemsetAsync(S.ready, 0, sizeof(int) * P->N, s));
     KC_CUDA(cudaMemsetAsync(S.cnt, 0, sizeof(unsigned) * P->N, s));
     KC_CUDA(cudaMemsetAsync(S.acc, 0, sizeof(double) * P->N * NR, s));
     a.ticket = S.ticket + 1;
-    ::kc::note_launch(), bwd_solve_k<T, NR><<<grid, 256, 0, s>>>(a);
+    if constexpr (std::is_same<T, float>::value) ::kc::note_launch(), bwd_solve_pair_k<NR><<<grid, 256, 0, s>>>(a);
+    else ::kc::note_launch(), bwd_solve_k<T, NR><<<grid, 256, 0, s>>>(a);
     KC_CUDA(cudaGetLastError());
     return KC_OK;
 }
@@ -360,6 +582,8 @@ kc_status solver_apply(Solver& S, const T* val, const double* diag, double diag_
     a.b = rhs;
     a.y = S.y;
     a.x = z;
+    a.yf = (float2*)S.y;  // same bytes as the FP64 vector
+    a.xf = S.xf;
     a.acc = S.acc;
     a.cnt = S.cnt;
     a.ready = S.ready;

@@ -16,6 +16,7 @@ struct Solver {
     unsigned long long* ticket = nullptr;
     int* status = nullptr;
     double* y = nullptr;
+    float2* xf = nullptr;  // FP32 form: x as (hi, lo) pairs
     int nrhs_cap = 0;
     long long spin = 4000000000LL;
 };
