@@ -32,13 +32,21 @@ kc_status cuda_fail(cudaError_t e, const char* what);
 enum : int { DEV_OK = 0, DEV_TIMEOUT = 1, DEV_BAD_INPUT = 2 };
 
 // ------------------------------------------------------- stream scratch
+// The scratch comes from the device's default stream-ordered memory pool.
+// Its release threshold is 0 unless set, which hands freed memory back to the
+// driver at every synchronisation, so each call would map its scratch (GBs
+// for a 2^20-point schedule) afresh; keep_pool_warm() lets the pool keep up to
+// SCRATCH_KEEP_BYTES of freed memory for the next call (once per device).
+constexpr uint64_t SCRATCH_KEEP_BYTES = 16ull << 30;
+void keep_pool_warm();
+
 // Stream-ordered scratch: every buffer is freed (cudaFreeAsync) when the
 // arena goes out of scope, after the work enqueued before that point.
 struct Arena {
     cudaStream_t s;
     void* ptrs[64];
     int n = 0;
-    explicit Arena(cudaStream_t st) : s(st) {}
+    explicit Arena(cudaStream_t st) : s(st) { keep_pool_warm(); }
     ~Arena() {
         for (int i = n - 1; i >= 0; --i) cudaFreeAsync(ptrs[i], s);
     }
@@ -86,6 +94,11 @@ __device__ __forceinline__ void red_release_add_u32(unsigned* p, unsigned v) {
     asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 __device__ __forceinline__ int ld_volatile_s32(const int* p) { return *(volatile const int*)p; }
+// Acquire-release fence at GPU scope: after relaxed loads of ready flags it
+// orders the loads that follow (acquire); before a flag is released it orders
+// this thread's earlier writes (release).  Lighter than __threadfence()
+// (sequentially consistent).
+__device__ __forceinline__ void fence_acq_rel_gpu() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
 // relaxed load at GPU scope: an acquire fence after it completes the synchronisation
 __device__ __forceinline__ unsigned ld_relaxed_u32(const unsigned* p) {
     unsigned v;

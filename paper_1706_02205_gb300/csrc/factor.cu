@@ -329,7 +329,7 @@ __device__ __forceinline__ int task_begin(const FactorArgs<T>& A, RowTable<T>& t
             if (lane == 0) atomicCAS(A.status, 0, DEV_TIMEOUT);
             return 2;
         }
-        __threadfence();  // acquire: the columns' values are visible from here on
+        fence_acq_rel_gpu();  // acquire: the columns' values are visible from here on
         T vv[DEPS];
 #pragma unroll
         for (int u = 0; u < DEPS; ++u) vv[u] = kk[u] >= 0 ? ldcg(&A.val[X.a0 + e0 + lane + 32 * u]) : (T)0;
@@ -369,7 +369,7 @@ __device__ __forceinline__ int task_begin(const FactorArgs<T>& A, RowTable<T>& t
 // Publish one finished task of column i.
 template <typename T>
 __device__ __forceinline__ void task_end(const FactorArgs<T>& A, int i, int lane) {
-    __threadfence();
+    fence_acq_rel_gpu();
     __syncwarp();
     if (lane == 0 && i != A.hold_col) red_release_add_u32(&A.done[i], 1u);
 }

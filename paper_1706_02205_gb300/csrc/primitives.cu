@@ -28,6 +28,20 @@ int64_t launch_count() { return g_launches.load(std::memory_order_relaxed); }
 void set_factor_kernel_ms(double ms) { g_factor_ms = ms; }
 double factor_kernel_ms() { return g_factor_ms; }
 
+void keep_pool_warm() {
+    static std::atomic<uint64_t> done{0};  // bit per device
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return;
+    const uint64_t bit = 1ull << dev;
+    if (done.load(std::memory_order_relaxed) & bit) return;
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+        uint64_t keep = SCRATCH_KEEP_BYTES;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    }
+    done.fetch_or(bit, std::memory_order_relaxed);
+}
+
 int sm_count() {
     int dev = 0, n = 0;
     cudaGetDevice(&dev);

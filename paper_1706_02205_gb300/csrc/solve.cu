@@ -149,7 +149,7 @@ __device__ __forceinline__ bool points_ready(const int* ready, const int (&kk)[D
     for (int u = 0; u < D; ++u)
         if (ok && ((pend >> u) & 1u)) ok = spin_flag(&ready[kk[u]], status, lim);
     ok = __all_sync(0xffffffffu, ok);
-    __threadfence();  // acquire: the points' values are visible from here on
+    fence_acq_rel_gpu();  // acquire: the points' values are visible from here on
     return ok;
 }
 
@@ -200,13 +200,13 @@ __global__ void __launch_bounds__(256) fwd_solve_k(SolveArgs<T> A) {
                 const int e = e0 + lane + 32 * u;
                 kk[u] = e < n ? __ldg(&A.col[a + e]) : -1;
             }
+            double w[D];  // static data: loaded before the wait
+#pragma unroll
+            for (int u = 0; u < D; ++u) w[u] = kk[u] >= 0 ? (double)__ldg(&A.val[a + e0 + lane + 32 * u]) : 0.0;
             if (!points_ready<D>(A.ready, kk, A.status, A.spin_limit)) {
                 if (lane == 0) atomicCAS(A.status, 0, DEV_TIMEOUT);
                 return;
             }
-            double w[D];
-#pragma unroll
-            for (int u = 0; u < D; ++u) w[u] = kk[u] >= 0 ? (double)__ldg(&A.val[a + e0 + lane + 32 * u]) : 0.0;
             gather_fma<NR, D>(A.y, kk, w, acc);
         }
         const double s = reduce_scatter<NR>(acc, lane);
@@ -216,7 +216,7 @@ __global__ void __launch_bounds__(256) fwd_solve_k(SolveArgs<T> A) {
             if (!(dj > 0.0)) dj = A.diag_fallback;
             A.y[(int64_t)j * NR + r] = (A.b[(int64_t)j * NR + r] - s) / dj;
         }
-        __threadfence();
+        fence_acq_rel_gpu();
         __syncwarp();
         if (lane == 0) st_release_s32(&A.ready[j], 1);
     }
@@ -252,13 +252,13 @@ __global__ void __launch_bounds__(256) bwd_solve_k(SolveArgs<T> A) {
                 jj[u] = q < nq ? __ldg(&A.rowidx[qs + q]) : -1;
                 pp[u] = q < nq ? __ldg(&A.slot[qs + q]) : 0;
             }
+            double w[D];  // static data: loaded before the wait
+#pragma unroll
+            for (int u = 0; u < D; ++u) w[u] = jj[u] >= 0 ? (double)__ldg(&A.val[pp[u]]) : 0.0;
             if (!points_ready<D>(A.ready, jj, A.status, A.spin_limit)) {
                 if (lane == 0) atomicCAS(A.status, 0, DEV_TIMEOUT);
                 return;
             }
-            double w[D];
-#pragma unroll
-            for (int u = 0; u < D; ++u) w[u] = jj[u] >= 0 ? (double)__ldg(&A.val[pp[u]]) : 0.0;
             gather_fma<NR, D>(A.x, jj, w, acc);
         }
         double s = reduce_scatter<NR>(acc, lane);
@@ -267,14 +267,14 @@ __global__ void __launch_bounds__(256) bwd_solve_k(SolveArgs<T> A) {
         bool finish = true;
         if (nch > 1) {
             if (wr) atomicAdd(&A.acc[(int64_t)i * NR + r], s);
-            __threadfence();
+            fence_acq_rel_gpu();
             __syncwarp();
             unsigned prev = 0;
             if (lane == 0) prev = atomicAdd(&A.cnt[i], 1u);
             prev = __shfl_sync(FULL, prev, 0);
             finish = (prev == nch - 1);
             if (finish) {
-                __threadfence();
+                fence_acq_rel_gpu();
                 s = __ldcg(&A.acc[(int64_t)i * NR + r]);
             }
         }
@@ -284,7 +284,7 @@ __global__ void __launch_bounds__(256) bwd_solve_k(SolveArgs<T> A) {
                 if (!(di > 0.0)) di = A.diag_fallback;
                 A.x[(int64_t)i * NR + r] = (A.y[(int64_t)i * NR + r] - s) / di;
             }
-            __threadfence();
+            fence_acq_rel_gpu();
             __syncwarp();
             if (lane == 0) st_release_s32(&A.ready[i], 1);
         }
@@ -404,13 +404,13 @@ __global__ void __launch_bounds__(256) fwd_solve_pair_k(SolveArgs<float> A) {
                 const int e = e0 + lane + 32 * u;
                 kk[u] = e < n ? __ldg(&A.col[a + e]) : -1;
             }
+            float w[D];  // static data: loaded before the wait
+#pragma unroll
+            for (int u = 0; u < D; ++u) w[u] = kk[u] >= 0 ? __ldg(&A.val[a + e0 + lane + 32 * u]) : 0.f;
             if (!points_ready<D>(A.ready, kk, A.status, A.spin_limit)) {
                 if (lane == 0) atomicCAS(A.status, 0, DEV_TIMEOUT);
                 return;
             }
-            float w[D];
-#pragma unroll
-            for (int u = 0; u < D; ++u) w[u] = kk[u] >= 0 ? __ldg(&A.val[a + e0 + lane + 32 * u]) : 0.f;
             gather_pair_add<NR, D>(A.yf, kk, w, s, c);
         }
         const double sum = reduce_scatter_pair<NR>(s, c, lane);
@@ -420,7 +420,7 @@ __global__ void __launch_bounds__(256) fwd_solve_pair_k(SolveArgs<float> A) {
             if (!(dj > 0.0)) dj = A.diag_fallback;
             A.yf[(int64_t)j * NR + r] = pair_of((A.b[(int64_t)j * NR + r] - sum) / dj);
         }
-        __threadfence();
+        fence_acq_rel_gpu();
         __syncwarp();
         if (lane == 0) st_release_s32(&A.ready[j], 1);
     }
@@ -456,13 +456,13 @@ __global__ void __launch_bounds__(256) bwd_solve_pair_k(SolveArgs<float> A) {
                 jj[u] = q < nq ? __ldg(&A.rowidx[qs + q]) : -1;
                 pp[u] = q < nq ? __ldg(&A.slot[qs + q]) : 0;
             }
+            float w[D];  // static data: loaded before the wait
+#pragma unroll
+            for (int u = 0; u < D; ++u) w[u] = jj[u] >= 0 ? __ldg(&A.val[pp[u]]) : 0.f;
             if (!points_ready<D>(A.ready, jj, A.status, A.spin_limit)) {
                 if (lane == 0) atomicCAS(A.status, 0, DEV_TIMEOUT);
                 return;
             }
-            float w[D];
-#pragma unroll
-            for (int u = 0; u < D; ++u) w[u] = jj[u] >= 0 ? __ldg(&A.val[pp[u]]) : 0.f;
             gather_pair_add<NR, D>(A.xf, jj, w, s, c);
         }
         double sum = reduce_scatter_pair<NR>(s, c, lane);
@@ -471,14 +471,14 @@ __global__ void __launch_bounds__(256) bwd_solve_pair_k(SolveArgs<float> A) {
         bool finish = true;
         if (nch > 1) {
             if (wr) atomicAdd(&A.acc[(int64_t)i * NR + r], sum);
-            __threadfence();
+            fence_acq_rel_gpu();
             __syncwarp();
             unsigned prev = 0;
             if (lane == 0) prev = atomicAdd(&A.cnt[i], 1u);
             prev = __shfl_sync(FULL, prev, 0);
             finish = (prev == nch - 1);
             if (finish) {
-                __threadfence();
+                fence_acq_rel_gpu();
                 sum = __ldcg(&A.acc[(int64_t)i * NR + r]);
             }
         }
@@ -490,7 +490,7 @@ __global__ void __launch_bounds__(256) bwd_solve_pair_k(SolveArgs<float> A) {
                 A.xf[(int64_t)i * NR + r] = pair_of(xi);
                 A.x[(int64_t)i * NR + r] = xi;
             }
-            __threadfence();
+            fence_acq_rel_gpu();
             __syncwarp();
             if (lane == 0) st_release_s32(&A.ready[i], 1);
         }
