@@ -292,24 +292,6 @@ __global__ void __launch_bounds__(256) bwd_solve_k(SolveArgs<T> A) {
 }
 
 // ------------------------------------------------ FP32 form: float pairs
-template <int NR>
-__device__ __forceinline__ void gather_pair(const float2* v, int k, float* hi, float* lo) {
-    if constexpr (NR == 1) {
-        const float2 w = __ldcg(v + k);
-        hi[0] = w.x;
-        lo[0] = w.y;
-    } else {
-        const float4* p = (const float4*)(v + (int64_t)k * NR);
-#pragma unroll
-        for (int q = 0; q < NR / 2; ++q) {
-            const float4 w = __ldcg(p + q);
-            hi[2 * q] = w.x;
-            lo[2 * q] = w.y;
-            hi[2 * q + 1] = w.z;
-            lo[2 * q + 1] = w.w;
-        }
-    }
-}
 // (s, c) += w (hi + lo): TwoProduct of w hi, TwoSum into s, small terms into c.
 // The _rn intrinsics keep every rounding where the error-free steps need it.
 __device__ __forceinline__ void pair_add(float& s, float& c, float w, float hi, float lo) {
@@ -334,12 +316,28 @@ __device__ __forceinline__ float2 pair_of(double v) {
 }
 __device__ __forceinline__ double value_of(float2 p) { return (double)p.x + (double)p.y; }
 
-// reduce-scatter of NR (s, c) pairs (as reduce_scatter); returns the FP64 sum
+// Lane layout of the pair kernels: an entry's NR right-hand sides are split
+// over P lanes of NRL each (NR = 16: two lanes of 8; else one lane), so a lane
+// keeps NRL compensated sums and gathers NRL pairs per entry: half the
+// registers of one lane per entry at NR = 16, hence twice the resident warps.
 template <int NR>
-__device__ __forceinline__ double reduce_scatter_pair(float (&s)[NR], float (&c)[NR], int lane) {
+struct PairLayout {
+    static constexpr int NRL = NR > 8 ? 8 : NR;  // right-hand sides per lane
+    static constexpr int P = NR / NRL;           // lanes per entry (1 or 2)
+    static constexpr int SLOTS = 32 / P;         // entries per warp and round
+    static constexpr int L = NRL == 1 ? 0 : NRL == 2 ? 1 : NRL == 4 ? 2 : 3;  // halving levels
+};
+
+// Reduce-scatter of the NRL (s, c) pairs over the lanes holding the same block
+// of right-hand sides (offsets 16, 8, ... down to P); returns the FP64 sum of
+// right-hand side pair_rhs<NR>(lane).
+template <int NR>
+__device__ __forceinline__ double reduce_scatter_pair(float (&s)[PairLayout<NR>::NRL],
+                                                      float (&c)[PairLayout<NR>::NRL], int lane) {
+    using PL = PairLayout<NR>;
     const unsigned FULL = 0xffffffffu;
 #pragma unroll
-    for (int h = NR / 2, o = 16; h >= 1; h >>= 1, o >>= 1) {
+    for (int h = PL::NRL / 2, o = 16; h >= 1; h >>= 1, o >>= 1) {
         const bool up = (lane & o) != 0;
 #pragma unroll
         for (int q = 0; q < h; ++q) {
@@ -351,39 +349,73 @@ __device__ __forceinline__ double reduce_scatter_pair(float (&s)[NR], float (&c)
             pair_merge(s[q], c[q], rs, rc);
         }
     }
-    constexpr int L = NR == 1 ? 0 : NR == 2 ? 1 : NR == 4 ? 2 : NR == 8 ? 3 : 4;
 #pragma unroll
-    for (int o = 16 >> L; o >= 1; o >>= 1) {
+    for (int o = 16 >> PL::L; o >= PL::P; o >>= 1) {
         const float rs = __shfl_xor_sync(FULL, s[0], o), rc = __shfl_xor_sync(FULL, c[0], o);
         pair_merge(s[0], c[0], rs, rc);
     }
     return (double)s[0] + (double)c[0];
 }
+template <int NR>
+__device__ __forceinline__ int pair_rhs(int lane) {
+    using PL = PairLayout<NR>;
+    int r = (lane & (PL::P - 1)) * PL::NRL;
+#pragma unroll
+    for (int h = PL::NRL / 2, o = 16; h >= 1; h >>= 1, o >>= 1)
+        if (lane & o) r += h;
+    return r;
+}
+// one writer per right-hand side: the lanes sharing one differ only in the
+// bits between the block bits and the halving bits
+template <int NR>
+__device__ __forceinline__ bool pair_writer(int lane) {
+    using PL = PairLayout<NR>;
+    return (lane & ((32 >> PL::L) - 1) & ~(PL::P - 1)) == 0;
+}
 
-// (s, c)[r] += w[u] * v[k[u]][r], E gathers at a time, nothing for empty slots
+// (s, c)[r] += w[u] * v[k[u]][block + r], E gathers at a time, nothing for empty slots
 template <int NR, int D>
-__device__ __forceinline__ void gather_pair_add(const float2* v, const int (&k)[D], const float (&w)[D],
-                                                float (&s)[NR], float (&c)[NR]) {
-    constexpr int E0 = NR >= 2 ? 16 / NR : 8;  // at most 16 pairs in flight per lane
+__device__ __forceinline__ void gather_pair_add(const float2* v, const int (&k)[D], const float (&w)[D], int block,
+                                                float (&s)[PairLayout<NR>::NRL], float (&c)[PairLayout<NR>::NRL]) {
+    constexpr int NRL = PairLayout<NR>::NRL;
+    constexpr int E0 = NRL >= 2 ? 16 / NRL : 8;  // at most 16 pairs in flight per lane
     constexpr int E = E0 < D ? E0 : D;
 #pragma unroll
     for (int u0 = 0; u0 < D; u0 += E) {
-        float hi[E][NR], lo[E][NR];
+        float hi[E][NRL], lo[E][NRL];
 #pragma unroll
         for (int q = 0; q < E; ++q)
-            if (k[u0 + q] >= 0) gather_pair<NR>(v, k[u0 + q], hi[q], lo[q]);
+            if (k[u0 + q] >= 0) {
+                const float2* p = v + (int64_t)k[u0 + q] * NR + block;
+                if constexpr (NRL == 1) {
+                    const float2 x = __ldcg(p);
+                    hi[q][0] = x.x;
+                    lo[q][0] = x.y;
+                } else {
+#pragma unroll
+                    for (int m = 0; m < NRL / 2; ++m) {
+                        const float4 x = __ldcg((const float4*)p + m);
+                        hi[q][2 * m] = x.x;
+                        lo[q][2 * m] = x.y;
+                        hi[q][2 * m + 1] = x.z;
+                        lo[q][2 * m + 1] = x.w;
+                    }
+                }
+            }
 #pragma unroll
         for (int q = 0; q < E; ++q)
             if (k[u0 + q] >= 0)
 #pragma unroll
-                for (int r = 0; r < NR; ++r) pair_add(s[r], c[r], w[u0 + q], hi[q][r], lo[q][r]);
+                for (int r = 0; r < NRL; ++r) pair_add(s[r], c[r], w[u0 + q], hi[q][r], lo[q][r]);
     }
 }
 
 template <int NR>
-__global__ void __launch_bounds__(256) fwd_solve_pair_k(SolveArgs<float> A) {
-    constexpr int D = 8;
+__global__ void __launch_bounds__(256, 3) fwd_solve_pair_k(SolveArgs<float> A) {
+    using PL = PairLayout<NR>;
+    constexpr int D = PL::NRL >= 8 ? 6 : 8;  // entries per lane and round (within 80 registers)
     const int lane = lane_id();
+    const int el = lane / PL::P, block = (lane & (PL::P - 1)) * PL::NRL;
     const unsigned FULL = 0xffffffffu;
     for (;;) {
         unsigned long long t = 0;
@@ -394,28 +426,27 @@ __global__ void __launch_bounds__(256) fwd_solve_pair_k(SolveArgs<float> A) {
         const int j = A.order[t];
         const int64_t a = A.rowptr[j];
         const int n = (int)(A.rowptr[j + 1] - 1 - a);
-        float s[NR], c[NR];
+        float s[PL::NRL], c[PL::NRL];
 #pragma unroll
-        for (int r = 0; r < NR; ++r) s[r] = c[r] = 0.f;
-        for (int e0 = 0; e0 < n; e0 += 32 * D) {
+        for (int r = 0; r < PL::NRL; ++r) s[r] = c[r] = 0.f;
+        for (int e0 = 0; e0 < n; e0 += PL::SLOTS * D) {
             int kk[D];
-#pragma unroll
-            for (int u = 0; u < D; ++u) {
-                const int e = e0 + lane + 32 * u;
-                kk[u] = e < n ? __ldg(&A.col[a + e]) : -1;
-            }
             float w[D];  // static data: loaded before the wait
 #pragma unroll
-            for (int u = 0; u < D; ++u) w[u] = kk[u] >= 0 ? __ldg(&A.val[a + e0 + lane + 32 * u]) : 0.f;
+            for (int u = 0; u < D; ++u) {
+                const int e = e0 + el + PL::SLOTS * u;
+                kk[u] = e < n ? __ldg(&A.col[a + e]) : -1;
+                w[u] = e < n ? __ldg(&A.val[a + e]) : 0.f;
+            }
             if (!points_ready<D>(A.ready, kk, A.status, A.spin_limit)) {
                 if (lane == 0) atomicCAS(A.status, 0, DEV_TIMEOUT);
                 return;
             }
-            gather_pair_add<NR, D>(A.yf, kk, w, s, c);
+            gather_pair_add<NR, D>(A.yf, kk, w, block, s, c);
         }
         const double sum = reduce_scatter_pair<NR>(s, c, lane);
-        if (rhs_writer<NR>(lane)) {
-            const int r = rhs_of_lane<NR>(lane);
+        if (pair_writer<NR>(lane)) {
+            const int r = pair_rhs<NR>(lane);
             double dj = A.diag[j];
             if (!(dj > 0.0)) dj = A.diag_fallback;
             A.yf[(int64_t)j * NR + r] = pair_of((A.b[(int64_t)j * NR + r] - sum) / dj);
@@ -427,9 +458,11 @@ __global__ void __launch_bounds__(256) fwd_solve_pair_k(SolveArgs<float> A) {
 }
 
 template <int NR>
-__global__ void __launch_bounds__(256) bwd_solve_pair_k(SolveArgs<float> A) {
+__global__ void __launch_bounds__(256, 3) bwd_solve_pair_k(SolveArgs<float> A) {
+    using PL = PairLayout<NR>;
     constexpr int D = 4;
     const int lane = lane_id();
+    const int el = lane / PL::P, block = (lane & (PL::P - 1)) * PL::NRL;
     const unsigned FULL = 0xffffffffu;
     for (;;) {
         unsigned long long t = 0;
@@ -444,30 +477,27 @@ __global__ void __launch_bounds__(256) bwd_solve_pair_k(SolveArgs<float> A) {
         const unsigned nch = m <= 0 ? 1u : (unsigned)((m + A.rpt - 1) / A.rpt);
         const int64_t qs = c0 + 1 + (int64_t)ch * A.rpt;
         const int nq = (int)(min(c1, qs + A.rpt) - qs);
-        float s[NR], c[NR];
+        float s[PL::NRL], c[PL::NRL];
 #pragma unroll
-        for (int r = 0; r < NR; ++r) s[r] = c[r] = 0.f;
-        for (int q0 = 0; q0 < nq; q0 += 32 * D) {
+        for (int r = 0; r < PL::NRL; ++r) s[r] = c[r] = 0.f;
+        for (int q0 = 0; q0 < nq; q0 += PL::SLOTS * D) {
             int jj[D];
-            int64_t pp[D];
-#pragma unroll
-            for (int u = 0; u < D; ++u) {
-                const int q = q0 + lane + 32 * u;
-                jj[u] = q < nq ? __ldg(&A.rowidx[qs + q]) : -1;
-                pp[u] = q < nq ? __ldg(&A.slot[qs + q]) : 0;
-            }
             float w[D];  // static data: loaded before the wait
 #pragma unroll
-            for (int u = 0; u < D; ++u) w[u] = jj[u] >= 0 ? __ldg(&A.val[pp[u]]) : 0.f;
+            for (int u = 0; u < D; ++u) {
+                const int q = q0 + el + PL::SLOTS * u;
+                jj[u] = q < nq ? __ldg(&A.rowidx[qs + q]) : -1;
+                w[u] = q < nq ? __ldg(&A.val[__ldg(&A.slot[qs + q])]) : 0.f;
+            }
             if (!points_ready<D>(A.ready, jj, A.status, A.spin_limit)) {
                 if (lane == 0) atomicCAS(A.status, 0, DEV_TIMEOUT);
                 return;
             }
-            gather_pair_add<NR, D>(A.xf, jj, w, s, c);
+            gather_pair_add<NR, D>(A.xf, jj, w, block, s, c);
         }
         double sum = reduce_scatter_pair<NR>(s, c, lane);
-        const bool wr = rhs_writer<NR>(lane);
-        const int r = rhs_of_lane<NR>(lane);
+        const bool wr = pair_writer<NR>(lane);
+        const int r = pair_rhs<NR>(lane);
         bool finish = true;
         if (nch > 1) {
             if (wr) atomicAdd(&A.acc[(int64_t)i * NR + r], sum);
