@@ -98,19 +98,38 @@ __global__ void ord_band_k(const double* __restrict__ v2, const int* __restrict_
     if (q < N && stat[q] == 0 && v2[q] >= T) blist[atomicAdd(nb, 1ULL)] = (int32_t)q;
 }
 
+// per band cell: the largest squared distance (as bits) of its undecided band
+// points, -1 if none; a dominance scan skips the cells whose largest value is
+// below its own (no point of larger key there)
+__global__ void ord_cellmax_k(const int32_t* __restrict__ bsorted, const int64_t* __restrict__ bstart,
+                              int64_t ncells, const double* __restrict__ v2, const int* __restrict__ stat,
+                              long long* __restrict__ cmax) {
+    const int64_t cidx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (cidx >= ncells) return;
+    long long m = -1;
+    const long long* __restrict__ v2b = (const long long*)v2;
+    for (int64_t f = bstart[cidx]; f < bstart[cidx + 1]; ++f) {
+        const int p = bsorted[f];
+        if (stat[p] == 0) m = max(m, v2b[p]);
+    }
+    cmax[cidx] = m;
+}
+
 // one thread per band point: is it dominant?
 __global__ void ord_dominance_k(Grid gb, const int32_t* __restrict__ bsorted, const int64_t* __restrict__ bstart,
                                 int64_t nb, const double* __restrict__ xg, int d, const int32_t* __restrict__ idg,
                                 const double* __restrict__ v2, const int* __restrict__ stat, double T,
                                 int32_t* __restrict__ sel, unsigned long long* __restrict__ nsel,
                                 unsigned long long* __restrict__ nactive, const float* __restrict__ xgf,
-                                float delta) {
+                                float delta, const long long* __restrict__ cmax) {
     int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= nb) return;
     const int q = bsorted[e];
     if (stat[q] != 0) return;
     const double vq = v2[q];
     if (!(vq >= T)) return;
+    const long long bq = __double_as_longlong(vq);
+    const long long* __restrict__ v2b = (const long long*)v2;
     atomicAdd(nactive, 1ULL);
     const double* xq = xg + (int64_t)q * d;
     const float rq = sqrtf((float)vq);
@@ -152,22 +171,24 @@ __global__ void ord_dominance_k(Grid gb, const int32_t* __restrict__ bsorted, co
                         ++nseg;
                     }
                 }
-                for (int sg = 0; sg < nseg && dom; ++sg) {
-                    const int64_t f0 = bstart[base + seg[sg][0]], f1 = bstart[base + seg[sg][1] + 1];
-                    for (int64_t f = f0; f < f1; ++f) {
-                        const int p = bsorted[f];
-                        if (p == q || stat[p] != 0) continue;
-                        const double vp = v2[p];
-                        if (vp > vq || (vp == vq && idg[p] < idq)) {
-                            if (xgf && screen_f32(xgf + (int64_t)p * d, xgf + (int64_t)q * d, d, rq, delta) == 0)
-                                continue;  // surely farther than sqrt(vq)
-                            if (dist2_exact(xg + (int64_t)p * d, xq, d) < vq) {
-                                dom = false;
-                                break;
+                for (int sg = 0; sg < nseg && dom; ++sg)
+                    for (int cx = seg[sg][0]; cx <= seg[sg][1] && dom; ++cx) {
+                        if (cmax[base + cx] < bq) continue;  // no larger key in this cell
+                        const int64_t f0 = bstart[base + cx], f1 = bstart[base + cx + 1];
+                        for (int64_t f = f0; f < f1; ++f) {
+                            const int p = bsorted[f];
+                            if (p == q || stat[p] != 0) continue;
+                            const long long bp = v2b[p];
+                            if (bp > bq || (bp == bq && idg[p] < idq)) {
+                                if (xgf && screen_f32(xgf + (int64_t)p * d, xgf + (int64_t)q * d, d, rq, delta) == 0)
+                                    continue;  // surely farther than sqrt(vq)
+                                if (dist2_exact(xg + (int64_t)p * d, xq, d) < vq) {
+                                    dom = false;
+                                    break;
+                                }
                             }
                         }
                     }
-                }
             }
     }
     if (dom) sel[atomicAdd(nsel, 1ULL)] = q;
@@ -176,10 +197,18 @@ __global__ void ord_dominance_k(Grid gb, const int32_t* __restrict__ bsorted, co
 // ---- greedy steps for the coarsest points: one launch selects the argmax of
 // the previous launch's per-block candidates and pushes it to every point.
 constexpr int GREEDY_BLOCKS_PER_SM = 4;
-constexpr int64_t GREEDY_STEPS = 512;
+#ifndef KC_GREEDY_STEPS
+#define KC_GREEDY_STEPS 256
+#endif
+constexpr int64_t GREEDY_STEPS = KC_GREEDY_STEPS;  // coarsest points selected one per launch
 
+// Keys compare on the bit patterns of the squared distances: for v >= 0
+// (and +inf) IEEE doubles order like their bits as integers, and integer
+// compares stay off the GB300's small FP64 pipe.
+__device__ __forceinline__ long long vbits(double v) { return __double_as_longlong(v); }
 __device__ __forceinline__ bool key_above(double va, int ia, double vb, int ib) {
-    return va > vb || (va == vb && ia < ib);
+    const long long a = vbits(va), b = vbits(vb);
+    return a > b || (a == b && ia < ib);
 }
 
 // per-block best (v2 desc, original index asc) over undecided points; cand_g = -1 if none
@@ -374,6 +403,8 @@ kc_status order_impl(const double* x, int64_t N, int d, int32_t* perm, double* l
     KC_TRY(A.get(&sbox, N));
     KC_TRY(A.get(&ioff, N + 1));
     KC_TRY(A.get(&bstart, 2 * N + 2));
+    long long* cmax;  // per band cell (at most 2 N + 1 cells)
+    KC_TRY(A.get(&cmax, 2 * N + 2));
     KC_TRY(A.get(&ctr, 8));
     // float copy of the coordinates (minus the box corner) for FP32 screens of
     // the distance tests; exact FP64 tests decide every close call
@@ -445,8 +476,10 @@ kc_status order_impl(const double* x, int64_t N, int d, int32_t* perm, double* l
         for (;;) {
             if (++rounds > 1000000) return fail(KC_ECUDA, "ordering: too many rounds");
             KC_CUDA(cudaMemsetAsync(ctr + 3, 0, 2 * sizeof(unsigned long long), s));
+            ::kc::note_launch(), ord_cellmax_k<<<blocks_for(gb.ncells, 256), 256, 0, s>>>(bsorted, bstart, gb.ncells, v2,
+                                                                                         stat, cmax);
             ::kc::note_launch(), ord_dominance_k<<<blocks_for(nb, 128), 128, 0, s>>>(gb, bsorted, bstart, nb, xg, d, idg, v2, stat, T, sel,
-                                                                ctr + 3, ctr + 4, xgf, delta);
+                                                                ctr + 3, ctr + 4, xgf, delta, cmax);
             unsigned long long hs[2];
             KC_CUDA(cudaMemcpyAsync(hs, ctr + 3, sizeof(hs), cudaMemcpyDeviceToHost, s));
             KC_CUDA(cudaStreamSynchronize(s));
