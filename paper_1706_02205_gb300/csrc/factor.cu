@@ -266,12 +266,18 @@ __device__ __forceinline__ bool spin_done(const unsigned* f, const int* status, 
     return true;
 }
 
+// Matern parameters of column i's set, read where they are used (not kept in
+// registers through the merges).
+template <typename T>
+__device__ __forceinline__ const KernelParams& kparams(const FactorArgs<T>& A, int i) {
+    return A.col_set ? A.kps[A.col_set[i]] : A.kp;
+}
+
 // Everything a task knows after its prologue.
 template <typename T>
 struct TaskCtx {
     int i, c, nr;
     int64_t a0, a1;  // R_i = col[a0..a1), L_ii at a1
-    KernelParams kp;
     bool zero;       // dropped pivot: the whole column is zero
     bool staged;     // row i is in the table (else binary search in global memory)
     double Lii;
@@ -296,7 +302,6 @@ __device__ __forceinline__ int task_begin(const FactorArgs<T>& A, RowTable<T>& t
     X.a0 = A.rowptr[X.i];
     X.a1 = A.rowptr[X.i + 1] - 1;
     X.nr = (int)(X.a1 - X.a0);
-    X.kp = A.col_set ? A.kps[A.col_set[X.i]] : A.kp;
 
     X.staged = 2 * X.nr <= (1 << A.hbits);  // load factor <= 1/2 (linear-probing misses stay short)
     if (X.staged) tab.clear(lane);
@@ -349,7 +354,8 @@ __device__ __forceinline__ int task_begin(const FactorArgs<T>& A, RowTable<T>& t
     T inv = (T)0;
     int zero = 0;
     if (lane == 0) {
-        const double p = (X.kp.sigma2 + X.kp.nugget) - sq.total();
+        const KernelParams& kp = kparams(A, X.i);
+        const double p = (kp.sigma2 + kp.nugget) - sq.total();
         zero = !(p > 0.0);
         Lii = zero ? 0.0 : sqrt(p);
         inv = zero ? (T)0 : Acc<T>::recip(Lii);
@@ -437,7 +443,7 @@ __device__ __forceinline__ void batch_rows(const FactorArgs<T>& A, const TaskCtx
         const int j = __ldg(&A.rowidx[b0 + lane]);
         my_b = __ldg(&A.slot[b0 + lane]);
         my_e0 = __ldg(&A.rowptr[j]);
-        if (!X.zero) my_th = theta_off<T>(X.kp, A.d, A.x + (int64_t)j * A.d, A.x + (int64_t)X.i * A.d);
+        if (!X.zero) my_th = theta_off<T>(kparams(A, X.i), A.d, A.x + (int64_t)j * A.d, A.x + (int64_t)X.i * A.d);
     }
 }
 
