@@ -547,9 +547,15 @@ __global__ void from_point_major_k(const double* __restrict__ xp, const int32_t*
     }
 }
 
+// Rows of a column per backward-solve task (wider columns are cut into chunks
+// that combine their sums atomically).
+#ifndef KC_SOLVE_ROWS
+#define KC_SOLVE_ROWS 128
+#endif
+
 kc_status solver_init(Solver& S, const kc_pattern* P, int nrhs_cap, const kc_opts* o, Arena& A, cudaStream_t s) {
     S.P = P;
-    S.rpt = (o && o->rows_per_task > 0) ? o->rows_per_task : 64;
+    S.rpt = (o && o->rows_per_task > 0) ? o->rows_per_task : KC_SOLVE_ROWS;
     if (o && o->spin_limit_cycles > 0) S.spin = o->spin_limit_cycles;
     KC_TRY(build_tasks(P, S.rpt, A, s, &S.tasks, &S.ntasks, &S.maxr));
     S.nrhs_cap = nrhs_cap;
