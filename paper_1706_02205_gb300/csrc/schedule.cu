@@ -13,36 +13,33 @@
 
 namespace kc {
 
-// rowof[e] = row of CSR entry e
-__global__ void row_of_k(const int64_t* __restrict__ rowptr, int64_t N, int32_t* __restrict__ rowof) {
+// Sort items of the CSR entries: key = column, value = (row << pb) | position
+// with pb bits for positions, so the sorted items carry their rows (no gather
+// after the sort).
+__global__ void col_keys_k(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col, int64_t N, int pb,
+                           uint32_t* __restrict__ key, int64_t* __restrict__ val) {
     int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     int lane = lane_id();
     int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t j = warp; j < N; j += nw) {
-        int64_t a = rowptr[j], b = rowptr[j + 1];
-        for (int64_t e = a + lane; e < b; e += 32) rowof[e] = (int32_t)j;
-    }
-}
-
-__global__ void col_keys_k(const int32_t* __restrict__ col, int64_t nnz, uint32_t* __restrict__ key,
-                           int64_t* __restrict__ val) {
-    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e < nnz) {
-        key[e] = (uint32_t)col[e];
-        val[e] = e;
+        const int64_t a = rowptr[j], b = rowptr[j + 1];
+        for (int64_t e = a + lane; e < b; e += 32) {
+            key[e] = (uint32_t)col[e];
+            val[e] = (j << pb) | e;
+        }
     }
 }
 
 // After the stable sort by column: slot[q] = CSR position, rowidx[q] = its row,
 // colptr[c] = first q of column c (every column holds its diagonal).
 __global__ void csc_finish_k(const uint32_t* __restrict__ skey, const int64_t* __restrict__ sval, int64_t nnz,
-                             const int32_t* __restrict__ rowof, int64_t N, int64_t* __restrict__ colptr,
-                             int32_t* __restrict__ rowidx, int64_t* __restrict__ slot) {
+                             int64_t N, int pb, int64_t* __restrict__ colptr, int32_t* __restrict__ rowidx,
+                             int64_t* __restrict__ slot) {
     int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (q < nnz) {
-        int64_t e = sval[q];
-        slot[q] = e;
-        rowidx[q] = rowof[e];
+        const int64_t v = sval[q];
+        slot[q] = v & (((int64_t)1 << pb) - 1);
+        rowidx[q] = (int32_t)(v >> pb);
         uint32_t c = skey[q];
         if (q == 0 || skey[q - 1] != c) colptr[c] = q;
     }
@@ -51,9 +48,20 @@ __global__ void csc_finish_k(const uint32_t* __restrict__ skey, const int64_t* _
 
 // level[j] = 1 + max level over row j; rows claimed in index order, so a row
 // waits only on rows with smaller index that were claimed before it.
+__device__ __forceinline__ int ld_relaxed_level(const int* p) {
+    int v;
+    asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+// level[j] = 1 + max level over row j; rows claimed in index order, so a row
+// waits only on rows with smaller index that were claimed before it.  Each
+// lane reads up to 8 of the row's levels with relaxed loads all in flight
+// together and spins (bounded, with back-off) only on those not yet set.
+// Only the level values are read, so no acquire ordering is needed.
 __global__ void levels_k(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col, int64_t N,
                          int* __restrict__ level, unsigned long long* __restrict__ ticket, int* __restrict__ depth,
                          int* __restrict__ status, long long spin_limit) {
+    constexpr int D = 8;
     int lane = lane_id();
     for (;;) {
         unsigned long long t = 0;
@@ -61,26 +69,37 @@ __global__ void levels_k(const int64_t* __restrict__ rowptr, const int32_t* __re
         t = __shfl_sync(0xffffffffu, t, 0);
         if ((int64_t)t >= N) return;
         if (ld_volatile_s32(status) != 0) return;
-        int64_t j = (int64_t)t;
-        int64_t a = rowptr[j], b = rowptr[j + 1] - 1;
+        const int64_t j = (int64_t)t;
+        const int64_t a = rowptr[j];
+        const int n = (int)(rowptr[j + 1] - 1 - a);
         int m = 0;
         bool ok = true;
-        for (int64_t e = a + lane; e < b && ok; e += 32) {
-            int k = __ldg(&col[e]);
-            int v = ld_acquire_s32(&level[k]);
-            if (v == 0) {
-                long long t0 = clock64();
-                unsigned ns = 32;
-                while ((v = ld_acquire_s32(&level[k])) == 0) {
-                    if (clock64() - t0 > spin_limit || ld_volatile_s32(status) != 0) {
-                        ok = false;
-                        break;
-                    }
-                    __nanosleep(ns);
-                    if (ns < 512) ns <<= 1;
-                }
+        for (int e0 = 0; e0 < n; e0 += 32 * D) {
+            int kk[D], v[D];
+#pragma unroll
+            for (int u = 0; u < D; ++u) {
+                const int e = e0 + lane + 32 * u;
+                kk[u] = e < n ? __ldg(&col[a + e]) : -1;
             }
-            m = max(m, v);
+#pragma unroll
+            for (int u = 0; u < D; ++u) v[u] = kk[u] >= 0 ? ld_relaxed_level(&level[kk[u]]) : 0;
+#pragma unroll
+            for (int u = 0; u < D; ++u) {
+                if (kk[u] >= 0 && v[u] == 0 && ok) {
+                    const long long t0 = clock64();
+                    unsigned ns = 32;
+                    while ((v[u] = ld_relaxed_level(&level[kk[u]])) == 0) {
+                        if (clock64() - t0 > spin_limit || ld_volatile_s32(status) != 0) {
+                            ok = false;
+                            break;
+                        }
+                        __nanosleep(ns);
+                        if (ns < 512) ns <<= 1;
+                    }
+                }
+                m = max(m, v[u]);
+            }
+            if (!__all_sync(0xffffffffu, ok)) break;
         }
         if (!__all_sync(0xffffffffu, ok)) {
             if (lane == 0) atomicCAS(status, 0, DEV_TIMEOUT);
@@ -94,7 +113,6 @@ __global__ void levels_k(const int64_t* __restrict__ rowptr, const int32_t* __re
         }
     }
 }
-
 __global__ void level_keys_k(const int* __restrict__ level, int64_t N, uint32_t* __restrict__ key,
                              int64_t* __restrict__ val) {
     int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -128,20 +146,19 @@ kc_status schedule_impl(int64_t N, const int64_t* rowptr, const int32_t* col, in
                         int32_t* depth_out, cudaStream_t s) {
     Arena A(s);
     // CSC by a stable sort of the CSR entries by column
-    int32_t* rowof;
+    const int pb = bits_for(nnz);
+    if (pb + bits_for(N) > 63) return fail(KC_EINVAL, "schedule: N and nnz too large for packed sort values");
     uint32_t *k0, *k1;
     int64_t *v0, *v1;
-    KC_TRY(A.get(&rowof, nnz));
     KC_TRY(A.get(&k0, nnz));
     KC_TRY(A.get(&k1, nnz));
     KC_TRY(A.get(&v0, nnz));
     KC_TRY(A.get(&v1, nnz));
     int sms = sm_count();
-    ::kc::note_launch(), row_of_k<<<sms * 8, 256, 0, s>>>(rowptr, N, rowof);
-    ::kc::note_launch(), col_keys_k<<<blocks_for(nnz, 256), 256, 0, s>>>(col, nnz, k0, v0);
+    ::kc::note_launch(), col_keys_k<<<sms * 8, 256, 0, s>>>(rowptr, col, N, pb, k0, v0);
     KC_CUDA(cudaGetLastError());
     KC_TRY(radix_sort_u32_i64(k0, v0, k1, v1, nnz, bits_for(N), A, s));
-    ::kc::note_launch(), csc_finish_k<<<blocks_for(nnz, 256), 256, 0, s>>>(k1, v1, nnz, rowof, N, colptr, rowidx, slot);
+    ::kc::note_launch(), csc_finish_k<<<blocks_for(nnz, 256), 256, 0, s>>>(k1, v1, nnz, N, pb, colptr, rowidx, slot);
     KC_CUDA(cudaGetLastError());
 
     // levels
