@@ -217,9 +217,59 @@ kc_status pattern_count_impl(const double* xo, const double* l, int64_t N, int d
 constexpr int SORT_WARP_CAP = 1024;
 constexpr int SORT_BLOCK_CAP = 16384;
 
+// Bitonic sort of 32*E keys held E per lane (element t = lane*E + r):
+// compare-exchanges at distance >= E go through shfl_xor, shorter ones
+// between a lane's own registers.  The keys of a row are distinct.
+template <int E>
+__device__ __forceinline__ void warp_bitonic(int (&v)[E], int lane) {
+    for (int k = 2; k <= 32 * E; k <<= 1) {
+        for (int jj = k >> 1; jj >= E; jj >>= 1) {  // partners in other lanes
+            const int lm = jj / E;
+            const bool lower = (lane & lm) == 0;
+#pragma unroll
+            for (int r = 0; r < E; ++r) {
+                const int pv = __shfl_xor_sync(0xffffffffu, v[r], lm);
+                const bool up = ((lane * E + r) & k) == 0;
+                v[r] = (lower == up) ? min(v[r], pv) : max(v[r], pv);
+            }
+        }
+#pragma unroll
+        for (int jb = E / 2; jb >= 1; jb >>= 1) {  // partners in this lane (compile-time distances)
+            if (jb < k)
+#pragma unroll
+                for (int r = 0; r < E; ++r)
+                    if ((r & jb) == 0) {
+                        const bool up = ((lane * E + r) & k) == 0;
+                        const int x0 = v[r], x1 = v[r | jb];
+                        if ((x0 > x1) == up) {
+                            v[r] = x1;
+                            v[r | jb] = x0;
+                        }
+                    }
+        }
+    }
+}
+template <int E>
+__device__ __forceinline__ void sort_row_regs(int32_t* __restrict__ c, int L, int lane) {
+    int v[E];
+#pragma unroll
+    for (int r = 0; r < E; ++r) {
+        const int t = lane * E + r;
+        v[r] = t < L ? c[t] : INT_MAX;
+    }
+    warp_bitonic<E>(v, lane);
+#pragma unroll
+    for (int r = 0; r < E; ++r) {
+        const int t = lane * E + r;
+        if (t < L) c[t] = v[r];
+    }
+}
+
+// One warp per row: put the diagonal last and sort the off-diagonal entries
+// (written in arbitrary order by the fill's atomics) in registers; rows longer
+// than SORT_WARP_CAP go to the block sort.
 __global__ void row_sort_warp_k(const int64_t* __restrict__ rowptr, int64_t N, int32_t* __restrict__ col,
                                 int32_t* __restrict__ long_rows, unsigned long long* __restrict__ nlong) {
-    __shared__ int buf[8][SORT_WARP_CAP];
     const int w = threadIdx.x >> 5, lane = lane_id();
     const int64_t j = (int64_t)blockIdx.x * 8 + w;
     if (j >= N) return;
@@ -231,27 +281,13 @@ __global__ void row_sort_warp_k(const int64_t* __restrict__ rowptr, int64_t N, i
         if (lane == 0) long_rows[atomicAdd(nlong, 1ULL)] = (int32_t)j;
         return;
     }
-    int P = 1;
-    while (P < L) P <<= 1;
-    int* s = buf[w];
-    for (int t = lane; t < P; t += 32) s[t] = t < L ? col[a + t] : INT_MAX;
-    __syncwarp();
-    for (int k = 2; k <= P; k <<= 1)
-        for (int jj = k >> 1; jj > 0; jj >>= 1) {
-            for (int t = lane; t < P; t += 32) {
-                int u = t ^ jj;
-                if (u > t) {
-                    int x0 = s[t], x1 = s[u];
-                    bool up = (t & k) == 0;
-                    if ((x0 > x1) == up) {
-                        s[t] = x1;
-                        s[u] = x0;
-                    }
-                }
-            }
-            __syncwarp();
-        }
-    for (int t = lane; t < L; t += 32) col[a + t] = s[t];
+    int32_t* c = col + a;
+    if (L <= 32) sort_row_regs<1>(c, L, lane);
+    else if (L <= 64) sort_row_regs<2>(c, L, lane);
+    else if (L <= 128) sort_row_regs<4>(c, L, lane);
+    else if (L <= 256) sort_row_regs<8>(c, L, lane);
+    else if (L <= 512) sort_row_regs<16>(c, L, lane);
+    else sort_row_regs<32>(c, L, lane);
 }
 
 __global__ void row_sort_block_k(const int64_t* __restrict__ rowptr, int32_t* __restrict__ col,
