@@ -303,7 +303,7 @@ __device__ __forceinline__ int task_begin(const FactorArgs<T>& A, RowTable<T>& t
     X.a1 = A.rowptr[X.i + 1] - 1;
     X.nr = (int)(X.a1 - X.a0);
 
-    X.staged = 2 * X.nr <= (1 << A.hbits);  // load factor <= 1/2 (linear-probing misses stay short)
+    X.staged = 4 * X.nr <= 3 * (1 << A.hbits);  // load factor <= 3/4 (linear probing stays short)
     if (X.staged) tab.clear(lane);
     __syncwarp();
     // R_i in rounds of DEPS entries per lane: the column indices, the completion
@@ -926,10 +926,11 @@ static kc_status apply_opts(FactorCore& F, const kc_opts* o) {
 }
 
 static void pick_hash(FactorCore& F) {
-    // hash table: at least twice the longest row (load factor <= 1/2), 128..2048 slots;
-    // longer rows fall back to binary search in global memory
+    // hash table: 4/3 of the longest row at least (load factor <= 3/4), a power
+    // of two in 128..2048 slots; a longer row falls back to binary search in
+    // global memory
     int hb = 7;
-    while (hb < 11 && (1 << hb) < 2 * F.maxr) ++hb;
+    while (hb < 11 && 3 * (1 << hb) < 4 * F.maxr) ++hb;
     F.hbits = hb;
     // staging depth: 16 loads per lane in flight for long rows (FP32 form),
     // else 8; the FP64 form takes at most 8
