@@ -91,8 +91,8 @@ typedef struct {
 /* Options of the persistent kernels (zero-initialise for defaults). */
 typedef struct {
     int64_t spin_limit_cycles;     /* bound of every device wait; 0 -> ~4e9 cycles */
-    int32_t rows_per_task;         /* rows of a column per task; 0 -> about (nnz - N) / (depth x resident
-                                      warps), a power of two in 16..128 */
+    int32_t rows_per_task;         /* rows of a column per task; 0 -> factor: about (nnz - N) / (depth x
+                                      resident warps), a power of two in 16..128; backward solve: 128 */
     int32_t ctas_per_sm;           /* persistent grid = SMs x this; 0 -> occupancy */
     int32_t warps_per_cta;         /* 0 -> the CTA size (8, 4, 2 or 1 warps) with the most resident warps */
     int32_t test_hold_column;      /* test hook: 0 = off; c+1 makes column c never signal
@@ -109,6 +109,10 @@ typedef struct {
 } kc_opts;
 
 const char* kc_last_error(void);
+/* Version of this interface (structs and signatures); a binding built for
+ * another version must not call the library.  2: kc_schedule takes the points,
+ * kc_opts has stage_bytes. */
+#define KC_ABI_VERSION 2
 int32_t kc_abi_version(void);
 
 /* Number of kernels this library has launched in the process so far

@@ -63,7 +63,7 @@ extern "C" {
 
 const char* kc_last_error(void) { return last_error_cstr(); }
 
-int32_t kc_abi_version(void) { return 1; }
+int32_t kc_abi_version(void) { return KC_ABI_VERSION; }
 
 int64_t kc_launch_count(void) { return launch_count(); }
 

@@ -48,6 +48,7 @@ class kc_opts(C.Structure):
 
 
 _lib = None
+ABI_VERSION = 2  # KC_ABI_VERSION of include/kchol.h that these signatures follow
 
 
 def lib():
@@ -61,6 +62,9 @@ def lib():
         P = C.POINTER
         L.kc_last_error.restype = C.c_char_p
         L.kc_abi_version.restype = i32
+        if L.kc_abi_version() != ABI_VERSION:
+            raise ImportError(f"libkchol.so has interface version {L.kc_abi_version()}, this binding needs "
+                              f"{ABI_VERSION}; rebuild it with __graft_entry__.build()")
         L.kc_launch_count.restype = i64
         L.kc_last_factor_kernel_ms.restype = dbl
         sigs = {

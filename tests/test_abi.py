@@ -33,7 +33,10 @@ def test_library_exports_every_declared_symbol(so):
     for n in _declared():
         assert hasattr(lib, n), n
     lib.kc_abi_version.restype = ctypes.c_int32
-    assert lib.kc_abi_version() >= 1
+    # the library, the header and the Python binding agree on the interface version
+    from paper_1706_02205_gb300 import kchol
+    hdr = open(os.path.join(ROOT, "include", "kchol.h")).read()
+    assert int(re.search(r"#define KC_ABI_VERSION (\d+)", hdr).group(1)) == lib.kc_abi_version() == kchol.ABI_VERSION
 
 
 def test_binding_lists_match_header(so):
