@@ -44,7 +44,8 @@ void keep_pool_warm();
 // arena goes out of scope, after the work enqueued before that point.
 struct Arena {
     cudaStream_t s;
-    void* ptrs[64];
+    static constexpr int CAP = 128;
+    void* ptrs[CAP];
     int n = 0;
     explicit Arena(cudaStream_t st) : s(st) { keep_pool_warm(); }
     ~Arena() {
@@ -52,7 +53,7 @@ struct Arena {
     }
     template <typename T>
     kc_status get(T** out, size_t count) {
-        if (n == 64) return fail(KC_ENOMEM, "scratch arena full");
+        if (n == CAP) return fail(KC_ENOMEM, "scratch arena full");
         void* p = nullptr;
         size_t bytes = count * sizeof(T);
         if (bytes == 0) bytes = 16;

@@ -1,4 +1,6 @@
+#include <algorithm>
 #include <cmath>
+#include <vector>
 
 #include "grid.cuh"
 
@@ -203,6 +205,127 @@ kc_status bbox_all(const double* x, int64_t N, int d, Origin* lo, double* E, Are
         e = fmax(e, mx - mn);
     }
     *E = e;
+    return KC_OK;
+}
+
+// Per block: sum of x and of the products x_a x_b (a <= b, packed) over its
+// points, a thread per pair.
+__global__ void moments_k(const double* __restrict__ x, int64_t N, int d, double* __restrict__ part) {
+    const int np = d * (d + 1) / 2;
+    const int per = (int)((N + gridDim.x - 1) / gridDim.x);
+    const int64_t q0 = (int64_t)blockIdx.x * per, q1 = min(N, q0 + per);
+    for (int t = threadIdx.x; t < np + d; t += blockDim.x) {
+        double s = 0.0;
+        if (t < np) {
+            int a = 0, r = t;  // pair (a, b) of the packed upper triangle
+            while (r >= d - a) {
+                r -= d - a;
+                ++a;
+            }
+            const int b = a + r;
+            for (int64_t q = q0; q < q1; ++q) s = fma(x[q * d + a], x[q * d + b], s);
+        } else {
+            const int a = t - np;
+            for (int64_t q = q0; q < q1; ++q) s += x[q * d + a];
+        }
+        part[(int64_t)blockIdx.x * (np + d) + t] = s;
+    }
+}
+
+struct Axes3 {
+    double v[3][MAXD];
+};
+__global__ void project_k(const double* __restrict__ x, int64_t N, int d, Axes3 ax, double* __restrict__ out) {
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= N) return;
+    for (int t = 0; t < 3; ++t) {
+        double s = 0.0;
+        for (int k = 0; k < d; ++k) s = fma(ax.v[t][k], x[q * d + k], s);
+        out[q * 3 + t] = s;
+    }
+}
+
+// Eigenvectors of the symmetric d x d matrix a (row-major, destroyed) by the
+// cyclic Jacobi method: plane rotations that zero one off-diagonal entry at a
+// time, accumulated in v (columns = eigenvectors), until the off-diagonal part
+// is negligible; eigenvalues end on the diagonal of a.
+static void jacobi_eigen(int d, double* a, double* v) {
+    for (int i = 0; i < d; ++i)
+        for (int j = 0; j < d; ++j) v[i * d + j] = i == j ? 1.0 : 0.0;
+    for (int sweep = 0; sweep < 64; ++sweep) {
+        double off = 0.0, tot = 0.0;
+        for (int i = 0; i < d; ++i)
+            for (int j = 0; j < d; ++j) {
+                tot += a[i * d + j] * a[i * d + j];
+                if (i != j) off += a[i * d + j] * a[i * d + j];
+            }
+        if (!(off > 1e-30 * tot)) break;
+        for (int p = 0; p < d - 1; ++p)
+            for (int q = p + 1; q < d; ++q) {
+                const double apq = a[p * d + q];
+                if (apq == 0.0) continue;
+                const double theta = (a[q * d + q] - a[p * d + p]) / (2.0 * apq);
+                const double t = (theta >= 0 ? 1.0 : -1.0) / (std::fabs(theta) + std::sqrt(theta * theta + 1.0));
+                const double c = 1.0 / std::sqrt(t * t + 1.0), s = t * c;
+                for (int k = 0; k < d; ++k) {  // columns p, q
+                    const double akp = a[k * d + p], akq = a[k * d + q];
+                    a[k * d + p] = c * akp - s * akq;
+                    a[k * d + q] = s * akp + c * akq;
+                }
+                for (int k = 0; k < d; ++k) {  // rows p, q
+                    const double apk = a[p * d + k], aqk = a[q * d + k];
+                    a[p * d + k] = c * apk - s * aqk;
+                    a[q * d + k] = s * apk + c * aqk;
+                }
+                for (int k = 0; k < d; ++k) {
+                    const double vkp = v[k * d + p], vkq = v[k * d + q];
+                    v[k * d + p] = c * vkp - s * vkq;
+                    v[k * d + q] = s * vkp + c * vkq;
+                }
+            }
+    }
+}
+
+kc_status grid_coords(const double* x, int64_t N, int d, Arena& A, cudaStream_t s, const double** gx, int* gs) {
+    if (d <= 3) {
+        *gx = x;
+        *gs = d;
+        return KC_OK;
+    }
+    if (d > MAXD) return fail(KC_EINVAL, "d must be <= 32");
+    const int np = d * (d + 1) / 2, nb = 152;
+    double* part;
+    KC_TRY(A.get(&part, (size_t)nb * (np + d)));
+    ::kc::note_launch(), moments_k<<<nb, 256, 0, s>>>(x, N, d, part);
+    KC_CUDA(cudaGetLastError());
+    std::vector<double> h((size_t)nb * (np + d));
+    KC_CUDA(cudaMemcpyAsync(h.data(), part, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, s));
+    KC_CUDA(cudaStreamSynchronize(s));
+    std::vector<double> m(np + d, 0.0), cov((size_t)d * d), vec((size_t)d * d);
+    for (int b = 0; b < nb; ++b)
+        for (int t = 0; t < np + d; ++t) m[t] += h[(size_t)b * (np + d) + t];
+    for (int a = 0, t = 0; a < d; ++a)
+        for (int b = a; b < d; ++b, ++t) {
+            const double c = m[t] / (double)N - (m[np + a] / (double)N) * (m[np + b] / (double)N);
+            cov[a * d + b] = cov[b * d + a] = c;
+        }
+    jacobi_eigen(d, cov.data(), vec.data());
+    std::vector<int> idx(d);
+    for (int i = 0; i < d; ++i) idx[i] = i;
+    std::sort(idx.begin(), idx.end(), [&](int i, int j) { return cov[i * d + i] > cov[j * d + j]; });
+    Axes3 ax;
+    for (int t = 0; t < 3; ++t) {
+        double nrm = 0.0;
+        for (int k = 0; k < d; ++k) nrm += vec[k * d + idx[t]] * vec[k * d + idx[t]];
+        nrm = std::sqrt(nrm);  // 1 up to rounding; renormalised so |v_t| <= 1 holds
+        for (int k = 0; k < MAXD; ++k) ax.v[t][k] = k < d ? vec[k * d + idx[t]] / (nrm * (1.0 + 1e-14)) : 0.0;
+    }
+    double* out;
+    KC_TRY(A.get(&out, (size_t)N * 3));
+    ::kc::note_launch(), project_k<<<blocks_for(N, 256), 256, 0, s>>>(x, N, d, ax, out);
+    KC_CUDA(cudaGetLastError());
+    *gx = out;
+    *gs = 3;
     return KC_OK;
 }
 

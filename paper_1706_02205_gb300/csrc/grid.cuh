@@ -112,6 +112,15 @@ kc_status grid_build(const Grid& g, const double* x, int d, const int32_t* ids, 
 // Bounding box of x (row-major N x d) over the first min(d,3) axes; host out.
 kc_status bbox(const double* x, int64_t N, int d, double* lo, double* hi, Arena& A, cudaStream_t s);
 
+// Grid coordinates of the points x (row-major N x d): for d <= 3 the points
+// themselves (*gx = x, *gs = d); for d > 3 their projections on the three
+// principal axes of the point cloud (*gx: device N x 3 from the arena, *gs =
+// 3).  The axes are orthonormal, so a grid coordinate of two points differs
+// by no more than their distance and every search box stays exact; for data
+// near a low-dimensional subspace they keep the boxes as tight as the data
+// (the first three raw coordinates are an arbitrary projection of it).
+kc_status grid_coords(const double* x, int64_t N, int d, Arena& A, cudaStream_t s, const double** gx, int* gs);
+
 // Bounding box over all d <= 32 axes (host out), for the float copies used by
 // the FP32 distance screens; E = the largest extent.
 constexpr int MAXD = 32;

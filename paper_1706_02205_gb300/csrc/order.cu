@@ -51,6 +51,14 @@ kc_status check_finite(const double* x, int64_t n, Arena& A, cudaStream_t s) {
     return KC_OK;
 }
 
+// out[q] = rows ids[q] of the n x w array a
+__global__ void gather_rows_k(const double* __restrict__ a, int w, const int32_t* __restrict__ ids, int64_t n,
+                              double* __restrict__ out) {
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q < n)
+        for (int t = 0; t < w; ++t) out[q * w + t] = a[(int64_t)ids[q] * w + t];
+}
+
 // state in grid order (gpos): coordinates xg, original index idg, v2, stat
 __global__ void ord_init_k(const double* __restrict__ x, int d, const int32_t* __restrict__ gsorted, int64_t N,
                            double* __restrict__ xg, int32_t* __restrict__ idg, double* __restrict__ v2,
@@ -121,7 +129,8 @@ __global__ void ord_dominance_k(Grid gb, const int32_t* __restrict__ bsorted, co
                                 const double* __restrict__ v2, const int* __restrict__ stat, double T,
                                 int32_t* __restrict__ sel, unsigned long long* __restrict__ nsel,
                                 unsigned long long* __restrict__ nactive, const float* __restrict__ xgf,
-                                float delta, const long long* __restrict__ cmax) {
+                                float delta, const long long* __restrict__ cmax, const double* __restrict__ gxg,
+                                int gs) {
     int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= nb) return;
     const int q = bsorted[e];
@@ -142,7 +151,7 @@ __global__ void ord_dominance_k(Grid gb, const int32_t* __restrict__ bsorted, co
     int c[3] = {0, 0, 0};
     int maxr = 0;
     for (int t = 0; t < dg; ++t) {
-        c[t] = cell_coord(gb, xq[t], t);
+        c[t] = cell_coord(gb, gxg[(int64_t)q * gs + t], t);
         maxr = max(maxr, span_for(gb, R, t));
     }
     bool dom = true;
@@ -302,12 +311,12 @@ __global__ void ord_mark_k(const int32_t* __restrict__ sel, int64_t ns, int* __r
 
 // cell-rows of the fine grid covered by the update ball of each selected
 // point: the box is computed once per point (query_box) and kept in sbox
-__global__ void ord_items_k(Grid g, const int32_t* __restrict__ sel, int64_t ns, const double* __restrict__ xg,
-                            int d, const double* __restrict__ v2, int64_t* __restrict__ cnt, int4* __restrict__ sbox) {
+__global__ void ord_items_k(Grid g, const int32_t* __restrict__ sel, int64_t ns, const double* __restrict__ gxg,
+                            int gs, const double* __restrict__ v2, int64_t* __restrict__ cnt, int4* __restrict__ sbox) {
     int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= ns) return;
     const int p = sel[k];
-    const int4 b = query_box(g, xg + (int64_t)p * d, sqrt(v2[p]));
+    const int4 b = query_box(g, gxg + (int64_t)p * gs, sqrt(v2[p]));
     sbox[k] = b;
     int lo[3], hi[3];
     box_range(g, b, lo, hi);
@@ -376,15 +385,19 @@ __global__ void ord_out_k(const uint64_t* __restrict__ skey, const int64_t* __re
 kc_status order_impl(const double* x, int64_t N, int d, int32_t* perm, double* l, double* x_ord, cudaStream_t s) {
     Arena A(s);
     KC_TRY(check_finite(x, N * d, A, s));
+    // grid coordinates: the points (d <= 3) or their principal-axes projections
+    const double* gx;
+    int gs;
+    KC_TRY(grid_coords(x, N, d, A, s, &gx, &gs));
     double lo[3], hi[3];
-    KC_TRY(bbox(x, N, d, lo, hi, A, s));
+    KC_TRY(bbox(gx, N, gs, lo, hi, A, s));
     // fine grid of all points, about two points per cell
-    Grid g0 = make_grid(d, lo, hi, N, 0.0, N / 2 > 1 ? N / 2 : 1);
+    Grid g0 = make_grid(gs, lo, hi, N, 0.0, N / 2 > 1 ? N / 2 : 1);
     int32_t* gsorted;
     int64_t* cstart;
     KC_TRY(A.get(&gsorted, N));
     KC_TRY(A.get(&cstart, g0.ncells + 1));
-    KC_TRY(grid_build(g0, x, d, nullptr, N, gsorted, cstart, A, s));
+    KC_TRY(grid_build(g0, gx, gs, nullptr, N, gsorted, cstart, A, s));
 
     double *xg, *v2;
     int32_t *idg, *blist, *bsorted, *sel, *item_sel;
@@ -415,6 +428,14 @@ kc_status order_impl(const double* x, int64_t N, int d, int32_t* perm, double* l
     const float delta = (float)(E * 1.1920928955078125e-07);  // 2^-23 E
     KC_TRY(A.get(&xgf, N * d));
     ::kc::note_launch(), ord_init_k<<<blocks_for(N, 256), 256, 0, s>>>(x, d, gsorted, N, xg, idg, v2, stat, org, xgf);
+    // grid coordinates in grid order
+    const double* gxg = xg;
+    if (gx != x) {
+        double* p;
+        KC_TRY(A.get(&p, (size_t)N * gs));
+        ::kc::note_launch(), gather_rows_k<<<blocks_for(N, 256), 256, 0, s>>>(gx, gs, gsorted, N, p);
+        gxg = p;
+    }
     KC_CUDA(cudaGetLastError());
     int64_t item_cap = 0;
     item_sel = nullptr;
@@ -462,12 +483,12 @@ kc_status order_impl(const double* x, int64_t N, int d, int32_t* perm, double* l
         const int64_t nb = (int64_t)hnb;
         // band cells a quarter of the largest search radius (bounded by the
         // cell budget), scanned nearest ring first
-        Grid gb = make_grid(d, lo, hi, nb, vmax > 0 ? 0.25 * sqrt(vmax) : 0.0, 2 * nb + 1);
+        Grid gb = make_grid(gs, lo, hi, nb, vmax > 0 ? 0.25 * sqrt(vmax) : 0.0, 2 * nb + 1);
         {
             Arena B(s);
             int64_t* bst;
             KC_TRY(B.get(&bst, gb.ncells + 1));
-            KC_TRY(grid_build(gb, xg, d, blist, nb, bsorted, bst, B, s));
+            KC_TRY(grid_build(gb, gxg, gs, blist, nb, bsorted, bst, B, s));
             KC_CUDA(cudaMemcpyAsync(bstart, bst, sizeof(int64_t) * (gb.ncells + 1), cudaMemcpyDeviceToDevice, s));
         }
         const int band_r0 = rounds;
@@ -479,7 +500,7 @@ kc_status order_impl(const double* x, int64_t N, int d, int32_t* perm, double* l
             ::kc::note_launch(), ord_cellmax_k<<<blocks_for(gb.ncells, 256), 256, 0, s>>>(bsorted, bstart, gb.ncells, v2,
                                                                                          stat, cmax);
             ::kc::note_launch(), ord_dominance_k<<<blocks_for(nb, 128), 128, 0, s>>>(gb, bsorted, bstart, nb, xg, d, idg, v2, stat, T, sel,
-                                                                ctr + 3, ctr + 4, xgf, delta, cmax);
+                                                                ctr + 3, ctr + 4, xgf, delta, cmax, gxg, gs);
             unsigned long long hs[2];
             KC_CUDA(cudaMemcpyAsync(hs, ctr + 3, sizeof(hs), cudaMemcpyDeviceToHost, s));
             KC_CUDA(cudaStreamSynchronize(s));
@@ -496,7 +517,7 @@ kc_status order_impl(const double* x, int64_t N, int d, int32_t* perm, double* l
             band_sel += (int64_t)hs[0];
             if (ns == 0) return fail(KC_ECUDA, "ordering: no dominant point in a nonempty band");
             ::kc::note_launch(), ord_mark_k<<<blocks_for(ns, 256), 256, 0, s>>>(sel, ns, stat);
-            ::kc::note_launch(), ord_items_k<<<blocks_for(ns, 256), 256, 0, s>>>(g0, sel, ns, xg, d, v2, icnt, sbox);
+            ::kc::note_launch(), ord_items_k<<<blocks_for(ns, 256), 256, 0, s>>>(g0, sel, ns, gxg, gs, v2, icnt, sbox);
             Arena R(s);  // per-round scratch of the scan
             KC_TRY(exclusive_scan_i64(icnt, ioff, ns, R, s));
             int64_t nitems = 0;

@@ -53,11 +53,11 @@ __device__ __forceinline__ bool in_s(double d2, double R) {
     return __dsqrt_rn(d2) <= R;
 }
 
-__global__ void pat_items_k(Grid g, const double* __restrict__ xo, const double* __restrict__ l, int64_t N, int d,
+__global__ void pat_items_k(Grid g, const double* __restrict__ gxo, int gst, const double* __restrict__ l, int64_t N,
                             double rho, int64_t* __restrict__ cnt, int4* __restrict__ colbox) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
-    const int4 b = query_box(g, xo + i * d, col_radius(rho, l[i]));
+    const int4 b = query_box(g, gxo + i * gst, col_radius(rho, l[i]));
     colbox[i] = b;
     int lo[3], hi[3];
     box_range(g, b, lo, hi);
@@ -141,9 +141,13 @@ struct PatSetup {
 static kc_status pat_setup(const double* xo, const double* l, int64_t N, int d, double rho, PatSetup& S, Arena& A,
                            cudaStream_t s) {
     KC_TRY(check_finite(xo, N * d, A, s));
+    // grid coordinates: the points (d <= 3) or their principal-axes projections
+    const double* gxo;
+    int gst;
+    KC_TRY(grid_coords(xo, N, d, A, s, &gxo, &gst));
     double lo[3], hi[3];
-    KC_TRY(bbox(xo, N, d, lo, hi, A, s));
-    S.g = make_grid(d, lo, hi, N, 0.0, N / 2 > 1 ? N / 2 : 1);
+    KC_TRY(bbox(gxo, N, gst, lo, hi, A, s));
+    S.g = make_grid(gst, lo, hi, N, 0.0, N / 2 > 1 ? N / 2 : 1);
     Origin org;
     double E = 0.0;
     KC_TRY(bbox_all(xo, N, d, &org, &E, A, s));
@@ -152,14 +156,14 @@ static kc_status pat_setup(const double* xo, const double* l, int64_t N, int d, 
     KC_TRY(A.get(&S.xof, N * d));
     KC_TRY(A.get(&S.gs, N));
     KC_TRY(A.get(&S.cstart, S.g.ncells + 1));
-    KC_TRY(grid_build(S.g, xo, d, nullptr, N, S.gs, S.cstart, A, s));
+    KC_TRY(grid_build(S.g, gxo, gst, nullptr, N, S.gs, S.cstart, A, s));
     KC_TRY(A.get(&S.xs, N * d));
     ::kc::note_launch(), pat_gather_k<<<blocks_for(N, 256), 256, 0, s>>>(xo, S.gs, N, d, org, S.xs, S.xsf, S.xof);
     int64_t* cnt;
     KC_TRY(A.get(&cnt, N));
     KC_TRY(A.get(&S.off, N + 1));
     KC_TRY(A.get(&S.colbox, N));
-    ::kc::note_launch(), pat_items_k<<<blocks_for(N, 256), 256, 0, s>>>(S.g, xo, l, N, d, rho, cnt, S.colbox);
+    ::kc::note_launch(), pat_items_k<<<blocks_for(N, 256), 256, 0, s>>>(S.g, gxo, gst, l, N, rho, cnt, S.colbox);
     KC_CUDA(cudaGetLastError());
     KC_TRY(exclusive_scan_i64(cnt, S.off, N, A, s));
     KC_CUDA(cudaMemcpyAsync(&S.nitems, S.off + N, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
