@@ -13,8 +13,11 @@ Owhadi, arXiv:1706.02205):
 * ``sortsparse``         -- ordering and pattern by the paper's heap algorithm
                             (Algorithm 3, Section 4.1).
 * ``pattern``            -- S_rho by definition (Section 2.3), O(N^2).
-* ``matern`` / ``theta`` -- Matern covariance, closed forms for nu in
-                            {1/2, 3/2, 5/2} (Eq. (Matern), Section 4.4).
+* ``matern`` / ``cauchy`` / ``theta`` -- covariance functions of Section 4.4:
+                            Matern (Eq. (Matern)), closed forms for nu in
+                            {1/2, 3/2, 5/2}, other nu > 0 through ``bessel_k``
+                            (the integral representation of K_nu, Abramowitz &
+                            Stegun 9.6.24); the Cauchy class of Gneiting.
 * ``ichol``              -- ICHOL(0), Algorithm 2, left-looking form; the
                             zero-column rule for nonpositive pivots (Section 4.4).
 * ``solve_lower`` / ``solve_upper`` / ``pcg`` -- task (2) of Section 1, and CG
@@ -22,6 +25,8 @@ Owhadi, arXiv:1706.02205):
 * ``frob_error``         -- the sampled error estimator E (Section 4.4).
 * ``pca_truncate`` / ``pca_error_power`` -- rank-k PCA from the first k
                             columns (Section 2.5).
+* ``l_matvec`` / ``lt_matvec`` / ``logdet`` -- tasks (1), (3), (4) of Section 1
+                            with the factor: L z, L^T v, 2 sum log L_ii.
 * ``work_counters``      -- exact multiply-add / merge-step / operand counts of
                             the left-looking factor (roofline denominators).
 
@@ -81,28 +86,39 @@ def lib():
         L.ko_sortsparse_free.argtypes = [C.POINTER(_SortSparseResult)]
         L.ko_pattern_count.argtypes = [f64p, f64p, i, I, d, I, i64p]
         L.ko_pattern_fill.argtypes = [f64p, f64p, i, I, d, I, i64p, i32p]
+        K = C.POINTER(KoKernel)
+        L.ko_bessel_k.restype = d
+        L.ko_bessel_k.argtypes = [d, d]
         L.ko_matern.restype = d
         L.ko_matern.argtypes = [d, d, d, d]
+        L.ko_cauchy.restype = d
+        L.ko_cauchy.argtypes = [d, d, d, d, d]
+        L.ko_cov.restype = d
+        L.ko_cov.argtypes = [d, K]
         L.ko_theta.restype = d
-        L.ko_theta.argtypes = [f64p, I, i, i, d, d, d, d]
+        L.ko_theta.argtypes = [f64p, I, i, i, K]
         L.ko_csr_to_csc.argtypes = [i, i64p, i32p, i64p, i32p, i64p]
         L.ko_ichol.restype = i
-        L.ko_ichol.argtypes = [f64p, i, I, d, d, d, d, i64p, i32p, f64p, u8p, I, C.c_void_p]
+        L.ko_ichol.argtypes = [f64p, i, I, K, i64p, i32p, f64p, u8p, I, C.c_void_p]
         L.ko_solve_lower.argtypes = [i, i64p, i32p, f64p, f64p, f64p, f64p]
         L.ko_solve_upper.argtypes = [i, i64p, i32p, f64p, f64p, f64p, f64p]
-        L.ko_theta_s_matvec.argtypes = [f64p, i, I, d, d, d, d, i64p, i32p, f64p, f64p]
-        L.ko_theta_dense_matvec.argtypes = [f64p, i, I, d, d, d, d, f64p, f64p]
+        L.ko_l_matvec.argtypes = [i, i64p, i32p, f64p, f64p, f64p]
+        L.ko_lt_matvec.argtypes = [i, i64p, i32p, f64p, f64p, f64p]
+        L.ko_logdet.restype = d
+        L.ko_logdet.argtypes = [i, i64p, f64p, C.POINTER(C.c_int64)]
+        L.ko_theta_s_matvec.argtypes = [f64p, i, I, K, i64p, i32p, f64p, f64p]
+        L.ko_theta_dense_matvec.argtypes = [f64p, i, I, K, f64p, f64p]
         L.ko_pcg.restype = I
-        L.ko_pcg.argtypes = [f64p, i, I, d, d, d, d, i64p, i32p, f64p, f64p, I, f64p, d, I, f64p,
+        L.ko_pcg.argtypes = [f64p, i, I, K, i64p, i32p, f64p, f64p, I, f64p, d, I, f64p,
                              C.POINTER(C.c_double), C.POINTER(C.c_int32)]
         L.ko_llt_entry.restype = d
         L.ko_llt_entry.argtypes = [i64p, i32p, f64p, i, i]
-        L.ko_frob_error.argtypes = [f64p, i, I, d, d, d, d, i64p, i32p, f64p, i64p, i, i64p, i64p,
+        L.ko_frob_error.argtypes = [f64p, i, I, K, i64p, i32p, f64p, i64p, i, i64p, i64p,
                                     C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double),
                                     C.POINTER(C.c_int64)]
         L.ko_pca_truncate.argtypes = [i, i64p, i32p, f64p, i32p, I, f64p]
         L.ko_pca_error_power.restype = d
-        L.ko_pca_error_power.argtypes = [f64p, i, I, d, d, d, d, I, f64p, f64p, I]
+        L.ko_pca_error_power.argtypes = [f64p, i, I, K, I, f64p, f64p, I]
         L.ko_work_counters.argtypes = [i, i64p, i32p] + [C.POINTER(C.c_int64)] * 4
         _lib = L
     return _lib
@@ -115,17 +131,35 @@ def _pts(x):
     return x, x.shape[0], x.shape[1]
 
 
-class Kernel:
-    """Matern covariance parameters: smoothness nu in {0.5, 1.5, 2.5}, length
-    scale ell, variance sigma2, and a nugget added on the diagonal."""
+MATERN = 0
+CAUCHY = 1
 
-    def __init__(self, nu=1.5, ell=0.2, sigma2=1.0, nugget=0.0):
-        if nu not in (0.5, 1.5, 2.5):
-            raise ValueError("nu must be 0.5, 1.5 or 2.5")
+
+class KoKernel(C.Structure):
+    _fields_ = [("family", C.c_int32), ("nu", C.c_double), ("ell", C.c_double), ("sigma2", C.c_double),
+                ("nugget", C.c_double), ("alpha", C.c_double), ("beta", C.c_double)]
+
+
+class Kernel:
+    """Covariance parameters (Section 4.4): the Matern class (smoothness
+    nu > 0, length scale ell, variance sigma2) or, with family=CAUCHY, the
+    Cauchy class (ell, alpha in (0, 2], beta > 0, sigma2); a nugget is added
+    on the diagonal."""
+
+    def __init__(self, nu=1.5, ell=0.2, sigma2=1.0, nugget=0.0, family=MATERN, alpha=1.0, beta=1.0):
+        if family == MATERN and not nu > 0:
+            raise ValueError("nu must be positive")
+        if family == CAUCHY and not (0 < alpha <= 2 and beta > 0):
+            raise ValueError("the Cauchy class needs 0 < alpha <= 2 and beta > 0")
+        self.family = int(family)
         self.nu, self.ell, self.sigma2, self.nugget = float(nu), float(ell), float(sigma2), float(nugget)
+        self.alpha, self.beta = float(alpha), float(beta)
+
+    def c(self):
+        return KoKernel(self.family, self.nu, self.ell, self.sigma2, self.nugget, self.alpha, self.beta)
 
     def args(self):
-        return (self.nu, self.ell, self.sigma2, self.nugget)
+        return (C.byref(self.c()),)
 
 
 # --------------------------------------------------------------------------
@@ -184,8 +218,23 @@ def csr_to_csc(rowptr, col):
 # kernel entries
 # --------------------------------------------------------------------------
 
+def bessel_k(nu, x):
+    """K_nu(x), x > 0, from the integral representation (A&S 9.6.24)."""
+    return lib().ko_bessel_k(float(nu), float(x))
+
+
 def matern(r, nu, ell, sigma2=1.0):
     return lib().ko_matern(float(r), float(nu), float(ell), float(sigma2))
+
+
+def cauchy(r, ell, alpha, beta, sigma2=1.0):
+    return lib().ko_cauchy(float(r), float(ell), float(alpha), float(beta), float(sigma2))
+
+
+def cov(r, kern: Kernel):
+    """The covariance function of kern at distance r (no nugget)."""
+    k = kern.c()
+    return lib().ko_cov(float(r), C.byref(k))
 
 
 def theta(x_ord, a, b, kern: Kernel):
@@ -240,6 +289,30 @@ def solve_upper(rowptr, col, val, diag, y):
     lib().ko_solve_upper(N, rowptr, col, val, np.ascontiguousarray(diag, np.float64),
                          np.ascontiguousarray(y, np.float64), x)
     return x
+
+
+def l_matvec(rowptr, col, val, z):
+    """y = L z in ordered positions (task (4): a sample of N(0, L L^T) when z ~ N(0, I))."""
+    N = rowptr.shape[0] - 1
+    y = np.zeros(N)
+    lib().ko_l_matvec(N, rowptr, col, np.ascontiguousarray(val, np.float64), np.ascontiguousarray(z, np.float64), y)
+    return y
+
+
+def lt_matvec(rowptr, col, val, v):
+    """w = L^T v in ordered positions."""
+    N = rowptr.shape[0] - 1
+    w = np.zeros(N)
+    lib().ko_lt_matvec(N, rowptr, col, np.ascontiguousarray(val, np.float64), np.ascontiguousarray(v, np.float64), w)
+    return w
+
+
+def logdet(rowptr, val):
+    """(2 sum log L_ii over kept columns, number of dropped columns): task (3)."""
+    N = rowptr.shape[0] - 1
+    z = C.c_int64(0)
+    v = lib().ko_logdet(N, rowptr, np.ascontiguousarray(val, np.float64), C.byref(z))
+    return v, int(z.value)
 
 
 def theta_s_matvec(x_ord, rowptr, col, kern: Kernel, v):

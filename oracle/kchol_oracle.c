@@ -302,12 +302,40 @@ void ko_pattern_fill(const double* xo, const double* l, i64 N, i32 d, double rho
 }
 
 /* ------------------------------------------------------------------------ */
-/* Matern covariance, Eq. (Matern) of Section 4.4, closed forms for          */
-/* nu = 1/2, 3/2, 5/2 (K_{nu} of half-integer order is elementary):          */
-/*   t = sqrt(2 nu) r / ell                                                  */
-/*   nu=1/2: sigma2 e^{-t};  3/2: sigma2 (1+t) e^{-t};                        */
-/*   5/2: sigma2 (1 + t + t^2/3) e^{-t}.  Nugget added on the diagonal only.  */
+/* Covariance functions of Section 4.4.                                      */
+/*                                                                          */
+/* Matern, Eq. (Matern):                                                    */
+/*   G(r) = sigma2 2^{1-nu} / Gamma(nu) t^nu K_nu(t),  t = sqrt(2 nu) r / ell */
+/* with closed forms for nu = 1/2, 3/2, 5/2 (K of half-integer order is     */
+/* elementary):  1/2: sigma2 e^{-t};  3/2: sigma2 (1+t) e^{-t};             */
+/*   5/2: sigma2 (1 + t + t^2/3) e^{-t}.                                    */
+/* Other nu > 0 use K_nu from its integral representation                   */
+/*   K_nu(x) = int_0^inf exp(-x cosh s) cosh(nu s) ds     (x > 0)           */
+/* (Abramowitz & Stegun 9.6.24), by the trapezoidal rule: the integrand is  */
+/* entire and decays double-exponentially, so a fixed small step converges  */
+/* to working precision.  G(0) = sigma2.                                    */
+/*                                                                          */
+/* Cauchy class (Gneiting), Section 4.4:                                    */
+/*   G(r) = sigma2 (1 + (r/ell)^alpha)^{-beta/alpha}.                        */
+/*                                                                          */
+/* The nugget is added on the diagonal only.                                */
 /* ------------------------------------------------------------------------ */
+
+double ko_bessel_k(double nu, double x) {
+    if (!(x > 0.0)) return INFINITY;
+    const double h = 1.0 / 64.0;
+    double sum = 0.5 * exp(-x); /* s = 0: cosh(0) = 1 */
+    double prev = sum;
+    for (i64 k = 1;; ++k) {
+        double s = h * (double)k;
+        double f = exp(-x * cosh(s)) * cosh(nu * s);
+        sum += f;
+        if (f < prev && f <= 1e-18 * sum) break;
+        if (!(f > 0.0) && k > 1) break;
+        prev = f;
+    }
+    return h * sum;
+}
 
 double ko_matern(double r, double nu, double ell, double sigma2) {
     if (nu == 0.5) {
@@ -320,21 +348,35 @@ double ko_matern(double r, double nu, double ell, double sigma2) {
         double t = sqrt(5.0) * r / ell;
         return sigma2 * (1.0 + t + t * t / 3.0) * exp(-t);
     }
-    return NAN;
+    if (!(nu > 0.0)) return NAN;
+    double t = sqrt(2.0 * nu) * r / ell;
+    if (t == 0.0) return sigma2;
+    double k = ko_bessel_k(nu, t);
+    if (k == 0.0) return 0.0;
+    return sigma2 * exp((1.0 - nu) * log(2.0) - lgamma(nu) + nu * log(t)) * k;
 }
 
-typedef struct { double nu, ell, sigma2, nugget; } ko_kernel;
+double ko_cauchy(double r, double ell, double alpha, double beta, double sigma2) {
+    return sigma2 * pow(1.0 + pow(r / ell, alpha), -beta / alpha);
+}
+
+/* family 0: Matern (nu, ell, sigma2); 1: Cauchy (ell, alpha, beta, sigma2) */
+typedef struct { i32 family; double nu, ell, sigma2, nugget, alpha, beta; } ko_kernel;
+
+double ko_cov(double r, const ko_kernel* K) {
+    if (K->family == 1) return ko_cauchy(r, K->ell, K->alpha, K->beta, K->sigma2);
+    return ko_matern(r, K->nu, K->ell, K->sigma2);
+}
 
 static double theta_pos(const double* xo, i32 d, i64 a, i64 b, const ko_kernel* K) {
     double r = sqrt(d2_of(xo + a * d, xo + b * d, d));
-    double v = ko_matern(r, K->nu, K->ell, K->sigma2);
+    double v = ko_cov(r, K);
     if (a == b) v += K->nugget;
     return v;
 }
 
-double ko_theta(const double* xo, i32 d, i64 a, i64 b, double nu, double ell, double sigma2, double nugget) {
-    ko_kernel K = {nu, ell, sigma2, nugget};
-    return theta_pos(xo, d, a, b, &K);
+double ko_theta(const double* xo, i32 d, i64 a, i64 b, const ko_kernel* K) {
+    return theta_pos(xo, d, a, b, K);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -375,9 +417,8 @@ void ko_csr_to_csc(i64 N, const i64* rowptr, const i32* col, i64* colptr, i32* r
 /* pivot p before the test.  Returns the number of zeroed columns.          */
 /* ------------------------------------------------------------------------ */
 
-i64 ko_ichol(const double* xo, i64 N, i32 d, double nu, double ell, double sigma2, double nugget,
+i64 ko_ichol(const double* xo, i64 N, i32 d, const ko_kernel* K,
              const i64* rowptr, const i32* col, double* val, char* zero_col, i32 rev, double* piv) {
-    ko_kernel K = {nu, ell, sigma2, nugget};
     i64 nnz = rowptr[N];
     i64* colptr = (i64*)malloc(sizeof(i64) * ((size_t)N + 1));
     i32* rowidx = (i32*)malloc(sizeof(i32) * (size_t)(nnz > 0 ? nnz : 1));
@@ -387,7 +428,7 @@ i64 ko_ichol(const double* xo, i64 N, i32 d, double nu, double ell, double sigma
     i64 zeroed = 0;
     for (i64 i = 0; i < N; ++i) {
         i64 a0 = rowptr[i], a1 = rowptr[i + 1] - 1; /* row i without its diagonal: [a0, a1) */
-        double p = theta_pos(xo, d, i, i, &K);
+        double p = theta_pos(xo, d, i, i, K);
         if (!rev) for (i64 e = a0; e < a1; ++e) p -= val[e] * val[e];
         else for (i64 e = a1 - 1; e >= a0; --e) p -= val[e] * val[e];
         if (piv) piv[i] = p;
@@ -403,7 +444,7 @@ i64 ko_ichol(const double* xo, i64 N, i32 d, double nu, double ell, double sigma
             i64 b0 = rowptr[j];
             i64 bij = slot[q];                 /* position of (j,i) in row j */
             /* merge row j (k < i) with row i (k < i) */
-            double s = theta_pos(xo, d, j, i, &K);
+            double s = theta_pos(xo, d, j, i, K);
             if (!rev) {
                 i64 u = a0, v = b0;
                 while (u < a1 && v < bij) {
@@ -452,32 +493,67 @@ void ko_solve_upper(i64 N, const i64* rowptr, const i32* col, const double* val,
 }
 
 /* ------------------------------------------------------------------------ */
+/* Tasks (1), (3), (4) of Section 1 with the factor standing in for Theta:  */
+/*   (1) Theta v ~ L (L^T v);  (3) logdet Theta ~ 2 sum_i log L_ii;          */
+/*   (4) a sample of N(0, L L^T) is L z for z ~ N(0, I).                     */
+/* All in ordered positions; L is the CSR factor with its diagonal last in   */
+/* each row (zero for a dropped column).                                     */
+/* ------------------------------------------------------------------------ */
+
+/* y = L z */
+void ko_l_matvec(i64 N, const i64* rowptr, const i32* col, const double* val, const double* z, double* y) {
+    for (i64 j = 0; j < N; ++j) {
+        double s = 0.0;
+        for (i64 e = rowptr[j]; e < rowptr[j + 1]; ++e) s += val[e] * z[col[e]];
+        y[j] = s;
+    }
+}
+
+/* w = L^T v: entry (j, k) of L adds L_jk v_j to w_k */
+void ko_lt_matvec(i64 N, const i64* rowptr, const i32* col, const double* val, const double* v, double* w) {
+    for (i64 k = 0; k < N; ++k) w[k] = 0.0;
+    for (i64 j = 0; j < N; ++j)
+        for (i64 e = rowptr[j]; e < rowptr[j + 1]; ++e) w[col[e]] += val[e] * v[j];
+}
+
+/* 2 sum log L_ii over the kept columns; *zeroed = number of dropped ones
+   (then L L^T is singular and its log-determinant is -infinity) */
+double ko_logdet(i64 N, const i64* rowptr, const double* val, i64* zeroed) {
+    double s = 0.0;
+    i64 z = 0;
+    for (i64 i = 0; i < N; ++i) {
+        double Lii = val[rowptr[i + 1] - 1];
+        if (Lii > 0.0) s += log(Lii);
+        else z++;
+    }
+    *zeroed = z;
+    return 2.0 * s;
+}
+
+/* ------------------------------------------------------------------------ */
 /* y = Theta^S v: the kernel matrix restricted to the symmetric pattern S,   */
 /* entries from the coordinates (the sparse matrix the factorisation sees).  */
 /* ------------------------------------------------------------------------ */
 
-void ko_theta_s_matvec(const double* xo, i64 N, i32 d, double nu, double ell, double sigma2, double nugget,
+void ko_theta_s_matvec(const double* xo, i64 N, i32 d, const ko_kernel* K,
                        const i64* rowptr, const i32* col, const double* v, double* y) {
-    ko_kernel K = {nu, ell, sigma2, nugget};
     for (i64 j = 0; j < N; ++j) y[j] = 0.0;
     for (i64 j = 0; j < N; ++j) {
         for (i64 e = rowptr[j]; e < rowptr[j + 1] - 1; ++e) {
             i64 k = col[e];
-            double t = theta_pos(xo, d, j, k, &K);
+            double t = theta_pos(xo, d, j, k, K);
             y[j] += t * v[k];
             y[k] += t * v[j];
         }
-        y[j] += theta_pos(xo, d, j, j, &K) * v[j];
+        y[j] += theta_pos(xo, d, j, j, K) * v[j];
     }
 }
 
 /* y = Theta v with the dense kernel matrix (O(N^2)). */
-void ko_theta_dense_matvec(const double* xo, i64 N, i32 d, double nu, double ell, double sigma2, double nugget,
-                           const double* v, double* y) {
-    ko_kernel K = {nu, ell, sigma2, nugget};
+void ko_theta_dense_matvec(const double* xo, i64 N, i32 d, const ko_kernel* K, const double* v, double* y) {
     for (i64 j = 0; j < N; ++j) {
         double s = 0.0;
-        for (i64 k = 0; k < N; ++k) s += theta_pos(xo, d, j, k, &K) * v[k];
+        for (i64 k = 0; k < N; ++k) s += theta_pos(xo, d, j, k, K) * v[k];
         y[j] = s;
     }
 }
@@ -495,7 +571,7 @@ static double dotv(i64 n, const double* a, const double* b) {
     return s;
 }
 
-i32 ko_pcg(const double* xo, i64 N, i32 d, double nu, double ell, double sigma2, double nugget,
+i32 ko_pcg(const double* xo, i64 N, i32 d, const ko_kernel* K,
            const i64* rowptr, const i32* col, const double* val, const double* diag, i32 op,
            const double* b, double rtol, i32 maxit, double* x, double* relres, i32* status) {
     double* r = (double*)malloc(sizeof(double) * (size_t)N);
@@ -515,8 +591,8 @@ i32 ko_pcg(const double* xo, i64 N, i32 d, double nu, double ell, double sigma2,
     double rz = dotv(N, r, z);
     for (it = 0; it < maxit; ++it) {
         if (rn / bn <= rtol) { *status = 0; break; }
-        if (op == 2) ko_theta_dense_matvec(xo, N, d, nu, ell, sigma2, nugget, p, q);
-        else ko_theta_s_matvec(xo, N, d, nu, ell, sigma2, nugget, rowptr, col, p, q);
+        if (op == 2) ko_theta_dense_matvec(xo, N, d, K, p, q);
+        else ko_theta_s_matvec(xo, N, d, K, rowptr, col, p, q);
         double pq = dotv(N, p, q);
         if (!(pq > 0.0)) { *status = 2; break; }
         double alpha = rz / pq;
@@ -531,8 +607,8 @@ i32 ko_pcg(const double* xo, i64 N, i32 d, double nu, double ell, double sigma2,
     }
     if (it == maxit && rn / bn <= rtol) *status = 0;
     /* true residual */
-    if (op == 2) ko_theta_dense_matvec(xo, N, d, nu, ell, sigma2, nugget, x, q);
-    else ko_theta_s_matvec(xo, N, d, nu, ell, sigma2, nugget, rowptr, col, x, q);
+    if (op == 2) ko_theta_dense_matvec(xo, N, d, K, x, q);
+    else ko_theta_s_matvec(xo, N, d, K, rowptr, col, x, q);
     for (i64 i = 0; i < N; ++i) q[i] = b[i] - q[i];
     *relres = sqrt(dotv(N, q, q)) / bn;
 done:
@@ -562,17 +638,16 @@ double ko_llt_entry(const i64* rowptr, const i32* col, const double* val, i64 a,
     return llt_entry(rowptr, col, val, a, b);
 }
 
-void ko_frob_error(const double* xo, i64 N, i32 d, double nu, double ell, double sigma2, double nugget,
+void ko_frob_error(const double* xo, i64 N, i32 d, const ko_kernel* K,
                    const i64* rowptr, const i32* col, const double* val, const i64* pos,
                    i64 m, const i64* pi, const i64* pj, const char* keep,
                    double* num2, double* den2, i64* kept) {
-    ko_kernel K = {nu, ell, sigma2, nugget};
     double a = 0.0, b = 0.0; i64 c = 0;
     (void)N;
     for (i64 t = 0; t < m; ++t) {
         if (keep && !keep[t]) continue;
         i64 i = pos[pi[t]], j = pos[pj[t]];
-        double th = theta_pos(xo, d, i, j, &K);
+        double th = theta_pos(xo, d, i, j, K);
         double e = llt_entry(rowptr, col, val, i, j) - th;
         a += e * e; b += th * th; c++;
     }
@@ -594,7 +669,7 @@ void ko_pca_truncate(i64 N, const i64* rowptr, const i32* col, const double* val
 
 /* Power iteration for ||Theta - Lk Lk^T||_2 on ORIGINAL order coordinates x.
    v0: unit start vector.  Returns |v^T B v| after iters steps. */
-double ko_pca_error_power(const double* x, i64 N, i32 d, double nu, double ell, double sigma2, double nugget,
+double ko_pca_error_power(const double* x, i64 N, i32 d, const ko_kernel* K,
                           i32 k, const double* Lk, const double* v0, i32 iters) {
     double* v = (double*)malloc(sizeof(double) * (size_t)N);
     double* w = (double*)malloc(sizeof(double) * (size_t)N);
@@ -602,7 +677,7 @@ double ko_pca_error_power(const double* x, i64 N, i32 d, double nu, double ell, 
     for (i64 i = 0; i < N; ++i) v[i] = v0[i];
     double est = 0.0;
     for (i32 it = 0; it < iters; ++it) {
-        ko_theta_dense_matvec(x, N, d, nu, ell, sigma2, nugget, v, w);
+        ko_theta_dense_matvec(x, N, d, K, v, w);
         for (i32 a = 0; a < k; ++a) { double s = 0.0; for (i64 i = 0; i < N; ++i) s += Lk[i + N * a] * v[i]; c[a] = s; }
         for (i32 a = 0; a < k; ++a) for (i64 i = 0; i < N; ++i) w[i] -= Lk[i + N * a] * c[a];
         est = fabs(dotv(N, v, w));
