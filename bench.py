@@ -312,6 +312,80 @@ def factor_traffic(bop):
     return TRAFFIC_CAPTURE["dram_per_algorithmic_byte"] * bop
 
 
+def make_kernel(args):
+    """The covariance function the options name (--family, --nu, --ell, --alpha, --beta)."""
+    from paper_1706_02205_gb300 import kchol as kc
+    if args.family == "cauchy":
+        return kc.Kernel(ell=args.ell, family=kc.CAUCHY, alpha=args.alpha, beta=args.beta)
+    return kc.Kernel(args.nu, args.ell)
+
+
+def kernel_name(k):
+    if k.family == 1:
+        return f"Cauchy l={k.ell} alpha={k.alpha} beta={k.beta}"
+    return f"Matern-{k.nu} l={k.ell}" + (f" nugget {k.nugget}" if k.nugget else "")
+
+
+def run_tasks(args):
+    """Tasks (1), (3), (4) with the factor on the 1024 x 1024 jittered grid
+    (rho = 3, FP32 form): L L^T v for 16 and 1 vectors, one sample L z, and
+    log det.  Each call includes its permutations to and from the original
+    order; times are CUDA events around the call after warm-up."""
+    import torch
+
+    from paper_1706_02205_gb300 import kchol as kc
+    x = torch.from_numpy(inputs.jittered_grid(args.n_side, seed=inputs.seed_for(2))).cuda()
+    kern = make_kernel(args)
+    perm, l, xo = kc.order_points(x)
+    pat = kc.build_pattern(xo, l, args.rho)
+    val, diag, zp = kc.factor(pat, xo, kern, kc.FP32_FORM)
+    N, nnz, s = pat.N, pat.nnz, 4
+    v16 = torch.from_numpy(inputs.rhs(N, 16, seed=inputs.seed_for(2, 70))).cuda()
+    v1 = v16[:1].contiguous()
+    stream = torch.cuda.current_stream()
+
+    def timed(fn):
+        for _ in range(args.warmup):
+            fn()
+        ms = []
+        for _ in range(args.steps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        return statistics.median(ms)
+
+    # algorithmic bytes: L pass = rowptr, col and val once, diag, the vectors in
+    # and out once; L^T pass = colptr, rowidx, slot and val once, diag, the
+    # vectors; the permutations read and write each vector once more
+    def bytes_l(ns):
+        return (N + 1) * 8 + nnz * (4 + s) + N * 8 + 2 * N * ns * 8
+
+    def bytes_lt(ns):
+        return (N + 1) * 8 + nnz * (4 + 8 + s) + N * 8 + 2 * N * ns * 8
+
+    def bytes_perm(nrhs, ns):
+        return 2 * (N * nrhs * 8 + N * ns * 8 + N * 4)
+
+    out = {"workload": f"tasks on jittered grid {args.n_side}x{args.n_side} (N={N}), {kernel_name(kern)}, "
+                       f"rho={args.rho}, FP32 form", "N": N, "nnz": nnz, "zero_pivots": zp, "calls": {}}
+    for name, fn, b in (
+            ("llt_matvec_16", lambda: kc.llt_matvec(pat, kc.FP32_FORM, val, diag, perm, v16),
+             bytes_l(16) + bytes_lt(16) + bytes_perm(16, 16)),
+            ("llt_matvec_1", lambda: kc.llt_matvec(pat, kc.FP32_FORM, val, diag, perm, v1),
+             bytes_l(1) + bytes_lt(1) + bytes_perm(1, 1)),
+            ("sample_l_matvec_1", lambda: kc.l_matvec(pat, kc.FP32_FORM, val, diag, perm, v1),
+             bytes_l(1) + bytes_perm(1, 1)),
+            ("lt_matvec_1", lambda: kc.lt_matvec(pat, kc.FP32_FORM, val, diag, perm, v1),
+             bytes_lt(1) + bytes_perm(1, 1)),
+            ("logdet", lambda: kc.logdet(pat, diag), N * 8)):
+        ms = timed(fn)
+        out["calls"][name] = {"ms": ms, "algorithmic_bytes": b, "GB_per_s": b / (ms * 1e-3) / 1e9}
+    return out
+
+
 def run_factor_only(args):
     """Factor-only probe (the launch profiled by ncu): order + pattern once,
     then the FP32-form factor `--steps` times on the same pattern."""
@@ -323,11 +397,11 @@ def run_factor_only(args):
         kern, rho = kc.Kernel(2.5, 0.3, 1.0, 1e-6), 4.0
     else:
         x = torch.from_numpy(inputs.jittered_grid(args.n_side, seed=inputs.seed_for(2))).cuda()
-        kern, rho = kc.Kernel(args.nu, args.ell), args.rho
+        kern, rho = make_kernel(args), args.rho
     perm, l, xo = kc.order_points(x)
     pat = kc.build_pattern(xo, l, rho)
     prec = kc.FP64 if args.prec == "fp64" else kc.FP32_FORM
-    out = {"workload": f"factor-only {args.geom}", "N": pat.N, "nnz": pat.nnz, "depth": pat.depth, "prec": args.prec,
+    out = {"workload": f"factor-only {args.geom}", "kernel": kernel_name(kern), "N": pat.N, "nnz": pat.nnz, "depth": pat.depth, "prec": args.prec,
            "algorithmic_bytes": bytes_op(pat.rowptr.cpu().numpy(), pat.N, x.shape[1], 8 if args.prec == "fp64" else 4),
            "runs": []}
     for rpt, lanes, unroll, adapt, stage, warps in itertools.product(args.rpt, args.lanes, args.unroll, args.adaptive,
@@ -547,7 +621,12 @@ def main():
     ap.add_argument("--cpu-side", type=int, default=320)
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--traffic", type=float, default=None, help="ncu DRAM bytes per factor launch, if measured")
-    ap.add_argument("--workload", default="grid2d", choices=["grid2d", "cube3d", "factor", "batch", "serve", "refine"],
+    ap.add_argument("--family", default="matern", choices=["matern", "cauchy"],
+                    help="covariance family of the factor-only and tasks workloads")
+    ap.add_argument("--alpha", type=float, default=1.0, help="Cauchy alpha")
+    ap.add_argument("--beta", type=float, default=0.2, help="Cauchy beta")
+    ap.add_argument("--workload", default="grid2d",
+                    choices=["grid2d", "cube3d", "factor", "batch", "serve", "refine", "tasks"],
                     help="grid2d: the headline step (default); cube3d: 3-D factor + PCA; factor: factor-only "
                          "probe; batch: many sets in one launch; serve: request stream")
     ap.add_argument("--n3", type=int, default=2**18)
@@ -584,6 +663,8 @@ def main():
         line = run_batch(args)
     elif args.workload == "serve":
         line = run_serve(args)
+    elif args.workload == "tasks":
+        line = run_tasks(args)
     elif args.workload == "refine":
         line = run_refine(args)
     else:

@@ -53,14 +53,26 @@ typedef enum {
     KC_EINDEF = 7      /* CG met nonpositive curvature */
 } kc_status;
 
-/* Matern covariance (Eq. (Matern), Section 4.4) with nu in {0.5, 1.5, 2.5}
- * (closed forms of K_nu for half-integer nu), length scale ell, variance
- * sigma2; nugget is added on the diagonal only (Section 4.3). */
+/* Covariance function (Section 4.4); nugget is added on the diagonal only
+ * (Section 4.3), and Theta_ii = sigma2 + nugget for every family.
+ * KC_MATERN (Eq. (Matern)): sigma2 2^{1-nu}/Gamma(nu) t^nu K_nu(t) with
+ *   t = sqrt(2 nu) r / ell, nu in (0, 50].  nu = 0.5, 1.5, 2.5 use the
+ *   closed forms (K of half-integer order is elementary); other nu evaluate
+ *   K_nu by Temme's series (t <= 2) or Steed's continued fraction (t > 2) and
+ *   the upward recurrence, in double (the FP32 form rounds that value).
+ * KC_CAUCHY (the Cauchy class of Gneiting, Section 4.4):
+ *   sigma2 (1 + (r/ell)^alpha)^{-beta/alpha}, 0 < alpha <= 2, beta > 0
+ *   (nu is ignored); the FP32 form evaluates it in float.
+ * A struct zero-initialised past nugget is a Matern kernel. */
+typedef enum { KC_MATERN = 0, KC_CAUCHY = 1 } kc_family;
 typedef struct {
     double nu;
     double ell;
     double sigma2;
     double nugget;
+    int32_t family;  /* kc_family */
+    double alpha;    /* KC_CAUCHY */
+    double beta;     /* KC_CAUCHY */
 } kc_kernel;
 
 typedef enum { KC_RULE_MAX = 0, KC_RULE_MIN = 1 } kc_rule;
@@ -111,8 +123,9 @@ typedef struct {
 const char* kc_last_error(void);
 /* Version of this interface (structs and signatures); a binding built for
  * another version must not call the library.  2: kc_schedule takes the points,
- * kc_opts has stage_bytes. */
-#define KC_ABI_VERSION 2
+ * kc_opts has stage_bytes.  3: kc_kernel has family, alpha, beta;
+ * kc_kernel_eval, kc_l_matvec, kc_lt_matvec, kc_llt_matvec, kc_logdet. */
+#define KC_ABI_VERSION 3
 int32_t kc_abi_version(void);
 
 /* Number of kernels this library has launched in the process so far
@@ -175,7 +188,7 @@ kc_status kc_factor(const kc_pattern* pat, const double* x_ord, int32_t d, const
  * sets are factored together by concatenating their patterns
  * block-diagonally (positions of set s shifted by its offset, coordinates
  * padded to a common d with zeros): col_set (device int32[N]) gives the set of
- * every column and kerns[set] (host, nsets entries) its Matern parameters;
+ * every column and kerns[set] (host, nsets entries) its covariance function;
  * with nsets == 1, col_set may be NULL.  x_ord must stay valid while the plan
  * is used.  kc_factor_plan_finish synchronises and reports a timeout or the
  * dropped pivots of the last launch.  kc_factor_plan_tune times every
@@ -260,6 +273,42 @@ kc_status kc_pca_truncate(const kc_pattern* pat, int32_t prec, const void* val, 
 kc_status kc_pca_error(const double* x, int64_t N, int32_t d, const kc_kernel* kern, int32_t k,
                        const float* Lk, const double* v0, int32_t iters, double* estimate_out,
                        void* stream);
+
+/* ---- the covariance function alone ------------------------------------- *
+ * out[i] = G(r[i]) for n distances (device double[n] each, n >= 0), without
+ * the nugget, evaluated exactly as the factor evaluates its entries:
+ * KC_FP64 in double; KC_FP32_FORM with r rounded to float first and the
+ * result widened.  Stream-ordered (no synchronisation). */
+kc_status kc_kernel_eval(const kc_kernel* kern, int32_t prec, const double* r, int64_t n, double* out,
+                         void* stream);
+
+/* ---- tasks (1), (3) and (4) of Section 1 with the factor ---------------- *
+ * L is a factor from kc_factor: val in prec (CSR layout of pat), diag its
+ * FP64 diagonal (0 for a dropped column, which stays zero).  perm (device
+ * int32[N]) is the ordering: position k holds original point perm[k].
+ * Vectors are device double[nrhs*N], column-major (vector r at offset r*N),
+ * in original point order; 1 <= nrhs <= 16; outputs must not alias inputs.
+ *   kc_l_matvec:   y = P L P^T z   (task (4): for z ~ N(0, I), y is a sample
+ *                                   of N(0, P L L^T P^T), L L^T ~ Theta)
+ *   kc_lt_matvec:  y = P L^T P^T v
+ *   kc_llt_matvec: y = P L L^T P^T v   (task (1): approximates Theta v)
+ * Products and sums in FP64.  L z gathers along the rows of L, L^T v along
+ * its columns (the CSC of pat): no atomics, every sum in a fixed order, so
+ * the result is the same bits on every run.  Stream-ordered. */
+kc_status kc_l_matvec(const kc_pattern* pat, int32_t prec, const void* val, const double* diag,
+                      const int32_t* perm, const double* z, int32_t nrhs, double* y, void* stream);
+kc_status kc_lt_matvec(const kc_pattern* pat, int32_t prec, const void* val, const double* diag,
+                       const int32_t* perm, const double* v, int32_t nrhs, double* y, void* stream);
+kc_status kc_llt_matvec(const kc_pattern* pat, int32_t prec, const void* val, const double* diag,
+                        const int32_t* perm, const double* v, int32_t nrhs, double* y, void* stream);
+
+/* Task (3): logdet_out (host) = log det(L L^T) = 2 sum_i log diag[i] over
+ * the kept pivots (diag: device double[N]); zero_pivots_out (host, may be
+ * NULL) = the dropped ones (then L L^T is singular and the sum covers the
+ * rest).  A fixed reduction order: the same bits on every run.
+ * Synchronises. */
+kc_status kc_logdet(const kc_pattern* pat, const double* diag, double* logdet_out, int64_t* zero_pivots_out,
+                    void* stream);
 
 #ifdef __cplusplus
 }

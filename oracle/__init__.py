@@ -99,7 +99,7 @@ def lib():
         L.ko_theta.argtypes = [f64p, I, i, i, K]
         L.ko_csr_to_csc.argtypes = [i, i64p, i32p, i64p, i32p, i64p]
         L.ko_ichol.restype = i
-        L.ko_ichol.argtypes = [f64p, i, I, K, i64p, i32p, f64p, u8p, I, C.c_void_p]
+        L.ko_ichol.argtypes = [f64p, i, I, K, i64p, i32p, f64p, u8p, I, C.c_void_p, I]
         L.ko_solve_lower.argtypes = [i, i64p, i32p, f64p, f64p, f64p, f64p]
         L.ko_solve_upper.argtypes = [i, i64p, i32p, f64p, f64p, f64p, f64p]
         L.ko_l_matvec.argtypes = [i, i64p, i32p, f64p, f64p, f64p]
@@ -246,18 +246,21 @@ def theta(x_ord, a, b, kern: Kernel):
 # factor, solves, refinement
 # --------------------------------------------------------------------------
 
-def ichol(x_ord, rowptr, col, kern: Kernel, reverse_sums=False, pivots=False):
+def ichol(x_ord, rowptr, col, kern: Kernel, reverse_sums=False, pivots=False, store_f32=False):
     """ICHOL(0) values on the CSR pattern; returns (val float64[nnz], zero_col bool[N])
     and, with pivots=True, also the pivot p of every column before its test.
     reverse_sums=True sums in descending k (same arithmetic, other rounding
-    order) to measure the problem's sensitivity to FP64 rounding order."""
+    order) to measure the problem's sensitivity to FP64 rounding order;
+    store_f32=True rounds each off-diagonal Theta_ji and L_ji to float when
+    it is computed (the roundings of a factor with float entries), to size
+    FP32-form tolerances."""
     x_ord, N, d = _pts(x_ord)
     val = np.zeros(int(rowptr[-1]), np.float64)
     zc = np.zeros(N, np.int8)
     piv = np.zeros(N, np.float64)
     lib().ko_ichol(x_ord, N, d, *kern.args(), np.ascontiguousarray(rowptr, np.int64),
                    np.ascontiguousarray(col, np.int32), val, zc, int(bool(reverse_sums)),
-                   piv.ctypes.data_as(C.c_void_p))
+                   piv.ctypes.data_as(C.c_void_p), int(bool(store_f32)))
     if pivots:
         return val, zc.astype(bool), piv
     return val, zc.astype(bool)

@@ -414,11 +414,16 @@ void ko_csr_to_csc(i64 N, const i64* rowptr, const i32* col, i64* colptr, i32* r
 /* Sums run in ascending k (rev=1: descending, the same arithmetic in the   */
 /* other order, used only to measure how much FP64 rounding order moves the */
 /* result).  val[] follows the CSR layout; piv (optional) receives every     */
-/* pivot p before the test.  Returns the number of zeroed columns.          */
+/* pivot p before the test.  store_f32=1 rounds every off-diagonal Theta_ji */
+/* and every off-diagonal entry of L to float as soon as it is computed      */
+/* (later columns then use the rounded values; pivots and L_ii stay double): */
+/* the roundings of a factor with float entries kept in float, used only to  */
+/* size test tolerances.  Returns the number of zeroed columns.              */
 /* ------------------------------------------------------------------------ */
 
 i64 ko_ichol(const double* xo, i64 N, i32 d, const ko_kernel* K,
-             const i64* rowptr, const i32* col, double* val, char* zero_col, i32 rev, double* piv) {
+             const i64* rowptr, const i32* col, double* val, char* zero_col, i32 rev, double* piv,
+             i32 store_f32) {
     i64 nnz = rowptr[N];
     i64* colptr = (i64*)malloc(sizeof(i64) * ((size_t)N + 1));
     i32* rowidx = (i32*)malloc(sizeof(i32) * (size_t)(nnz > 0 ? nnz : 1));
@@ -445,6 +450,7 @@ i64 ko_ichol(const double* xo, i64 N, i32 d, const ko_kernel* K,
             i64 bij = slot[q];                 /* position of (j,i) in row j */
             /* merge row j (k < i) with row i (k < i) */
             double s = theta_pos(xo, d, j, i, K);
+            if (store_f32) s = (double)(float)s;
             if (!rev) {
                 i64 u = a0, v = b0;
                 while (u < a1 && v < bij) {
@@ -462,7 +468,8 @@ i64 ko_ichol(const double* xo, i64 N, i32 d, const ko_kernel* K,
                     else --v;
                 }
             }
-            val[bij] = s / Lii;
+            double q = s / Lii;
+            val[bij] = store_f32 ? (double)(float)q : q;
         }
     }
     free(colptr); free(rowidx); free(slot);

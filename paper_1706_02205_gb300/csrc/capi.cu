@@ -38,6 +38,10 @@ kc_status pca_truncate_impl(const kc_pattern* P, int prec, const void* val, cons
                             cudaStream_t s);
 kc_status pca_error_impl(const double* x, int64_t N, int d, const kc_kernel* kern, int k, const float* Lk,
                          const double* v0, int iters, double* est_out, cudaStream_t s);
+kc_status factor_matvec_impl(const kc_pattern* P, int prec, const void* val, const double* diag, const int32_t* perm,
+                             const double* in, int nrhs, double* out, int which, cudaStream_t s);
+kc_status logdet_impl(const kc_pattern* P, const double* diag, double* logdet_out, int64_t* zero_out, cudaStream_t s);
+kc_status kernel_eval_impl(const kc_kernel* kern, int prec, const double* r, int64_t n, double* out, cudaStream_t s);
 }  // namespace kc
 
 using namespace kc;
@@ -200,6 +204,42 @@ kc_status kc_pca_error(const double* x, int64_t N, int32_t d, const kc_kernel* k
     KC_TRY(check_points(x, N, d));
     if (k < 0 || k > N || (k > 0 && !Lk) || !v0 || iters < 1) return fail(KC_EINVAL, "bad PCA error arguments");
     return pca_error_impl(x, N, d, kern, k, Lk, v0, iters, estimate_out, (cudaStream_t)stream);
+}
+
+kc_status kc_kernel_eval(const kc_kernel* kern, int32_t prec, const double* r, int64_t n, double* out,
+                         void* stream) {
+    if (n < 0 || (n > 0 && (!r || !out))) return fail(KC_EINVAL, "bad kernel evaluation arguments");
+    return kernel_eval_impl(kern, prec, r, n, out, (cudaStream_t)stream);
+}
+
+static kc_status matvec_entry(const kc_pattern* pat, int32_t prec, const void* val, const double* diag,
+                              const int32_t* perm, const double* in, int32_t nrhs, double* out, int which,
+                              void* stream) {
+    KC_TRY(check_pattern(pat));
+    if (!val || !diag || !perm || !in || !out) return fail(KC_EINVAL, "arrays must be non-NULL");
+    return factor_matvec_impl(pat, prec, val, diag, perm, in, nrhs, out, which, (cudaStream_t)stream);
+}
+
+kc_status kc_l_matvec(const kc_pattern* pat, int32_t prec, const void* val, const double* diag, const int32_t* perm,
+                      const double* z, int32_t nrhs, double* y, void* stream) {
+    return matvec_entry(pat, prec, val, diag, perm, z, nrhs, y, 0, stream);
+}
+
+kc_status kc_lt_matvec(const kc_pattern* pat, int32_t prec, const void* val, const double* diag, const int32_t* perm,
+                       const double* v, int32_t nrhs, double* y, void* stream) {
+    return matvec_entry(pat, prec, val, diag, perm, v, nrhs, y, 1, stream);
+}
+
+kc_status kc_llt_matvec(const kc_pattern* pat, int32_t prec, const void* val, const double* diag, const int32_t* perm,
+                        const double* v, int32_t nrhs, double* y, void* stream) {
+    return matvec_entry(pat, prec, val, diag, perm, v, nrhs, y, 2, stream);
+}
+
+kc_status kc_logdet(const kc_pattern* pat, const double* diag, double* logdet_out, int64_t* zero_pivots_out,
+                    void* stream) {
+    KC_TRY(check_pattern(pat));
+    if (!diag || !logdet_out) return fail(KC_EINVAL, "diag and logdet_out must be non-NULL");
+    return logdet_impl(pat, diag, logdet_out, zero_pivots_out, (cudaStream_t)stream);
 }
 
 }  // extern "C"

@@ -157,11 +157,21 @@ inline kc_status allow_dynamic_smem(F* func) {
     return KC_OK;
 }
 
+// Covariance function of one point set (Section 4.4), as the kernels use it.
+//   nu_code 0, 1, 2: Matern with nu = 1/2, 3/2, 5/2 (closed forms);
+//   nu_code 3: Matern with another nu = n + mu, |mu| <= 1/2 (Bessel K_nu);
+//   nu_code 4: the Cauchy class.
 struct KernelParams {
     int nu_code;
-    double scale;   // sqrt(2 nu) / ell
+    int n;          // code 3: integer part of nu + 1/2
+    double scale;   // codes 0-3: sqrt(2 nu) / ell; code 4: 1 / ell
     double sigma2;
     double nugget;
+    double nu, mu;               // code 3
+    double gam1, gam2, gp, gm;   // code 3: (1/G(1-mu) -+ 1/G(1+mu)) / (2 mu | 2), G(1+mu), G(1-mu)
+    double fact;                 // code 3: mu pi / sin(mu pi)
+    double lognorm;              // code 3: log(2^{1-nu} / Gamma(nu))
+    double alpha, expo;          // code 4: alpha, -beta / alpha
 };
 kc_status kernel_params(const kc_kernel* k, KernelParams* out);
 

@@ -46,6 +46,7 @@
 #include <vector>
 
 #include "grid.cuh"
+#include "covariance.cuh"
 
 namespace kc {
 
@@ -226,27 +227,29 @@ struct Acc<float> {
     __device__ __forceinline__ static float recip(double Lii) { return __frcp_rn((float)Lii); }
 };
 
-template <typename T>
-__device__ __forceinline__ T theta_off(const KernelParams& kp, int d, const double* xj, const double* xi);
-
-template <>
-__device__ __forceinline__ double theta_off<double>(const KernelParams& kp, int d, const double* xj,
-                                                    const double* xi) {
-    double s = 0.0;
-    for (int t = 0; t < d; ++t) {
-        double u = xj[t] - xi[t];
-        s = fma(u, u, s);
+// Theta_ji off the diagonal.  GEN = false: the closed-form Matern kernels only
+// (nu = 1/2, 3/2, 5/2); GEN = true: every covariance function, in its own
+// kernel instantiation, so that the calls behind the other families cost the
+// closed-form kernels no registers.
+template <typename T, bool GEN>
+__device__ __forceinline__ T theta_off(const KernelParams& kp, int d, const double* xj, const double* xi) {
+    if constexpr (sizeof(T) == 8) {
+        double s = 0.0;
+        for (int t = 0; t < d; ++t) {
+            double u = xj[t] - xi[t];
+            s = fma(u, u, s);
+        }
+        if constexpr (GEN) return cov_f64(kp, sqrt(s));
+        else return matern_f64(sqrt(s), kp.nu_code, kp.scale, kp.sigma2);
+    } else {
+        float s = 0.f;
+        for (int t = 0; t < d; ++t) {
+            float u = (float)(xj[t] - xi[t]);
+            s = fmaf(u, u, s);
+        }
+        if constexpr (GEN) return cov_f32(kp, sqrtf(s));
+        else return matern_f32(sqrtf(s), kp.nu_code, (float)kp.scale, (float)kp.sigma2);
     }
-    return matern_f64(sqrt(s), kp.nu_code, kp.scale, kp.sigma2);
-}
-template <>
-__device__ __forceinline__ float theta_off<float>(const KernelParams& kp, int d, const double* xj, const double* xi) {
-    float s = 0.f;
-    for (int t = 0; t < d; ++t) {
-        float u = (float)(xj[t] - xi[t]);
-        s = fmaf(u, u, s);
-    }
-    return matern_f32(sqrtf(s), kp.nu_code, (float)kp.scale, (float)kp.sigma2);
 }
 
 // done[k] starts at minus the number of tasks of column k and every finished
@@ -433,7 +436,7 @@ __device__ __forceinline__ void merge_global(const FactorArgs<T>& A, const RowTa
 
 // Row-j bookkeeping of the rows b0+lane of a batch: the slot of L_ji, the
 // start of row j, and Theta_ji (loads and exponentials overlap across lanes).
-template <typename T>
+template <typename T, bool GEN>
 __device__ __forceinline__ void batch_rows(const FactorArgs<T>& A, const TaskCtx<T>& X, int64_t b0, int nb, int lane,
                                            int64_t& my_e0, int64_t& my_b, T& my_th) {
     my_e0 = 0;
@@ -443,7 +446,7 @@ __device__ __forceinline__ void batch_rows(const FactorArgs<T>& A, const TaskCtx
         const int j = __ldg(&A.rowidx[b0 + lane]);
         my_b = __ldg(&A.slot[b0 + lane]);
         my_e0 = __ldg(&A.rowptr[j]);
-        if (!X.zero) my_th = theta_off<T>(kparams(A, X.i), A.d, A.x + (int64_t)j * A.d, A.x + (int64_t)X.i * A.d);
+        if (!X.zero) my_th = theta_off<T, GEN>(kparams(A, X.i), A.d, A.x + (int64_t)j * A.d, A.x + (int64_t)X.i * A.d);
     }
 }
 
@@ -454,7 +457,7 @@ __device__ __forceinline__ void batch_rows(const FactorArgs<T>& A, const TaskCtx
 #define KC_FACTOR_MIN_BLOCKS 4
 #endif
 
-template <typename T, int U>
+template <typename T, int U, bool GEN>
 __global__ void __launch_bounds__(256, U >= 16 ? 3 : KC_FACTOR_MIN_BLOCKS) ichol_persistent_k(FactorArgs<T> A) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = lane_id();
@@ -473,7 +476,7 @@ __global__ void __launch_bounds__(256, U >= 16 ? 3 : KC_FACTOR_MIN_BLOCKS) ichol
             const int nb = (int)min((int64_t)32, qe - b0);
             int64_t my_e0, my_b;
             T my_th;
-            batch_rows(A, X, b0, nb, lane, my_e0, my_b, my_th);
+            batch_rows<T, GEN>(A, X, b0, nb, lane, my_e0, my_b, my_th);
             for (int r0 = 0; r0 < nb; r0 += ng) {
                 const int r = r0 + g;
                 const bool act = r < nb;
@@ -621,7 +624,7 @@ __device__ __forceinline__ void merge_smem(const RowTable<T>& tab, const int* cs
     }
 }
 
-template <typename T, int U>
+template <typename T, int U, bool GEN>
 __global__ void __launch_bounds__(128) ichol_bulk_k(FactorArgs<T> A) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = lane_id();
@@ -655,7 +658,7 @@ __global__ void __launch_bounds__(128) ichol_bulk_k(FactorArgs<T> A) {
             const int nb = (int)min((int64_t)32, qe - b0);
             int64_t my_e0, my_b;
             T my_th;
-            batch_rows(A, X, b0, nb, lane, my_e0, my_b, my_th);
+            batch_rows<T, GEN>(A, X, b0, nb, lane, my_e0, my_b, my_th);
             uint32_t off0 = 0, meta0 = 0, off1 = 0, meta1 = 0;  // the lane's row in buffer 0 / 1
             Stage cur;
             if (bulk) cur = stage_issue(A, bufs, &bars[0], 0, 0, nb, lane, my_e0, my_b, off0, meta0);
@@ -798,6 +801,7 @@ struct FactorCore {
     KernelParams kp;
     const int32_t* col_set = nullptr;
     KernelParams* kps = nullptr;
+    bool general = false;  // some set's kernel is not a closed-form Matern
     int rpt = 128, lanes = 0, unroll = 8, warps = 8, hbits = 7, ctas = 0, adaptive = 0;
     int stage_req = 0;    // requested stage-buffer bytes: 0 automatic, < 0 register form
     int stage_bytes = 0;  // chosen (0: register form)
@@ -807,7 +811,7 @@ struct FactorCore {
     int hold = -1;
 };
 
-template <typename T, int U>
+template <typename T, int U, bool GEN>
 static kc_status launch_core(const FactorCore& F, T* val, double* diag, cudaStream_t s) {
     FactorArgs<T> a;
     a.N = F.P.N;
@@ -837,7 +841,7 @@ static kc_status launch_core(const FactorCore& F, T* val, double* diag, cudaStre
     a.adaptive = F.adaptive;
     a.stage_bytes = F.stage_bytes;
     const size_t table = (size_t)(1 << F.hbits) * (sizeof(int) + sizeof(T));
-    const bool bulk = F.stage_bytes > 0;
+    const bool bulk = !GEN && F.stage_bytes > 0;  // the other kernel families: register form
     // bulk form: table, two stage buffers, two mbarriers per warp (128-byte aligned)
     a.warp_smem = (int)(bulk ? (table + 2 * (size_t)F.stage_bytes + 16 + 127) / 128 * 128 : table);
     int warps = bulk ? F.bulk_warps : F.warps;
@@ -848,7 +852,9 @@ static kc_status launch_core(const FactorCore& F, T* val, double* diag, cudaStre
         warps = std::min(warps, optin / a.warp_smem);
         if (warps < 1) return fail(KC_EINVAL, "factor: stage_bytes too large for one warp's shared memory");
     }
-    auto kfn = bulk ? ichol_bulk_k<T, U> : ichol_persistent_k<T, U>;
+    auto kfn = ichol_persistent_k<T, U, GEN>;
+    if constexpr (!GEN)
+        if (bulk) kfn = ichol_bulk_k<T, U, false>;
     int per_sm = 0;
     KC_TRY(allow_dynamic_smem(kfn));
     if (!bulk && F.warps_auto) {
@@ -881,13 +887,19 @@ static kc_status launch_core(const FactorCore& F, T* val, double* diag, cudaStre
     return KC_OK;
 }
 
+// The closed-form Matern kernels take the unroll asked for; the other
+// families one instantiation per precision (register form, 8 loads in flight
+// per lane in the FP32 form, 4 in FP64).
 static kc_status launch_any(const FactorCore& F, void* val, double* diag, cudaStream_t s) {
+    if (F.general)
+        return F.prec == KC_FP64 ? launch_core<double, 4, true>(F, (double*)val, diag, s)
+                                 : launch_core<float, 8, true>(F, (float*)val, diag, s);
     if (F.prec == KC_FP64)
-        return F.unroll >= 8 ? launch_core<double, 8>(F, (double*)val, diag, s)
-                             : launch_core<double, 4>(F, (double*)val, diag, s);
-    if (F.unroll >= 16) return launch_core<float, 16>(F, (float*)val, diag, s);
-    return F.unroll >= 8 ? launch_core<float, 8>(F, (float*)val, diag, s)
-                         : launch_core<float, 4>(F, (float*)val, diag, s);
+        return F.unroll >= 8 ? launch_core<double, 8, false>(F, (double*)val, diag, s)
+                             : launch_core<double, 4, false>(F, (double*)val, diag, s);
+    if (F.unroll >= 16) return launch_core<float, 16, false>(F, (float*)val, diag, s);
+    return F.unroll >= 8 ? launch_core<float, 8, false>(F, (float*)val, diag, s)
+                         : launch_core<float, 4, false>(F, (float*)val, diag, s);
 }
 
 static kc_status read_status(const FactorCore& F, int64_t* zero_out, cudaStream_t s) {
@@ -958,6 +970,7 @@ kc_status factor_impl(const kc_pattern* P, const double* x, int d, const kc_kern
     if (prec != KC_FP64 && prec != KC_FP32_FORM) return fail(KC_EINVAL, "prec must be KC_FP64 or KC_FP32_FORM");
     FactorCore F;
     KC_TRY(kernel_params(kern, &F.kp));
+    F.general = F.kp.nu_code > 2;
     KC_TRY(apply_opts(F, o));
     F.P = *P;
     F.prec = prec;
@@ -1019,6 +1032,7 @@ kc_status plan_create_impl(const kc_pattern* P, const double* x, int d, const kc
     kc_status st = kernel_params(&kerns[0], &F.kp);
     if (st == KC_OK) st = apply_opts(F, o);
     if (st != KC_OK) return bail(st);
+    F.general = F.kp.nu_code > 2;
     F.P = *P;
     F.prec = prec;
     F.d = d;
@@ -1041,8 +1055,10 @@ kc_status plan_create_impl(const kc_pattern* P, const double* x, int d, const kc
     if ((st = plan_alloc(pl, (void**)&F.status, 64)) != KC_OK) return bail(st);
     if (nsets > 1) {
         std::vector<KernelParams> h(nsets);
-        for (int k = 0; k < nsets; ++k)
+        for (int k = 0; k < nsets; ++k) {
             if ((st = kernel_params(&kerns[k], &h[k])) != KC_OK) return bail(st);
+            if (h[k].nu_code > 2) F.general = true;
+        }
         if ((st = plan_alloc(pl, (void**)&F.kps, sizeof(KernelParams) * nsets)) != KC_OK) return bail(st);
         if (cudaMemcpy(F.kps, h.data(), sizeof(KernelParams) * nsets, cudaMemcpyHostToDevice) != cudaSuccess)
             return bail(fail(KC_ECUDA, "plan: kernel parameter copy"));

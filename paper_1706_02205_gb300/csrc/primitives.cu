@@ -49,17 +49,60 @@ int sm_count() {
     return n > 0 ? n : 1;
 }
 
+// Taylor coefficients of 1/Gamma(z) = sum_{k>=1} c_k z^k (Abramowitz & Stegun
+// 6.1.34): 1/Gamma(1+mu) = sum_k c_k mu^{k-1}, entire, so for |mu| <= 1/2 the
+// even and odd parts give Temme's gamma_1 and gamma_2 without the
+// cancellation of their difference quotient.
+static const double RGAMMA_TAYLOR[26] = {
+    1.0, 0.5772156649015329, -0.6558780715202538, -0.0420026350340952, 0.1665386113822915,
+    -0.0421977345555443, -0.0096219715278770, 0.0072189432466630, -0.0011651675918591,
+    -0.0002152416741149, 0.0001280502823882, -0.0000201348547807, -0.0000012504934821,
+    0.0000011330272320, -0.0000002056338417, 0.0000000061160950, 0.0000000050020075,
+    -0.0000000011812746, 0.0000000001043427, 0.0000000000077823, -0.0000000000036968,
+    0.0000000000005100, -0.0000000000000206, -0.0000000000000054, 0.0000000000000014,
+    0.0000000000000001};
+
 kc_status kernel_params(const kc_kernel* k, KernelParams* out) {
     if (!k) return fail(KC_EINVAL, "kernel parameters are NULL");
     if (!(k->ell > 0.0) || !(k->sigma2 > 0.0) || !(k->nugget >= 0.0))
         return fail(KC_EINVAL, "kernel needs ell > 0, sigma2 > 0, nugget >= 0");
+    *out = KernelParams{};
+    out->sigma2 = k->sigma2;
+    out->nugget = k->nugget;
+    if (k->family == KC_CAUCHY) {
+        if (!(k->alpha > 0.0 && k->alpha <= 2.0) || !(k->beta > 0.0))
+            return fail(KC_EINVAL, "the Cauchy class needs 0 < alpha <= 2 and beta > 0");
+        out->nu_code = 4;
+        out->scale = 1.0 / k->ell;
+        out->alpha = k->alpha;
+        out->expo = -k->beta / k->alpha;
+        return KC_OK;
+    }
+    if (k->family != KC_MATERN) return fail(KC_EINVAL, "family must be KC_MATERN or KC_CAUCHY");
+    if (!(k->nu > 0.0 && k->nu <= 50.0)) return fail(KC_EINVAL, "nu must be in (0, 50]");
+    out->scale = sqrt(2.0 * k->nu) / k->ell;
+    out->nu = k->nu;
     if (k->nu == 0.5) out->nu_code = 0;
     else if (k->nu == 1.5) out->nu_code = 1;
     else if (k->nu == 2.5) out->nu_code = 2;
-    else return fail(KC_EINVAL, "nu must be 0.5, 1.5 or 2.5");
-    out->scale = sqrt(2.0 * k->nu) / k->ell;
-    out->sigma2 = k->sigma2;
-    out->nugget = k->nugget;
+    else {
+        out->nu_code = 3;
+        const double n = floor(k->nu + 0.5);
+        const double mu = k->nu - n;
+        double odd = 0.0, even = 0.0;  // sum c_{2m} mu^{2m-2}, sum c_{2m+1} mu^{2m}
+        for (int i = 25; i >= 0; --i) {
+            if (i & 1) odd = odd * mu * mu + RGAMMA_TAYLOR[i];
+            else even = even * mu * mu + RGAMMA_TAYLOR[i];
+        }
+        out->n = (int)n;
+        out->mu = mu;
+        out->gam1 = -odd;
+        out->gam2 = even;
+        out->gp = 1.0 / (even + mu * odd);  // Gamma(1 + mu)
+        out->gm = 1.0 / (even - mu * odd);  // Gamma(1 - mu)
+        out->fact = mu == 0.0 ? 1.0 : mu * M_PI / sin(mu * M_PI);
+        out->lognorm = (1.0 - k->nu) * log(2.0) - lgamma(k->nu);
+    }
     return KC_OK;
 }
 

@@ -10,6 +10,7 @@
 // a9's error check uses the same dense product with FP32 entries and
 // compensated (Dot2) tile sums combined in FP64.
 #include "solver.cuh"
+#include "covariance.cuh"
 
 namespace kc {
 
@@ -48,7 +49,7 @@ __global__ void __launch_bounds__(DM_THREADS) dense_theta_f64_k(const double* __
                 double u = xj[t] - sx[kk * d + t];
                 s = fma(u, u, s);
             }
-            double th = matern_f64(sqrt(s), kp.nu_code, kp.scale, kp.sigma2);
+            double th = cov_f64(kp, sqrt(s));
             if (k0 + kk == j) th += kp.nugget;
 #pragma unroll
             for (int r = 0; r < NRHS; ++r) acc[r] = fma(th, sv[kk * NRHS + r], acc[r]);
@@ -309,7 +310,6 @@ __global__ void __launch_bounds__(DM_THREADS) dense_theta_f32_k(const double* __
     const int64_t j = (int64_t)blockIdx.x * DM_THREADS + threadIdx.x;
     float xj[4] = {0.f, 0.f, 0.f, 0.f};
     for (int t = 0; t < d; ++t) xj[t] = j < N ? (float)x[j * d + t] : 0.f;
-    const float sc = (float)kp.scale, s2 = (float)kp.sigma2;
     double acc = 0.0;
     for (int64_t k0 = 0; k0 < N; k0 += DM_THREADS) {
         __syncthreads();
@@ -325,7 +325,7 @@ __global__ void __launch_bounds__(DM_THREADS) dense_theta_f32_k(const double* __
             float u0 = xj[0] - sx[kk * 4], u1 = xj[1] - sx[kk * 4 + 1], u2 = xj[2] - sx[kk * 4 + 2],
                   u3 = xj[3] - sx[kk * 4 + 3];
             float rr = fmaf(u0, u0, fmaf(u1, u1, fmaf(u2, u2, u3 * u3)));
-            float th = matern_f32(sqrtf(rr), kp.nu_code, sc, s2);
+            float th = cov_f32(kp, sqrtf(rr));
             float a = th, b = sv[kk];
             float pr = a * b, ep = fmaf(a, b, -pr);
             float ns = s + pr, zz = ns - s;

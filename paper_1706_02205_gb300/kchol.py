@@ -31,8 +31,12 @@ class KcError(RuntimeError):
         self.status = status
 
 
+MATERN, CAUCHY = 0, 1
+
+
 class kc_kernel(C.Structure):
-    _fields_ = [("nu", C.c_double), ("ell", C.c_double), ("sigma2", C.c_double), ("nugget", C.c_double)]
+    _fields_ = [("nu", C.c_double), ("ell", C.c_double), ("sigma2", C.c_double), ("nugget", C.c_double),
+                ("family", C.c_int32), ("alpha", C.c_double), ("beta", C.c_double)]
 
 
 class kc_pattern(C.Structure):
@@ -48,7 +52,7 @@ class kc_opts(C.Structure):
 
 
 _lib = None
-ABI_VERSION = 2  # KC_ABI_VERSION of include/kchol.h that these signatures follow
+ABI_VERSION = 3  # KC_ABI_VERSION of include/kchol.h that these signatures follow
 
 
 def lib():
@@ -87,6 +91,11 @@ def lib():
             "kc_pattern_concat": [i32, P(vp), P(vp), P(C.c_int64), vp, vp, vp, vp],
             "kc_points_concat": [i32, P(vp), P(C.c_int64), P(C.c_int32), i32, vp, vp],
             "kc_index_concat": [i32, P(vp), P(C.c_int64), vp, vp],
+            "kc_kernel_eval": [P(kc_kernel), i32, vp, i64, vp, vp],
+            "kc_l_matvec": [P(kc_pattern), i32, vp, vp, vp, vp, i32, vp, vp],
+            "kc_lt_matvec": [P(kc_pattern), i32, vp, vp, vp, vp, i32, vp, vp],
+            "kc_llt_matvec": [P(kc_pattern), i32, vp, vp, vp, vp, i32, vp, vp],
+            "kc_logdet": [P(kc_pattern), vp, P(C.c_double), P(C.c_int64), vp],
         }
         for name, args in sigs.items():
             f = getattr(L, name)
@@ -101,7 +110,8 @@ def lib():
 EXPORTED = ("kc_last_error", "kc_abi_version", "kc_launch_count", "kc_last_factor_kernel_ms", "kc_order_points", "kc_pattern_count", "kc_pattern_fill",
             "kc_schedule", "kc_factor", "kc_solve", "kc_solve_noalloc", "kc_refine", "kc_pca_truncate", "kc_pca_error",
             "kc_factor_plan_create", "kc_factor_plan_launch", "kc_factor_plan_finish", "kc_factor_plan_tune",
-            "kc_factor_plan_destroy", "kc_pattern_concat", "kc_points_concat", "kc_index_concat")
+            "kc_factor_plan_destroy", "kc_pattern_concat", "kc_points_concat", "kc_index_concat", "kc_kernel_eval",
+            "kc_l_matvec", "kc_lt_matvec", "kc_llt_matvec", "kc_logdet")
 
 
 def launch_count() -> int:
@@ -140,15 +150,19 @@ def _dev(t: torch.Tensor, dtype, name):
 
 @dataclass
 class Kernel:
-    """Matern covariance: nu in {0.5, 1.5, 2.5}, length scale ell, variance
-    sigma2, nugget on the diagonal."""
+    """Covariance function: the Matern class (smoothness nu in (0, 50],
+    length scale ell, variance sigma2) or, with family=CAUCHY, the Cauchy
+    class (ell, alpha in (0, 2], beta > 0, sigma2); nugget on the diagonal."""
     nu: float = 1.5
     ell: float = 0.2
     sigma2: float = 1.0
     nugget: float = 0.0
+    family: int = MATERN
+    alpha: float = 1.0
+    beta: float = 1.0
 
     def c(self):
-        return kc_kernel(self.nu, self.ell, self.sigma2, self.nugget)
+        return kc_kernel(self.nu, self.ell, self.sigma2, self.nugget, self.family, self.alpha, self.beta)
 
 
 def make_opts(spin_limit_cycles=0, rows_per_task=0, ctas_per_sm=0, warps_per_cta=0, test_hold_column=-1,
@@ -313,6 +327,51 @@ def pca_error(x, kern: Kernel, Lk, v0, iters=50, stream=None):
     _check(lib().kc_pca_error(_ptr(x), N, d, C.byref(kk), Lk.shape[0], _ptr(Lk), _ptr(v0), int(iters),
                               C.byref(est), _stream(stream)))
     return float(est.value)
+
+
+def kernel_eval(kern: Kernel, prec, r, stream=None):
+    """The covariance function at distances r (float64 tensor), as the factor
+    evaluates its entries in precision prec (no nugget)."""
+    _dev(r, torch.float64, "r")
+    out = torch.empty_like(r)
+    k = kern.c()
+    _check(lib().kc_kernel_eval(C.byref(k), int(prec), _ptr(r), r.numel(), _ptr(out), _stream(stream)))
+    return out
+
+
+def _factor_mv(fn, pat, prec, val, diag, perm, v, stream):
+    _dev(v, torch.float64, "vector")
+    one = v.dim() == 1
+    if one:
+        v = v[None]
+    y = torch.empty_like(v)
+    _check(fn(pat.c(), int(prec), _ptr(val), _ptr(diag), _ptr(perm), _ptr(v), v.shape[0], _ptr(y), _stream(stream)))
+    return y[0] if one else y
+
+
+def l_matvec(pat: Pattern, prec, val, diag, perm, z, stream=None):
+    """y = P L P^T z; z (nrhs, N) or (N,) float64 in original order.  For
+    z ~ N(0, I), y is a sample of N(0, L L^T) (task (4))."""
+    return _factor_mv(lib().kc_l_matvec, pat, prec, val, diag, perm, z, stream)
+
+
+def lt_matvec(pat: Pattern, prec, val, diag, perm, v, stream=None):
+    """y = P L^T P^T v."""
+    return _factor_mv(lib().kc_lt_matvec, pat, prec, val, diag, perm, v, stream)
+
+
+def llt_matvec(pat: Pattern, prec, val, diag, perm, v, stream=None):
+    """y = P L L^T P^T v, the factor's approximation of Theta v (task (1))."""
+    return _factor_mv(lib().kc_llt_matvec, pat, prec, val, diag, perm, v, stream)
+
+
+def logdet(pat: Pattern, diag, stream=None):
+    """(log det(L L^T) over the kept pivots, number of dropped pivots): task (3)."""
+    _dev(diag, torch.float64, "diag")
+    v = C.c_double(0.0)
+    z = C.c_int64(0)
+    _check(lib().kc_logdet(pat.c(), _ptr(diag), C.byref(v), C.byref(z), _stream(stream)))
+    return float(v.value), int(z.value)
 
 
 # ------------------------------------------------------------------ the path

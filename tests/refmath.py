@@ -32,6 +32,27 @@ def dense_theta(x, nu, ell, sigma2=1.0, nugget=0.0):
     return T
 
 
+def dense_cov(x, kern):
+    """Dense Theta of any covariance family (attributes family, nu, ell,
+    sigma2, nugget, alpha, beta): the Cauchy class
+    sigma2 (1 + (r/ell)^alpha)^{-beta/alpha} (family 1) in NumPy, else the
+    Matern Bessel definition; nugget on the diagonal."""
+    if getattr(kern, "family", 0) == 1:
+        D = cdist(x, x)
+        T = kern.sigma2 * (1.0 + (D / kern.ell) ** kern.alpha) ** (-kern.beta / kern.alpha)
+        T[np.diag_indices_from(T)] = kern.sigma2 + kern.nugget
+        return T
+    return dense_theta(x, kern.nu, kern.ell, kern.sigma2, kern.nugget)
+
+
+def cov_values(r, kern):
+    """The covariance function (no nugget) at distances r, by its definition."""
+    r = np.asarray(r, dtype=np.float64)
+    if getattr(kern, "family", 0) == 1:
+        return kern.sigma2 * (1.0 + (r / kern.ell) ** kern.alpha) ** (-kern.beta / kern.alpha)
+    return matern_general(r, kern.nu, kern.ell, kern.sigma2)
+
+
 def dense_lower(rowptr, col, val, N):
     L = np.zeros((N, N))
     for j in range(N):

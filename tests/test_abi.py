@@ -42,7 +42,7 @@ def test_library_exports_every_declared_symbol(so):
 def test_binding_lists_match_header(so):
     from paper_1706_02205_gb300 import kchol
 
-    assert set(kchol.EXPORTED) <= set(_declared())
+    assert set(kchol.EXPORTED) == set(_declared())
 
 
 def test_argument_errors_without_gpu(so):
@@ -54,3 +54,49 @@ def test_argument_errors_without_gpu(so):
     st = lib.kc_schedule(ctypes.c_int64(0), None, None, None, ctypes.c_int32(0), None, None, None, None, None, None,
                          None)
     assert st == 1
+
+
+def test_new_entries_reject_bad_arguments_without_gpu(so):
+    from paper_1706_02205_gb300 import kchol
+    lib = kchol.lib()
+    bad = [kchol.Kernel(nu=0.0), kchol.Kernel(nu=60.0), kchol.Kernel(ell=0.0),
+           kchol.Kernel(family=kchol.CAUCHY, alpha=2.5), kchol.Kernel(family=kchol.CAUCHY, beta=0.0),
+           kchol.Kernel(family=7)]
+    for k in bad:
+        kk = k.c()
+        assert lib.kc_kernel_eval(ctypes.byref(kk), 0, None, 0, None, None) == kchol.KC_EINVAL, k
+    ok = kchol.Kernel(nu=0.8).c()
+    assert lib.kc_kernel_eval(ctypes.byref(ok), 5, None, 0, None, None) == kchol.KC_EINVAL  # bad prec
+    for name in ("kc_l_matvec", "kc_lt_matvec", "kc_llt_matvec"):
+        assert getattr(lib, name)(None, 0, None, None, None, None, 1, None, None) == kchol.KC_EINVAL
+    v = ctypes.c_double(0.0)
+    assert lib.kc_logdet(None, None, ctypes.byref(v), None, None) == kchol.KC_EINVAL
+
+
+def test_struct_layouts_match_header(tmp_path):
+    """Offsets of the ABI structs as a C compiler lays them out from the header
+    equal the binding's ctypes layouts."""
+    import shutil
+    import subprocess
+    if not shutil.which("gcc"):
+        pytest.skip("no C compiler")
+    from paper_1706_02205_gb300 import kchol
+    structs = {"kc_kernel": kchol.kc_kernel, "kc_opts": kchol.kc_opts, "kc_pattern": kchol.kc_pattern}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "kchol.h"', "int main(void) {"]
+    for name, cls in structs.items():
+        lines.append(f'printf("{name} size %zu\\n", sizeof({name}));')
+        for f, _ in cls._fields_:
+            lines.append(f'printf("{name} {f} %zu\\n", offsetof({name}, {f}));')
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.check_call(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
+    got = {}
+    for line in subprocess.check_output([str(exe)], text=True).splitlines():
+        a, b, c = line.split()
+        got[(a, b)] = int(c)
+    for name, cls in structs.items():
+        assert got[(name, "size")] == ctypes.sizeof(cls), name
+        for f, _ in cls._fields_:
+            assert got[(name, f)] == getattr(cls, f).offset, (name, f)

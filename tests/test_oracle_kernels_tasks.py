@@ -73,16 +73,6 @@ def test_cauchy_special_cases():
     assert oracle.cov(1e6, k) > 0.5 * (1e6 / 0.4) ** -0.025
 
 
-def _dense_cov(x, kern):
-    from scipy.spatial.distance import cdist
-    D = cdist(x, x)
-    if kern.family == oracle.CAUCHY:
-        T = kern.sigma2 * (1.0 + (D / kern.ell) ** kern.alpha) ** (-kern.beta / kern.alpha)
-        T[np.diag_indices_from(T)] = kern.sigma2 + kern.nugget
-        return T
-    return refmath.dense_theta(x, kern.nu, kern.ell, kern.sigma2, kern.nugget)
-
-
 KERNELS = [
     ("cauchy_0.4_0.5_0.025", oracle.Kernel(family=oracle.CAUCHY, ell=0.4, alpha=0.5, beta=0.025, nugget=1e-3)),
     ("cauchy_0.2_1_0.2", oracle.Kernel(family=oracle.CAUCHY, ell=0.2, alpha=1.0, beta=0.2, nugget=1e-4)),
@@ -100,7 +90,7 @@ def test_rho_infinity_dense_cholesky_other_kernels(name, kern):
     val, zc = oracle.ichol(xo, rp, col, kern)
     assert not zc.any()
     L = refmath.dense_lower(rp, col, val, N)
-    C = np.linalg.cholesky(_dense_cov(xo, kern))
+    C = np.linalg.cholesky(refmath.dense_cov(xo, kern))
     nrm = np.linalg.norm(C, axis=1)
     assert np.max(np.abs(L - C) / nrm[:, None]) < 1e-9
 
@@ -159,3 +149,23 @@ def test_logdet_sparse_pattern_is_slogdet_of_llt_and_counts_drops():
     assert z == int(zc.sum()) > 0
     dg = val[rp[1:] - 1]
     assert abs(ld - 2 * math.fsum(np.log(dg[dg > 0]))) <= 1e-12 * abs(ld)
+
+
+def test_ichol_float_storage_mode():
+    """store_f32: every off-diagonal entry is a float, each satisfies its
+    defining equation L_ji L_ii = float(Theta_ji) - sum_k L_jk L_ik to the
+    float rounding of L_ji, and the factor stays within float-level distance
+    of the FP64 one."""
+    xo, rp, col, val, zc, kern = _factor(N=800, rho=3.0, nu=0.5, ell=0.2, seed=76)
+    v32, zc32 = oracle.ichol(xo, rp, col, kern, store_f32=True)
+    off = np.ones(len(col), bool)
+    off[rp[1:] - 1] = False
+    assert np.array_equal(v32[off], v32[off].astype(np.float32).astype(np.float64))
+    L = refmath.dense_lower(rp, col, v32, xo.shape[0])
+    Th = refmath.dense_theta(xo, 0.5, 0.2)
+    rows = np.repeat(np.arange(xo.shape[0]), np.diff(rp))
+    for e in np.nonzero(off)[0][::37]:
+        j, i = rows[e], col[e]
+        s = float(np.float32(Th[j, i])) - L[j, :i] @ L[i, :i]
+        assert abs(v32[e] * L[i, i] - s) <= (2.0**-24 * abs(v32[e]) + 1e-15) * L[i, i] + 1e-14, e
+    assert np.max(np.abs(v32 - val)) < 1e-4 and not zc32.any()
