@@ -89,6 +89,8 @@ def lib():
         K = C.POINTER(KoKernel)
         L.ko_bessel_k.restype = d
         L.ko_bessel_k.argtypes = [d, d]
+        L.ko_bessel_k_scaled.restype = d
+        L.ko_bessel_k_scaled.argtypes = [d, d]
         L.ko_matern.restype = d
         L.ko_matern.argtypes = [d, d, d, d]
         L.ko_cauchy.restype = d
@@ -221,6 +223,11 @@ def csr_to_csc(rowptr, col):
 def bessel_k(nu, x):
     """K_nu(x), x > 0, from the integral representation (A&S 9.6.24)."""
     return lib().ko_bessel_k(float(nu), float(x))
+
+
+def bessel_k_scaled(nu, x):
+    """e^x K_nu(x), x > 0, the same integral with e^x taken inside."""
+    return lib().ko_bessel_k_scaled(float(nu), float(x))
 
 
 def matern(r, nu, ell, sigma2=1.0):

@@ -313,7 +313,9 @@ void ko_pattern_fill(const double* xo, const double* l, i64 N, i32 d, double rho
 /*   K_nu(x) = int_0^inf exp(-x cosh s) cosh(nu s) ds     (x > 0)           */
 /* (Abramowitz & Stegun 9.6.24), by the trapezoidal rule: the integrand is  */
 /* entire and decays double-exponentially, so a fixed small step converges  */
-/* to working precision.  G(0) = sigma2.                                    */
+/* to working precision.  G takes e^x K_nu(x) (the factor inside the        */
+/* integral) and e^{-t} with its other factors, so it stays accurate where  */
+/* K_nu alone would underflow.  G(0) = sigma2.                              */
 /*                                                                          */
 /* Cauchy class (Gneiting), Section 4.4:                                    */
 /*   G(r) = sigma2 (1 + (r/ell)^alpha)^{-beta/alpha}.                        */
@@ -321,14 +323,21 @@ void ko_pattern_fill(const double* xo, const double* l, i64 N, i32 d, double rho
 /* The nugget is added on the diagonal only.                                */
 /* ------------------------------------------------------------------------ */
 
-double ko_bessel_k(double nu, double x) {
+/* e^x K_nu(x): the same integral with the factor e^x taken inside,
+   exp(-x (cosh s - 1)) = exp(-2 x sinh^2(s/2)), so that no term underflows
+   where K_nu itself leaves the double range.  ko_bessel_k is this times
+   e^{-x}. */
+double ko_bessel_k_scaled(double nu, double x) {
     if (!(x > 0.0)) return INFINITY;
-    const double h = 1.0 / 64.0;
-    double sum = 0.5 * exp(-x); /* s = 0: cosh(0) = 1 */
+    /* the trapezoidal error falls like exp(-pi^2/(2h)) but the integrand's
+       size off the real axis grows with x: the step shrinks like 1/x */
+    const double h = x > 512.0 ? 8.0 / x : 1.0 / 64.0;
+    double sum = 0.5; /* s = 0 */
     double prev = sum;
     for (i64 k = 1;; ++k) {
         double s = h * (double)k;
-        double f = exp(-x * cosh(s)) * cosh(nu * s);
+        double u = sinh(0.5 * s);
+        double f = exp(-2.0 * x * u * u) * cosh(nu * s);
         sum += f;
         if (f < prev && f <= 1e-18 * sum) break;
         if (!(f > 0.0) && k > 1) break;
@@ -336,6 +345,8 @@ double ko_bessel_k(double nu, double x) {
     }
     return h * sum;
 }
+
+double ko_bessel_k(double nu, double x) { return exp(-x) * ko_bessel_k_scaled(nu, x); }
 
 double ko_matern(double r, double nu, double ell, double sigma2) {
     if (nu == 0.5) {
@@ -351,9 +362,8 @@ double ko_matern(double r, double nu, double ell, double sigma2) {
     if (!(nu > 0.0)) return NAN;
     double t = sqrt(2.0 * nu) * r / ell;
     if (t == 0.0) return sigma2;
-    double k = ko_bessel_k(nu, t);
-    if (k == 0.0) return 0.0;
-    return sigma2 * exp((1.0 - nu) * log(2.0) - lgamma(nu) + nu * log(t)) * k;
+    double k = ko_bessel_k_scaled(nu, t);
+    return sigma2 * exp((1.0 - nu) * log(2.0) - lgamma(nu) + nu * log(t) - t) * k;
 }
 
 double ko_cauchy(double r, double ell, double alpha, double beta, double sigma2) {

@@ -172,8 +172,28 @@ struct KernelParams {
     double fact;                 // code 3: mu pi / sin(mu pi)
     double lognorm;              // code 3: log(2^{1-nu} / Gamma(nu))
     double alpha, expo;          // code 4: alpha, -beta / alpha
+    int iser;                    // code 3: the I-series of coef applies for t <= 2 (nu not near an integer)
+    int cheb;                    // code 3: the Chebyshev pieces of coef apply for t > 2 (nu <= 8)
+    const double* coef;          // code 3: device table of KC_COEF_LEN doubles (matern_coef_table), or NULL
 };
 kc_status kernel_params(const kc_kernel* k, KernelParams* out);
+
+// Per-kernel table of a Matern of general nu (code 3), KC_COEF_LEN doubles:
+//   [0, KC_ISER)             a_k, [KC_ISER, 2 KC_ISER) b_k: for t <= 2,
+//     G / sigma2 = sum_k a_k s^k - t^{2 nu} sum_k b_k s^k, s = t^2 / 4
+//     (the power series of I_{-nu} and I_nu in K_nu = pi (I_{-nu} - I_nu) / (2 sin(nu pi)));
+//   then KC_CHEB_P pieces of KC_CHEB_N Chebyshev coefficients: piece p fits
+//     e^t sqrt(t) K_nu(t) on [2^{p+1}, 2^{p+2}].
+constexpr int KC_ISER = 24;
+constexpr int KC_CHEB_N = 24;
+constexpr int KC_CHEB_P = 9;
+constexpr int KC_COEF_LEN = 2 * KC_ISER + KC_CHEB_P * KC_CHEB_N;
+void matern_coef_table(const KernelParams& kp, double* tab);
+// Fill a device table (dst, KC_COEF_LEN doubles) for kp and point kp.coef at
+// it; a no-op for kernels without one.
+kc_status upload_coef(KernelParams& kp, double* dst, cudaStream_t s);
+// Same with the table taken from the arena.
+kc_status upload_coef(KernelParams& kp, Arena& A, cudaStream_t s);
 
 template <typename T>
 __device__ __forceinline__ T warp_sum(T v) {

@@ -978,6 +978,7 @@ kc_status factor_impl(const kc_pattern* P, const double* x, int d, const kc_kern
     F.x = x;
     auto_rows(F);
     Arena A(s);
+    KC_TRY(upload_coef(F.kp, A, s));
     KC_TRY(build_tasks(P, F.rpt, A, s, &F.tasks, &F.ntasks, &F.maxr, F.adaptive != 0));
     pick_hash(F);
     KC_TRY(A.get(&F.done, P->N));
@@ -1053,11 +1054,21 @@ kc_status plan_create_impl(const kc_pattern* P, const double* x, int d, const kc
     if ((st = plan_alloc(pl, (void**)&F.ticket, 64)) != KC_OK) return bail(st);
     if ((st = plan_alloc(pl, (void**)&F.zp, 64)) != KC_OK) return bail(st);
     if ((st = plan_alloc(pl, (void**)&F.status, 64)) != KC_OK) return bail(st);
+    if (F.kp.nu_code == 3) {
+        double* tab;
+        if ((st = plan_alloc(pl, (void**)&tab, sizeof(double) * KC_COEF_LEN)) != KC_OK) return bail(st);
+        if ((st = upload_coef(F.kp, tab, s)) != KC_OK) return bail(st);
+    }
     if (nsets > 1) {
         std::vector<KernelParams> h(nsets);
         for (int k = 0; k < nsets; ++k) {
             if ((st = kernel_params(&kerns[k], &h[k])) != KC_OK) return bail(st);
             if (h[k].nu_code > 2) F.general = true;
+            if (h[k].nu_code == 3) {
+                double* tab;
+                if ((st = plan_alloc(pl, (void**)&tab, sizeof(double) * KC_COEF_LEN)) != KC_OK) return bail(st);
+                if ((st = upload_coef(h[k], tab, s)) != KC_OK) return bail(st);
+            }
         }
         if ((st = plan_alloc(pl, (void**)&F.kps, sizeof(KernelParams) * nsets)) != KC_OK) return bail(st);
         if (cudaMemcpy(F.kps, h.data(), sizeof(KernelParams) * nsets, cudaMemcpyHostToDevice) != cudaSuccess)

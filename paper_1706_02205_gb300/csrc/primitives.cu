@@ -4,7 +4,10 @@
 #include <cmath>
 #include <atomic>
 
+#include <vector>
+
 #include "common.cuh"
+#include "covariance.cuh"
 
 namespace kc {
 
@@ -102,8 +105,59 @@ kc_status kernel_params(const kc_kernel* k, KernelParams* out) {
         out->gm = 1.0 / (even - mu * odd);  // Gamma(1 - mu)
         out->fact = mu == 0.0 ? 1.0 : mu * M_PI / sin(mu * M_PI);
         out->lognorm = (1.0 - k->nu) * log(2.0) - lgamma(k->nu);
+        out->iser = fabs(mu) >= 0.02 ? 1 : 0;
+        out->cheb = k->nu <= 8.0 ? 1 : 0;
     }
     return KC_OK;
+}
+
+void matern_coef_table(const KernelParams& kp, double* tab) {
+    const double nu = kp.nu;
+    // power series: a_0 = 1 (reflection formula), a_k = a_{k-1} / (k (k - nu));
+    // b_0 = 4^{-nu} Gamma(1 - nu) / Gamma(1 + nu), b_k = b_{k-1} / (k (k + nu))
+    double a = 1.0, b = kp.iser ? pow(4.0, -nu) * tgamma(1.0 - nu) / tgamma(1.0 + nu) : 0.0;
+    for (int k = 0; k < KC_ISER; ++k) {
+        if (k > 0) {
+            a /= k * (k - nu);
+            b /= k * (k + nu);
+        }
+        tab[k] = kp.iser ? a : 0.0;
+        tab[KC_ISER + k] = b;
+    }
+    // Chebyshev interpolants of e^t sqrt(t) K_nu(t) on [2^{p+1}, 2^{p+2}]
+    double f[KC_CHEB_N];
+    for (int p = 0; p < KC_CHEB_P; ++p) {
+        double* c = tab + 2 * KC_ISER + p * KC_CHEB_N;
+        for (int j = 0; j < KC_CHEB_N; ++j) {
+            const double t = ldexp(3.0 + cos(M_PI * (j + 0.5) / KC_CHEB_N), p);
+            double g0, g1;
+            steed_scaled(t, kp.mu, g0, g1);
+            f[j] = k_upward(t, kp.mu, kp.n, g0, g1);
+        }
+        for (int k = 0; k < KC_CHEB_N; ++k) {
+            double sum = 0.0;
+            for (int j = 0; j < KC_CHEB_N; ++j) sum += f[j] * cos(M_PI * k * (j + 0.5) / KC_CHEB_N);
+            c[k] = kp.cheb ? 2.0 * sum / KC_CHEB_N : 0.0;
+        }
+    }
+}
+
+kc_status upload_coef(KernelParams& kp, double* dst, cudaStream_t s) {
+    if (kp.nu_code != 3) return KC_OK;
+    std::vector<double> tab(KC_COEF_LEN);
+    matern_coef_table(kp, tab.data());
+    // from pageable memory the call returns once the table is staged, so it may
+    // go out of scope afterwards
+    KC_CUDA(cudaMemcpyAsync(dst, tab.data(), sizeof(double) * KC_COEF_LEN, cudaMemcpyHostToDevice, s));
+    kp.coef = dst;
+    return KC_OK;
+}
+
+kc_status upload_coef(KernelParams& kp, Arena& A, cudaStream_t s) {
+    if (kp.nu_code != 3) return KC_OK;
+    double* dst;
+    KC_TRY(A.get(&dst, KC_COEF_LEN));
+    return upload_coef(kp, dst, s);
 }
 
 // ------------------------------------------------------------------ scan

@@ -169,6 +169,7 @@ kc_status refine_impl(const kc_pattern* P, const double* x_ord, int d, const kc_
     int ns = 1;
     while (ns < nrhs) ns <<= 1;  // padded slot count (extra columns stay zero)
     Arena A(s);
+    KC_TRY(upload_coef(kp, A, s));
     Solver S;
     KC_TRY(solver_init(S, P, ns, o, A, s));
     const int64_t n = N * ns;
@@ -379,6 +380,7 @@ kc_status pca_error_impl(const double* x, int64_t N, int d, const kc_kernel* ker
     KC_TRY(kernel_params(kern, &kp));
     if (d > 4) return fail(KC_EINVAL, "kc_pca_error supports d <= 4");
     Arena A(s);
+    KC_TRY(upload_coef(kp, A, s));
     double *v, *w, *c, *partial, *sc;
     KC_TRY(A.get(&v, N));
     KC_TRY(A.get(&w, N));

@@ -5,9 +5,9 @@
 //
 // L z is a gather along the CSR rows of L (one warp per row, lanes over its
 // entries, coalesced col/val reads); L^T v a gather along the columns through
-// the CSC of the pattern (one warp per column; rowidx and slot coalesced, the
-// values fetched through slot).  No atomics: each output is one warp's sum in
-// a fixed order, so results repeat bit for bit.  Vectors are point-major
+// the CSC of the pattern (one warp per chunk of a column; rowidx and slot
+// coalesced, the values fetched through slot).  No atomics: each output is a
+// sum in a fixed order, so results repeat bit for bit.  Vectors are point-major
 // inside (x[k * NS + r], NS = nrhs padded to a power of two), so one point's
 // components share a 32-byte sector.
 #include <algorithm>
@@ -59,46 +59,124 @@ __global__ void __launch_bounds__(TK_THREADS) l_rows_k(const int64_t* __restrict
 }
 
 // y = L^T v: column i of L is rowidx[colptr[i] .. colptr[i+1]), the diagonal
-// first; slot gives each entry's CSR position in val.
-template <typename T, int NS>
-__global__ void __launch_bounds__(TK_THREADS) lt_cols_k(const int64_t* __restrict__ colptr,
-                                                        const int32_t* __restrict__ rowidx,
-                                                        const int64_t* __restrict__ slot, const T* __restrict__ val,
-                                                        const double* __restrict__ diag, int64_t N,
-                                                        const double* __restrict__ v, double* __restrict__ y) {
-    const int64_t i = (int64_t)blockIdx.x * TK_WARPS + (threadIdx.x >> 5);
+// first; slot gives each entry's CSR position in val.  Maximin columns are
+// very uneven (the first column holds every point), so each column is cut
+// into chunks of at most LT_CHUNK entries below its diagonal, one warp per
+// chunk; a column of one chunk writes its result directly, a longer one
+// leaves per-chunk sums that lt_finish_k adds in chunk order.
+constexpr int LT_CHUNK = 1024;
+
+__global__ void lt_count_k(const int64_t* __restrict__ colptr, int64_t N, int32_t* __restrict__ cnt) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
+    const int64_t len = colptr[i + 1] - colptr[i] - 1;
+    cnt[i] = len <= LT_CHUNK ? 1 : (int32_t)((len + LT_CHUNK - 1) / LT_CHUNK);
+}
+
+__global__ void lt_owner_k(const int64_t* __restrict__ off, int64_t N, int32_t* __restrict__ owner) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    for (int64_t c = off[i]; c < off[i + 1]; ++c) owner[c] = (int32_t)i;
+}
+
+template <typename T, int NS>
+__global__ void __launch_bounds__(TK_THREADS) lt_chunks_k(const int64_t* __restrict__ colptr,
+                                                          const int32_t* __restrict__ rowidx,
+                                                          const int64_t* __restrict__ slot, const T* __restrict__ val,
+                                                          const double* __restrict__ diag,
+                                                          const int64_t* __restrict__ off,
+                                                          const int32_t* __restrict__ owner, int64_t N,
+                                                          const double* __restrict__ v, double* __restrict__ y,
+                                                          double* __restrict__ part) {
+    const int64_t c = (int64_t)blockIdx.x * TK_WARPS + (threadIdx.x >> 5);
+    if (c >= off[N]) return;
+    const int i = owner[c];
+    const int64_t k = c - off[i];
+    const int64_t q0 = colptr[i] + 1 + k * LT_CHUNK;
+    const int64_t q1 = min(colptr[i + 1], q0 + LT_CHUNK);
     double acc[NS];
 #pragma unroll
     for (int r = 0; r < NS; ++r) acc[r] = 0.0;
-    const int64_t q1 = colptr[i + 1];
-    for (int64_t q = colptr[i] + 1 + lane_id(); q < q1; q += 32)
+    for (int64_t q = q0 + lane_id(); q < q1; q += 32)
         gather_fma<NS>(acc, (double)__ldg(&val[__ldg(&slot[q])]), v, __ldg(&rowidx[q]));
-    finish_row<NS>(acc, diag[i], v, i, y);
+    if (off[i + 1] - off[i] == 1) {
+        finish_row<NS>(acc, diag[i], v, i, y);
+    } else {
+        const int lane = lane_id();
+        double mine = 0.0;
+#pragma unroll
+        for (int r = 0; r < NS; ++r) {
+            const double t = warp_sum(acc[r]);
+            if (lane == r) mine = t;
+        }
+        if (lane < NS) part[c * NS + lane] = mine;
+    }
+}
+
+// y[i][r] of the columns cut into several chunks: the chunk sums in order
+template <int NS>
+__global__ void lt_finish_k(const int64_t* __restrict__ off, int64_t N, const double* __restrict__ diag,
+                            const double* __restrict__ v, const double* __restrict__ part, double* __restrict__ y) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= N * NS) return;
+    const int64_t i = t / NS;
+    const int r = (int)(t % NS);
+    const int64_t c0 = off[i], c1 = off[i + 1];
+    if (c1 - c0 == 1) return;
+    double s = 0.0;
+    for (int64_t c = c0; c < c1; ++c) s += part[c * NS + r];
+    y[i * NS + r] = fma(diag[i], v[i * NS + r], s);
+}
+
+// Chunk layout of the columns (independent of the vectors): off[i] = first
+// chunk of column i, off[N] = chunks in all; owner[c] = column of chunk c.
+struct LtChunks {
+    int64_t* off = nullptr;
+    int32_t* owner = nullptr;
+    int64_t cap = 0;  // chunks at most: N + (nnz - N) / LT_CHUNK
+};
+
+static kc_status lt_chunks_build(const kc_pattern* P, Arena& A, cudaStream_t s, LtChunks& C) {
+    const int64_t N = P->N;
+    C.cap = N + (P->nnz - N) / LT_CHUNK + 1;
+    int32_t* cnt;
+    KC_TRY(A.get(&cnt, N));
+    KC_TRY(A.get(&C.off, N + 1));
+    KC_TRY(A.get(&C.owner, C.cap));
+    note_launch(), lt_count_k<<<blocks_for(N, 256), 256, 0, s>>>(P->colptr, N, cnt);
+    KC_CUDA(cudaGetLastError());
+    KC_TRY(exclusive_scan_i32_to_i64(cnt, C.off, N, A, s));
+    note_launch(), lt_owner_k<<<blocks_for(N, 256), 256, 0, s>>>(C.off, N, C.owner);
+    KC_CUDA(cudaGetLastError());
+    return KC_OK;
 }
 
 template <typename T, int NS>
 static kc_status mv_launch(const kc_pattern* P, bool transpose, const T* val, const double* diag, const double* in,
-                           double* out, cudaStream_t s) {
-    const unsigned g = blocks_for(P->N, TK_WARPS);
-    if (transpose)
-        note_launch(), lt_cols_k<T, NS><<<g, TK_THREADS, 0, s>>>(P->colptr, P->rowidx, P->slot, val, diag, P->N, in,
-                                                                 out);
-    else
-        note_launch(), l_rows_k<T, NS><<<g, TK_THREADS, 0, s>>>(P->rowptr, P->col, val, diag, P->N, in, out);
+                           double* out, const LtChunks& C, double* part, cudaStream_t s) {
+    if (transpose) {
+        // the grid covers the most chunks there can be; surplus warps return
+        note_launch(), lt_chunks_k<T, NS><<<blocks_for(C.cap, TK_WARPS), TK_THREADS, 0, s>>>(
+            P->colptr, P->rowidx, P->slot, val, diag, C.off, C.owner, P->N, in, out, part);
+        KC_CUDA(cudaGetLastError());
+        note_launch(), lt_finish_k<NS><<<blocks_for(P->N * NS, 256), 256, 0, s>>>(C.off, P->N, diag, in, part, out);
+    } else {
+        note_launch(), l_rows_k<T, NS><<<blocks_for(P->N, TK_WARPS), TK_THREADS, 0, s>>>(P->rowptr, P->col, val, diag,
+                                                                                         P->N, in, out);
+    }
     KC_CUDA(cudaGetLastError());
     return KC_OK;
 }
 
 template <typename T>
 static kc_status mv_dispatch(const kc_pattern* P, bool transpose, const T* val, const double* diag, const double* in,
-                             double* out, int ns, cudaStream_t s) {
+                             double* out, int ns, const LtChunks& C, double* part, cudaStream_t s) {
     switch (ns) {
-        case 1: return mv_launch<T, 1>(P, transpose, val, diag, in, out, s);
-        case 2: return mv_launch<T, 2>(P, transpose, val, diag, in, out, s);
-        case 4: return mv_launch<T, 4>(P, transpose, val, diag, in, out, s);
-        case 8: return mv_launch<T, 8>(P, transpose, val, diag, in, out, s);
-        default: return mv_launch<T, 16>(P, transpose, val, diag, in, out, s);
+        case 1: return mv_launch<T, 1>(P, transpose, val, diag, in, out, C, part, s);
+        case 2: return mv_launch<T, 2>(P, transpose, val, diag, in, out, C, part, s);
+        case 4: return mv_launch<T, 4>(P, transpose, val, diag, in, out, C, part, s);
+        case 8: return mv_launch<T, 8>(P, transpose, val, diag, in, out, C, part, s);
+        default: return mv_launch<T, 16>(P, transpose, val, diag, in, out, C, part, s);
     }
 }
 
@@ -111,13 +189,18 @@ kc_status factor_matvec_impl(const kc_pattern* P, int prec, const void* val, con
     int ns = 1;
     while (ns < nrhs) ns <<= 1;
     Arena A(s);
-    double *a, *b;
+    double *a, *b, *part = nullptr;
     KC_TRY(A.get(&a, P->N * ns));
     KC_TRY(A.get(&b, P->N * ns));
+    LtChunks C;
+    if (which != 0) {
+        KC_TRY(lt_chunks_build(P, A, s, C));
+        KC_TRY(A.get(&part, C.cap * ns));
+    }
     KC_TRY(to_point_major(in, perm, P->N, nrhs, a, s, ns));
     auto step = [&](bool tr, const double* x, double* y) {
-        return prec == KC_FP64 ? mv_dispatch<double>(P, tr, (const double*)val, diag, x, y, ns, s)
-                               : mv_dispatch<float>(P, tr, (const float*)val, diag, x, y, ns, s);
+        return prec == KC_FP64 ? mv_dispatch<double>(P, tr, (const double*)val, diag, x, y, ns, C, part, s)
+                               : mv_dispatch<float>(P, tr, (const float*)val, diag, x, y, ns, C, part, s);
     };
     const double* res = b;
     if (which == 0) KC_TRY(step(false, a, b));
@@ -218,6 +301,8 @@ kc_status kernel_eval_impl(const kc_kernel* kern, int prec, const double* r, int
     KC_TRY(kernel_params(kern, &kp));
     if (prec != KC_FP64 && prec != KC_FP32_FORM) return fail(KC_EINVAL, "prec must be KC_FP64 or KC_FP32_FORM");
     if (n == 0) return KC_OK;
+    Arena A(s);
+    KC_TRY(upload_coef(kp, A, s));
     note_launch(), kernel_eval_k<<<blocks_for(n, 256), 256, 0, s>>>(kp, prec, r, n, out);
     KC_CUDA(cudaGetLastError());
     return KC_OK;

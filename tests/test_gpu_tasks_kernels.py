@@ -77,6 +77,21 @@ def test_kernel_eval_matches_oracle(name, kw):
     assert got[0] == 1.0 and got32[0] == 1.0
 
 
+@pytest.mark.parametrize("nu", [0.01, 0.3, 1.01, 1.98, 2.0, 4.4, 7.9, 9.3, 20.5])
+def test_kernel_eval_every_branch(nu):
+    """Orders that take each evaluation path: the power series (t <= 2) or
+    Temme's series (nu within 0.02 of an integer); the Chebyshev pieces
+    (t > 2, nu <= 8) or Steed's continued fraction (nu > 8); zero beyond
+    t = 1024."""
+    kg, ko = pair(nu=nu, ell=0.1)
+    t = np.concatenate([[0.0], np.geomspace(1e-6, 2.0, 400), np.linspace(2.0, 40.0, 800)[1:],
+                        np.geomspace(40.0, 1100.0, 300)])
+    r = t * 0.1 / math.sqrt(2 * nu)
+    want = np.array([oracle.cov(v, ko) for v in r])
+    got = H(kc.kernel_eval(kg, kc.FP64, T(r)))
+    np.testing.assert_allclose(got, want, rtol=1e-12, atol=1e-300)
+
+
 def test_kernel_eval_empty_and_bad_args():
     kg, _ = pair(nu=0.8)
     assert kc.kernel_eval(kg, kc.FP64, torch.empty(0, dtype=torch.float64, device=DEV)).numel() == 0

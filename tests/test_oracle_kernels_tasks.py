@@ -24,12 +24,35 @@ from tests import refmath
 scipy_special = pytest.importorskip("scipy.special")
 
 
-@pytest.mark.parametrize("nu", [0.1, 0.3, 0.5, 0.75, 1.0, 1.5, 2.2, 3.7, 7.5])
+@pytest.mark.parametrize("nu", [0.01, 0.1, 0.3, 0.5, 0.75, 1.0, 1.01, 1.5, 1.98, 2.2, 3.7, 7.5, 9.3, 20.5])
 def test_bessel_k_vs_scipy(nu):
     x = np.geomspace(1e-6, 300.0, 120)
     got = np.array([oracle.bessel_k(nu, v) for v in x])
     want = scipy_special.kv(nu, x)
-    np.testing.assert_allclose(got, want, rtol=2e-13)
+    m = want < 1e300  # SciPy's range
+    np.testing.assert_allclose(got[m], want[m], rtol=2e-13)
+
+
+@pytest.mark.parametrize("nu", [0.3, 1.01, 3.7, 20.5])
+def test_bessel_k_scaled_vs_scipy(nu):
+    """e^x K_nu(x) against SciPy's kve, out to x where K_nu underflows."""
+    x = np.geomspace(1e-4, 5000.0, 200)
+    got = np.array([oracle.bessel_k_scaled(nu, v) for v in x])
+    want = scipy_special.kve(nu, x)
+    m = want < 1e300
+    np.testing.assert_allclose(got[m], want[m], rtol=2e-13)
+
+
+def test_matern_far_tail_vs_bessel():
+    """Where K_nu(t) is below the normal double range the Matern value is
+    still right (e^{-t} taken with the other factors)."""
+    from scipy.special import gammaln
+    for nu in (3.3, 20.5):
+        t = np.linspace(500.0, 720.0, 40)
+        r = t * 0.1 / np.sqrt(2 * nu)
+        want = np.exp((1 - nu) * np.log(2) - gammaln(nu) + nu * np.log(t) - t) * scipy_special.kve(nu, t)
+        got = np.array([oracle.matern(v, nu, 0.1) for v in r])
+        np.testing.assert_allclose(got, want, rtol=1e-12, atol=0)
 
 
 def test_bessel_k_half_integer_closed_forms():
