@@ -27,6 +27,10 @@ Owhadi, arXiv:1706.02205):
                             columns (Section 2.5).
 * ``l_matvec`` / ``lt_matvec`` / ``logdet`` -- tasks (1), (3), (4) of Section 1
                             with the factor: L z, L^T v, 2 sum log L_ii.
+* ``ichol_given`` / ``pattern_reverse`` / ``gather_entries`` / ``reverse_factor``
+                         -- Section 6: ICHOL(0) of a given sparse matrix (the
+                            precision matrix, or sigma^2 A + I) in the reverse
+                            maximin order on the min-rule pattern.
 * ``work_counters``      -- exact multiply-add / merge-step / operand counts of
                             the left-looking factor (roofline denominators).
 
@@ -102,6 +106,11 @@ def lib():
         L.ko_csr_to_csc.argtypes = [i, i64p, i32p, i64p, i32p, i64p]
         L.ko_ichol.restype = i
         L.ko_ichol.argtypes = [f64p, i, I, K, i64p, i32p, f64p, u8p, I, C.c_void_p, I]
+        L.ko_ichol_given.restype = i
+        L.ko_ichol_given.argtypes = [i, i64p, i32p, f64p, f64p, u8p, I, I]
+        L.ko_pattern_reverse.argtypes = [i, i64p, i32p, i64p, i32p]
+        L.ko_gather_entries.restype = i
+        L.ko_gather_entries.argtypes = [i, i64p, i32p, i32p, i64p, i32p, f64p, f64p]
         L.ko_solve_lower.argtypes = [i, i64p, i32p, f64p, f64p, f64p, f64p]
         L.ko_solve_upper.argtypes = [i, i64p, i32p, f64p, f64p, f64p, f64p]
         L.ko_l_matvec.argtypes = [i, i64p, i32p, f64p, f64p, f64p]
@@ -271,6 +280,59 @@ def ichol(x_ord, rowptr, col, kern: Kernel, reverse_sums=False, pivots=False, st
     if pivots:
         return val, zc.astype(bool), piv
     return val, zc.astype(bool)
+
+
+def ichol_given(rowptr, col, aval, reverse_sums=False, store_f32=False):
+    """ICHOL(0) of a given symmetric matrix on the pattern: aval[e] is its entry
+    at the CSR position e (Section 6).  Returns (val, zero_col)."""
+    N = rowptr.shape[0] - 1
+    val = np.zeros(int(rowptr[-1]), np.float64)
+    zc = np.zeros(N, np.int8)
+    lib().ko_ichol_given(N, np.ascontiguousarray(rowptr, np.int64), np.ascontiguousarray(col, np.int32),
+                         np.ascontiguousarray(aval, np.float64), val, zc, int(bool(reverse_sums)),
+                         int(bool(store_f32)))
+    return val, zc.astype(bool)
+
+
+def pattern_reverse(colptr, rowidx):
+    """CSR (rowptr, col) of a symmetric pattern in the reversed order, from the
+    CSC of its lower triangle in the original (maximin) order (Section 6)."""
+    N = colptr.shape[0] - 1
+    rowptr = np.zeros(N + 1, np.int64)
+    col = np.zeros(int(colptr[-1]), np.int32)
+    lib().ko_pattern_reverse(N, np.ascontiguousarray(colptr, np.int64), np.ascontiguousarray(rowidx, np.int32),
+                             rowptr, col)
+    return rowptr, col
+
+
+def gather_entries(rowptr, col, orig, a_rowptr, a_col, a_val):
+    """(aval, outside): the given matrix (CSR in original numbering) at every
+    pattern position (orig: position -> original index), and the number of
+    its off-diagonal entries outside the pattern."""
+    N = rowptr.shape[0] - 1
+    aval = np.zeros(int(rowptr[-1]), np.float64)
+    out = lib().ko_gather_entries(N, np.ascontiguousarray(rowptr, np.int64), np.ascontiguousarray(col, np.int32),
+                                  np.ascontiguousarray(orig, np.int32), np.ascontiguousarray(a_rowptr, np.int64),
+                                  np.ascontiguousarray(a_col, np.int32), np.ascontiguousarray(a_val, np.float64),
+                                  aval)
+    return aval, int(out)
+
+
+def reverse_factor(x, a_rowptr, a_col, a_val, rho, store_f32=False):
+    """Section 6: maximin ordering of x, the min-rule pattern, reversed, the
+    given matrix gathered onto it and factored.  Returns a dict with the
+    reversed order (orig[q] = original index of position q), the pattern,
+    the entries, the factor and its dropped columns."""
+    x, N, d = _pts(x)
+    perm, l = maximin_brute(x)
+    rp, col = pattern(x[perm], l, rho, RULE_MIN)
+    colptr, rowidx, _ = csr_to_csc(rp, col)
+    rrp, rcol = pattern_reverse(colptr, rowidx)
+    orig = np.ascontiguousarray(perm[::-1])
+    aval, outside = gather_entries(rrp, rcol, orig, a_rowptr, a_col, a_val)
+    val, zc = ichol_given(rrp, rcol, aval, store_f32=store_f32)
+    return dict(perm=perm, l=l, orig=orig, rowptr=rrp, col=rcol, aval=aval, outside=outside, val=val,
+                zero_col=zc)
 
 
 def diag_of(rowptr, val):

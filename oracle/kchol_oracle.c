@@ -431,9 +431,16 @@ void ko_csr_to_csc(i64 N, const i64* rowptr, const i32* col, i64* colptr, i32* r
 /* size test tolerances.  Returns the number of zeroed columns.              */
 /* ------------------------------------------------------------------------ */
 
-i64 ko_ichol(const double* xo, i64 N, i32 d, const ko_kernel* K,
-             const i64* rowptr, const i32* col, double* val, char* zero_col, i32 rev, double* piv,
-             i32 store_f32) {
+/* Entries of the matrix being factored, by CSR position e of (j, i) in the  */
+/* pattern: from the covariance function (xo, K) or, when aval is given,    */
+/* aval[e] (the matrix given on the pattern, Section 6).                    */
+static double entry_at(const double* xo, i32 d, const ko_kernel* K, const double* aval, i64 e, i64 j, i64 i) {
+    return aval ? aval[e] : theta_pos(xo, d, j, i, K);
+}
+
+static i64 ichol_any(const double* xo, i64 N, i32 d, const ko_kernel* K, const double* aval,
+                     const i64* rowptr, const i32* col, double* val, char* zero_col, i32 rev, double* piv,
+                     i32 store_f32) {
     i64 nnz = rowptr[N];
     i64* colptr = (i64*)malloc(sizeof(i64) * ((size_t)N + 1));
     i32* rowidx = (i32*)malloc(sizeof(i32) * (size_t)(nnz > 0 ? nnz : 1));
@@ -443,7 +450,7 @@ i64 ko_ichol(const double* xo, i64 N, i32 d, const ko_kernel* K,
     i64 zeroed = 0;
     for (i64 i = 0; i < N; ++i) {
         i64 a0 = rowptr[i], a1 = rowptr[i + 1] - 1; /* row i without its diagonal: [a0, a1) */
-        double p = theta_pos(xo, d, i, i, K);
+        double p = entry_at(xo, d, K, aval, a1, i, i);
         if (!rev) for (i64 e = a0; e < a1; ++e) p -= val[e] * val[e];
         else for (i64 e = a1 - 1; e >= a0; --e) p -= val[e] * val[e];
         if (piv) piv[i] = p;
@@ -459,7 +466,7 @@ i64 ko_ichol(const double* xo, i64 N, i32 d, const ko_kernel* K,
             i64 b0 = rowptr[j];
             i64 bij = slot[q];                 /* position of (j,i) in row j */
             /* merge row j (k < i) with row i (k < i) */
-            double s = theta_pos(xo, d, j, i, K);
+            double s = entry_at(xo, d, K, aval, bij, j, i);
             if (store_f32) s = (double)(float)s;
             if (!rev) {
                 i64 u = a0, v = b0;
@@ -484,6 +491,73 @@ i64 ko_ichol(const double* xo, i64 N, i32 d, const ko_kernel* K,
     }
     free(colptr); free(rowidx); free(slot);
     return zeroed;
+}
+
+i64 ko_ichol(const double* xo, i64 N, i32 d, const ko_kernel* K,
+             const i64* rowptr, const i32* col, double* val, char* zero_col, i32 rev, double* piv,
+             i32 store_f32) {
+    return ichol_any(xo, N, d, K, NULL, rowptr, col, val, zero_col, rev, piv, store_f32);
+}
+
+/* ICHOL(0) of a given symmetric matrix A: aval[e] is A_ji for the CSR entry */
+/* e = (j, i), i <= j, of the pattern (Section 6: the reverse-order factor    */
+/* of the precision matrix, or of sigma^2 A + I for a nugget).               */
+i64 ko_ichol_given(i64 N, const i64* rowptr, const i32* col, const double* aval, double* val, char* zero_col,
+                   i32 rev, i32 store_f32) {
+    return ichol_any(NULL, N, 0, NULL, aval, rowptr, col, val, zero_col, rev, NULL, store_f32);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Reverse elimination order (Section 6): position q of the reversed order   */
+/* is position N-1-q of the maximin order.  The lower triangle of a          */
+/* symmetric pattern in reversed positions is the upper one in maximin      */
+/* positions: row q lists N-1-b for the rows b of maximin column a = N-1-q   */
+/* (b >= a), ascending, so the diagonal comes last.  colptr/rowidx: the CSC  */
+/* of the maximin-order lower triangle.                                      */
+/* ------------------------------------------------------------------------ */
+
+void ko_pattern_reverse(i64 N, const i64* colptr, const i32* rowidx, i64* rowptr_out, i32* col_out) {
+    rowptr_out[0] = 0;
+    for (i64 q = 0; q < N; ++q) {
+        i64 a = N - 1 - q;
+        rowptr_out[q + 1] = rowptr_out[q] + (colptr[a + 1] - colptr[a]);
+    }
+    for (i64 q = 0; q < N; ++q) {
+        i64 a = N - 1 - q, w = rowptr_out[q];
+        for (i64 e = colptr[a + 1] - 1; e >= colptr[a]; --e) col_out[w++] = (i32)(N - 1 - rowidx[e]);
+    }
+}
+
+/* aval[e] = A(orig[j], orig[i]) for each CSR entry e = (j, i) of the        */
+/* pattern, where orig maps a position to its original index and A is given  */
+/* by CSR rows in original numbering (columns ascending); 0 where A has no   */
+/* entry.  Returns the number of A's entries (u, v), u != v, whose position   */
+/* pair is not in the pattern (ICHOL(0) drops them, Algorithm 2).           */
+i64 ko_gather_entries(i64 N, const i64* rowptr, const i32* col, const i32* orig, const i64* arp, const i32* acol,
+                      const double* aval_in, double* aval) {
+    for (i64 j = 0; j < N; ++j)
+        for (i64 e = rowptr[j]; e < rowptr[j + 1]; ++e) {
+            i64 u = orig[j], v = orig[col[e]];
+            double a = 0.0;
+            for (i64 f = arp[u]; f < arp[u + 1]; ++f)
+                if (acol[f] == v) { a = aval_in[f]; break; }
+            aval[e] = a;
+        }
+    i32* pos = (i32*)malloc(sizeof(i32) * (size_t)(N > 0 ? N : 1));
+    for (i64 q = 0; q < N; ++q) pos[orig[q]] = (i32)q;
+    i64 outside = 0;
+    for (i64 u = 0; u < N; ++u)
+        for (i64 f = arp[u]; f < arp[u + 1]; ++f) {
+            i64 v = acol[f];
+            if (v == u) continue;
+            i64 j = pos[u] > pos[v] ? pos[u] : pos[v], i = pos[u] > pos[v] ? pos[v] : pos[u];
+            int found = 0;
+            for (i64 e = rowptr[j]; e < rowptr[j + 1]; ++e)
+                if (col[e] == i) { found = 1; break; }
+            if (!found) outside++;
+        }
+    free(pos);
+    return outside;
 }
 
 /* ------------------------------------------------------------------------ */

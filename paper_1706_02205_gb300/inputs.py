@@ -22,6 +22,12 @@ Workloads
 * ``rhs(N, nrhs)``: right-hand sides ~ N(0, I), column-major (N x nrhs).
 * ``sample_pairs(N, m)``: index pairs i.i.d. uniform on I x I, the sample the
   paper's error estimator E draws (Section 4.4).
+* ``grid_operator(n_side)``: a sparse symmetric positive-definite matrix on the
+  nodes of an n_side x n_side grid in [0,1]^2 -- the 5-point graph Laplacian
+  with seeded rough edge weights (log-uniform in [1/10, 10]) plus a
+  zeroth-order term -- standing in for the discretised elliptic operators
+  whose inverse is a kernel matrix (Section 6); nodes listed in a seeded
+  random order, matrix given by CSR rows in that order.
 """
 from __future__ import annotations
 
@@ -143,3 +149,36 @@ def request_points(req) -> np.ndarray:
     if req["kind"] == "swiss":
         return swiss_roll(req["N"], ambient=req["d"], seed=req["seed"])
     return uniform(req["N"], req["d"], seed=req["seed"])
+
+
+def grid_operator(n_side: int, shift: float = 1.0, contrast: float = 10.0, seed: int = seed_for(6)):
+    """(x, rowptr, col, val): nodes x (N, 2), N = n_side^2, and the CSR rows
+    (columns ascending, diagonal included) of A = sum over grid edges (u, v)
+    of w_uv (e_u - e_v)(e_u - e_v)^T + shift * I, w_uv log-uniform in
+    [1/contrast, contrast], scaled by n_side^2 (the mesh size h^-2)."""
+    r = rng(seed)
+    N = n_side * n_side
+    h = 1.0 / n_side
+    gi, gj = np.meshgrid(np.arange(n_side), np.arange(n_side), indexing="ij")
+    order = r.permutation(N)            # node of each list position
+    pos = np.empty(N, np.int64)
+    pos[order] = np.arange(N)
+    x = np.stack([(gi.ravel() + 0.5) * h, (gj.ravel() + 0.5) * h], 1)[order]
+    node = np.arange(N).reshape(n_side, n_side)
+    eu = np.concatenate([node[:-1, :].ravel(), node[:, :-1].ravel()])
+    ev = np.concatenate([node[1:, :].ravel(), node[:, 1:].ravel()])
+    w = np.exp(r.uniform(-math.log(contrast), math.log(contrast), eu.shape[0])) * n_side * n_side
+    u, v = pos[eu], pos[ev]
+    rows = np.concatenate([u, v, u, v, np.arange(N)])
+    cols = np.concatenate([v, u, u, v, np.arange(N)])
+    vals = np.concatenate([-w, -w, w, w, np.full(N, shift)])
+    key = rows * N + cols
+    o = np.argsort(key, kind="stable")
+    key, vals = key[o], vals[o]
+    uk, start = np.unique(key, return_index=True)
+    sums = np.add.reduceat(vals, start)
+    rr, cc = uk // N, uk % N
+    rowptr = np.zeros(N + 1, np.int64)
+    np.add.at(rowptr, rr + 1, 1)
+    rowptr = np.cumsum(rowptr)
+    return x, rowptr, cc.astype(np.int32), sums
