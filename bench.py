@@ -289,14 +289,14 @@ def run_ours(args, rank, world):
 # ------------------------------------------------ other workloads (ours)
 
 # DRAM traffic of the FP32-form factor kernel per algorithmic byte, from the ncu capture summarised in
-# profiles/ichol_fp32_jittered512_ncu_full.md (512x512 grid: dram read + write = 27.503 GB for
+# profiles/ichol_fp32_jittered512_ncu_full.md (512x512 grid: dram read + write = 27.497 GB for
 # B_op = 26.388 GB).  Both are sums over the same (j, i) pairs, so the ratio carries to the full size.
 # It is reported only while the kernel sources are the ones the counters were taken on.
 TRAFFIC_CAPTURE = {"sources": ("paper_1706_02205_gb300/csrc/factor.cu", "paper_1706_02205_gb300/csrc/common.cuh",
                                "paper_1706_02205_gb300/csrc/grid.cuh", "paper_1706_02205_gb300/csrc/covariance.cuh",
                                "include/kchol.h"),
-                   "sha256": "45db5350d0809c9723b0fa52239adfe4ce3e045a0e2858db4da08d71e5515600",
-                   "dram_per_algorithmic_byte": (26.561619 + 0.941381) / 26.387813}
+                   "sha256": "2a281c0855e5670c61a21c65898c4eebfab937594eeb04663d72dcbf39e59b19",
+                   "dram_per_algorithmic_byte": (26.555428 + 0.941292) / 26.387813}
 
 
 def factor_traffic(bop):
@@ -386,6 +386,72 @@ def run_tasks(args):
         ms = timed(fn)
         out["calls"][name] = {"ms": ms, "algorithmic_bytes": b, "GB_per_s": b / (ms * 1e-3) / 1e9}
     return out
+
+
+def run_pde(args):
+    """Section 6: the rough-coefficient grid operator (5-point stencil, edge
+    weights log-uniform in [1/10, 10], plus --shift times the identity; the
+    default 100 = 1/l^2 for the range l = 0.1 of the headline kernel) on the
+    n_side x n_side grid, standing in for a precision matrix A = Theta^{-1}: maximin
+    order, min-rule pattern, reversed, A gathered onto it, FP32-form factor,
+    one solve.  Phases timed with CUDA events after warm-up; the residual
+    ||A x - b|| / ||b|| of the approximate direct solve is measured outside."""
+    import torch
+
+    from paper_1706_02205_gb300 import kchol as kc
+    n = args.n_side
+    x_h, rp_h, col_h, val_h = inputs.grid_operator(n, shift=args.shift)
+    x = torch.from_numpy(x_h).cuda()
+    rp, col, val = (torch.from_numpy(a).cuda() for a in (rp_h, col_h, val_h))
+    N = n * n
+    b = torch.from_numpy(inputs.rhs(N, 1, seed=inputs.seed_for(6, 2))).cuda()
+    dmax = float(val_h.max())
+    stream = torch.cuda.current_stream()
+    names = ("order", "pattern", "reverse", "gather", "factor", "solve")
+    ph = {k: [] for k in names}
+    for it in range(args.warmup + args.steps):
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(len(names) + 1)]
+        ev[0].record(stream)
+        perm, l, xo = kc.order_points(x)
+        ev[1].record(stream)
+        pat = kc.build_pattern(xo, l, args.rho, kc.RULE_MIN)
+        ev[2].record(stream)
+        rpat = kc.pattern_reverse(pat, xo)
+        orig = perm.flip(0).contiguous()
+        ev[3].record(stream)
+        aval, _ = kc.gather_entries(rpat, orig, rp, col, val, count_outside=False)
+        ev[4].record(stream)
+        v, dg, zp = kc.factor_given(rpat, aval, kc.FP32_FORM)
+        ev[5].record(stream)
+        xs = kc.solve(rpat, kc.FP32_FORM, v, dg, kc.Kernel(sigma2=dmax), orig, b)
+        ev[6].record(stream)
+        torch.cuda.synchronize()
+        if it >= args.warmup:
+            for k, nm in enumerate(names):
+                ph[nm].append(ev[k].elapsed_time(ev[k + 1]))
+    _, outside = kc.gather_entries(rpat, orig, rp, col, val)
+    A = torch.sparse_csr_tensor(rp, col.long(), val, size=(N, N))
+    res = float(torch.linalg.vector_norm(A @ xs[0] - b[0]) / torch.linalg.vector_norm(b[0]))
+    # CG on A preconditioned by the factor, to 1e-10
+    cg = []
+    for it in range(args.warmup + args.steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        xr, iters, rr, st = kc.refine_sparse(rpat, kc.FP32_FORM, v, dg, orig, rp, col, val, b, rtol=1e-10,
+                                             maxit=500)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if it >= args.warmup:
+            cg.append(e0.elapsed_time(e1))
+    cg_res = float(torch.linalg.vector_norm(A @ xr[0] - b[0]) / torch.linalg.vector_norm(b[0]))
+    med = {k: statistics.median(v_) for k, v_ in ph.items()}
+    return {"workload": f"grid operator {n}x{n} (N={N}), rough coefficients, shift {args.shift}, reverse "
+                        f"maximin order, min-rule rho={args.rho}, FP32 form", "N": N, "nnz": rpat.nnz, "depth": rpat.depth,
+            "zero_pivots": zp, "entries_outside_pattern": outside, "phases_ms": med,
+            "total_ms": sum(med.values()), "factor_nnz_per_s": rpat.nnz / (med["factor"] * 1e-3),
+            "factor_kernel_ms": kc.last_factor_kernel_ms(), "direct_solve_relres": res,
+            "cg_to_1e-10": {"ms": statistics.median(cg), "iterations": iters, "status": st,
+                            "true_relres": cg_res}}
 
 
 def run_factor_only(args):
@@ -626,9 +692,10 @@ def main():
     ap.add_argument("--family", default="matern", choices=["matern", "cauchy"],
                     help="covariance family of the factor-only and tasks workloads")
     ap.add_argument("--alpha", type=float, default=1.0, help="Cauchy alpha")
+    ap.add_argument("--shift", type=float, default=100.0, help="pde workload: zeroth-order term of the operator")
     ap.add_argument("--beta", type=float, default=0.2, help="Cauchy beta")
     ap.add_argument("--workload", default="grid2d",
-                    choices=["grid2d", "cube3d", "factor", "batch", "serve", "refine", "tasks"],
+                    choices=["grid2d", "cube3d", "factor", "batch", "serve", "refine", "tasks", "pde"],
                     help="grid2d: the headline step (default); cube3d: 3-D factor + PCA; factor: factor-only "
                          "probe; batch: many sets in one launch; serve: request stream")
     ap.add_argument("--n3", type=int, default=2**18)
@@ -667,6 +734,8 @@ def main():
         line = run_serve(args)
     elif args.workload == "tasks":
         line = run_tasks(args)
+    elif args.workload == "pde":
+        line = run_pde(args)
     elif args.workload == "refine":
         line = run_refine(args)
     else:

@@ -124,7 +124,8 @@ const char* kc_last_error(void);
 /* Version of this interface (structs and signatures); a binding built for
  * another version must not call the library.  2: kc_schedule takes the points,
  * kc_opts has stage_bytes.  3: kc_kernel has family, alpha, beta;
- * kc_kernel_eval, kc_l_matvec, kc_lt_matvec, kc_llt_matvec, kc_logdet. */
+ * kc_kernel_eval, kc_l_matvec, kc_lt_matvec, kc_llt_matvec, kc_logdet,
+ * kc_pattern_reverse, kc_gather_entries, kc_factor_given, kc_refine_sparse. */
 #define KC_ABI_VERSION 3
 int32_t kc_abi_version(void);
 
@@ -309,6 +310,56 @@ kc_status kc_llt_matvec(const kc_pattern* pat, int32_t prec, const void* val, co
  * Synchronises. */
 kc_status kc_logdet(const kc_pattern* pat, const double* diag, double* logdet_out, int64_t* zero_pivots_out,
                     void* stream);
+
+/* ---- Section 6: factors of a given sparse matrix, reverse order ---------- *
+ * The precision matrix A = Theta^{-1} (a discretised elliptic operator) has
+ * near-sparse Cholesky factors in the reverse maximin order on the pattern
+ * of the min rule, dist(i, j) <= rho min(l[i], l[j]) (kc_pattern_count with
+ * KC_RULE_MIN); so has sigma^2 A + I, which gives Theta + sigma^2 I =
+ * Theta (sigma^2 A + I) for a nugget sigma^2.
+ *
+ * kc_pattern_reverse: from the CSC (colptr int64[N+1], rowidx int32[nnz],
+ * device; kc_schedule's output) of a maximin-order lower-triangular pattern,
+ * the CSR rows (rowptr_out int64[N+1], col_out int32[nnz], device) of the
+ * same symmetric pattern in the reversed order, where position q is maximin
+ * position N-1-q: columns ascending, diagonal last.  Stream-ordered.
+ *
+ * kc_gather_entries: aval_out[e] (device double[nnz]) = A(orig[j], orig[i])
+ * for every entry e = (j, i) of the pattern (rowptr, col, device), where
+ * orig (device int32[N]) maps a position to the original index and A is
+ * N x N, given by CSR rows in original numbering (a_rowptr int64[N+1],
+ * a_col int32, a_val double, device; columns ascending within each row,
+ * both triangles stored); 0 where A has no entry.  outside_out (host, may be
+ * NULL; synchronises when given) = the number of A's off-diagonal entries
+ * (u, v) whose positions are not in the pattern: ICHOL(0) drops them
+ * (Algorithm 2), so a nonzero count means the pattern is too small for A.
+ *
+ * kc_factor_given: ICHOL(0) (Algorithm 2, left-looking form, as kc_factor)
+ * of the symmetric matrix whose lower triangle on pat is aval (device
+ * double[nnz], CSR layout of pat).  val, diag, zero_pivots_out, opts and the
+ * errors as for kc_factor; the FP32 form rounds the entries to float.  A
+ * dropped pivot leaves diag 0: kc_solve then divides by
+ * sqrt(kern->sigma2 + kern->nugget), so pass a kernel whose sigma2 is of the
+ * size of A's diagonal.  Synchronises. */
+kc_status kc_pattern_reverse(int64_t N, const int64_t* colptr, const int32_t* rowidx, int64_t* rowptr_out,
+                             int32_t* col_out, void* stream);
+kc_status kc_gather_entries(int64_t N, const int64_t* rowptr, const int32_t* col, const int32_t* orig,
+                            const int64_t* a_rowptr, const int32_t* a_col, const double* a_val, double* aval_out,
+                            int64_t* outside_out, void* stream);
+kc_status kc_factor_given(const kc_pattern* pat, const double* aval, int32_t prec, void* val, double* diag,
+                          int64_t* zero_pivots_out, const kc_opts* opts, void* stream);
+
+/* CG on A x = b for the given sparse symmetric positive-definite A (CSR in
+ * original numbering as for kc_gather_entries), preconditioned by L L^T, the
+ * factor of kc_factor_given on pat (val in prec, diag; perm: position ->
+ * original index).  A is applied in positions by a sparse product (one warp
+ * per row, FP64, a fixed summation order).  b, x, nrhs, rtol, maxit,
+ * iters_out, relres_out and the errors as for kc_refine; a dropped pivot
+ * divides by 1.  Synchronises. */
+kc_status kc_refine_sparse(const kc_pattern* pat, int32_t prec, const void* val, const double* diag,
+                           const int32_t* perm, const int64_t* a_rowptr, const int32_t* a_col, const double* a_val,
+                           const double* b, int32_t nrhs, double rtol, int32_t maxit, double* x, int32_t* iters_out,
+                           double* relres_out, const kc_opts* opts, void* stream);
 
 #ifdef __cplusplus
 }

@@ -42,6 +42,17 @@ kc_status factor_matvec_impl(const kc_pattern* P, int prec, const void* val, con
                              const double* in, int nrhs, double* out, int which, cudaStream_t s);
 kc_status logdet_impl(const kc_pattern* P, const double* diag, double* logdet_out, int64_t* zero_out, cudaStream_t s);
 kc_status kernel_eval_impl(const kc_kernel* kern, int prec, const double* r, int64_t n, double* out, cudaStream_t s);
+kc_status factor_given_impl(const kc_pattern* P, const double* aval, int prec, void* val, double* diag,
+                            int64_t* zero_out, const kc_opts* o, cudaStream_t s);
+kc_status refine_sparse_impl(const kc_pattern* P, int prec, const void* val, const double* diag,
+                             const int32_t* perm, const int64_t* arp, const int32_t* acol, const double* aval,
+                             const double* b, int nrhs, double rtol, int maxit, double* x_out, int32_t* iters_out,
+                             double* relres_out, const kc_opts* o, cudaStream_t s);
+kc_status pattern_reverse_impl(int64_t N, const int64_t* colptr, const int32_t* rowidx, int64_t* rowptr, int32_t* col,
+                               cudaStream_t s);
+kc_status gather_impl(int64_t N, const int64_t* rowptr, const int32_t* col, const int32_t* orig, const int64_t* arp,
+                      const int32_t* acol, const double* aval_in, double* aval, int64_t* outside_out,
+                      cudaStream_t s);
 }  // namespace kc
 
 using namespace kc;
@@ -240,6 +251,41 @@ kc_status kc_logdet(const kc_pattern* pat, const double* diag, double* logdet_ou
     KC_TRY(check_pattern(pat));
     if (!diag || !logdet_out) return fail(KC_EINVAL, "diag and logdet_out must be non-NULL");
     return logdet_impl(pat, diag, logdet_out, zero_pivots_out, (cudaStream_t)stream);
+}
+
+kc_status kc_pattern_reverse(int64_t N, const int64_t* colptr, const int32_t* rowidx, int64_t* rowptr_out,
+                             int32_t* col_out, void* stream) {
+    if (N < 1 || N > INT32_MAX) return fail(KC_EINVAL, "N must be in 1..2^31-1");
+    if (!colptr || !rowidx || !rowptr_out || !col_out) return fail(KC_EINVAL, "arrays must be non-NULL");
+    return pattern_reverse_impl(N, colptr, rowidx, rowptr_out, col_out, (cudaStream_t)stream);
+}
+
+kc_status kc_gather_entries(int64_t N, const int64_t* rowptr, const int32_t* col, const int32_t* orig,
+                            const int64_t* a_rowptr, const int32_t* a_col, const double* a_val, double* aval_out,
+                            int64_t* outside_out, void* stream) {
+    if (N < 1 || N > INT32_MAX) return fail(KC_EINVAL, "N must be in 1..2^31-1");
+    if (!rowptr || !col || !orig || !a_rowptr || !a_col || !a_val || !aval_out)
+        return fail(KC_EINVAL, "arrays must be non-NULL");
+    return gather_impl(N, rowptr, col, orig, a_rowptr, a_col, a_val, aval_out, outside_out, (cudaStream_t)stream);
+}
+
+kc_status kc_factor_given(const kc_pattern* pat, const double* aval, int32_t prec, void* val, double* diag,
+                          int64_t* zero_pivots_out, const kc_opts* opts, void* stream) {
+    KC_TRY(check_pattern(pat));
+    if (!aval || !val || !diag) return fail(KC_EINVAL, "arrays must be non-NULL");
+    return factor_given_impl(pat, aval, prec, val, diag, zero_pivots_out, opts, (cudaStream_t)stream);
+}
+
+kc_status kc_refine_sparse(const kc_pattern* pat, int32_t prec, const void* val, const double* diag,
+                           const int32_t* perm, const int64_t* a_rowptr, const int32_t* a_col, const double* a_val,
+                           const double* b, int32_t nrhs, double rtol, int32_t maxit, double* x, int32_t* iters_out,
+                           double* relres_out, const kc_opts* opts, void* stream) {
+    KC_TRY(check_pattern(pat));
+    if (!val || !diag || !perm || !a_rowptr || !a_col || !a_val || !b || !x)
+        return fail(KC_EINVAL, "arrays must be non-NULL");
+    if (!(rtol > 0.0) || maxit < 0) return fail(KC_EINVAL, "rtol must be > 0 and maxit >= 0");
+    return refine_sparse_impl(pat, prec, val, diag, perm, a_rowptr, a_col, a_val, b, nrhs, rtol, maxit, x,
+                              iters_out, relres_out, opts, (cudaStream_t)stream);
 }
 
 }  // extern "C"

@@ -70,6 +70,7 @@ struct FactorArgs {
     int* status;
     unsigned long long* zero_piv;
     KernelParams kp;                 // kernel of a single set
+    const double* __restrict__ aval;  // given entries (ENT = 2): the matrix on the pattern, CSR layout
     const int32_t* __restrict__ col_set;  // set of every column (NULL: one set)
     const KernelParams* __restrict__ kps; // kernels of the sets
     long long spin_limit;
@@ -227,10 +228,13 @@ struct Acc<float> {
     __device__ __forceinline__ static float recip(double Lii) { return __frcp_rn((float)Lii); }
 };
 
-// Theta_ji off the diagonal.  GEN = false: the closed-form Matern kernels only
-// (nu = 1/2, 3/2, 5/2); GEN = true: every covariance function, in its own
-// kernel instantiation, so that the calls behind the other families cost the
-// closed-form kernels no registers.
+// Where the entries come from (a template parameter of the kernels, so that
+// each instantiation holds only its own entry code):
+//   ENT = 0: the closed-form Matern kernels (nu = 1/2, 3/2, 5/2);
+//   ENT = 1: every covariance function (the calls behind the other families
+//            would cost the closed-form kernels registers);
+//   ENT = 2: a given matrix on the pattern (aval, Section 6).
+// Theta_ji off the diagonal from the coordinates (ENT 0 and 1, GEN = ENT == 1).
 template <typename T, bool GEN>
 __device__ __forceinline__ T theta_off(const KernelParams& kp, int d, const double* xj, const double* xi) {
     if constexpr (sizeof(T) == 8) {
@@ -291,7 +295,7 @@ struct TaskCtx {
 // R_i is complete, put row i into the table, form the pivot in FP64.
 // Returns 0 (task ready), 1 (no tasks left), 2 (stop: a wait ran out or the
 // kernel is stopping).
-template <typename T>
+template <typename T, int ENT>
 __device__ __forceinline__ int task_begin(const FactorArgs<T>& A, RowTable<T>& tab, int lane, TaskCtx<T>& X) {
     const unsigned FULL = 0xffffffffu;
     unsigned long long t = 0;
@@ -357,8 +361,14 @@ __device__ __forceinline__ int task_begin(const FactorArgs<T>& A, RowTable<T>& t
     T inv = (T)0;
     int zero = 0;
     if (lane == 0) {
-        const KernelParams& kp = kparams(A, X.i);
-        const double p = (kp.sigma2 + kp.nugget) - sq.total();
+        double thii;
+        if constexpr (ENT == 2) {
+            thii = A.aval[X.a1];
+        } else {
+            const KernelParams& kp = kparams(A, X.i);
+            thii = kp.sigma2 + kp.nugget;
+        }
+        const double p = thii - sq.total();
         zero = !(p > 0.0);
         Lii = zero ? 0.0 : sqrt(p);
         inv = zero ? (T)0 : Acc<T>::recip(Lii);
@@ -436,7 +446,7 @@ __device__ __forceinline__ void merge_global(const FactorArgs<T>& A, const RowTa
 
 // Row-j bookkeeping of the rows b0+lane of a batch: the slot of L_ji, the
 // start of row j, and Theta_ji (loads and exponentials overlap across lanes).
-template <typename T, bool GEN>
+template <typename T, int ENT>
 __device__ __forceinline__ void batch_rows(const FactorArgs<T>& A, const TaskCtx<T>& X, int64_t b0, int nb, int lane,
                                            int64_t& my_e0, int64_t& my_b, T& my_th) {
     my_e0 = 0;
@@ -446,7 +456,13 @@ __device__ __forceinline__ void batch_rows(const FactorArgs<T>& A, const TaskCtx
         const int j = __ldg(&A.rowidx[b0 + lane]);
         my_b = __ldg(&A.slot[b0 + lane]);
         my_e0 = __ldg(&A.rowptr[j]);
-        if (!X.zero) my_th = theta_off<T, GEN>(kparams(A, X.i), A.d, A.x + (int64_t)j * A.d, A.x + (int64_t)X.i * A.d);
+        if constexpr (ENT == 2) {
+            if (!X.zero) my_th = (T)__ldg(&A.aval[my_b]);
+        } else {
+            if (!X.zero)
+                my_th = theta_off<T, ENT == 1>(kparams(A, X.i), A.d, A.x + (int64_t)j * A.d,
+                                               A.x + (int64_t)X.i * A.d);
+        }
     }
 }
 
@@ -457,7 +473,7 @@ __device__ __forceinline__ void batch_rows(const FactorArgs<T>& A, const TaskCtx
 #define KC_FACTOR_MIN_BLOCKS 4
 #endif
 
-template <typename T, int U, bool GEN>
+template <typename T, int U, int ENT>
 __global__ void __launch_bounds__(256, U >= 16 ? 3 : KC_FACTOR_MIN_BLOCKS) ichol_persistent_k(FactorArgs<T> A) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = lane_id();
@@ -466,7 +482,7 @@ __global__ void __launch_bounds__(256, U >= 16 ? 3 : KC_FACTOR_MIN_BLOCKS) ichol
     const unsigned FULL = 0xffffffffu;
     TaskCtx<T> X;
     for (;;) {
-        if (task_begin(A, tab, lane, X) != 0) return;
+        if (task_begin<T, ENT>(A, tab, lane, X) != 0) return;
         const int G = lanes_per_row<T>(A.lanes);
         const int ng = 32 / G, g = lane / G, sub = lane % G;
         const int rows = rows_of_task(A.rowptr, X.i, A.rpt, A.adaptive);
@@ -476,7 +492,7 @@ __global__ void __launch_bounds__(256, U >= 16 ? 3 : KC_FACTOR_MIN_BLOCKS) ichol
             const int nb = (int)min((int64_t)32, qe - b0);
             int64_t my_e0, my_b;
             T my_th;
-            batch_rows<T, GEN>(A, X, b0, nb, lane, my_e0, my_b, my_th);
+            batch_rows<T, ENT>(A, X, b0, nb, lane, my_e0, my_b, my_th);
             for (int r0 = 0; r0 < nb; r0 += ng) {
                 const int r = r0 + g;
                 const bool act = r < nb;
@@ -624,7 +640,7 @@ __device__ __forceinline__ void merge_smem(const RowTable<T>& tab, const int* cs
     }
 }
 
-template <typename T, int U, bool GEN>
+template <typename T, int U, int ENT>
 __global__ void __launch_bounds__(128) ichol_bulk_k(FactorArgs<T> A) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = lane_id();
@@ -644,7 +660,7 @@ __global__ void __launch_bounds__(128) ichol_bulk_k(FactorArgs<T> A) {
     uint32_t phase = 0;  // bit b: parity of the next phase of barrier b
     TaskCtx<T> X;
     for (;;) {
-        if (task_begin(A, tab, lane, X) != 0) return;
+        if (task_begin<T, ENT>(A, tab, lane, X) != 0) return;
         // values of finished columns were written by other SMs through the generic
         // proxy and acquired above; the bulk copies read them through the async proxy
         asm volatile("fence.proxy.async.global;" ::: "memory");
@@ -658,7 +674,7 @@ __global__ void __launch_bounds__(128) ichol_bulk_k(FactorArgs<T> A) {
             const int nb = (int)min((int64_t)32, qe - b0);
             int64_t my_e0, my_b;
             T my_th;
-            batch_rows<T, GEN>(A, X, b0, nb, lane, my_e0, my_b, my_th);
+            batch_rows<T, ENT>(A, X, b0, nb, lane, my_e0, my_b, my_th);
             uint32_t off0 = 0, meta0 = 0, off1 = 0, meta1 = 0;  // the lane's row in buffer 0 / 1
             Stage cur;
             if (bulk) cur = stage_issue(A, bufs, &bars[0], 0, 0, nb, lane, my_e0, my_b, off0, meta0);
@@ -798,10 +814,11 @@ struct FactorCore {
     unsigned long long* ticket = nullptr;
     unsigned long long* zp = nullptr;
     int* status = nullptr;
-    KernelParams kp;
+    KernelParams kp{};
     const int32_t* col_set = nullptr;
     KernelParams* kps = nullptr;
     bool general = false;  // some set's kernel is not a closed-form Matern
+    const double* aval = nullptr;  // given entries (kc_factor_given)
     int rpt = 128, lanes = 0, unroll = 8, warps = 8, hbits = 7, ctas = 0, adaptive = 0;
     int stage_req = 0;    // requested stage-buffer bytes: 0 automatic, < 0 register form
     int stage_bytes = 0;  // chosen (0: register form)
@@ -811,7 +828,7 @@ struct FactorCore {
     int hold = -1;
 };
 
-template <typename T, int U, bool GEN>
+template <typename T, int U, int ENT>
 static kc_status launch_core(const FactorCore& F, T* val, double* diag, cudaStream_t s) {
     FactorArgs<T> a;
     a.N = F.P.N;
@@ -832,6 +849,7 @@ static kc_status launch_core(const FactorCore& F, T* val, double* diag, cudaStre
     a.status = F.status;
     a.zero_piv = F.zp;
     a.kp = F.kp;
+    a.aval = F.aval;
     a.col_set = F.col_set;
     a.kps = F.kps;
     a.spin_limit = F.spin;
@@ -841,7 +859,7 @@ static kc_status launch_core(const FactorCore& F, T* val, double* diag, cudaStre
     a.adaptive = F.adaptive;
     a.stage_bytes = F.stage_bytes;
     const size_t table = (size_t)(1 << F.hbits) * (sizeof(int) + sizeof(T));
-    const bool bulk = !GEN && F.stage_bytes > 0;  // the other kernel families: register form
+    const bool bulk = ENT == 0 && F.stage_bytes > 0;  // the other entry sources: register form
     // bulk form: table, two stage buffers, two mbarriers per warp (128-byte aligned)
     a.warp_smem = (int)(bulk ? (table + 2 * (size_t)F.stage_bytes + 16 + 127) / 128 * 128 : table);
     int warps = bulk ? F.bulk_warps : F.warps;
@@ -852,9 +870,9 @@ static kc_status launch_core(const FactorCore& F, T* val, double* diag, cudaStre
         warps = std::min(warps, optin / a.warp_smem);
         if (warps < 1) return fail(KC_EINVAL, "factor: stage_bytes too large for one warp's shared memory");
     }
-    auto kfn = ichol_persistent_k<T, U, GEN>;
-    if constexpr (!GEN)
-        if (bulk) kfn = ichol_bulk_k<T, U, false>;
+    auto kfn = ichol_persistent_k<T, U, ENT>;
+    if constexpr (ENT == 0)
+        if (bulk) kfn = ichol_bulk_k<T, U, 0>;
     int per_sm = 0;
     KC_TRY(allow_dynamic_smem(kfn));
     if (!bulk && F.warps_auto) {
@@ -887,19 +905,22 @@ static kc_status launch_core(const FactorCore& F, T* val, double* diag, cudaStre
     return KC_OK;
 }
 
-// The closed-form Matern kernels take the unroll asked for; the other
-// families one instantiation per precision (register form, 8 loads in flight
+// The closed-form Matern kernels take the unroll asked for; the other entry
+// sources one instantiation per precision (register form, 8 loads in flight
 // per lane in the FP32 form, 4 in FP64).
 static kc_status launch_any(const FactorCore& F, void* val, double* diag, cudaStream_t s) {
+    if (F.aval)
+        return F.prec == KC_FP64 ? launch_core<double, 4, 2>(F, (double*)val, diag, s)
+                                 : launch_core<float, 8, 2>(F, (float*)val, diag, s);
     if (F.general)
-        return F.prec == KC_FP64 ? launch_core<double, 4, true>(F, (double*)val, diag, s)
-                                 : launch_core<float, 8, true>(F, (float*)val, diag, s);
+        return F.prec == KC_FP64 ? launch_core<double, 4, 1>(F, (double*)val, diag, s)
+                                 : launch_core<float, 8, 1>(F, (float*)val, diag, s);
     if (F.prec == KC_FP64)
-        return F.unroll >= 8 ? launch_core<double, 8, false>(F, (double*)val, diag, s)
-                             : launch_core<double, 4, false>(F, (double*)val, diag, s);
-    if (F.unroll >= 16) return launch_core<float, 16, false>(F, (float*)val, diag, s);
-    return F.unroll >= 8 ? launch_core<float, 8, false>(F, (float*)val, diag, s)
-                         : launch_core<float, 4, false>(F, (float*)val, diag, s);
+        return F.unroll >= 8 ? launch_core<double, 8, 0>(F, (double*)val, diag, s)
+                             : launch_core<double, 4, 0>(F, (double*)val, diag, s);
+    if (F.unroll >= 16) return launch_core<float, 16, 0>(F, (float*)val, diag, s);
+    return F.unroll >= 8 ? launch_core<float, 8, 0>(F, (float*)val, diag, s)
+                         : launch_core<float, 4, 0>(F, (float*)val, diag, s);
 }
 
 static kc_status read_status(const FactorCore& F, int64_t* zero_out, cudaStream_t s) {
@@ -965,12 +986,18 @@ static void auto_rows(FactorCore& F) {
     F.rpt = r;
 }
 
-kc_status factor_impl(const kc_pattern* P, const double* x, int d, const kc_kernel* kern, int prec, void* val,
-                      double* diag, int64_t* zero_out, const kc_opts* o, cudaStream_t s) {
+// One factorisation: entries from the covariance function kern at the
+// points x, or (kern NULL) the given matrix aval on the pattern.
+static kc_status factor_run(const kc_pattern* P, const double* x, int d, const kc_kernel* kern, const double* aval,
+                            int prec, void* val, double* diag, int64_t* zero_out, const kc_opts* o, cudaStream_t s) {
     if (prec != KC_FP64 && prec != KC_FP32_FORM) return fail(KC_EINVAL, "prec must be KC_FP64 or KC_FP32_FORM");
     FactorCore F;
-    KC_TRY(kernel_params(kern, &F.kp));
-    F.general = F.kp.nu_code > 2;
+    if (kern) {
+        KC_TRY(kernel_params(kern, &F.kp));
+        F.general = F.kp.nu_code > 2;
+    } else {
+        F.aval = aval;
+    }
     KC_TRY(apply_opts(F, o));
     F.P = *P;
     F.prec = prec;
@@ -998,6 +1025,16 @@ kc_status factor_impl(const kc_pattern* P, const double* x, int d, const kc_kern
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     return st;
+}
+
+kc_status factor_impl(const kc_pattern* P, const double* x, int d, const kc_kernel* kern, int prec, void* val,
+                      double* diag, int64_t* zero_out, const kc_opts* o, cudaStream_t s) {
+    return factor_run(P, x, d, kern, nullptr, prec, val, diag, zero_out, o, s);
+}
+
+kc_status factor_given_impl(const kc_pattern* P, const double* aval, int prec, void* val, double* diag,
+                            int64_t* zero_out, const kc_opts* o, cudaStream_t s) {
+    return factor_run(P, nullptr, 0, nullptr, aval, prec, val, diag, zero_out, o, s);
 }
 
 }  // namespace kc

@@ -157,19 +157,118 @@ __global__ void sub_k(double* __restrict__ dst, const double* __restrict__ a, co
     if (t < n) dst[t] = a[t] - b[t];
 }
 
+// y[k][r] = sum_m A(orig[k], orig[m]) v[m][r] in positions (point-major,
+// stride NS): one warp per row, A given by CSR rows in original numbering,
+// pos the inverse of orig.  Each output is one warp's sum in a fixed order.
+template <int NS>
+__global__ void __launch_bounds__(256) sparse_pos_mv_k(const int64_t* __restrict__ arp,
+                                                       const int32_t* __restrict__ acol,
+                                                       const double* __restrict__ aval,
+                                                       const int32_t* __restrict__ orig, const int32_t* __restrict__ pos,
+                                                       int64_t N, const double* __restrict__ v, double* __restrict__ y) {
+    const int64_t k = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+    if (k >= N) return;
+    const int u = orig[k];
+    double acc[NS];
+#pragma unroll
+    for (int r = 0; r < NS; ++r) acc[r] = 0.0;
+    for (int64_t f = arp[u] + lane_id(); f < arp[u + 1]; f += 32) {
+        const double a = __ldg(&aval[f]);
+        const double* vm = v + (int64_t)__ldg(&pos[__ldg(&acol[f])]) * NS;
+#pragma unroll
+        for (int r = 0; r < NS; ++r) acc[r] = fma(a, __ldg(vm + r), acc[r]);
+    }
+    double mine = 0.0;
+#pragma unroll
+    for (int r = 0; r < NS; ++r) {
+        const double t = warp_sum(acc[r]);
+        if (lane_id() == r) mine = t;
+    }
+    if (lane_id() < NS) y[k * NS + lane_id()] = mine;
+}
+
+__global__ void inverse_index_k(const int32_t* __restrict__ orig, int64_t N, int32_t* __restrict__ pos) {
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q < N) pos[orig[q]] = (int32_t)q;
+}
+
+struct SparseOp {
+    const int64_t* arp;
+    const int32_t* acol;
+    const double* aval;
+    const int32_t* orig;
+    const int32_t* pos;
+};
+
+static kc_status sparse_pos_mv(const SparseOp& M, int64_t N, const double* v, double* y, int ns, cudaStream_t s) {
+    const unsigned g = blocks_for(N, 8);
+    switch (ns) {
+        case 1: ::kc::note_launch(), sparse_pos_mv_k<1><<<g, 256, 0, s>>>(M.arp, M.acol, M.aval, M.orig, M.pos, N, v, y); break;
+        case 2: ::kc::note_launch(), sparse_pos_mv_k<2><<<g, 256, 0, s>>>(M.arp, M.acol, M.aval, M.orig, M.pos, N, v, y); break;
+        case 4: ::kc::note_launch(), sparse_pos_mv_k<4><<<g, 256, 0, s>>>(M.arp, M.acol, M.aval, M.orig, M.pos, N, v, y); break;
+        case 8: ::kc::note_launch(), sparse_pos_mv_k<8><<<g, 256, 0, s>>>(M.arp, M.acol, M.aval, M.orig, M.pos, N, v, y); break;
+        default: ::kc::note_launch(), sparse_pos_mv_k<16><<<g, 256, 0, s>>>(M.arp, M.acol, M.aval, M.orig, M.pos, N, v, y);
+    }
+    KC_CUDA(cudaGetLastError());
+    return KC_OK;
+}
+
+// The operator of the CG: the dense Theta from the coordinates (kernel given)
+// or a given sparse matrix (M.arp given).
+struct CgOperator {
+    const double* x_ord = nullptr;
+    int d = 0;
+    KernelParams kp{};
+    SparseOp M{};
+    kc_status apply(int64_t N, const double* v, double* y, int ns, cudaStream_t s) const {
+        if (M.arp) return sparse_pos_mv(M, N, v, y, ns, s);
+        return dense_theta_f64(x_ord, N, d, kp, v, y, ns, s);
+    }
+};
+
+static kc_status refine_core(const kc_pattern* P, CgOperator& op, double fb, int prec, const void* val,
+                             const double* diag, const int32_t* perm, const double* b, int nrhs, double rtol,
+                             int maxit, double* x_out, int32_t* iters_out, double* relres_out, const kc_opts* o,
+                             Arena& A, cudaStream_t s);
+
 kc_status refine_impl(const kc_pattern* P, const double* x_ord, int d, const kc_kernel* kern, int prec,
                       const void* val, const double* diag, const int32_t* perm, const double* b, int nrhs,
                       double rtol, int maxit, double* x_out, int32_t* iters_out, double* relres_out,
                       const kc_opts* o, cudaStream_t s) {
-    KernelParams kp;
-    KC_TRY(kernel_params(kern, &kp));
+    CgOperator op;
+    KC_TRY(kernel_params(kern, &op.kp));
+    op.x_ord = x_ord;
+    op.d = d;
+    Arena A(s);
+    KC_TRY(upload_coef(op.kp, A, s));
+    return refine_core(P, op, sqrt(op.kp.sigma2 + op.kp.nugget), prec, val, diag, perm, b, nrhs, rtol, maxit, x_out,
+                       iters_out, relres_out, o, A, s);
+}
+
+kc_status refine_sparse_impl(const kc_pattern* P, int prec, const void* val, const double* diag,
+                             const int32_t* perm, const int64_t* arp, const int32_t* acol, const double* aval,
+                             const double* b, int nrhs, double rtol, int maxit, double* x_out, int32_t* iters_out,
+                             double* relres_out, const kc_opts* o, cudaStream_t s) {
+    CgOperator op;
+    Arena A(s);
+    int32_t* pos;
+    KC_TRY(A.get(&pos, P->N));
+    ::kc::note_launch(), inverse_index_k<<<blocks_for(P->N, 256), 256, 0, s>>>(perm, P->N, pos);
+    KC_CUDA(cudaGetLastError());
+    op.M = SparseOp{arp, acol, aval, perm, pos};
+    return refine_core(P, op, 1.0, prec, val, diag, perm, b, nrhs, rtol, maxit, x_out, iters_out, relres_out, o, A,
+                       s);
+}
+
+static kc_status refine_core(const kc_pattern* P, CgOperator& op, double fb, int prec, const void* val,
+                             const double* diag, const int32_t* perm, const double* b, int nrhs, double rtol,
+                             int maxit, double* x_out, int32_t* iters_out, double* relres_out, const kc_opts* o,
+                             Arena& A, cudaStream_t s) {
     if (nrhs < 1 || nrhs > 16) return fail(KC_EINVAL, "nrhs must be in 1..16");
     if (prec != KC_FP64 && prec != KC_FP32_FORM) return fail(KC_EINVAL, "bad prec");
     const int64_t N = P->N;
     int ns = 1;
     while (ns < nrhs) ns <<= 1;  // padded slot count (extra columns stay zero)
-    Arena A(s);
-    KC_TRY(upload_coef(kp, A, s));
     Solver S;
     KC_TRY(solver_init(S, P, ns, o, A, s));
     const int64_t n = N * ns;
@@ -199,7 +298,6 @@ kc_status refine_impl(const kc_pattern* P, const double* x_ord, int d, const kc_
         KC_CUDA(cudaMemcpy2DAsync(bp, sizeof(double) * ns, tmp, sizeof(double) * nrhs, sizeof(double) * nrhs, N,
                                   cudaMemcpyDeviceToDevice, s));
     }
-    const double fb = sqrt(kp.sigma2 + kp.nugget);
     auto precond = [&](const double* in, double* out) -> kc_status {
         if (prec == KC_FP64) return solver_apply<double>(S, (const double*)val, diag, fb, in, out, ns, s);
         return solver_apply<float>(S, (const float*)val, diag, fb, in, out, ns, s);
@@ -233,7 +331,7 @@ kc_status refine_impl(const kc_pattern* P, const double* x_ord, int d, const kc_
         }
         if (it >= maxit) break;
         KC_CUDA(cudaMemcpyAsync(active, h_active, sizeof(int) * ns, cudaMemcpyHostToDevice, s));
-        KC_TRY(dense_theta_f64(x_ord, N, d, kp, p, q, ns, s));
+        KC_TRY(op.apply(N, p, q, ns, s));
         KC_TRY(dots(p, q, N, ns, partial, pq, s));
         KC_CUDA(cudaMemcpyAsync(h_pq, pq, sizeof(double) * ns, cudaMemcpyDeviceToHost, s));
         KC_CUDA(cudaStreamSynchronize(s));
@@ -252,8 +350,8 @@ kc_status refine_impl(const kc_pattern* P, const double* x_ord, int d, const kc_
         ++it;
     }
     KC_TRY(solver_check(S, s));
-    // true residual b - Theta x
-    KC_TRY(dense_theta_f64(x_ord, N, d, kp, xs, q, ns, s));
+    // true residual b - (operator) x
+    KC_TRY(op.apply(N, xs, q, ns, s));
     ::kc::note_launch(), sub_k<<<gb, 256, 0, s>>>(r, bp, q, n);
     KC_TRY(dots(r, r, N, ns, partial, rr, s));
     KC_CUDA(cudaMemcpyAsync(h_rr, rr, sizeof(double) * ns, cudaMemcpyDeviceToHost, s));

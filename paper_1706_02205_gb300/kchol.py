@@ -96,6 +96,11 @@ def lib():
             "kc_lt_matvec": [P(kc_pattern), i32, vp, vp, vp, vp, i32, vp, vp],
             "kc_llt_matvec": [P(kc_pattern), i32, vp, vp, vp, vp, i32, vp, vp],
             "kc_logdet": [P(kc_pattern), vp, P(C.c_double), P(C.c_int64), vp],
+            "kc_pattern_reverse": [i64, vp, vp, vp, vp, vp],
+            "kc_gather_entries": [i64, vp, vp, vp, vp, vp, vp, vp, P(C.c_int64), vp],
+            "kc_factor_given": [P(kc_pattern), vp, i32, vp, vp, P(C.c_int64), P(kc_opts), vp],
+            "kc_refine_sparse": [P(kc_pattern), i32, vp, vp, vp, vp, vp, vp, vp, i32, dbl, i32, vp, P(C.c_int32),
+                                 P(C.c_double), P(kc_opts), vp],
         }
         for name, args in sigs.items():
             f = getattr(L, name)
@@ -111,7 +116,8 @@ EXPORTED = ("kc_last_error", "kc_abi_version", "kc_launch_count", "kc_last_facto
             "kc_schedule", "kc_factor", "kc_solve", "kc_solve_noalloc", "kc_refine", "kc_pca_truncate", "kc_pca_error",
             "kc_factor_plan_create", "kc_factor_plan_launch", "kc_factor_plan_finish", "kc_factor_plan_tune",
             "kc_factor_plan_destroy", "kc_pattern_concat", "kc_points_concat", "kc_index_concat", "kc_kernel_eval",
-            "kc_l_matvec", "kc_lt_matvec", "kc_llt_matvec", "kc_logdet")
+            "kc_l_matvec", "kc_lt_matvec", "kc_llt_matvec", "kc_logdet", "kc_pattern_reverse",
+            "kc_gather_entries", "kc_factor_given", "kc_refine_sparse")
 
 
 def launch_count() -> int:
@@ -388,6 +394,88 @@ def pipeline(x, rho, kern: Kernel, prec=FP32_FORM, rule=RULE_MAX, opts=None, str
     pat = build_pattern(xo, l, rho, rule, stream)
     val, diag, zp = factor(pat, xo, kern, prec, opts, stream=stream)
     return dict(perm=perm, l=l, x_ord=xo, pat=pat, val=val, diag=diag, zero_pivots=zp)
+
+
+# ------------------------------------- Section 6: given matrix, reverse order
+
+def pattern_reverse(pat: Pattern, x_ord=None, stream=None) -> Pattern:
+    """The symmetric pattern of pat in the reversed order (position q holds
+    position N-1-q of pat's order), scheduled; x_ord: pat's points, whose
+    reversal orders each level spatially."""
+    N = pat.N
+    rowptr = torch.empty(N + 1, dtype=torch.int64, device=pat.rowptr.device)
+    col = torch.empty(pat.nnz, dtype=torch.int32, device=pat.rowptr.device)
+    _check(lib().kc_pattern_reverse(N, _ptr(pat.colptr), _ptr(pat.rowidx), _ptr(rowptr), _ptr(col),
+                                    _stream(stream)))
+    xr = x_ord.flip(0).contiguous() if x_ord is not None else None
+    return schedule(rowptr, col, xr, stream)
+
+
+def gather_entries(pat: Pattern, orig, a_rowptr, a_col, a_val, count_outside=True, stream=None):
+    """(aval float64[nnz], outside): the matrix A (CSR in original numbering,
+    columns ascending) at every pattern position; orig maps a position to
+    its original index.  outside = A's off-diagonal entries not in the
+    pattern (None unless count_outside)."""
+    _dev(orig, torch.int32, "orig")
+    _dev(a_rowptr, torch.int64, "a_rowptr")
+    _dev(a_col, torch.int32, "a_col")
+    _dev(a_val, torch.float64, "a_val")
+    aval = torch.empty(pat.nnz, dtype=torch.float64, device=orig.device)
+    out = C.c_int64(0)
+    _check(lib().kc_gather_entries(pat.N, _ptr(pat.rowptr), _ptr(pat.col), _ptr(orig), _ptr(a_rowptr), _ptr(a_col),
+                                   _ptr(a_val), _ptr(aval), C.byref(out) if count_outside else None,
+                                   _stream(stream)))
+    return aval, (int(out.value) if count_outside else None)
+
+
+def factor_given(pat: Pattern, aval, prec=FP32_FORM, opts: kc_opts | None = None, val=None, diag=None,
+                 stream=None):
+    """ICHOL(0) of the symmetric matrix given on the pattern (aval, CSR
+    layout) -> (val, diag, zero_pivots)."""
+    _dev(aval, torch.float64, "aval")
+    dt = torch.float64 if prec == FP64 else torch.float32
+    if val is None:
+        val = torch.empty(pat.nnz, dtype=dt, device=aval.device)
+    if diag is None:
+        diag = torch.empty(pat.N, dtype=torch.float64, device=aval.device)
+    zp = C.c_int64(0)
+    _check(lib().kc_factor_given(pat.c(), _ptr(aval), int(prec), _ptr(val), _ptr(diag), C.byref(zp),
+                                 C.byref(opts) if opts is not None else None, _stream(stream)))
+    return val, diag, int(zp.value)
+
+
+def refine_sparse(pat: Pattern, prec, val, diag, perm, a_rowptr, a_col, a_val, b, rtol=1e-10, maxit=200,
+                  opts=None, stream=None):
+    """CG on the given sparse A (CSR, original numbering) preconditioned by its
+    factor -> (x, iters, relres per rhs, status)."""
+    _dev(b, torch.float64, "b")
+    if b.dim() == 1:
+        b = b[None]
+    nrhs = b.shape[0]
+    x = torch.empty_like(b)
+    it = C.c_int32(0)
+    rr = (C.c_double * nrhs)()
+    st = lib().kc_refine_sparse(pat.c(), int(prec), _ptr(val), _ptr(diag), _ptr(perm), _ptr(a_rowptr), _ptr(a_col),
+                                _ptr(a_val), _ptr(b), nrhs, float(rtol), int(maxit), _ptr(x), C.byref(it), rr,
+                                C.byref(opts) if opts is not None else None, _stream(stream))
+    if st not in (KC_OK, KC_ENOTCONV, KC_EINDEF):
+        _check(st)
+    return x, int(it.value), list(rr), st
+
+
+def reverse_factor(x, a_rowptr, a_col, a_val, rho, prec=FP32_FORM, opts=None, stream=None):
+    """Section 6 on the device: maximin ordering of the points x, the
+    min-rule pattern, reversed, the matrix A (CSR, original numbering)
+    gathered onto it and factored.  ``orig`` (position -> original index)
+    is the permutation the solves take."""
+    perm, l, xo = order_points(x, stream)
+    pat = build_pattern(xo, l, rho, RULE_MIN, stream)
+    rpat = pattern_reverse(pat, xo, stream)
+    orig = perm.flip(0).contiguous()
+    aval, outside = gather_entries(rpat, orig, a_rowptr, a_col, a_val, stream=stream)
+    val, diag, zp = factor_given(rpat, aval, prec, opts, stream=stream)
+    return dict(perm=perm, l=l, x_ord=xo, orig=orig, pat=rpat, aval=aval, outside=outside, val=val, diag=diag,
+                zero_pivots=zp)
 
 
 # ------------------------------------------------------ plans and batching

@@ -71,6 +71,12 @@ def test_new_entries_reject_bad_arguments_without_gpu(so):
         assert getattr(lib, name)(None, 0, None, None, None, None, 1, None, None) == kchol.KC_EINVAL
     v = ctypes.c_double(0.0)
     assert lib.kc_logdet(None, None, ctypes.byref(v), None, None) == kchol.KC_EINVAL
+    assert lib.kc_pattern_reverse(0, None, None, None, None, None) == kchol.KC_EINVAL
+    assert lib.kc_pattern_reverse(4, None, None, None, None, None) == kchol.KC_EINVAL
+    assert lib.kc_gather_entries(4, None, None, None, None, None, None, None, None, None) == kchol.KC_EINVAL
+    assert lib.kc_factor_given(None, None, 0, None, None, None, None, None) == kchol.KC_EINVAL
+    assert lib.kc_refine_sparse(None, 0, None, None, None, None, None, None, None, 1, 1e-10, 10, None, None, None,
+                                None, None) == kchol.KC_EINVAL
 
 
 def test_struct_layouts_match_header(tmp_path):
