@@ -31,6 +31,8 @@ Owhadi, arXiv:1706.02205):
                          -- Section 6: ICHOL(0) of a given sparse matrix (the
                             precision matrix, or sigma^2 A + I) in the reverse
                             maximin order on the min-rule pattern.
+* ``supernodal``         -- the supernodal multicolour ordering and pattern
+                            (Construction of the stability section), brute force.
 * ``work_counters``      -- exact multiply-add / merge-step / operand counts of
                             the left-looking factor (roofline denominators).
 
@@ -109,6 +111,10 @@ def lib():
         L.ko_ichol_given.restype = i
         L.ko_ichol_given.argtypes = [i, i64p, i32p, f64p, f64p, u8p, I, I]
         L.ko_pattern_reverse.argtypes = [i, i64p, i32p, i64p, i32p]
+        L.ko_supernodal.restype = i
+        L.ko_supernodal.argtypes = [f64p, i, I, i32p, f64p, d, i32p, i32p, i32p, i32p, i64p,
+                                    C.POINTER(C.POINTER(C.c_int32))]
+        L.ko_free.argtypes = [C.c_void_p]
         L.ko_gather_entries.restype = i
         L.ko_gather_entries.argtypes = [i, i64p, i32p, i32p, i64p, i32p, f64p, f64p]
         L.ko_solve_lower.argtypes = [i, i64p, i32p, f64p, f64p, f64p, f64p]
@@ -292,6 +298,28 @@ def ichol_given(rowptr, col, aval, reverse_sums=False, store_f32=False):
                          np.ascontiguousarray(aval, np.float64), val, zc, int(bool(reverse_sums)),
                          int(bool(store_f32)))
     return val, zc.astype(bool)
+
+
+def supernodal(x, rho):
+    """The supernodal multicolour ordering and pattern (the paper's
+    Construction, stability section) from the maximin ordering of x: order
+    (new position -> original index), level, node (maximin index of the
+    supernode) and colour of every new position, and the CSR pattern (lower
+    triangle in the new order).  O(N^2): small cases only."""
+    x, N, d = _pts(x)
+    perm, l = maximin_brute(x)
+    order = np.zeros(N, np.int32)
+    level = np.zeros(N, np.int32)
+    node = np.zeros(N, np.int32)
+    color = np.zeros(N, np.int32)
+    rowptr = np.zeros(N + 1, np.int64)
+    cp = C.POINTER(C.c_int32)()
+    nnz = lib().ko_supernodal(x, N, d, perm, l, float(rho), order, level, node, color, rowptr, C.byref(cp))
+    try:
+        col = np.ctypeslib.as_array(cp, shape=(nnz,)).copy() if nnz else np.zeros(0, np.int32)
+    finally:
+        lib().ko_free(cp)
+    return dict(perm=perm, l=l, order=order, level=level, node=node, color=color, rowptr=rowptr, col=col)
 
 
 def pattern_reverse(colptr, rowidx):

@@ -508,6 +508,142 @@ i64 ko_ichol_given(i64 N, const i64* rowptr, const i32* col, const double* aval,
 }
 
 /* ------------------------------------------------------------------------ */
+/* Supernodal multicolour ordering and sparsity pattern (the Construction of */
+/* the stability section).  Readings: h = 1/2; the scale l[1] (the largest  */
+/* finite length scale) normalises the hierarchy, so point m of the maximin  */
+/* order is on level k(m) = the smallest k >= 1 with l[m] >= l[1] 2^-k (the  */
+/* first point, l = inf, on level 1), and the hierarchical pseudometric is   */
+/* d(a, b) = dist(a, b) / (l[1] 2^-min(k(a), k(b))), so d <= rho reads      */
+/* dist <= R_min(k(a),k(b)) with R_k = (rho l[1]) 2^-k.                      */
+/*  - supernodes of level k: greedily in maximin order, a point becomes one  */
+/*    unless an earlier supernode of its level lies within d <= rho (so two  */
+/*    supernodes are farther apart than rho, their rho/2-balls are disjoint,  */
+/*    and every point lies within rho of one);                               */
+/*  - every point goes to the nearest supernode of its level (squared        */
+/*    distance, ties to the smaller index);                                 */
+/*  - supernode pattern: (A, B) whenever members a of A and b of B have      */
+/*    d(a, b) <= rho (A with itself included);                              */
+/*  - colours: per level, greedy in maximin order of the supernodes, the     */
+/*    smallest colour no earlier same-level neighbour in the pattern has;    */
+/*  - ordering: by level, colour, supernode (maximin index of the supernode),  */
+/*    then maximin index;                                                   */
+/*  - pattern S: (q, p), p <= q in the new order, whenever the supernodes of  */
+/*    q and p are a pattern pair.                                           */
+/* Inputs: x (original order), the maximin perm and l (ko_maximin_brute).    */
+/* Outputs: order[q] (original index at new position q), level, node (the    */
+/* maximin index of the supernode) and colour of every new position, and    */
+/* the CSR rows of S (rowptr[N+1]; col through *col_out, malloc'd; free it   */
+/* with ko_free).                                                            */
+/* ------------------------------------------------------------------------ */
+
+static double R_of(double rl1, i32 k) { return ldexp(rl1, -k); }
+
+typedef struct { i32 level, color, node, m; } sn_key;
+
+static int sn_cmp(const void* pa, const void* pb) {
+    const sn_key* a = (const sn_key*)pa;
+    const sn_key* b = (const sn_key*)pb;
+    if (a->level != b->level) return a->level < b->level ? -1 : 1;
+    if (a->color != b->color) return a->color < b->color ? -1 : 1;
+    if (a->node != b->node) return a->node < b->node ? -1 : 1;
+    return a->m < b->m ? -1 : (a->m > b->m);
+}
+
+void ko_free(void* p) { free(p); }
+
+i64 ko_supernodal(const double* x, i64 N, i32 d, const i32* perm, const double* l, double rho, i32* order,
+                  i32* level_out, i32* node_out, i32* color_out, i64* rowptr, i32** col_out) {
+    double* xo = (double*)malloc(sizeof(double) * (size_t)(N * d));
+    for (i64 m = 0; m < N; ++m)
+        for (i32 t = 0; t < d; ++t) xo[m * d + t] = x[(i64)perm[m] * d + t];
+    const double l1 = N > 1 ? l[1] : 1.0;
+    const double rl1 = rho * l1;
+    i32* lev = (i32*)malloc(sizeof(i32) * (size_t)N);
+    for (i64 m = 0; m < N; ++m) {
+        i32 k = 1;
+        if (m > 0)
+            while (!(l[m] >= ldexp(l1, -k))) ++k;
+        lev[m] = k;
+    }
+    /* supernodes, greedy per level in maximin order */
+    char* sup = (char*)calloc((size_t)N, 1);
+    for (i64 m = 0; m < N; ++m) {
+        int take = 1;
+        const double R = R_of(rl1, lev[m]);
+        for (i64 s = 0; s < m && take; ++s)
+            if (sup[s] && lev[s] == lev[m] && sqrt(d2_of(xo + m * d, xo + s * d, d)) <= R) take = 0;
+        sup[m] = (char)take;
+    }
+    /* nearest supernode of the same level */
+    i32* node = (i32*)malloc(sizeof(i32) * (size_t)N);
+    for (i64 m = 0; m < N; ++m) {
+        double best = INFINITY;
+        i32 bs = -1;
+        for (i64 s = 0; s < N; ++s)
+            if (sup[s] && lev[s] == lev[m]) {
+                double e = d2_of(xo + m * d, xo + s * d, d);
+                if (e < best) { best = e; bs = (i32)s; }
+            }
+        node[m] = bs;
+    }
+    /* supernode pattern as a dense N x N bit set over supernode indices */
+    char* adj = (char*)calloc((size_t)(N * N), 1);
+    for (i64 a = 0; a < N; ++a)
+        for (i64 b = 0; b <= a; ++b) {
+            i32 kmin = lev[a] < lev[b] ? lev[a] : lev[b];
+            if (a == b || sqrt(d2_of(xo + a * d, xo + b * d, d)) <= R_of(rl1, kmin)) {
+                adj[(i64)node[a] * N + node[b]] = 1;
+                adj[(i64)node[b] * N + node[a]] = 1;
+            }
+        }
+    /* greedy colours per level in supernode (maximin) order */
+    i32* colr = (i32*)malloc(sizeof(i32) * (size_t)N);
+    char* used = (char*)malloc((size_t)N + 1);
+    for (i64 s = 0; s < N; ++s) {
+        colr[s] = -1;
+        if (!sup[s]) continue;
+        memset(used, 0, (size_t)N + 1);
+        for (i64 t = 0; t < s; ++t)
+            if (sup[t] && lev[t] == lev[s] && adj[s * N + t] && colr[t] >= 0) used[colr[t]] = 1;
+        i32 c = 0;
+        while (used[c]) ++c;
+        colr[s] = c;
+    }
+    /* the ordering */
+    sn_key* keys = (sn_key*)malloc(sizeof(sn_key) * (size_t)N);
+    for (i64 m = 0; m < N; ++m) keys[m] = (sn_key){lev[m], colr[node[m]], node[m], (i32)m};
+    qsort(keys, (size_t)N, sizeof(sn_key), sn_cmp);
+    i32* pos = (i32*)malloc(sizeof(i32) * (size_t)N);
+    for (i64 q = 0; q < N; ++q) {
+        i32 m = keys[q].m;
+        order[q] = perm[m];
+        level_out[q] = lev[m];
+        node_out[q] = node[m];
+        color_out[q] = colr[node[m]];
+        pos[m] = (i32)q;
+    }
+    /* the pattern in the new order */
+    i32* mat = (i32*)malloc(sizeof(i32) * (size_t)N); /* maximin index at new position */
+    for (i64 q = 0; q < N; ++q) mat[q] = keys[q].m;
+    rowptr[0] = 0;
+    for (i64 q = 0; q < N; ++q) {
+        i64 c = 0;
+        for (i64 p = 0; p <= q; ++p)
+            if (adj[(i64)node[mat[q]] * N + node[mat[p]]]) ++c;
+        rowptr[q + 1] = rowptr[q] + c;
+    }
+    i32* col = (i32*)malloc(sizeof(i32) * (size_t)(rowptr[N] > 0 ? rowptr[N] : 1));
+    for (i64 q = 0; q < N; ++q) {
+        i64 w = rowptr[q];
+        for (i64 p = 0; p <= q; ++p)
+            if (adj[(i64)node[mat[q]] * N + node[mat[p]]]) col[w++] = (i32)p;
+    }
+    *col_out = col;
+    free(xo); free(lev); free(sup); free(node); free(adj); free(colr); free(used); free(keys); free(pos); free(mat);
+    return rowptr[N];
+}
+
+/* ------------------------------------------------------------------------ */
 /* Reverse elimination order (Section 6): position q of the reversed order   */
 /* is position N-1-q of the maximin order.  The lower triangle of a          */
 /* symmetric pattern in reversed positions is the upper one in maximin      */
