@@ -454,6 +454,63 @@ def run_pde(args):
                             "true_relres": cg_res}}
 
 
+def run_supernodal(args):
+    """The supernodal multicolour ordering and pattern on the 1024 x 1024
+    jittered grid (rho, kernel as for the headline), FP32 form: the maximin
+    order and max-rule pattern it starts from, the construction, the new
+    pattern's schedule and the factor; phases by CUDA events after warm-up,
+    with the maximin factor on the same points beside it."""
+    import torch
+
+    from paper_1706_02205_gb300 import kchol as kc
+    x = torch.from_numpy(inputs.jittered_grid(args.n_side, seed=inputs.seed_for(2))).cuda()
+    kern = make_kernel(args)
+    stream = torch.cuda.current_stream()
+    names = ("order", "pattern", "schedule", "supernodal", "schedule_new", "factor")
+    ph = {k: [] for k in names}
+    for it in range(args.warmup + args.steps):
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(len(names) + 1)]
+        ev[0].record(stream)
+        perm0, l, xo = kc.order_points(x)
+        ev[1].record(stream)
+        rowptr, nnz0 = kc.pattern_count(xo, l, args.rho)
+        col = kc.pattern_fill(xo, l, args.rho, rowptr, nnz0)
+        ev[2].record(stream)
+        pat0 = kc.schedule(rowptr, col, xo)
+        ev[3].record(stream)
+        N, d = xo.shape
+        newm = torch.empty(N, dtype=torch.int32, device=x.device)
+        x_new = torch.empty_like(xo)
+        rp = torch.empty(N + 1, dtype=torch.int64, device=x.device)
+        import ctypes as C
+        nn = C.c_int64(0)
+        kc._check(kc.lib().kc_supernodal_count(kc._ptr(xo), kc._ptr(l), d, float(args.rho), pat0.c(), kc._ptr(newm),
+                                               None, None, None, kc._ptr(x_new), kc._ptr(rp), C.byref(nn),
+                                               kc._stream(None)))
+        cl = torch.empty(int(nn.value), dtype=torch.int32, device=x.device)
+        kc._check(kc.lib().kc_supernodal_fill(kc._ptr(xo), kc._ptr(l), d, float(args.rho), pat0.c(), kc._ptr(rp),
+                                              kc._ptr(cl), kc._stream(None)))
+        ev[4].record(stream)
+        spat = kc.schedule(rp, cl, x_new)
+        ev[5].record(stream)
+        val, diag, zp = kc.factor(spat, x_new, kern, kc.FP32_FORM)
+        ev[6].record(stream)
+        torch.cuda.synchronize()
+        if it >= args.warmup:
+            for k, nm in enumerate(names):
+                ph[nm].append(ev[k].elapsed_time(ev[k + 1]))
+    sn_factor_kernel = kc.last_factor_kernel_ms()
+    _, _, zp0 = kc.factor(pat0, xo, kern, kc.FP32_FORM)
+    mm_factor_kernel = kc.last_factor_kernel_ms()
+    med = {k: statistics.median(v_) for k, v_ in ph.items()}
+    return {"workload": f"supernodal multicolour order, jittered grid {args.n_side}x{args.n_side} (N={N}), "
+                        f"{kernel_name(kern)}, rho={args.rho}, FP32 form", "N": N, "nnz": spat.nnz,
+            "depth": spat.depth, "zero_pivots": zp, "phases_ms": med,
+            "factor_kernel_ms": sn_factor_kernel, "factor_nnz_per_s": spat.nnz / (sn_factor_kernel * 1e-3),
+            "maximin": {"nnz": pat0.nnz, "depth": pat0.depth, "factor_kernel_ms": mm_factor_kernel,
+                        "zero_pivots": zp0}}
+
+
 def run_factor_only(args):
     """Factor-only probe (the launch profiled by ncu): order + pattern once,
     then the FP32-form factor `--steps` times on the same pattern."""
@@ -695,7 +752,8 @@ def main():
     ap.add_argument("--shift", type=float, default=100.0, help="pde workload: zeroth-order term of the operator")
     ap.add_argument("--beta", type=float, default=0.2, help="Cauchy beta")
     ap.add_argument("--workload", default="grid2d",
-                    choices=["grid2d", "cube3d", "factor", "batch", "serve", "refine", "tasks", "pde"],
+                    choices=["grid2d", "cube3d", "factor", "batch", "serve", "refine", "tasks", "pde",
+                             "supernodal"],
                     help="grid2d: the headline step (default); cube3d: 3-D factor + PCA; factor: factor-only "
                          "probe; batch: many sets in one launch; serve: request stream")
     ap.add_argument("--n3", type=int, default=2**18)
@@ -736,6 +794,8 @@ def main():
         line = run_tasks(args)
     elif args.workload == "pde":
         line = run_pde(args)
+    elif args.workload == "supernodal":
+        line = run_supernodal(args)
     elif args.workload == "refine":
         line = run_refine(args)
     else:

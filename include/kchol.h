@@ -125,7 +125,8 @@ const char* kc_last_error(void);
  * another version must not call the library.  2: kc_schedule takes the points,
  * kc_opts has stage_bytes.  3: kc_kernel has family, alpha, beta;
  * kc_kernel_eval, kc_l_matvec, kc_lt_matvec, kc_llt_matvec, kc_logdet,
- * kc_pattern_reverse, kc_gather_entries, kc_factor_given, kc_refine_sparse. */
+ * kc_pattern_reverse, kc_gather_entries, kc_factor_given, kc_refine_sparse,
+ * kc_supernodal_count, kc_supernodal_fill. */
 #define KC_ABI_VERSION 3
 int32_t kc_abi_version(void);
 
@@ -360,6 +361,33 @@ kc_status kc_refine_sparse(const kc_pattern* pat, int32_t prec, const void* val,
                            const int32_t* perm, const int64_t* a_rowptr, const int32_t* a_col, const double* a_val,
                            const double* b, int32_t nrhs, double rtol, int32_t maxit, double* x, int32_t* iters_out,
                            double* relres_out, const kc_opts* opts, void* stream);
+
+/* ---- supernodal multicolour ordering and pattern ------------------------ *
+ * The Construction of the paper's stability section, from the maximin order
+ * (x_ord, l of kc_order_points) and its max-rule pattern S_rho of the same
+ * rho >= 1 (pat, scheduled; every pair the construction tests lies in it).
+ * Hierarchy: h = 1/2 and the largest finite length scale l[1] as the unit,
+ * so maximin position m is on level k(m) = the smallest k >= 1 with
+ * l[m] >= l[1] 2^-k (position 0 on level 1); d(a, b) = dist(a, b) /
+ * (l[1] 2^-min(k(a), k(b))).  Supernodes of a level are taken greedily in
+ * maximin order (unless an earlier supernode of the level is within d <=
+ * rho); each point joins the nearest supernode of its level (ties to the
+ * smaller index); supernodes A, B pair when members a, b have d(a, b) <=
+ * rho; colours are greedy per level in maximin order; the new order sorts
+ * by level, colour, supernode, maximin position; the pattern S holds (q, p),
+ * p <= q, whenever the supernodes of q and p pair.  Algorithm 2 on this
+ * order and pattern is the supernodal block factorisation.
+ * kc_supernodal_count: newm int32[N] (maximin position of every new
+ * position), level, node (maximin position of the supernode), colour
+ * (int32[N] each, may be NULL), x_new double[N*d] (the points in the new
+ * order), rowptr int64[N+1] of S, nnz_out (host).  kc_supernodal_fill: col
+ * int32[nnz] (ascending, diagonal last), from the same inputs and rowptr.
+ * Both synchronise; KC_EINVAL if a level needs more than 64 colours. */
+kc_status kc_supernodal_count(const double* x_ord, const double* l, int32_t d, double rho, const kc_pattern* pat,
+                              int32_t* newm, int32_t* level, int32_t* node, int32_t* color, double* x_new,
+                              int64_t* rowptr, int64_t* nnz_out, void* stream);
+kc_status kc_supernodal_fill(const double* x_ord, const double* l, int32_t d, double rho, const kc_pattern* pat,
+                             const int64_t* rowptr, int32_t* col, void* stream);
 
 #ifdef __cplusplus
 }

@@ -44,6 +44,9 @@ kc_status logdet_impl(const kc_pattern* P, const double* diag, double* logdet_ou
 kc_status kernel_eval_impl(const kc_kernel* kern, int prec, const double* r, int64_t n, double* out, cudaStream_t s);
 kc_status factor_given_impl(const kc_pattern* P, const double* aval, int prec, void* val, double* diag,
                             int64_t* zero_out, const kc_opts* o, cudaStream_t s);
+kc_status supernodal_impl(const double* x_ord, const double* l, int d, double rho, const kc_pattern* P,
+                          int32_t* newm, int32_t* level, int32_t* node_out, int32_t* color_out, double* x_new,
+                          int64_t* rowptr, int64_t* nnz_out, int32_t* col, cudaStream_t s);
 kc_status refine_sparse_impl(const kc_pattern* P, int prec, const void* val, const double* diag,
                              const int32_t* perm, const int64_t* arp, const int32_t* acol, const double* aval,
                              const double* b, int nrhs, double rtol, int maxit, double* x_out, int32_t* iters_out,
@@ -286,6 +289,27 @@ kc_status kc_refine_sparse(const kc_pattern* pat, int32_t prec, const void* val,
     if (!(rtol > 0.0) || maxit < 0) return fail(KC_EINVAL, "rtol must be > 0 and maxit >= 0");
     return refine_sparse_impl(pat, prec, val, diag, perm, a_rowptr, a_col, a_val, b, nrhs, rtol, maxit, x,
                               iters_out, relres_out, opts, (cudaStream_t)stream);
+}
+
+kc_status kc_supernodal_count(const double* x_ord, const double* l, int32_t d, double rho, const kc_pattern* pat,
+                              int32_t* newm, int32_t* level, int32_t* node, int32_t* color, double* x_new,
+                              int64_t* rowptr, int64_t* nnz_out, void* stream) {
+    KC_TRY(check_pattern(pat));
+    KC_TRY(check_points(x_ord, pat->N, d));
+    if (!l || !newm || !x_new || !rowptr || !nnz_out) return fail(KC_EINVAL, "arrays must be non-NULL");
+    if (!(rho >= 1.0)) return fail(KC_EINVAL, "the supernodal construction needs rho >= 1");
+    return supernodal_impl(x_ord, l, d, rho, pat, newm, level, node, color, x_new, rowptr, nnz_out, nullptr,
+                           (cudaStream_t)stream);
+}
+
+kc_status kc_supernodal_fill(const double* x_ord, const double* l, int32_t d, double rho, const kc_pattern* pat,
+                             const int64_t* rowptr, int32_t* col, void* stream) {
+    KC_TRY(check_pattern(pat));
+    KC_TRY(check_points(x_ord, pat->N, d));
+    if (!l || !rowptr || !col) return fail(KC_EINVAL, "arrays must be non-NULL");
+    if (!(rho >= 1.0)) return fail(KC_EINVAL, "the supernodal construction needs rho >= 1");
+    return supernodal_impl(x_ord, l, d, rho, pat, nullptr, nullptr, nullptr, nullptr, nullptr,
+                           const_cast<int64_t*>(rowptr), nullptr, col, (cudaStream_t)stream);
 }
 
 }  // extern "C"

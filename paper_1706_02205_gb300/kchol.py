@@ -99,6 +99,8 @@ def lib():
             "kc_pattern_reverse": [i64, vp, vp, vp, vp, vp],
             "kc_gather_entries": [i64, vp, vp, vp, vp, vp, vp, vp, P(C.c_int64), vp],
             "kc_factor_given": [P(kc_pattern), vp, i32, vp, vp, P(C.c_int64), P(kc_opts), vp],
+            "kc_supernodal_count": [vp, vp, i32, dbl, P(kc_pattern), vp, vp, vp, vp, vp, vp, P(C.c_int64), vp],
+            "kc_supernodal_fill": [vp, vp, i32, dbl, P(kc_pattern), vp, vp, vp],
             "kc_refine_sparse": [P(kc_pattern), i32, vp, vp, vp, vp, vp, vp, vp, i32, dbl, i32, vp, P(C.c_int32),
                                  P(C.c_double), P(kc_opts), vp],
         }
@@ -117,7 +119,8 @@ EXPORTED = ("kc_last_error", "kc_abi_version", "kc_launch_count", "kc_last_facto
             "kc_factor_plan_create", "kc_factor_plan_launch", "kc_factor_plan_finish", "kc_factor_plan_tune",
             "kc_factor_plan_destroy", "kc_pattern_concat", "kc_points_concat", "kc_index_concat", "kc_kernel_eval",
             "kc_l_matvec", "kc_lt_matvec", "kc_llt_matvec", "kc_logdet", "kc_pattern_reverse",
-            "kc_gather_entries", "kc_factor_given", "kc_refine_sparse")
+            "kc_gather_entries", "kc_factor_given", "kc_refine_sparse", "kc_supernodal_count",
+            "kc_supernodal_fill")
 
 
 def launch_count() -> int:
@@ -394,6 +397,45 @@ def pipeline(x, rho, kern: Kernel, prec=FP32_FORM, rule=RULE_MAX, opts=None, str
     pat = build_pattern(xo, l, rho, rule, stream)
     val, diag, zp = factor(pat, xo, kern, prec, opts, stream=stream)
     return dict(perm=perm, l=l, x_ord=xo, pat=pat, val=val, diag=diag, zero_pivots=zp)
+
+
+# ------------------------------- supernodal multicolour ordering and pattern
+
+def supernodal(x_ord, l, rho, pat: Pattern, stream=None):
+    """The supernodal multicolour ordering and pattern from the maximin order
+    (x_ord, l) and its max-rule pattern pat of the same rho -> dict with newm
+    (maximin position of every new position), level, node, color, x_new and
+    the scheduled pattern of the new order."""
+    _dev(x_ord, torch.float64, "x_ord")
+    _dev(l, torch.float64, "l")
+    N, d = x_ord.shape
+    dev = x_ord.device
+    newm = torch.empty(N, dtype=torch.int32, device=dev)
+    level = torch.empty(N, dtype=torch.int32, device=dev)
+    node = torch.empty(N, dtype=torch.int32, device=dev)
+    color = torch.empty(N, dtype=torch.int32, device=dev)
+    x_new = torch.empty_like(x_ord)
+    rowptr = torch.empty(N + 1, dtype=torch.int64, device=dev)
+    nnz = C.c_int64(0)
+    _check(lib().kc_supernodal_count(_ptr(x_ord), _ptr(l), d, float(rho), pat.c(), _ptr(newm), _ptr(level),
+                                     _ptr(node), _ptr(color), _ptr(x_new), _ptr(rowptr), C.byref(nnz),
+                                     _stream(stream)))
+    col = torch.empty(int(nnz.value), dtype=torch.int32, device=dev)
+    _check(lib().kc_supernodal_fill(_ptr(x_ord), _ptr(l), d, float(rho), pat.c(), _ptr(rowptr), _ptr(col),
+                                    _stream(stream)))
+    spat = schedule(rowptr, col, x_new, stream)
+    return dict(newm=newm, level=level, node=node, color=color, x_new=x_new, pat=spat)
+
+
+def supernodal_pipeline(x, rho, kern: Kernel, prec=FP32_FORM, opts=None, stream=None):
+    """order -> max-rule pattern -> supernodal ordering and pattern -> factor;
+    ``perm`` maps a new position to the original index."""
+    perm0, l, xo = order_points(x, stream)
+    pat0 = build_pattern(xo, l, rho, RULE_MAX, stream)
+    sn = supernodal(xo, l, rho, pat0, stream)
+    perm = perm0[sn["newm"].long()].contiguous()
+    val, diag, zp = factor(sn["pat"], sn["x_new"], kern, prec, opts, stream=stream)
+    return dict(perm=perm, sn=sn, pat=sn["pat"], x_new=sn["x_new"], val=val, diag=diag, zero_pivots=zp)
 
 
 # ------------------------------------- Section 6: given matrix, reverse order
