@@ -54,6 +54,7 @@ __global__ void __launch_bounds__(TK_THREADS) l_rows_k(const int64_t* __restrict
 #pragma unroll
     for (int r = 0; r < NS; ++r) acc[r] = 0.0;
     const int64_t e1 = rowptr[j + 1] - 1;
+#pragma unroll 4
     for (int64_t e = rowptr[j] + lane_id(); e < e1; e += 32) gather_fma<NS>(acc, (double)__ldg(&val[e]), z, __ldg(&col[e]));
     finish_row<NS>(acc, diag[j], z, j, y);
 }
@@ -97,6 +98,7 @@ __global__ void __launch_bounds__(TK_THREADS) lt_chunks_k(const int64_t* __restr
     double acc[NS];
 #pragma unroll
     for (int r = 0; r < NS; ++r) acc[r] = 0.0;
+#pragma unroll 4
     for (int64_t q = q0 + lane_id(); q < q1; q += 32)
         gather_fma<NS>(acc, (double)__ldg(&val[__ldg(&slot[q])]), v, __ldg(&rowidx[q]));
     if (off[i + 1] - off[i] == 1) {
