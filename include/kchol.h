@@ -126,7 +126,7 @@ const char* kc_last_error(void);
  * kc_opts has stage_bytes.  3: kc_kernel has family, alpha, beta;
  * kc_kernel_eval, kc_l_matvec, kc_lt_matvec, kc_llt_matvec, kc_logdet,
  * kc_pattern_reverse, kc_gather_entries, kc_factor_given, kc_refine_sparse,
- * kc_supernodal_count, kc_supernodal_fill. */
+ * kc_supernodal_count, kc_supernodal_fill, kc_supernodal. */
 #define KC_ABI_VERSION 3
 int32_t kc_abi_version(void);
 
@@ -382,12 +382,18 @@ kc_status kc_refine_sparse(const kc_pattern* pat, int32_t prec, const void* val,
  * (int32[N] each, may be NULL), x_new double[N*d] (the points in the new
  * order), rowptr int64[N+1] of S, nnz_out (host).  kc_supernodal_fill: col
  * int32[nnz] (ascending, diagonal last), from the same inputs and rowptr.
- * Both synchronise; KC_EINVAL if a level needs more than 64 colours. */
+ * kc_supernodal does both in one pass when col (device int32[col_capacity])
+ * holds nnz entries; otherwise it leaves col alone and the caller, seeing
+ * *nnz_out > col_capacity, completes with kc_supernodal_fill.  All
+ * synchronise; KC_EINVAL if a level needs more than 64 colours. */
 kc_status kc_supernodal_count(const double* x_ord, const double* l, int32_t d, double rho, const kc_pattern* pat,
                               int32_t* newm, int32_t* level, int32_t* node, int32_t* color, double* x_new,
                               int64_t* rowptr, int64_t* nnz_out, void* stream);
 kc_status kc_supernodal_fill(const double* x_ord, const double* l, int32_t d, double rho, const kc_pattern* pat,
                              const int64_t* rowptr, int32_t* col, void* stream);
+kc_status kc_supernodal(const double* x_ord, const double* l, int32_t d, double rho, const kc_pattern* pat,
+                        int32_t* newm, int32_t* level, int32_t* node, int32_t* color, double* x_new, int64_t* rowptr,
+                        int32_t* col, int64_t col_capacity, int64_t* nnz_out, void* stream);
 
 #ifdef __cplusplus
 }

@@ -46,7 +46,7 @@ kc_status factor_given_impl(const kc_pattern* P, const double* aval, int prec, v
                             int64_t* zero_out, const kc_opts* o, cudaStream_t s);
 kc_status supernodal_impl(const double* x_ord, const double* l, int d, double rho, const kc_pattern* P,
                           int32_t* newm, int32_t* level, int32_t* node_out, int32_t* color_out, double* x_new,
-                          int64_t* rowptr, int64_t* nnz_out, int32_t* col, cudaStream_t s);
+                          int64_t* rowptr, int64_t* nnz_out, int32_t* col, int64_t col_cap, cudaStream_t s);
 kc_status refine_sparse_impl(const kc_pattern* P, int prec, const void* val, const double* diag,
                              const int32_t* perm, const int64_t* arp, const int32_t* acol, const double* aval,
                              const double* b, int nrhs, double rtol, int maxit, double* x_out, int32_t* iters_out,
@@ -298,8 +298,20 @@ kc_status kc_supernodal_count(const double* x_ord, const double* l, int32_t d, d
     KC_TRY(check_points(x_ord, pat->N, d));
     if (!l || !newm || !x_new || !rowptr || !nnz_out) return fail(KC_EINVAL, "arrays must be non-NULL");
     if (!(rho >= 1.0)) return fail(KC_EINVAL, "the supernodal construction needs rho >= 1");
-    return supernodal_impl(x_ord, l, d, rho, pat, newm, level, node, color, x_new, rowptr, nnz_out, nullptr,
+    return supernodal_impl(x_ord, l, d, rho, pat, newm, level, node, color, x_new, rowptr, nnz_out, nullptr, 0,
                            (cudaStream_t)stream);
+}
+
+kc_status kc_supernodal(const double* x_ord, const double* l, int32_t d, double rho, const kc_pattern* pat,
+                        int32_t* newm, int32_t* level, int32_t* node, int32_t* color, double* x_new, int64_t* rowptr,
+                        int32_t* col, int64_t col_capacity, int64_t* nnz_out, void* stream) {
+    KC_TRY(check_pattern(pat));
+    KC_TRY(check_points(x_ord, pat->N, d));
+    if (!l || !newm || !x_new || !rowptr || !nnz_out || (col_capacity > 0 && !col))
+        return fail(KC_EINVAL, "arrays must be non-NULL");
+    if (!(rho >= 1.0)) return fail(KC_EINVAL, "the supernodal construction needs rho >= 1");
+    return supernodal_impl(x_ord, l, d, rho, pat, newm, level, node, color, x_new, rowptr, nnz_out, col,
+                           col_capacity, (cudaStream_t)stream);
 }
 
 kc_status kc_supernodal_fill(const double* x_ord, const double* l, int32_t d, double rho, const kc_pattern* pat,
@@ -309,7 +321,7 @@ kc_status kc_supernodal_fill(const double* x_ord, const double* l, int32_t d, do
     if (!l || !rowptr || !col) return fail(KC_EINVAL, "arrays must be non-NULL");
     if (!(rho >= 1.0)) return fail(KC_EINVAL, "the supernodal construction needs rho >= 1");
     return supernodal_impl(x_ord, l, d, rho, pat, nullptr, nullptr, nullptr, nullptr, nullptr,
-                           const_cast<int64_t*>(rowptr), nullptr, col, (cudaStream_t)stream);
+                           const_cast<int64_t*>(rowptr), nullptr, col, 0, (cudaStream_t)stream);
 }
 
 }  // extern "C"

@@ -473,9 +473,10 @@ static kc_status sn_order(const SnState& S, const int32_t* color, int64_t N, int
     return KC_OK;
 }
 
-// neighbour lists sorted by range start, then row counts (mode 0) or fill
+// neighbour lists sorted by range start, the row counts and rowptr, and the
+// rows themselves when col has room for them
 static kc_status sn_rows(const SnState& S, const int32_t* newm, const int32_t* start, const int32_t* end, int64_t N,
-                         int mode, int64_t* rowptr, int32_t* col, Arena& A, cudaStream_t s) {
+                         int64_t* rowptr, int64_t* nnz_out, int32_t* col, int64_t col_cap, Arena& A, cudaStream_t s) {
     int32_t *cnt, *list;
     int64_t* off;
     KC_TRY(A.get(&cnt, N));
@@ -495,24 +496,28 @@ static kc_status sn_rows(const SnState& S, const int32_t* newm, const int32_t* s
     KC_TRY(A.get(&list, ne));
     note_launch(), sn_nb_take_k<<<blocks_for(ne, 256), 256, 0, s>>>(v1, ne, list);
     KC_CUDA(cudaGetLastError());
-    if (mode == 0) {
+    if (nnz_out) {
         int64_t* rowcnt;
         KC_TRY(A.get(&rowcnt, N));
         note_launch(), sn_rows_k<<<blocks_for(N, SN_WARPS), SN_THREADS, 0, s>>>(newm, S.node, off, cnt, list, start,
                                                                                end, N, 0, rowcnt, nullptr, nullptr);
         KC_CUDA(cudaGetLastError());
         KC_TRY(exclusive_scan_i64(rowcnt, rowptr, N, A, s));
-    } else {
-        note_launch(), sn_rows_k<<<blocks_for(N, SN_WARPS), SN_THREADS, 0, s>>>(newm, S.node, off, cnt, list, start,
-                                                                               end, N, 1, nullptr, rowptr, col);
-        KC_CUDA(cudaGetLastError());
+        KC_TRY(sync_read(rowptr + N, nnz_out, sizeof(int64_t), s));
+        if (!col || *nnz_out > col_cap) return KC_OK;
     }
+    note_launch(), sn_rows_k<<<blocks_for(N, SN_WARPS), SN_THREADS, 0, s>>>(newm, S.node, off, cnt, list, start,
+                                                                           end, N, 1, nullptr, rowptr, col);
+    KC_CUDA(cudaGetLastError());
+    KC_CUDA(cudaStreamSynchronize(s));
     return KC_OK;
 }
 
+// nnz_out given: rowptr and nnz are computed, and col is filled when it holds
+// col_cap >= nnz entries; nnz_out NULL: col is filled from the given rowptr
 kc_status supernodal_impl(const double* x_ord, const double* l, int d, double rho, const kc_pattern* P,
                           int32_t* newm, int32_t* level, int32_t* node_out, int32_t* color_out, double* x_new,
-                          int64_t* rowptr, int64_t* nnz_out, int32_t* col, cudaStream_t s) {
+                          int64_t* rowptr, int64_t* nnz_out, int32_t* col, int64_t col_cap, cudaStream_t s) {
     const int64_t N = P->N;
     double l1 = 1.0;
     if (N > 1) KC_CUDA(cudaMemcpy(&l1, l + 1, sizeof(double), cudaMemcpyDeviceToHost));
@@ -533,14 +538,7 @@ kc_status supernodal_impl(const double* x_ord, const double* l, int d, double rh
     note_launch(), sn_scatter_k<<<blocks_for(N, 256), 256, 0, s>>>(mval, S.lev, S.node, color, x_ord, d, N, nm, level,
                                                                   node_out, color_out, x_new, start, end);
     KC_CUDA(cudaGetLastError());
-    if (!col) {
-        KC_TRY(sn_rows(S, nm, start, end, N, 0, rowptr, nullptr, A, s));
-        KC_TRY(sync_read(rowptr + N, nnz_out, sizeof(int64_t), s));
-        return KC_OK;
-    }
-    KC_TRY(sn_rows(S, nm, start, end, N, 1, rowptr, col, A, s));
-    KC_CUDA(cudaStreamSynchronize(s));
-    return KC_OK;
+    return sn_rows(S, nm, start, end, N, rowptr, nnz_out, col, col_cap, A, s);
 }
 
 }  // namespace kc

@@ -101,6 +101,7 @@ def lib():
             "kc_factor_given": [P(kc_pattern), vp, i32, vp, vp, P(C.c_int64), P(kc_opts), vp],
             "kc_supernodal_count": [vp, vp, i32, dbl, P(kc_pattern), vp, vp, vp, vp, vp, vp, P(C.c_int64), vp],
             "kc_supernodal_fill": [vp, vp, i32, dbl, P(kc_pattern), vp, vp, vp],
+            "kc_supernodal": [vp, vp, i32, dbl, P(kc_pattern), vp, vp, vp, vp, vp, vp, vp, i64, P(C.c_int64), vp],
             "kc_refine_sparse": [P(kc_pattern), i32, vp, vp, vp, vp, vp, vp, vp, i32, dbl, i32, vp, P(C.c_int32),
                                  P(C.c_double), P(kc_opts), vp],
         }
@@ -120,7 +121,7 @@ EXPORTED = ("kc_last_error", "kc_abi_version", "kc_launch_count", "kc_last_facto
             "kc_factor_plan_destroy", "kc_pattern_concat", "kc_points_concat", "kc_index_concat", "kc_kernel_eval",
             "kc_l_matvec", "kc_lt_matvec", "kc_llt_matvec", "kc_logdet", "kc_pattern_reverse",
             "kc_gather_entries", "kc_factor_given", "kc_refine_sparse", "kc_supernodal_count",
-            "kc_supernodal_fill")
+            "kc_supernodal_fill", "kc_supernodal")
 
 
 def launch_count() -> int:
@@ -401,11 +402,11 @@ def pipeline(x, rho, kern: Kernel, prec=FP32_FORM, rule=RULE_MAX, opts=None, str
 
 # ------------------------------- supernodal multicolour ordering and pattern
 
-def supernodal(x_ord, l, rho, pat: Pattern, stream=None):
+def supernodal(x_ord, l, rho, pat: Pattern, with_schedule=True, stream=None):
     """The supernodal multicolour ordering and pattern from the maximin order
     (x_ord, l) and its max-rule pattern pat of the same rho -> dict with newm
-    (maximin position of every new position), level, node, color, x_new and
-    the scheduled pattern of the new order."""
+    (maximin position of every new position), level, node, color, x_new,
+    rowptr, col and (with_schedule) the scheduled pattern of the new order."""
     _dev(x_ord, torch.float64, "x_ord")
     _dev(l, torch.float64, "l")
     N, d = x_ord.shape
@@ -417,14 +418,20 @@ def supernodal(x_ord, l, rho, pat: Pattern, stream=None):
     x_new = torch.empty_like(x_ord)
     rowptr = torch.empty(N + 1, dtype=torch.int64, device=dev)
     nnz = C.c_int64(0)
-    _check(lib().kc_supernodal_count(_ptr(x_ord), _ptr(l), d, float(rho), pat.c(), _ptr(newm), _ptr(level),
-                                     _ptr(node), _ptr(color), _ptr(x_new), _ptr(rowptr), C.byref(nnz),
-                                     _stream(stream)))
-    col = torch.empty(int(nnz.value), dtype=torch.int32, device=dev)
-    _check(lib().kc_supernodal_fill(_ptr(x_ord), _ptr(l), d, float(rho), pat.c(), _ptr(rowptr), _ptr(col),
-                                    _stream(stream)))
-    spat = schedule(rowptr, col, x_new, stream)
-    return dict(newm=newm, level=level, node=node, color=color, x_new=x_new, pat=spat)
+    # one pass when the guess holds the pattern (about 1.3x the max-rule one), else a second
+    cap = 2 * pat.nnz + N
+    col = torch.empty(cap, dtype=torch.int32, device=dev)
+    _check(lib().kc_supernodal(_ptr(x_ord), _ptr(l), d, float(rho), pat.c(), _ptr(newm), _ptr(level), _ptr(node),
+                               _ptr(color), _ptr(x_new), _ptr(rowptr), _ptr(col), cap, C.byref(nnz),
+                               _stream(stream)))
+    if nnz.value > cap:
+        col = torch.empty(int(nnz.value), dtype=torch.int32, device=dev)
+        _check(lib().kc_supernodal_fill(_ptr(x_ord), _ptr(l), d, float(rho), pat.c(), _ptr(rowptr), _ptr(col),
+                                        _stream(stream)))
+    else:
+        col = col[:nnz.value]
+    spat = schedule(rowptr, col, x_new, stream) if with_schedule else None
+    return dict(newm=newm, level=level, node=node, color=color, x_new=x_new, rowptr=rowptr, col=col, pat=spat)
 
 
 def supernodal_pipeline(x, rho, kern: Kernel, prec=FP32_FORM, opts=None, stream=None):

@@ -101,3 +101,33 @@ def test_supernodal_larger_structure():
     assert np.array_equal(H(perm0)[H(sn["newm"])], ref["order"])
     assert np.array_equal(H(sn["color"]), ref["color"])
     assert np.array_equal(H(sn["pat"].col), ref["col"])
+
+
+def test_supernodal_two_phase_when_the_buffer_is_short():
+    """kc_supernodal with too small a column buffer reports nnz and leaves the
+    buffer alone; kc_supernodal_fill then completes the same pattern, and the
+    count-only call gives the same rowptr."""
+    import ctypes as C
+    x = inputs.uniform(2000, 2, seed=112)
+    perm0, l, xo = kc.order_points(T(x))
+    pat0 = kc.build_pattern(xo, l, 3.0)
+    ref = kc.supernodal(xo, l, 3.0, pat0)
+    N, d = xo.shape
+    lib = kc.lib()
+    newm = torch.empty(N, dtype=torch.int32, device=DEV)
+    x_new = torch.empty_like(xo)
+    rp = torch.empty(N + 1, dtype=torch.int64, device=DEV)
+    col = torch.full((4,), -7, dtype=torch.int32, device=DEV)
+    nnz = C.c_int64(0)
+    kc._check(lib.kc_supernodal(kc._ptr(xo), kc._ptr(l), d, 3.0, pat0.c(), kc._ptr(newm), None, None, None,
+                                kc._ptr(x_new), kc._ptr(rp), kc._ptr(col), 4, C.byref(nnz), kc._stream(None)))
+    assert nnz.value == ref["pat"].nnz and torch.all(col == -7)
+    full = torch.empty(nnz.value, dtype=torch.int32, device=DEV)
+    kc._check(lib.kc_supernodal_fill(kc._ptr(xo), kc._ptr(l), d, 3.0, pat0.c(), kc._ptr(rp), kc._ptr(full),
+                                     kc._stream(None)))
+    assert torch.equal(rp, ref["pat"].rowptr) and torch.equal(full, ref["pat"].col)
+    rp2 = torch.empty_like(rp)
+    nn2 = C.c_int64(0)
+    kc._check(lib.kc_supernodal_count(kc._ptr(xo), kc._ptr(l), d, 3.0, pat0.c(), kc._ptr(newm), None, None, None,
+                                      kc._ptr(x_new), kc._ptr(rp2), C.byref(nn2), kc._stream(None)))
+    assert nn2.value == nnz.value and torch.equal(rp2, rp)
