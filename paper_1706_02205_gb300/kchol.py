@@ -439,7 +439,7 @@ def supernodal_pipeline(x, rho, kern: Kernel, prec=FP32_FORM, opts=None, stream=
     ``perm`` maps a new position to the original index."""
     perm0, l, xo = order_points(x, stream)
     pat0 = build_pattern(xo, l, rho, RULE_MAX, stream)
-    sn = supernodal(xo, l, rho, pat0, stream)
+    sn = supernodal(xo, l, rho, pat0, stream=stream)
     perm = perm0[sn["newm"].long()].contiguous()
     val, diag, zp = factor(sn["pat"], sn["x_new"], kern, prec, opts, stream=stream)
     return dict(perm=perm, sn=sn, pat=sn["pat"], x_new=sn["x_new"], val=val, diag=diag, zero_pivots=zp)
