@@ -126,7 +126,7 @@ const char* kc_last_error(void);
  * kc_opts has stage_bytes.  3: kc_kernel has family, alpha, beta;
  * kc_kernel_eval, kc_l_matvec, kc_lt_matvec, kc_llt_matvec, kc_logdet,
  * kc_pattern_reverse, kc_gather_entries, kc_factor_given, kc_refine_sparse,
- * kc_supernodal_count, kc_supernodal_fill, kc_supernodal. */
+ * kc_supernodal_count, kc_supernodal_fill, kc_supernodal, kc_pattern_validate. */
 #define KC_ABI_VERSION 3
 int32_t kc_abi_version(void);
 
@@ -169,6 +169,16 @@ kc_status kc_pattern_fill(const double* x_ord, const double* l, int64_t N, int32
 kc_status kc_schedule(int64_t N, const int64_t* rowptr, const int32_t* col, const double* x_ord, int32_t d,
                       int64_t* colptr, int32_t* rowidx, int64_t* slot, int32_t* level, int32_t* order,
                       int32_t* depth_out, void* stream);
+
+/* Check a pattern and its schedule (all device arrays of pat): rowptr from 0
+ * to nnz with every row nonempty, columns in range and ascending with the
+ * diagonal last; colptr likewise, row indices ascending with the diagonal
+ * first, each slot pointing at the same entry in the rows; order a
+ * permutation.  Every index is range-checked before it is used, so a corrupt
+ * pattern is reported (KC_EINVAL, naming the array and index) rather than
+ * read out of bounds.  The other entry points trust their pattern; run this
+ * on patterns that did not come from this library.  Synchronises. */
+kc_status kc_pattern_validate(const kc_pattern* pat, void* stream);
 
 /* ---- a5+a6: ICHOL(0) factor (Algorithm 2, left-looking form) ------------ *
  * For each column i in dependency order: p = Theta_ii - sum_k L_ik^2; if

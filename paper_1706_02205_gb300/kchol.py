@@ -102,6 +102,7 @@ def lib():
             "kc_supernodal_count": [vp, vp, i32, dbl, P(kc_pattern), vp, vp, vp, vp, vp, vp, P(C.c_int64), vp],
             "kc_supernodal_fill": [vp, vp, i32, dbl, P(kc_pattern), vp, vp, vp],
             "kc_supernodal": [vp, vp, i32, dbl, P(kc_pattern), vp, vp, vp, vp, vp, vp, vp, i64, P(C.c_int64), vp],
+            "kc_pattern_validate": [P(kc_pattern), vp],
             "kc_refine_sparse": [P(kc_pattern), i32, vp, vp, vp, vp, vp, vp, vp, i32, dbl, i32, vp, P(C.c_int32),
                                  P(C.c_double), P(kc_opts), vp],
         }
@@ -121,7 +122,7 @@ EXPORTED = ("kc_last_error", "kc_abi_version", "kc_launch_count", "kc_last_facto
             "kc_factor_plan_destroy", "kc_pattern_concat", "kc_points_concat", "kc_index_concat", "kc_kernel_eval",
             "kc_l_matvec", "kc_lt_matvec", "kc_llt_matvec", "kc_logdet", "kc_pattern_reverse",
             "kc_gather_entries", "kc_factor_given", "kc_refine_sparse", "kc_supernodal_count",
-            "kc_supernodal_fill", "kc_supernodal")
+            "kc_supernodal_fill", "kc_supernodal", "kc_pattern_validate")
 
 
 def launch_count() -> int:
@@ -250,6 +251,11 @@ def schedule(rowptr, col, x_ord=None, stream=None) -> Pattern:
                              _ptr(colptr), _ptr(rowidx), _ptr(slot), _ptr(level), _ptr(order), C.byref(depth),
                              _stream(stream)))
     return Pattern(rowptr, col, colptr, rowidx, slot, level, order, int(depth.value))
+
+
+def pattern_validate(pat: Pattern, stream=None):
+    """Raise KcError (KC_EINVAL) if the pattern or its schedule is malformed."""
+    _check(lib().kc_pattern_validate(pat.c(), _stream(stream)))
 
 
 # ------------------------------------------------------------------ a5, a6

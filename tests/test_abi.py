@@ -78,6 +78,7 @@ def test_new_entries_reject_bad_arguments_without_gpu(so):
     assert lib.kc_supernodal_count(None, None, 2, 3.0, None, None, None, None, None, None, None, None,
                                    None) == kchol.KC_EINVAL
     assert lib.kc_supernodal_fill(None, None, 2, 3.0, None, None, None, None) == kchol.KC_EINVAL
+    assert lib.kc_pattern_validate(None, None) == kchol.KC_EINVAL
     assert lib.kc_supernodal(None, None, 2, 3.0, None, None, None, None, None, None, None, None, 0, None,
                              None) == kchol.KC_EINVAL
     assert lib.kc_refine_sparse(None, 0, None, None, None, None, None, None, None, 1, 1e-10, 10, None, None, None,

@@ -1,0 +1,61 @@
+"""kc_pattern_validate: the patterns this library builds pass, and corrupted
+copies of them are reported (KC_EINVAL) without being used."""
+import numpy as np
+import pytest
+
+from paper_1706_02205_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_1706_02205_gb300 import kchol as kc  # noqa: E402
+
+DEV = torch.device("cuda:0")
+
+
+def _pattern():
+    x = torch.from_numpy(inputs.uniform(2000, 2, seed=121)).to(DEV)
+    perm, l, xo = kc.order_points(x)
+    return x, perm, l, xo, kc.build_pattern(xo, l, 3.0)
+
+
+def _copy(pat, **repl):
+    a = {k: getattr(pat, k).clone() for k in ("rowptr", "col", "colptr", "rowidx", "slot", "level", "order")}
+    for k, fn in repl.items():
+        fn(a[k])
+    return kc.Pattern(a["rowptr"], a["col"], a["colptr"], a["rowidx"], a["slot"], a["level"], a["order"], pat.depth)
+
+
+def test_library_patterns_pass():
+    x, perm, l, xo, pat = _pattern()
+    kc.pattern_validate(pat)
+    kc.pattern_validate(kc.build_pattern(xo, l, 2.0, kc.RULE_MIN))
+    kc.pattern_validate(kc.pattern_reverse(kc.build_pattern(xo, l, 2.0, kc.RULE_MIN), xo))
+    kc.pattern_validate(kc.supernodal(xo, l, 3.0, pat)["pat"])
+
+
+def _set(i, v):
+    def f(t):
+        t[i] = v
+    return f
+
+
+@pytest.mark.parametrize("what,repl", [
+    ("rowptr", {"rowptr": _set(5, 10**12)}),
+    ("col_order", {"col": lambda t: t.__setitem__(slice(100, 102), t[100:102].flip(0))}),
+    ("col_range", {"col": _set(300, -4)}),
+    ("colptr", {"colptr": _set(-1, 7)}),
+    ("rowidx", {"rowidx": _set(50, 10**9)}),
+    ("slot", {"slot": lambda t: t.__setitem__(40, t[41])}),
+    ("order", {"order": lambda t: t.__setitem__(3, t[4])}),
+])
+def test_corrupt_copies_are_reported(what, repl):
+    x, perm, l, xo, pat = _pattern()
+    bad = _copy(pat, **repl)
+    with pytest.raises(kc.KcError) as ei:
+        kc.pattern_validate(bad)
+    assert ei.value.status == kc.KC_EINVAL
+    kc.pattern_validate(pat)  # the original is untouched and passes
