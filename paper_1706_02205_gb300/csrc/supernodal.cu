@@ -151,7 +151,7 @@ __global__ void sn_assign_k(const double* __restrict__ x, int d, const int64_t* 
 // mode 0 counts per row, mode 1 fills at off[b].
 __global__ void sn_pairs_k(const double* __restrict__ x, int d, const int64_t* __restrict__ rowptr,
                            const int32_t* __restrict__ col, const int32_t* __restrict__ lev,
-                           const int32_t* __restrict__ node, int64_t N, double rl1, int mode,
+                           const int32_t* __restrict__ node, int64_t N, double rl1, int B, int mode,
                            int32_t* __restrict__ cnt, const int64_t* __restrict__ off, uint64_t* __restrict__ keys) {
     const int64_t b = (int64_t)blockIdx.x * SN_WARPS + (threadIdx.x >> 5);
     if (b >= N) return;
@@ -169,7 +169,7 @@ __global__ void sn_pairs_k(const double* __restrict__ x, int d, const int64_t* _
             const int32_t a = col[e];
             hit = sqrt(dist2_exact(xb, x + (int64_t)a * d, d)) <= sn_R(rl1, lev[a]);
             const uint32_t na = (uint32_t)node[a];
-            key = na < nb ? ((uint64_t)na << 32 | nb) : ((uint64_t)nb << 32 | na);
+            key = na < nb ? ((uint64_t)na << B | nb) : ((uint64_t)nb << B | na);
         }
         const unsigned bal = __ballot_sync(0xffffffffu, hit);
         if (mode && hit) keys[w + __popc(bal & ((1u << lane) - 1))] = key;
@@ -178,7 +178,7 @@ __global__ void sn_pairs_k(const double* __restrict__ x, int d, const int64_t* _
     }
     if (lane == 0) {
         const bool self = node[b] == (int32_t)b;  // the supernode's own block
-        if (mode && self) keys[w] = (uint64_t)nb << 32 | nb;
+        if (mode && self) keys[w] = (uint64_t)nb << B | nb;
         if (!mode) cnt[b] = n + (self ? 1 : 0);
     }
 }
@@ -196,11 +196,11 @@ __global__ void sn_unique_fill_k(const uint64_t* __restrict__ k, const int32_t* 
 // per supernode: earlier same-level neighbours (for the colours); mode 0
 // counts into cnt[hi], mode 1 fills
 __global__ void sn_color_adj_k(const uint64_t* __restrict__ pairs, int64_t np, const int32_t* __restrict__ lev,
-                               int mode, int32_t* __restrict__ cnt, const int64_t* __restrict__ off,
+                               int B, int mode, int32_t* __restrict__ cnt, const int64_t* __restrict__ off,
                                int32_t* __restrict__ fill, int32_t* __restrict__ list) {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= np) return;
-    const uint32_t lo = (uint32_t)(pairs[t] >> 32), hi = (uint32_t)pairs[t];
+    const uint32_t lo = (uint32_t)(pairs[t] >> B), hi = (uint32_t)(pairs[t] & ((1ULL << B) - 1));
     if (lo == hi || lev[lo] != lev[hi]) return;
     if (!mode) atomicAdd(&cnt[hi], 1);
     else list[off[hi] + atomicAdd(&fill[hi], 1)] = (int32_t)lo;
@@ -271,16 +271,17 @@ __global__ void sn_scatter_k(const int64_t* __restrict__ mval, const int32_t* __
 // sentinel that sorts last when lo == hi), one radix sort orders them by
 // supernode then start, and cnt[A] counts A's entries.
 __global__ void sn_nb_keys_k(const uint64_t* __restrict__ pairs, int64_t np, const int32_t* __restrict__ start,
-                             int32_t* __restrict__ cnt, uint64_t* __restrict__ key, int64_t* __restrict__ val) {
+                             int B, int32_t* __restrict__ cnt, uint64_t* __restrict__ key,
+                             int64_t* __restrict__ val) {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= np) return;
-    const uint32_t lo = (uint32_t)(pairs[t] >> 32), hi = (uint32_t)pairs[t];
+    const uint32_t lo = (uint32_t)(pairs[t] >> B), hi = (uint32_t)(pairs[t] & ((1ULL << B) - 1));
     atomicAdd(&cnt[lo], 1);
-    key[2 * t] = (uint64_t)lo << 32 | (uint32_t)start[hi];
+    key[2 * t] = (uint64_t)lo << B | (uint32_t)start[hi];
     val[2 * t] = hi;
     if (lo != hi) {
         atomicAdd(&cnt[hi], 1);
-        key[2 * t + 1] = (uint64_t)hi << 32 | (uint32_t)start[lo];
+        key[2 * t + 1] = (uint64_t)hi << B | (uint32_t)start[lo];
         val[2 * t + 1] = lo;
     } else {
         key[2 * t + 1] = ~0ULL;
@@ -323,8 +324,9 @@ struct SnState {
     int32_t* lev = nullptr;      // per maximin position
     int8_t* state = nullptr;     // supernode or not
     int32_t* node = nullptr;     // per maximin position
-    uint64_t* pairs = nullptr;   // unique supernode pairs (lo << 32 | hi), sorted
+    uint64_t* pairs = nullptr;   // unique supernode pairs (lo << B | hi), sorted
     int64_t npairs = 0;
+    int B = 1;                   // bits of an index: N - 1 < 2^B
 };
 
 static kc_status sync_read(const void* dev, void* host, size_t bytes, cudaStream_t s) {
@@ -342,7 +344,7 @@ static kc_status sn_pairs(const double* x, int d, const kc_pattern* P, double rl
     KC_TRY(A.get(&cnt, N));
     KC_TRY(A.get(&off, N + 1));
     note_launch(), sn_pairs_k<<<blocks_for(N, SN_WARPS), SN_THREADS, 0, s>>>(x, d, P->rowptr, P->col, S.lev, S.node,
-                                                                            N, rl1, 0, cnt, nullptr, nullptr);
+                                                                            N, rl1, S.B, 0, cnt, nullptr, nullptr);
     KC_CUDA(cudaGetLastError());
     KC_TRY(exclusive_scan_i32_to_i64(cnt, off, N, A, s));
     int64_t total = 0;
@@ -354,10 +356,10 @@ static kc_status sn_pairs(const double* x, int d, const kc_pattern* P, double rl
     KC_TRY(A.get(&v0, total));
     KC_TRY(A.get(&v1, total));
     note_launch(), sn_pairs_k<<<blocks_for(N, SN_WARPS), SN_THREADS, 0, s>>>(x, d, P->rowptr, P->col, S.lev, S.node,
-                                                                            N, rl1, 1, cnt, off, k0);
+                                                                            N, rl1, S.B, 1, cnt, off, k0);
     KC_CUDA(cudaGetLastError());
     KC_CUDA(cudaMemsetAsync(v0, 0, sizeof(int64_t) * total, s));
-    KC_TRY(radix_sort_u64_i64(k0, v0, k1, v1, total, 64, A, s));
+    KC_TRY(radix_sort_u64_i64(k0, v0, k1, v1, total, 2 * S.B, A, s));
     int32_t* first;
     int64_t* pos;
     KC_TRY(A.get(&first, total));
@@ -423,15 +425,15 @@ static kc_status sn_colors(const SnState& S, int64_t N, int32_t* color, Arena& A
     KC_TRY(A.get(&off, N + 1));
     KC_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * N, s));
     KC_CUDA(cudaMemsetAsync(fill, 0, sizeof(int32_t) * N, s));
-    note_launch(), sn_color_adj_k<<<blocks_for(S.npairs, 256), 256, 0, s>>>(S.pairs, S.npairs, S.lev, 0, cnt,
+    note_launch(), sn_color_adj_k<<<blocks_for(S.npairs, 256), 256, 0, s>>>(S.pairs, S.npairs, S.lev, S.B, 0, cnt,
                                                                            nullptr, nullptr, nullptr);
     KC_CUDA(cudaGetLastError());
     KC_TRY(exclusive_scan_i32_to_i64(cnt, off, N, A, s));
     int64_t total = 0;
     KC_TRY(sync_read(off + N, &total, sizeof(total), s));
     KC_TRY(A.get(&list, total));
-    note_launch(), sn_color_adj_k<<<blocks_for(S.npairs, 256), 256, 0, s>>>(S.pairs, S.npairs, S.lev, 1, cnt, off,
-                                                                           fill, list);
+    note_launch(), sn_color_adj_k<<<blocks_for(S.npairs, 256), 256, 0, s>>>(S.pairs, S.npairs, S.lev, S.B, 1, cnt,
+                                                                           off, fill, list);
     KC_CUDA(cudaGetLastError());
     KC_CUDA(cudaMemsetAsync(color, 0xff, sizeof(int32_t) * N, s));  // -1: uncoloured
     unsigned long long* pend;
@@ -489,9 +491,10 @@ static kc_status sn_rows(const SnState& S, const int32_t* newm, const int32_t* s
     KC_TRY(A.get(&k1, ne));
     KC_TRY(A.get(&v0, ne));
     KC_TRY(A.get(&v1, ne));
-    note_launch(), sn_nb_keys_k<<<blocks_for(S.npairs, 256), 256, 0, s>>>(S.pairs, S.npairs, start, cnt, k0, v0);
+    note_launch(), sn_nb_keys_k<<<blocks_for(S.npairs, 256), 256, 0, s>>>(S.pairs, S.npairs, start, S.B, cnt, k0,
+                                                                          v0);
     KC_CUDA(cudaGetLastError());
-    KC_TRY(radix_sort_u64_i64(k0, v0, k1, v1, ne, 64, A, s));
+    KC_TRY(radix_sort_u64_i64(k0, v0, k1, v1, ne, 2 * S.B + 1, A, s));  // + the sentinel bit
     KC_TRY(exclusive_scan_i32_to_i64(cnt, off, N, A, s));
     KC_TRY(A.get(&list, ne));
     note_launch(), sn_nb_take_k<<<blocks_for(ne, 256), 256, 0, s>>>(v1, ne, list);
@@ -524,6 +527,7 @@ kc_status supernodal_impl(const double* x_ord, const double* l, int d, double rh
     const double rl1 = rho * l1;
     Arena A(s);
     SnState S;
+    while (S.B < 31 && ((int64_t)1 << S.B) < N) ++S.B;
     KC_TRY(sn_nodes(x_ord, d, l, P, rl1, S, A, s));
     KC_TRY(sn_pairs(x_ord, d, P, rl1, S, A, s));
     int32_t* color;
