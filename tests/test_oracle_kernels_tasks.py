@@ -192,3 +192,14 @@ def test_ichol_float_storage_mode():
         s = float(np.float32(Th[j, i])) - L[j, :i] @ L[i, :i]
         assert abs(v32[e] * L[i, i] - s) <= (2.0**-24 * abs(v32[e]) + 1e-15) * L[i, i] + 1e-14, e
     assert np.max(np.abs(v32 - val)) < 1e-4 and not zc32.any()
+
+
+@pytest.mark.parametrize("name,kern", KERNELS + [("matern_2.5", oracle.Kernel(2.5, 0.3, 1.7, 1e-2))],
+                         ids=[k[0] for k in KERNELS] + ["matern_2.5"])
+def test_theta_entries_vs_dense(name, kern):
+    """Single entries Theta_ab (nugget on the diagonal only) equal the dense
+    matrix built from SciPy's Bessel function / NumPy."""
+    x = inputs.uniform(60, 3, seed=77)
+    T = refmath.dense_cov(x, kern)
+    got = np.array([[oracle.theta(x, a, b, kern) for b in range(60)] for a in range(60)])
+    np.testing.assert_allclose(got, T, rtol=1e-12, atol=0)
