@@ -17,8 +17,8 @@
 //
 // Every pair these rules test lies in the max-rule pattern S_rho of the same
 // rho (for a before b, d(a, b) <= rho means dist <= R_k(a) <= rho l[a]), so
-// the construction filters that pattern (rows for earlier, CSC columns for
-// later neighbours).  The two greedy passes run as rounds that reproduce the
+// the construction filters that pattern's rows (later neighbours follow by
+// symmetry).  The two greedy passes run as rounds that reproduce the
 // sequential result exactly: a point decides once every earlier neighbour
 // has (lexicographically first independent set; Jones-Plassmann colouring in
 // index order).  Rounds are host-driven launches, so no kernel waits.
@@ -47,13 +47,18 @@ __global__ void sn_level_k(const double* __restrict__ l, int64_t N, int32_t* __r
     lev[m] = k;
 }
 
-// conflicts of m: same level, dist <= R_k; earlier ones from row m of the
-// pattern, later ones from column m.  mode 0 counts, mode 1 fills.
+// conflicts of m: same level, dist <= R_k.  The earlier ones come from row m
+// of the pattern; the later ones by symmetry (m is a later conflict of each
+// of its earlier ones), so no CSC column is scanned (the first maximin
+// columns hold nearly every point).  mode 0 counts both kinds (cnt_e[m], and
+// cnt_l[i] += 1 for each earlier conflict i); mode 1 fills list[off[m] ..]
+// with the earlier conflicts first, then, from the other side, the later
+// ones (their order within the list is immaterial).
 __global__ void sn_conflicts_k(const double* __restrict__ x, int d, const int64_t* __restrict__ rowptr,
-                               const int32_t* __restrict__ col, const int64_t* __restrict__ colptr,
-                               const int32_t* __restrict__ rowidx, const int32_t* __restrict__ lev, int64_t N,
-                               double rl1, int mode, int32_t* __restrict__ cnt_e, int32_t* __restrict__ cnt,
-                               const int64_t* __restrict__ off, int32_t* __restrict__ list) {
+                               const int32_t* __restrict__ col, const int32_t* __restrict__ lev, int64_t N,
+                               double rl1, int mode, int32_t* __restrict__ cnt_e, int32_t* __restrict__ cnt_l,
+                               const int64_t* __restrict__ off, int32_t* __restrict__ fill_l,
+                               int32_t* __restrict__ list) {
     const int64_t m = (int64_t)blockIdx.x * SN_WARPS + (threadIdx.x >> 5);
     if (m >= N) return;
     const int lane = lane_id();
@@ -61,9 +66,8 @@ __global__ void sn_conflicts_k(const double* __restrict__ x, int d, const int64_
     const double R = sn_R(rl1, k);
     const double* xm = x + m * d;
     int64_t w = mode ? off[m] : 0;
-    int ne = 0, nl = 0;
-    // earlier: row m without its diagonal
-    const int64_t a0 = rowptr[m], a1 = rowptr[m + 1] - 1;
+    int ne = 0;
+    const int64_t a0 = rowptr[m], a1 = rowptr[m + 1] - 1;  // row m without its diagonal
     for (int64_t e0 = a0; e0 < a1; e0 += 32) {
         const int64_t e = e0 + lane;
         bool hit = false;
@@ -73,29 +77,24 @@ __global__ void sn_conflicts_k(const double* __restrict__ x, int d, const int64_
             hit = lev[i] == k && sqrt(dist2_exact(xm, x + (int64_t)i * d, d)) <= R;
         }
         const unsigned b = __ballot_sync(0xffffffffu, hit);
-        if (mode && hit) list[w + __popc(b & ((1u << lane) - 1))] = i;
+        if (hit) {
+            if (mode) {
+                list[w + __popc(b & ((1u << lane) - 1))] = i;
+                list[off[i] + cnt_e[i] + atomicAdd(&fill_l[i], 1)] = (int32_t)m;
+            } else {
+                atomicAdd(&cnt_l[i], 1);
+            }
+        }
         w += __popc(b);
         ne += __popc(b);
     }
-    // later: column m without its diagonal (first)
-    const int64_t c0 = colptr[m] + 1, c1 = colptr[m + 1];
-    for (int64_t q0 = c0; q0 < c1; q0 += 32) {
-        const int64_t q = q0 + lane;
-        bool hit = false;
-        int32_t j = -1;
-        if (q < c1) {
-            j = rowidx[q];
-            hit = lev[j] == k && sqrt(dist2_exact(xm, x + (int64_t)j * d, d)) <= R;
-        }
-        const unsigned b = __ballot_sync(0xffffffffu, hit);
-        if (mode && hit) list[w + __popc(b & ((1u << lane) - 1))] = j;
-        w += __popc(b);
-        nl += __popc(b);
-    }
-    if (!mode && lane == 0) {
-        cnt_e[m] = ne;
-        cnt[m] = ne + nl;
-    }
+    if (!mode && lane == 0) cnt_e[m] = ne;
+}
+
+__global__ void sn_sum_k(const int32_t* __restrict__ a, const int32_t* __restrict__ b, int64_t N,
+                         int32_t* __restrict__ c) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < N) c[t] = a[t] + b[t];
 }
 
 // one round of the greedy independent set: m joins when every earlier
@@ -383,20 +382,26 @@ static kc_status sn_nodes(const double* x, int d, const double* l, const kc_patt
     KC_TRY(A.get(&S.node, N));
     note_launch(), sn_level_k<<<blocks_for(N, 256), 256, 0, s>>>(l, N, S.lev);
     KC_CUDA(cudaGetLastError());
-    int32_t *cnt_e, *cnt, *list;
+    int32_t *cnt_e, *cnt_l, *fill_l, *cnt, *list;
     int64_t* off;
     KC_TRY(A.get(&cnt_e, N));
+    KC_TRY(A.get(&cnt_l, N));
+    KC_TRY(A.get(&fill_l, N));
     KC_TRY(A.get(&cnt, N));
     KC_TRY(A.get(&off, N + 1));
+    KC_CUDA(cudaMemsetAsync(cnt_l, 0, sizeof(int32_t) * N, s));
+    KC_CUDA(cudaMemsetAsync(fill_l, 0, sizeof(int32_t) * N, s));
     note_launch(), sn_conflicts_k<<<blocks_for(N, SN_WARPS), SN_THREADS, 0, s>>>(
-        x, d, P->rowptr, P->col, P->colptr, P->rowidx, S.lev, N, rl1, 0, cnt_e, cnt, nullptr, nullptr);
+        x, d, P->rowptr, P->col, S.lev, N, rl1, 0, cnt_e, cnt_l, nullptr, nullptr, nullptr);
+    KC_CUDA(cudaGetLastError());
+    note_launch(), sn_sum_k<<<blocks_for(N, 256), 256, 0, s>>>(cnt_e, cnt_l, N, cnt);
     KC_CUDA(cudaGetLastError());
     KC_TRY(exclusive_scan_i32_to_i64(cnt, off, N, A, s));
     int64_t total = 0;
     KC_TRY(sync_read(off + N, &total, sizeof(total), s));
     KC_TRY(A.get(&list, total));
     note_launch(), sn_conflicts_k<<<blocks_for(N, SN_WARPS), SN_THREADS, 0, s>>>(
-        x, d, P->rowptr, P->col, P->colptr, P->rowidx, S.lev, N, rl1, 1, cnt_e, cnt, off, list);
+        x, d, P->rowptr, P->col, S.lev, N, rl1, 1, cnt_e, cnt_l, off, fill_l, list);
     KC_CUDA(cudaGetLastError());
     KC_CUDA(cudaMemsetAsync(S.state, 0, N, s));
     unsigned long long* und;
