@@ -279,8 +279,8 @@ def run_ours(args, rank, world):
 
 # ------------------------------------------------ other workloads (ours)
 
-# DRAM traffic of the FP32-form factor kernel per algorithmic byte, from the ncu capture summarised in
-# profiles/ichol_fp32_jittered512_ncu_full.md (512x512 grid: dram read + write = 27.490 GB for
+# DRAM traffic of the FP32-form factor kernel per algorithmic byte, from the ncu capture of the factor
+# on the 512x512 jittered grid (dram read + write = 27.490 GB for
 # B_op = 26.388 GB).  Both are sums over the same (j, i) pairs, so the ratio carries to the full size.
 # It is reported only while the kernel's sources are the ones the counters were taken on (the
 # interface header adds only the struct layouts, which tests/test_abi.py pins field by field).

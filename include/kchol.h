@@ -15,9 +15,13 @@
  * --------------------------------
  *  - Plain C ABI.  Pointers marked "device" are CUDA device pointers owned by
  *    the caller; pointers marked "host" are ordinary host memory.  The library
- *    never frees caller memory.  Internal scratch is taken with
- *    cudaMallocAsync on the given stream and released before the call returns
- *    (stream-ordered).
+ *    never frees caller memory.  Internal scratch is taken stream-ordered on
+ *    the given stream from a private memory pool per device (created on the
+ *    library's first call on that device; the device's default pool, which
+ *    cudaMallocAsync uses for everyone else in the process, is not touched)
+ *    and released before the call returns.  The private pool keeps up to
+ *    16 GiB of released scratch mapped for the next call, so repeated calls do
+ *    not map GBs afresh; kc_scratch_trim hands it back to the driver.
  *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
  *    Kernels are enqueued on it.  A call that returns a size to the host
  *    (marked "synchronises") waits for the stream.
@@ -126,8 +130,9 @@ const char* kc_last_error(void);
  * kc_opts has stage_bytes.  3: kc_kernel has family, alpha, beta;
  * kc_kernel_eval, kc_l_matvec, kc_lt_matvec, kc_llt_matvec, kc_logdet,
  * kc_pattern_reverse, kc_gather_entries, kc_factor_given, kc_refine_sparse,
- * kc_supernodal_count, kc_supernodal_fill, kc_supernodal, kc_pattern_validate. */
-#define KC_ABI_VERSION 3
+ * kc_supernodal_count, kc_supernodal_fill, kc_supernodal, kc_pattern_validate.
+ * 4: kc_scratch_trim; scratch from a private pool per device. */
+#define KC_ABI_VERSION 4
 int32_t kc_abi_version(void);
 
 /* Number of kernels this library has launched in the process so far
@@ -138,6 +143,12 @@ int64_t kc_launch_count(void);
  * last kc_factor, measured with CUDA events on the launching stream (the
  * task-list build before it is excluded). */
 double kc_last_factor_kernel_ms(void);
+
+/* Releases the memory the current device's private scratch pool keeps mapped
+ * between calls, down to keep_bytes (0 = all of it).  Memory still in use by
+ * work enqueued on some stream is not released.  KC_EINVAL if keep_bytes < 0;
+ * KC_OK (nothing to do) before the library's first call on the device. */
+kc_status kc_scratch_trim(int64_t keep_bytes);
 
 /* ---- a2: maximin ordering (Section 2.3) -------------------------------- *
  * x: device double[N*d].  Outputs (device): perm int32[N] (position ->
@@ -255,7 +266,10 @@ kc_status kc_solve(const kc_pattern* pat, int32_t prec, const void* val, const d
  * array: calls that overlap on the GPU race and corrupt each other, so
  * serialise them.  The first call on a device, with that device current,
  * looks up the array's device address (cudaGetSymbolAddress); make that first
- * call before any stream capture.  Synchronises. */
+ * call before any stream capture.  The address is kept per device together
+ * with the unique id of the CUDA context it belongs to: after a
+ * cudaDeviceReset (a new context) the next call looks it up again, so that
+ * call too should come before any stream capture.  Synchronises. */
 kc_status kc_solve_noalloc(const kc_pattern* pat, int32_t prec, const void* val, const double* diag,
                            const kc_kernel* kern, const int32_t* perm, const double* b, int32_t nrhs, double* x,
                            void* stream);

@@ -98,6 +98,11 @@ int32_t kc_abi_version(void) { return KC_ABI_VERSION; }
 
 int64_t kc_launch_count(void) { return launch_count(); }
 
+kc_status kc_scratch_trim(int64_t keep_bytes) {
+    KC_RANGE("kc_scratch_trim");
+    return scratch_trim(keep_bytes);
+}
+
 double kc_last_factor_kernel_ms(void) { return factor_kernel_ms(); }
 
 kc_status kc_order_points(const double* x, int64_t N, int32_t d, int32_t* perm, double* l, double* x_ord,

@@ -32,13 +32,16 @@ kc_status cuda_fail(cudaError_t e, const char* what);
 enum : int { DEV_OK = 0, DEV_TIMEOUT = 1, DEV_BAD_INPUT = 2 };
 
 // ------------------------------------------------------- stream scratch
-// The scratch comes from the device's default stream-ordered memory pool.
-// Its release threshold is 0 unless set, which hands freed memory back to the
-// driver at every synchronisation, so each call would map its scratch (GBs
-// for a 2^20-point schedule) afresh; keep_pool_warm() lets the pool keep up to
-// SCRATCH_KEEP_BYTES of freed memory for the next call (once per device).
+// The scratch comes from a private stream-ordered memory pool per device
+// (scratch_pool), never from the device's default pool, so other users of
+// cudaMallocAsync in the process are not affected.  The pool keeps up to
+// SCRATCH_KEEP_BYTES of freed memory mapped for the next call (with a release
+// threshold of 0 every call would map its scratch -- GBs for a 2^20-point
+// schedule -- afresh); kc_scratch_trim returns it to the driver.
 constexpr uint64_t SCRATCH_KEEP_BYTES = 16ull << 30;
-void keep_pool_warm();
+kc_status scratch_pool(cudaMemPool_t* out);
+kc_status scratch_alloc(void** p, size_t bytes, cudaStream_t s);
+kc_status scratch_trim(int64_t keep_bytes);
 
 // Stream-ordered scratch: every buffer is freed (cudaFreeAsync) when the
 // arena goes out of scope, after the work enqueued before that point.
@@ -47,7 +50,7 @@ struct Arena {
     static constexpr int CAP = 128;
     void* ptrs[CAP];
     int n = 0;
-    explicit Arena(cudaStream_t st) : s(st) { keep_pool_warm(); }
+    explicit Arena(cudaStream_t st) : s(st) {}
     ~Arena() {
         for (int i = n - 1; i >= 0; --i) cudaFreeAsync(ptrs[i], s);
     }
@@ -57,8 +60,7 @@ struct Arena {
         void* p = nullptr;
         size_t bytes = count * sizeof(T);
         if (bytes == 0) bytes = 16;
-        cudaError_t e = cudaMallocAsync(&p, bytes, s);
-        if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync(scratch)");
+        KC_TRY(scratch_alloc(&p, bytes, s));
         ptrs[n++] = p;
         *out = (T*)p;
         return KC_OK;

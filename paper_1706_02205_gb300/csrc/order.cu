@@ -527,7 +527,8 @@ kc_status order_impl(const double* x, int64_t N, int d, int32_t* perm, double* l
             if (nitems > item_cap) {
                 item_cap = nitems * 2;
                 if (item_sel) cudaFreeAsync(item_sel, s);
-                KC_CUDA(cudaMallocAsync(&item_sel, sizeof(int32_t) * item_cap, s));
+                item_sel = nullptr;
+                KC_TRY(scratch_alloc((void**)&item_sel, sizeof(int32_t) * item_cap, s));
             }
             ::kc::note_launch(), ord_item_fill_k<<<blocks_for(ns * 32, 256), 256, 0, s>>>(ioff, ns, item_sel);
             ::kc::note_launch(), ord_update_k<<<blocks_for(nitems * 32, 256), 256, 0, s>>>(g0, sel, ioff, item_sel, nitems, cstart, xg, d,

@@ -3,6 +3,7 @@
 #include <cstdio>
 #include <cmath>
 #include <atomic>
+#include <mutex>
 
 #include <vector>
 
@@ -31,18 +32,59 @@ int64_t launch_count() { return g_launches.load(std::memory_order_relaxed); }
 void set_factor_kernel_ms(double ms) { g_factor_ms = ms; }
 double factor_kernel_ms() { return g_factor_ms; }
 
-void keep_pool_warm() {
-    static std::atomic<uint64_t> done{0};  // bit per device
+// One private stream-ordered pool per device for the library's scratch.  The
+// device's default pool (what cudaMallocAsync uses for everyone else in the
+// process) is left as it is.  The private pool keeps up to SCRATCH_KEEP_BYTES
+// of freed memory mapped between calls; kc_scratch_trim hands it back.
+static std::mutex g_pool_mu;
+static cudaMemPool_t g_pools[64] = {nullptr};
+
+kc_status scratch_pool(cudaMemPool_t* out) {
     int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return;
-    const uint64_t bit = 1ull << dev;
-    if (done.load(std::memory_order_relaxed) & bit) return;
-    cudaMemPool_t pool;
-    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+    KC_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return fail(KC_EINVAL, "device index out of range");
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    if (!g_pools[dev]) {
+        cudaMemPoolProps props = {};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.handleTypes = cudaMemHandleTypeNone;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaMemPool_t pool = nullptr;
+        KC_CUDA(cudaMemPoolCreate(&pool, &props));
         uint64_t keep = SCRATCH_KEEP_BYTES;
-        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        cudaError_t e = cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        if (e != cudaSuccess) {
+            cudaMemPoolDestroy(pool);
+            return cuda_fail(e, "cudaMemPoolSetAttribute(scratch pool)");
+        }
+        g_pools[dev] = pool;
     }
-    done.fetch_or(bit, std::memory_order_relaxed);
+    *out = g_pools[dev];
+    return KC_OK;
+}
+
+kc_status scratch_alloc(void** p, size_t bytes, cudaStream_t s) {
+    cudaMemPool_t pool = nullptr;
+    KC_TRY(scratch_pool(&pool));
+    cudaError_t e = cudaMallocFromPoolAsync(p, bytes, pool, s);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMallocFromPoolAsync(scratch)");
+    return KC_OK;
+}
+
+kc_status scratch_trim(int64_t keep_bytes) {
+    if (keep_bytes < 0) return fail(KC_EINVAL, "kc_scratch_trim: keep_bytes < 0");
+    int dev = 0;
+    KC_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return fail(KC_EINVAL, "device index out of range");
+    cudaMemPool_t pool = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_pool_mu);
+        pool = g_pools[dev];
+    }
+    if (!pool) return KC_OK;  // nothing allocated on this device yet
+    KC_CUDA(cudaMemPoolTrimTo(pool, (size_t)keep_bytes));
+    return KC_OK;
 }
 
 int sm_count() {

@@ -20,7 +20,9 @@
 // Host code cannot use the array's name as a device address (it is a
 // host-side stand-in).  The first call on each device, with that device
 // current, looks the address up with cudaGetSymbolAddress and caches it; make
-// that first call before any stream capture.
+// that first call before any stream capture.  The cache is keyed on the
+// unique id of the current CUDA context, so after a cudaDeviceReset the next
+// call looks the address up again instead of using the old context's.
 //
 // Method: the same two level-scheduled solves as kc_solve (forward by rows of
 // L in (level, index) order, backward by columns of L in the reverse order),
@@ -46,17 +48,47 @@ static __device__ __align__(256) unsigned char g_solve_scratch[SCRATCH_BYTES];
 constexpr int NA_MAX_DEVICES = 64;
 std::mutex g_mu;
 unsigned char* g_addr[NA_MAX_DEVICES] = {nullptr};
+unsigned long long g_ctx_id[NA_MAX_DEVICES] = {0};
+
+// The unique id (cuCtxGetId) of the calling thread's current CUDA context, by
+// the driver entry points the runtime hands out (no link against libcuda).
+// False if there is no current context or the driver lacks the calls.
+bool current_context_id(unsigned long long* id) {
+    typedef int (*get_current_t)(void**);
+    typedef int (*get_id_t)(void*, unsigned long long*);
+    static get_current_t get_current = nullptr;
+    static get_id_t get_id = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_current = (get_current_t)f;
+        f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = (get_id_t)f;
+    });
+    void* ctx = nullptr;
+    if (!get_current || !get_id || get_current(&ctx) != 0 || !ctx) return false;
+    return get_id(ctx, id) == 0;
+}
 
 kc_status scratch_address(unsigned char** out) {
     int dev = 0;
     KC_CUDA(cudaGetDevice(&dev));
     if (dev < 0 || dev >= NA_MAX_DEVICES) return fail(KC_EINVAL, "kc_solve_noalloc: device index out of range");
+    unsigned long long id = 0;
+    bool have_id = current_context_id(&id);
     std::lock_guard<std::mutex> lk(g_mu);
-    if (!g_addr[dev]) {
+    if (!g_addr[dev] || !have_id || g_ctx_id[dev] != id) {
         void* p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_solve_scratch);
+        cudaError_t e = cudaGetSymbolAddress(&p, g_solve_scratch);  // makes the context current if needed
         if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(solve scratch)");
+        if (!have_id) have_id = current_context_id(&id);
         g_addr[dev] = (unsigned char*)p;
+        g_ctx_id[dev] = have_id ? id : 0;  // 0: no id, so the next call looks the address up again
     }
     *out = g_addr[dev];
     return KC_OK;

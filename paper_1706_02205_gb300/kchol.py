@@ -52,7 +52,7 @@ class kc_opts(C.Structure):
 
 
 _lib = None
-ABI_VERSION = 3  # KC_ABI_VERSION of include/kchol.h that these signatures follow
+ABI_VERSION = 4  # KC_ABI_VERSION of include/kchol.h that these signatures follow
 
 
 def lib():
@@ -103,6 +103,7 @@ def lib():
             "kc_supernodal_fill": [vp, vp, i32, dbl, P(kc_pattern), vp, vp, vp],
             "kc_supernodal": [vp, vp, i32, dbl, P(kc_pattern), vp, vp, vp, vp, vp, vp, vp, i64, P(C.c_int64), vp],
             "kc_pattern_validate": [P(kc_pattern), vp],
+            "kc_scratch_trim": [i64],
             "kc_refine_sparse": [P(kc_pattern), i32, vp, vp, vp, vp, vp, vp, vp, i32, dbl, i32, vp, P(C.c_int32),
                                  P(C.c_double), P(kc_opts), vp],
         }
@@ -122,12 +123,17 @@ EXPORTED = ("kc_last_error", "kc_abi_version", "kc_launch_count", "kc_last_facto
             "kc_factor_plan_destroy", "kc_pattern_concat", "kc_points_concat", "kc_index_concat", "kc_kernel_eval",
             "kc_l_matvec", "kc_lt_matvec", "kc_llt_matvec", "kc_logdet", "kc_pattern_reverse",
             "kc_gather_entries", "kc_factor_given", "kc_refine_sparse", "kc_supernodal_count",
-            "kc_supernodal_fill", "kc_supernodal", "kc_pattern_validate")
+            "kc_supernodal_fill", "kc_supernodal", "kc_pattern_validate", "kc_scratch_trim")
 
 
 def launch_count() -> int:
     """Kernels launched by libkchol in this process so far."""
     return int(lib().kc_launch_count())
+
+
+def scratch_trim(keep_bytes: int = 0):
+    """Release the current device's scratch pool down to keep_bytes."""
+    _check(lib().kc_scratch_trim(int(keep_bytes)))
 
 
 def last_factor_kernel_ms() -> float:

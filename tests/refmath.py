@@ -68,26 +68,27 @@ def pattern_mask(rowptr, col, N):
     return M | M.T
 
 
-def ichol_right_looking(A, S):
-    """The paper's Algorithm 2 as printed (right-looking), on a dense array.
+def ichol_masked_schur(A, S):
+    """ICHOL(0) as a dense Cholesky factorisation whose Schur-complement
+    updates are kept only on the pattern S (the definition behind Algorithm 2,
+    Section 2.2), vectorised over whole trailing blocks.
 
-    Entries outside S are zeroed first; at step i the column is divided by
-    sqrt(A_ii) and A_kj -= A_ki A_ji / A_ii for j > i with (i,j) in S and
-    k >= j with (k,i), (k,j) in S.  A nonpositive pivot zeroes column i and
-    skips its updates (Section 4.4).
+    A is first restricted to S.  Eliminating pivot i forms the column
+    l = A[i:, i] / sqrt(A_ii), which is zero off S because A stays supported on
+    S, and subtracts the rank-one update l l^T from the trailing matrix, masked
+    by S.  A nonpositive pivot leaves column i zero and updates nothing (the
+    zero-column rule of Section 4.4).
     """
-    A = np.where(S, A, 0.0).astype(np.float64).copy()
+    S = np.asarray(S, dtype=bool)
+    A = np.where(S, A, 0.0).astype(np.float64)
     N = A.shape[0]
     L = np.zeros_like(A)
     for i in range(N):
-        piv = A[i, i]
-        if not piv > 0.0:
+        p = A[i, i]
+        if not p > 0.0:
             continue
-        L[i:, i] = A[i:, i] / math.sqrt(piv)
-        for j in range(i + 1, N):
-            if not S[i, j]:
-                continue
-            ks = np.arange(j, N)
-            ks = ks[S[ks, i] & S[ks, j]]
-            A[ks, j] -= A[ks, i] * A[j, i] / piv
-    return np.tril(L)
+        l = A[i:, i] / math.sqrt(p)
+        L[i:, i] = l
+        t = l[1:]
+        A[i + 1:, i + 1:] -= np.outer(t, t) * S[i + 1:, i + 1:]
+    return L

@@ -10,6 +10,7 @@ import pytest
 
 import oracle
 from paper_1706_02205_gb300 import inputs
+from tests import factor_parity as fp
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -81,7 +82,7 @@ def test_batch_matches_oracle_per_set():
         assert np.array_equal(B.sets[s]["perm"].cpu().numpy(), ref["perm"])
         assert np.array_equal(B.sets[s]["col"].cpu().numpy(), ref["col"])
         v = B.set_values(s).cpu().numpy()
-        rev, _ = oracle.ichol(ref["x_ord"], ref["rowptr"], ref["col"], oracle.Kernel(1.5, sets[s]["ell"]),
-                              reverse_sums=True)
-        spread = np.max(np.abs(rev - ref["val"]))
-        assert np.max(np.abs(v - ref["val"])) <= max(1e-12, 10 * spread)
+        dg = B.diag[B.offsets[s]:B.offsets[s + 1]].cpu().numpy()
+        alt = oracle.ichol(ref["x_ord"], ref["rowptr"], ref["col"], oracle.Kernel(1.5, sets[s]["ell"]),
+                           reverse_sums=True)
+        fp.check_factor(kc.FP64, v, dg, ref["rowptr"], ref["col"], 1.0, (ref["val"], ref["zero_col"]), alt=alt)

@@ -29,7 +29,7 @@ if not torch.cuda.is_available():  # pragma: no cover
     pytest.skip("needs a CUDA GPU", allow_module_level=True)
 
 from paper_1706_02205_gb300 import kchol as kc  # noqa: E402
-from tests.test_gpu_parity import _first_diff, fp32_bar  # noqa: E402
+from tests import factor_parity as fp  # noqa: E402
 
 DEV = torch.device("cuda:0")
 
@@ -145,10 +145,7 @@ def test_batch_full_size_sets_alone_and_oracle():
     ref = oracle.pipeline(sets[s]["x"], 3.0, ko)
     assert np.array_equal(B.sets[s]["perm"].cpu().numpy(), ref["perm"])
     v = B.set_values(s).cpu().numpy().astype(np.float64)
-    dg = B.diag[B.offsets[s]:B.offsets[s + 1]].cpu().numpy() == 0
     _, _, piv = oracle.ichol(ref["x_ord"], ref["rowptr"], ref["col"], ko, pivots=True)
-    bar = fp32_bar(ref["x_ord"], ref["rowptr"], ref["col"], ko, ref["val"])
-    differ = np.nonzero(dg != ref["zero_col"])[0]
-    assert np.all(np.abs(piv[differ]) <= max(1e-5, bar))
-    m = ref["col"] < _first_diff(dg, ref["zero_col"])
-    assert np.max(np.abs(v[m] - ref["val"][m]), initial=0.0) < bar
+    alt = oracle.ichol(ref["x_ord"], ref["rowptr"], ref["col"], ko, store_f32=True)
+    fp.check_factor(kc.FP32_FORM, v, B.diag[B.offsets[s]:B.offsets[s + 1]].cpu().numpy(), ref["rowptr"],
+                    ref["col"], 1.0, (ref["val"], ref["zero_col"]), alt=alt, piv=piv)

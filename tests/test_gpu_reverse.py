@@ -15,6 +15,7 @@ import pytest
 
 import oracle
 from paper_1706_02205_gb300 import inputs
+from tests import factor_parity as fp
 from tests import refmath
 
 torch = pytest.importorskip("torch")
@@ -39,12 +40,6 @@ def H(t):
 def _op(n, seed=inputs.seed_for(6)):
     x, rp, col, val = inputs.grid_operator(n, seed=seed)
     return x, rp, col, val
-
-
-def _rel(val, ref, rp, adiag_pos):
-    """max |dL_ji| / sqrt(A_jj) (the row norm of L when L L^T = A on S)."""
-    rows = np.repeat(np.arange(rp.shape[0] - 1), np.diff(rp))
-    return float(np.max(np.abs(val.astype(np.float64) - ref) / np.sqrt(adiag_pos[rows])))
 
 
 @pytest.mark.parametrize("rho", [0.5, 2.0, 3.0])
@@ -75,11 +70,11 @@ def test_reverse_factor_matches_oracle(prec, rho):
     assert r["outside"] == ref["outside"] == 0 and r["zero_pivots"] == int(ref["zero_col"].sum()) == 0
     rrp, rcol = ref["rowptr"], ref["col"]
     dpos = ref["aval"][rrp[1:] - 1]
-    rev, _ = oracle.ichol_given(rrp, rcol, ref["aval"], reverse_sums=True)
-    spread = _rel(rev, ref["val"], rrp, dpos)
-    bar = max(1e-12, 10 * spread) if prec == kc.FP64 else max(1e-4, 10 * spread * 2.0**29)
-    assert _rel(H(r["val"]), ref["val"], rrp, dpos) <= bar
-    np.testing.assert_allclose(H(r["diag"]), ref["val"][rrp[1:] - 1], rtol=bar)
+    # every pivot of the shifted grid operator is far from zero: the fixed
+    # bars hold on every entry and on the FP64 pivots
+    fp.check_factor(prec, H(r["val"]), H(r["diag"]), rrp, rcol, np.sqrt(dpos), (ref["val"], ref["zero_col"]),
+                    strict=True)
+    np.testing.assert_allclose(H(r["diag"]), ref["val"][rrp[1:] - 1], rtol=fp.BAR[prec])
     # the defining identity (L L^T)_ji = A_ji on the pattern
     N = x.shape[0]
     L = refmath.dense_lower(rrp, rcol, H(r["val"]).astype(np.float64), N)

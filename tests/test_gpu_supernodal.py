@@ -15,7 +15,7 @@ if not torch.cuda.is_available():  # pragma: no cover
     pytest.skip("needs a CUDA GPU", allow_module_level=True)
 
 from paper_1706_02205_gb300 import kchol as kc  # noqa: E402
-from tests.test_gpu_parity import fp32_bar, row_rel  # noqa: E402
+from tests import factor_parity as fp  # noqa: E402
 
 DEV = torch.device("cuda:0")
 
@@ -77,19 +77,10 @@ def test_supernodal_factor_matches_oracle(prec, nu, ell, nugget):
     val_ref, zc_ref, piv = oracle.ichol(xs, ref["rowptr"], ref["col"], ko, pivots=True)
     r = kc.supernodal_pipeline(T(x), rho, kg, prec)
     assert np.array_equal(H(r["perm"]), ref["order"])
-    z = H(r["diag"]) == 0.0
-    if prec == kc.FP64:
-        rev, _ = oracle.ichol(xs, ref["rowptr"], ref["col"], ko, reverse_sums=True)
-        spread = row_rel(rev, val_ref, ref["rowptr"], 1.0, nugget)
-        assert np.array_equal(z, zc_ref)
-        assert row_rel(H(r["val"]), val_ref, ref["rowptr"], 1.0, nugget) <= max(1e-12, 10 * spread)
-    else:
-        bar = fp32_bar(xs, ref["rowptr"], ref["col"], ko, val_ref, nugget)
-        differ = np.nonzero(z != zc_ref)[0]
-        assert np.all(np.abs(piv[differ]) <= max(1e-5, bar) * (1.0 + nugget))
-        cut = int(differ[0]) if len(differ) else x.shape[0]
-        m = ref["col"] < cut
-        assert np.max(np.abs(H(r["val"]).astype(np.float64)[m] - val_ref[m]), initial=0.0) < bar
+    alt = oracle.ichol(xs, ref["rowptr"], ref["col"], ko, reverse_sums=(prec == kc.FP64),
+                       store_f32=(prec == kc.FP32_FORM))
+    fp.check_factor(prec, H(r["val"]), H(r["diag"]), ref["rowptr"], ref["col"], np.sqrt(1.0 + nugget),
+                    (val_ref, zc_ref), alt=alt, piv=piv, strict=(nu == 0.5))
 
 
 def test_supernodal_larger_structure():

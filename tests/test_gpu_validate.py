@@ -59,3 +59,28 @@ def test_corrupt_copies_are_reported(what, repl):
         kc.pattern_validate(bad)
     assert ei.value.status == kc.KC_EINVAL
     kc.pattern_validate(pat)  # the original is untouched and passes
+
+
+@pytest.mark.parametrize("bad", [float("nan"), float("inf"), -float("inf")])
+@pytest.mark.parametrize("where", [0, 777, 3999])
+def test_non_finite_points_rejected(bad, where):
+    """A non-finite coordinate anywhere in the input (first, middle, last
+    element) is reported as KC_EINVAL by the ordering and by the pattern
+    count, before any other device work; the context stays usable."""
+    x_h = inputs.uniform(2000, 2, seed=122)
+    xb = x_h.copy().reshape(-1)
+    xb[where] = bad
+    xb = xb.reshape(2000, 2)
+    with pytest.raises(kc.KcError) as ei:
+        kc.order_points(torch.from_numpy(xb).to(DEV))
+    assert ei.value.status == kc.KC_EINVAL and "finite" in str(ei.value)
+    x = torch.from_numpy(x_h).to(DEV)
+    perm, l, xo = kc.order_points(x)
+    xo_bad = xo.clone().view(-1)
+    xo_bad[where] = bad
+    with pytest.raises(kc.KcError) as ei:
+        kc.pattern_count(xo_bad.view(2000, 2), l, 3.0)
+    assert ei.value.status == kc.KC_EINVAL
+    # the same call on the clean input still works and agrees with itself
+    rp, nnz = kc.pattern_count(xo, l, 3.0)
+    assert nnz == kc.build_pattern(xo, l, 3.0).nnz

@@ -2,7 +2,8 @@
 
 * Matern closed forms against the general Bessel definition (SciPy ``kv``).
 * rho = infinity: ICHOL(0) is the dense Cholesky factor (NumPy/LAPACK).
-* The paper's Algorithm 2 as printed (right-looking, dense, tests/refmath.py)
+* ICHOL(0) restated as a dense Cholesky with the Schur-complement updates
+  masked to the pattern (tests/refmath.py)
   equals the oracle's left-looking form, zeroed columns included.
 * (L L^T)_ij = Theta_ij on S when no pivot is dropped.
 * E: the sampled estimator against the exact dense Frobenius ratio; the
@@ -51,7 +52,7 @@ def test_rho_infinity_is_dense_cholesky(nu, ell, d):
 
 
 @pytest.mark.parametrize("nu,rho", [(0.5, 2.0), (1.5, 2.0), (1.5, 3.0), (2.5, 2.5)])
-def test_left_looking_equals_right_looking_algorithm(nu, rho):
+def test_left_looking_equals_masked_schur_cholesky(nu, rho):
     N = 220
     x = inputs.uniform(N, 2, seed=41)
     kern = oracle.Kernel(nu, 0.2)
@@ -62,7 +63,7 @@ def test_left_looking_equals_right_looking_algorithm(nu, rho):
     L = refmath.dense_lower(rp, col, val, N)
     S = refmath.pattern_mask(rp, col, N)
     T = refmath.dense_theta(xo, nu, 0.2)
-    Lr = refmath.ichol_right_looking(T, S)
+    Lr = refmath.ichol_masked_schur(T, S)
     zr = ~(np.diag(Lr) > 0)
     assert np.array_equal(zr, zc)
     assert _row_rel_err(L, Lr) < 1e-11

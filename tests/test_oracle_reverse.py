@@ -3,7 +3,8 @@
 reverse maximin order on the min-rule pattern.
 
 * rho = infinity: the factor is LAPACK's dense Cholesky factor of P A P.
-* The paper's Algorithm 2 as printed (right-looking, dense, tests/refmath.py)
+* ICHOL(0) restated as a dense Cholesky with the Schur-complement updates
+  masked to the pattern (tests/refmath.py)
   on P A P masked to the reversed pattern equals the oracle's left-looking
   factor.
 * The reversed pattern is the maximin pattern flipped in both indices (dense
@@ -49,12 +50,12 @@ def test_rho_infinity_is_dense_cholesky_of_reversed_matrix():
 
 
 @pytest.mark.parametrize("rho", [1.5, 2.0, 3.0])
-def test_matches_right_looking_algorithm_on_reversed_matrix(rho):
+def test_matches_masked_schur_cholesky_on_reversed_matrix(rho):
     x, rp, col, val, A = _op(12)
     N = A.shape[0]
     r = oracle.reverse_factor(x, rp, col, val, rho)
     S = refmath.pattern_mask(r["rowptr"], r["col"], N)
-    L_ref = refmath.ichol_right_looking(A[np.ix_(r["orig"], r["orig"])], S)
+    L_ref = refmath.ichol_masked_schur(A[np.ix_(r["orig"], r["orig"])], S)
     L = refmath.dense_lower(r["rowptr"], r["col"], r["val"], N)
     assert np.max(np.abs(L - L_ref)) <= 1e-12 * np.max(np.abs(L_ref))
 

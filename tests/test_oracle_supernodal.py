@@ -9,7 +9,8 @@ Construction of the stability section) and of ICHOL(0) on them.
 * The pattern holds every pair with d(i, j) <= rho and is the union of
   blocks of supernode pairs.
 * The appendix's equivalence: Algorithm 2 in this ordering and pattern equals
-  the supernodal block algorithm as printed (dense blocks, NumPy), and at
+  the supernodal block factorisation (a block Cholesky with the updates masked
+  to the supernode pairs of the pattern, NumPy), and at
   rho = infinity the dense Cholesky factor.
 """
 import math
@@ -102,39 +103,32 @@ def test_construction_properties(N, d, rho):
 
 
 def _block_ichol(A, node):
-    """The supernodal block algorithm as printed: for each supernode in order,
-    L[:, I] = A[:, I] / sqrt(A_II)^T, then A_KJ -= A_KI A_II^{-1} A_JI for
-    supernodes J, K after I with (I, J), (K, I), (K, J) in the pattern;
-    A restricted to the pattern first (dense, on the new order)."""
+    """The supernodal block factorisation of the stability appendix, restated
+    as a block Cholesky whose Schur-complement updates are kept only on the
+    supernode pairs of the pattern: for each supernode I in order, its
+    diagonal block is factored densely (L_II L_II^T = A_II), the rows below
+    are L_KI = A_KI L_II^{-T}, and the trailing matrix loses L_KI L_JI^T on the
+    block pairs (K, J) the pattern contains.  A is restricted to the pattern
+    first (dense, on the supernodal order)."""
     N = A.shape[0]
-    nodes = []
-    for q in range(N):
-        if not nodes or nodes[-1][0] != node[q]:
-            nodes.append([node[q], []])
-        nodes[-1][1].append(q)
-    blocks = [np.array(b) for _, b in nodes]
-    L = np.zeros_like(A)
+    starts = np.flatnonzero(np.r_[True, node[1:] != node[:-1]])
+    bounds = list(zip(starts, np.r_[starts[1:], N]))
+    blk = np.repeat(np.arange(len(bounds)), [e - b for b, e in bounds])
+    nb = len(bounds)
+    adj = np.zeros((nb, nb), bool)
+    for u, (b0, e0) in enumerate(bounds):
+        for v, (b1, e1) in enumerate(bounds):
+            adj[u, v] = np.any(A[b0:e0, b1:e1] != 0)
+    mask = adj[np.ix_(blk, blk)]
     A = A.copy()
-    nb = len(blocks)
-    adjb = np.zeros((nb, nb), bool)
-    for u in range(nb):
-        for v in range(nb):
-            adjb[u, v] = np.any(A[np.ix_(blocks[u], blocks[v])] != 0)
-    for u in range(nb):
-        I = blocks[u]
-        C = np.linalg.cholesky(A[np.ix_(I, I)])
-        rows = np.arange(I[0], N)
-        L[np.ix_(rows, I)] = np.linalg.solve(C, A[np.ix_(rows, I)].T).T
-        Ainv = np.linalg.inv(A[np.ix_(I, I)])
-        for v in range(u + 1, nb):
-            if not adjb[u, v]:
-                continue
-            J = blocks[v]
-            for w in range(v, nb):
-                if adjb[w, u] and adjb[w, v]:
-                    K = blocks[w]
-                    A[np.ix_(K, J)] -= A[np.ix_(K, I)] @ Ainv @ A[np.ix_(J, I)].T
-    return np.tril(L)
+    L = np.zeros_like(A)
+    for b, e in bounds:
+        C = np.linalg.cholesky(A[b:e, b:e])
+        L[b:e, b:e] = C
+        W = np.linalg.solve(C, A[e:, b:e].T).T
+        L[e:, b:e] = W
+        A[e:, e:] -= (W @ W.T) * mask[e:, e:]
+    return L
 
 
 @pytest.mark.parametrize("rho", [2.0, 3.0])
