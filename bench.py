@@ -138,7 +138,7 @@ def run_ours(args, rank, world):
         xs = kc.solve(pat, prec, val, diag, kern, perm, b)
         if ev:
             ev[5].record(stream)
-        return dict(perm=perm, xo=xo, pat=pat, val=val, diag=diag, zp=zp, xs=xs)
+        return dict(perm=perm, l=l, xo=xo, pat=pat, val=val, diag=diag, zp=zp, xs=xs)
 
     from paper_1706_02205_gb300 import replicas
     barrier = replicas.barrier
@@ -188,6 +188,20 @@ def run_ours(args, rank, world):
             s64_ms.append(e[1].elapsed_time(e[2]))
             f64_k.append(kc.last_factor_kernel_ms())
 
+    # the paper's accuracy measure (Section 4.4) of both headline factors: the
+    # sampled estimator E over 500,000 uniform index pairs, 50 repetitions
+    # (mean and standard deviation, as the paper reports it)
+    accuracy = {}
+    for pname, pr, vv, dd in (("fp32_form", kc.FP32_FORM, r["val"], r["diag"]), ("fp64", kc.FP64, v64, d64)):
+        es = []
+        for rep in range(args.e_reps):
+            pi_h, pj_h = inputs.sample_pairs(N, 500_000, seed=inputs.seed_for(2, 200 + rep))
+            n2, d2, _ = kc.frob_error(pat, pr, vv, dd, xo, kern, perm, torch.from_numpy(pi_h).to(dev),
+                                      torch.from_numpy(pj_h).to(dev))
+            es.append((n2 / d2) ** 0.5)
+        accuracy[pname] = {"E_mean": statistics.mean(es), "E_std": statistics.pstdev(es), "repetitions": len(es),
+                           "pairs_per_repetition": 500_000}
+
     # the other kernel of the workload on the same pattern (the pattern does not
     # depend on the kernel): factor only, both precisions
     other = {}
@@ -206,6 +220,28 @@ def run_ours(args, rank, world):
             res[pname] = {"kernel_ms": statistics.mean(ks), "kernel_nnz_per_s": nnz / (statistics.mean(ks) * 1e-3),
                           "zero_pivots": zps[-1]}
         other[f"matern_nu{nu2}"] = res
+
+    # rho = 2 and 5 (the other patterns of the configuration): ordering and
+    # pattern once, then each factor kernel timed after one warm-up
+    rho_sweep = {}
+    for rho2 in args.other_rho:
+        p2 = kc.build_pattern(xo, r["l"], rho2)
+        ent = {"nnz": p2.nnz, "depth": p2.depth}
+        for nu2 in [args.nu] + list(args.other_nu):
+            k2 = kc.Kernel(nu2, args.ell, 1.0, 0.0)
+            for pname, pr in (("fp32_form", kc.FP32_FORM), ("fp64", kc.FP64)):
+                ks = []
+                for it in range(1 + max(1, args.steps // 2)):
+                    flush.zero_()
+                    _, _, zz = kc.factor(p2, xo, k2, pr)
+                    torch.cuda.synchronize()
+                    if it >= 1:
+                        ks.append(kc.last_factor_kernel_ms())
+                km = statistics.mean(ks)
+                ent[f"matern_nu{nu2}_{pname}"] = {"kernel_ms": km, "kernel_nnz_per_s": p2.nnz / (km * 1e-3),
+                                                  "zero_pivots": zz}
+        rho_sweep[f"rho{rho2:g}"] = ent
+        del p2
 
     # end to end through the public calls from pinned host buffers
     xp = torch.from_numpy(x_h).pin_memory()
@@ -272,6 +308,23 @@ def run_ours(args, rank, world):
         "gpu_launches": launches,
         "clocks": clocks,
     }
+    # the triangular solves: compulsory bytes (pattern and L read once per
+    # direction, the right-hand sides in and out) over the solve phase
+    ns = 1 << max(0, (args.nrhs - 1).bit_length())
+    solve_bytes = (nnz * 8 + (N + 1) * 8) + (nnz * 16 + (N + 1) * 8) + 4 * N * ns * 8 + 2 * N * args.nrhs * 8
+    solve_ms = statistics.mean(phase["solve"])
+    line["solve_roofline"] = {"bound": "latency (dependency depth x row latency)", "algorithmic_bytes": solve_bytes,
+                              "achieved": solve_bytes / (solve_ms * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
+                              "frac": solve_bytes / (solve_ms * 1e-3) / 1e9 / hbm, "ms": solve_ms,
+                              "kernels": "fwd_solve_pair_k<16> + bwd_solve_pair_k<16> + permutations"}
+    line["rho_sweep"] = rho_sweep
+    line["accuracy_E"] = accuracy
+    if args.refine_side > 0:
+        line["refine_to_1e-10"] = run_refine(args)
+    if args.serve_leg:
+        from paper_1706_02205_gb300 import serve
+        args.serve_fracs = (0.8,)
+        line["serve"] = serve.bench(args)
     if args.cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args)
     return line
@@ -640,9 +693,14 @@ def run_batch(args):
 
 
 def run_refine(args):
-    """Time to a refined solve: factor (FP32 form or FP64) + CG on the dense
-    Theta preconditioned by the factor, 16 right-hand sides to relative
-    residual 1e-10, on a jittered grid small enough for O(N^2) products."""
+    """Time to a refined solve (task (2)): factor (FP32 form or FP64) + CG on the
+    dense Theta preconditioned by the factor, 16 right-hand sides to relative
+    residual 1e-10, on the jittered grid of side --refine-side (the dense FP64
+    product is O(N^2) per iteration: 2^16 points take about half a second per
+    iteration on the GB300, whose FP64 pipe is a small fraction of its FP32
+    rate, so 2^20 points would take over two minutes per iteration).  Each
+    form: one warm-up, then the factor and the CG timed on the device (the CG
+    synchronises every iteration for its convergence test)."""
     import torch
 
     from paper_1706_02205_gb300 import kchol as kc
@@ -653,7 +711,8 @@ def run_refine(args):
     perm, l, xo = kc.order_points(x)
     pat = kc.build_pattern(xo, l, args.rho)
     out = {"workload": f"jittered grid {n}x{n} (N={n * n}), Matern-{args.nu} l={args.ell}, rho={args.rho}, "
-                       f"{args.nrhs} rhs, CG on dense Theta to 1e-10", "N": n * n, "nnz": pat.nnz}
+                       f"{args.nrhs} rhs, CG on the dense Theta (FP64) preconditioned by the factor, to 1e-10",
+           "N": n * n, "nnz": pat.nnz}
     for name, prec in (("fp32_form", kc.FP32_FORM), ("fp64", kc.FP64)):
         kc.factor(pat, xo, kern, prec)  # warm-up
         torch.cuda.synchronize()
@@ -664,7 +723,7 @@ def run_refine(args):
         xs, it, rr, st = kc.refine(pat, xo, kern, prec, val, diag, perm, b, rtol=1e-10, maxit=500)
         torch.cuda.synchronize()
         t2 = time.perf_counter()
-        out[name] = {"factor_ms": (t1 - t0) * 1e3, "refine_ms": (t2 - t1) * 1e3, "total_ms": (t2 - t0) * 1e3,
+        out[name] = {"factor_ms": (t1 - t0) * 1e3, "refine_ms": (t2 - t1) * 1e3, "time_to_1e-10_ms": (t2 - t0) * 1e3,
                      "iterations": it, "max_true_relres": max(rr), "status": st, "zero_pivots": zp,
                      "ms_per_iteration": (t2 - t1) * 1e3 / max(1, it)}
     return out
@@ -672,6 +731,7 @@ def run_refine(args):
 
 def run_serve(args):
     from paper_1706_02205_gb300 import serve
+    args.serve_fracs = (0.5, 0.8, 0.95)
     return serve.bench(args)
 
 
@@ -697,10 +757,12 @@ def oracle_step(n_side, args):
 
 
 def cpu_baseline(args):
-    nnz, dt, N = oracle_step(args.cpu_side, args)
+    side = args.cpu_baseline_side
+    nnz, dt, N = oracle_step(side, args)
     return {"value": nnz / dt, "unit": "nnz(L)/s", "cores": 1, "kind": "oracle",
-            "sample": f"jittered grid {args.cpu_side}x{args.cpu_side} (N={N}), same kernel/rho/{args.nrhs} rhs; "
-                      f"one full step (order+pattern+factor+solve) single-threaded FP64 C, {dt:.1f} s"}
+            "sample": f"jittered grid {side}x{side} (N={N}, {N / (args.n_side ** 2):.3g} of the workload's points), "
+                      f"same kernel/rho/{args.nrhs} rhs; one full step (order+pattern+factor+solve) "
+                      f"single-threaded FP64 C, {dt:.1f} s"}
 
 
 def run_reference(args, rank, world):
@@ -737,7 +799,9 @@ def main():
     ap.add_argument("--ell", type=float, default=0.1)
     ap.add_argument("--rho", type=float, default=3.0)
     ap.add_argument("--nrhs", type=int, default=16)
-    ap.add_argument("--cpu-side", type=int, default=320)
+    ap.add_argument("--cpu-side", type=int, default=320, help="reference arm: jittered grid side of each step")
+    ap.add_argument("--cpu-baseline-side", type=int, default=512,
+                    help="cpu_baseline: jittered grid side of the bounded sample (1024 = the whole workload)")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--traffic", type=float, default=None, help="ncu DRAM bytes per factor launch, if measured")
     ap.add_argument("--family", default="matern", choices=["matern", "cauchy"],
@@ -761,7 +825,12 @@ def main():
                     help="factor-only: stage-buffer bytes (0 = automatic, -1 = register form)")
     ap.add_argument("--warps", type=int, nargs="*", default=[0], help="factor-only: warps per CTA (0 = default)")
     ap.add_argument("--n-req", type=int, default=40)
-    ap.add_argument("--refine-side", type=int, default=128)
+    ap.add_argument("--refine-side", type=int, default=256,
+                    help="grid side of the refined-solve leg (0: leave it out)")
+    ap.add_argument("--other-rho", type=float, nargs="*", default=[2.0, 5.0],
+                    help="patterns of the configuration also factored (kernels timed)")
+    ap.add_argument("--no-serve-leg", dest="serve_leg", action="store_false")
+    ap.add_argument("--e-reps", type=int, default=50, help="repetitions of the sampled error estimator")
     ap.add_argument("--slots", type=int, default=4)
     ap.add_argument("--serve-n-max", type=int, default=1_000_000)
     ap.add_argument("--prec", default="fp32", choices=["fp32", "fp64"])

@@ -131,7 +131,7 @@ const char* kc_last_error(void);
  * kc_kernel_eval, kc_l_matvec, kc_lt_matvec, kc_llt_matvec, kc_logdet,
  * kc_pattern_reverse, kc_gather_entries, kc_factor_given, kc_refine_sparse,
  * kc_supernodal_count, kc_supernodal_fill, kc_supernodal, kc_pattern_validate.
- * 4: kc_scratch_trim; scratch from a private pool per device. */
+ * 4: kc_scratch_trim, kc_frob_error; scratch from a private pool per device. */
 #define KC_ABI_VERSION 4
 int32_t kc_abi_version(void);
 
@@ -335,6 +335,25 @@ kc_status kc_llt_matvec(const kc_pattern* pat, int32_t prec, const void* val, co
  * Synchronises. */
 kc_status kc_logdet(const kc_pattern* pat, const double* diag, double* logdet_out, int64_t* zero_pivots_out,
                     void* stream);
+
+/* ---- the sampled error estimator of Section 4.4 -------------------------- *
+ * E^2 = num2 / den2 with num2 = sum_t ((L L^T)_{pi[t],pj[t]} - Theta_{pi[t],pj[t]})^2
+ * and den2 = sum_t Theta_{pi[t],pj[t]}^2 over the m pairs (device int64[m]
+ * each, original point numbering, 0..N-1: the caller draws them i.i.d.
+ * uniformly from I x I with replacement), or over the pairs with keep[t] != 0
+ * (device int8[m], may be NULL: every pair).  L is a factor from kc_factor
+ * (val in prec, CSR layout of pat, diag its FP64 pivots), perm the ordering
+ * and x_ord (device double[N*d]) the points in positions; kern the
+ * covariance function, evaluated in FP64 as the FP64 factor does, nugget on
+ * the diagonal.  (L L^T)_ij is a sparse row merge in FP64.  The sums run in a
+ * fixed order (same bits on every run).  Outputs (host): num2, den2 and the
+ * number of pairs kept (may be NULL).  A pair index outside 0..N-1 gives
+ * KC_EINVAL (detected on the device, never used as an index).
+ * Synchronises. */
+kc_status kc_frob_error(const kc_pattern* pat, int32_t prec, const void* val, const double* diag,
+                        const double* x_ord, int32_t d, const kc_kernel* kern, const int32_t* perm, const int64_t* pi,
+                        const int64_t* pj, int64_t m, const int8_t* keep, double* num2_out, double* den2_out,
+                        int64_t* kept_out, void* stream);
 
 /* ---- Section 6: factors of a given sparse matrix, reverse order ---------- *
  * The precision matrix A = Theta^{-1} (a discretised elliptic operator) has

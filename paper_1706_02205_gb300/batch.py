@@ -17,9 +17,21 @@ import torch
 from . import kchol as kc
 
 
-def prepare_sets(xs, rho, n_streams=8, rule=kc.RULE_MAX):
+def prepare_sets(xs, rho, n_streams=8, rule=kc.RULE_MAX, stream=None):
     """Order and build the pattern of every set (list of (N_s, d_s) float64 CUDA
-    tensors) on `n_streams` streams.  Returns a list of dicts."""
+    tensors) on `n_streams` streams, or one after another on `stream` (which
+    is then the only stream synchronised: other work on the device goes on).
+    Returns a list of dicts."""
+    if stream is not None:
+        out = []
+        with torch.cuda.stream(stream):
+            for x in xs:
+                perm, l, xo = kc.order_points(x, stream=stream)
+                rowptr, nnz = kc.pattern_count(xo, l, rho, rule, stream=stream)
+                col = kc.pattern_fill(xo, l, rho, rowptr, nnz, rule, stream=stream)
+                out.append({"perm": perm, "l": l, "x_ord": xo, "rowptr": rowptr, "col": col})
+        stream.synchronize()
+        return out
     streams = [torch.cuda.Stream() for _ in range(max(1, n_streams))]
 
     def one(k):
@@ -41,12 +53,12 @@ def prepare_sets(xs, rho, n_streams=8, rule=kc.RULE_MAX):
 class BatchFactor:
     """Block-diagonal batch of point sets with one factor plan."""
 
-    def __init__(self, xs, kerns, rho, prec=kc.FP32_FORM, opts=None, n_streams=8, prepared=None):
+    def __init__(self, xs, kerns, rho, prec=kc.FP32_FORM, opts=None, n_streams=8, prepared=None, stream=None):
         self.kerns = list(kerns)
         if len({(k.sigma2, k.nugget) for k in self.kerns}) > 1:
             raise ValueError("the sets of a batch share sigma2 and nugget (nu and ell may differ)")
         self.prec = prec
-        self.sets = prepared if prepared is not None else prepare_sets(xs, rho, n_streams)
+        self.sets = prepared if prepared is not None else prepare_sets(xs, rho, n_streams, stream=stream)
         self.Ns = [s["perm"].numel() for s in self.sets]
         self.offsets = [0]
         for n in self.Ns:
@@ -67,10 +79,10 @@ class BatchFactor:
     def tune(self):
         return self.plan.tune(self.val, self.diag)
 
-    def factor(self):
+    def factor(self, stream=None):
         """One launch; returns the number of dropped pivots."""
-        self.plan.launch(self.val, self.diag)
-        return self.plan.finish()
+        self.plan.launch(self.val, self.diag, stream=stream)
+        return self.plan.finish(stream=stream)
 
     def capture(self):
         """Record the plan's launch in a CUDA graph (replay with replay())."""
@@ -90,8 +102,8 @@ class BatchFactor:
         """Factor values of set s (its CSR rows, positions local to the set)."""
         return self.val[self.nnz_offsets[s]:self.nnz_offsets[s + 1]]
 
-    def solve(self, b):
+    def solve(self, b, stream=None):
         """Solve every set at once: b is (nrhs, sum N) in the concatenated
         original order.  A dropped pivot is replaced by sqrt(sigma2 + nugget),
         which the sets share (they may differ in nu and ell)."""
-        return kc.solve(self.pat, self.prec, self.val, self.diag, self.kerns[0], self.perm, b)
+        return kc.solve(self.pat, self.prec, self.val, self.diag, self.kerns[0], self.perm, b, stream=stream)

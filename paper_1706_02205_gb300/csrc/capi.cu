@@ -53,6 +53,10 @@ kc_status pca_error_impl(const double* x, int64_t N, int d, const kc_kernel* ker
 kc_status factor_matvec_impl(const kc_pattern* P, int prec, const void* val, const double* diag, const int32_t* perm,
                              const double* in, int nrhs, double* out, int which, cudaStream_t s);
 kc_status logdet_impl(const kc_pattern* P, const double* diag, double* logdet_out, int64_t* zero_out, cudaStream_t s);
+kc_status frob_error_impl(const kc_pattern* P, int prec, const void* val, const double* diag, const double* x_ord,
+                          int d, const kc_kernel* kern, const int32_t* perm, const int64_t* pi, const int64_t* pj,
+                          int64_t m, const int8_t* keep, double* num2_out, double* den2_out, int64_t* kept_out,
+                          cudaStream_t s);
 kc_status kernel_eval_impl(const kc_kernel* kern, int prec, const double* r, int64_t n, double* out, cudaStream_t s);
 kc_status factor_given_impl(const kc_pattern* P, const double* aval, int prec, void* val, double* diag,
                             int64_t* zero_out, const kc_opts* o, cudaStream_t s);
@@ -294,6 +298,19 @@ kc_status kc_logdet(const kc_pattern* pat, const double* diag, double* logdet_ou
     KC_TRY(check_pattern(pat));
     if (!diag || !logdet_out) return fail(KC_EINVAL, "diag and logdet_out must be non-NULL");
     return logdet_impl(pat, diag, logdet_out, zero_pivots_out, (cudaStream_t)stream);
+}
+
+kc_status kc_frob_error(const kc_pattern* pat, int32_t prec, const void* val, const double* diag,
+                        const double* x_ord, int32_t d, const kc_kernel* kern, const int32_t* perm, const int64_t* pi,
+                        const int64_t* pj, int64_t m, const int8_t* keep, double* num2_out, double* den2_out,
+                        int64_t* kept_out, void* stream) {
+    KC_RANGE("kc_frob_error");
+    KC_TRY(check_pattern(pat));
+    KC_TRY(check_points(x_ord, pat->N, d));
+    if (m < 0 || (m > 0 && (!pi || !pj))) return fail(KC_EINVAL, "kc_frob_error: bad pair arrays");
+    if (!val || !diag || !perm || !num2_out || !den2_out) return fail(KC_EINVAL, "arrays must be non-NULL");
+    return frob_error_impl(pat, prec, val, diag, x_ord, d, kern, perm, pi, pj, m, keep, num2_out, den2_out, kept_out,
+                           (cudaStream_t)stream);
 }
 
 kc_status kc_pattern_reverse(int64_t N, const int64_t* colptr, const int32_t* rowidx, int64_t* rowptr_out,

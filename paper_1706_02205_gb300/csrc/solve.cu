@@ -6,8 +6,12 @@
 //                     ready flags of its R_j.
 // Backward L^T x = y: x_i = (y_i - sum_{j in C_i} L_ji x_j) / L_ii, over the
 //                     CSC columns in reverse level order; wide columns are cut
-//                     into chunks of rows, each chunk adds its partial sums
-//                     atomically and the last chunk of a column finishes x_i.
+//                     into chunks of rows, each chunk stores its partial sums
+//                     in a slot of its own; the last chunk to finish of every
+//                     group of 32 adds its group's slots, and the last group
+//                     of a column to finish adds the group sums and finishes
+//                     x_i.  Every sum runs in a fixed order across the lanes
+//                     of a warp, so every result repeats bit for bit.
 //
 // Vectors are point-major inside with a power-of-two stride NR >= nrhs
 // (v[k * NR + r]), so one point's right-hand sides are one aligned run that a
@@ -52,8 +56,9 @@ struct SolveArgs {
     double* x;        // point-major output of the backward solve
     float2* yf;       // FP32 form: y as (hi, lo) pairs
     float2* xf;       // FP32 form: x as (hi, lo) pairs (gathered by later columns; x above gets FP64)
-    double* acc;      // point-major partial sums of wide columns
-    unsigned* cnt;    // finished chunks per column (backward)
+    double* acc;      // partial sums of the chunks of wide columns: NR per task, at the task's index
+    unsigned* cnt;    // finished chunk groups per column (backward)
+    unsigned* gcnt;   // finished chunks per group of 32, at the group's first task
     int* ready;       // per point flag
     unsigned long long* ticket;
     int* status;
@@ -176,6 +181,56 @@ __device__ __forceinline__ void gather_fma(const double* v, const int (&k)[D], c
     }
 }
 
+// Sum over cnt slots of NR doubles (slot p0, p0 + stride, ...) in a fixed
+// order: lane l takes right-hand side l % NR and every (32 / NR)-th slot from
+// l / NR on; the lanes of one right-hand side then add their sums by a fixed
+// butterfly.  Every lane returns the total of right-hand side lane % NR.
+template <int NR>
+__device__ __forceinline__ double combine_slots(const double* part, int64_t p0, int64_t stride, int cnt, int lane) {
+    constexpr int LP = 32 / NR;
+    const int r = lane % NR;
+    double s = 0.0;
+    for (int k = lane / NR; k < cnt; k += LP) s += __ldcg(&part[(p0 + (int64_t)k * stride) * NR + r]);
+#pragma unroll
+    for (int o = 16; o >= NR; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    return s;
+}
+
+// A chunk c of column i (task index ti, nch > 1 chunks) with its partial sums
+// already in its slot: counts it in its group of 32 chunks; the group's last
+// chunk adds the group's slots and leaves the sum in the group's first slot;
+// the column's last group adds the group sums.  Returns true (and the total
+// of right-hand side lane % NR in `total`) when this warp finishes column i.
+template <int NR>
+__device__ __forceinline__ bool combine_chunks(double* part, unsigned* gcnt, unsigned* cnt, int i, int64_t ti, int c,
+                                               unsigned nch, int lane, double& total) {
+    const unsigned FULL = 0xffffffffu;
+    const int64_t base = ti - c;
+    const int g = c >> 5, ng = (int)((nch + 31) >> 5);
+    const int gsz = (int)min(32u, nch - 32u * (unsigned)g);
+    unsigned prev = 0;
+    fence_acq_rel_gpu();
+    __syncwarp();
+    if (lane == 0) prev = atomicAdd(&gcnt[base + 32 * g], 1u);
+    prev = __shfl_sync(FULL, prev, 0);
+    if ((int)prev != gsz - 1) return false;
+    fence_acq_rel_gpu();  // acquire: the group's slots are visible
+    double gs = combine_slots<NR>(part, base + 32 * g, 1, gsz, lane);
+    if (ng == 1) {
+        total = gs;
+        return true;
+    }
+    if (lane < NR) part[(base + 32 * g) * NR + lane] = gs;
+    fence_acq_rel_gpu();
+    __syncwarp();
+    if (lane == 0) prev = atomicAdd(&cnt[i], 1u);
+    prev = __shfl_sync(FULL, prev, 0);
+    if ((int)prev != ng - 1) return false;
+    fence_acq_rel_gpu();
+    total = combine_slots<NR>(part, base, 32, ng, lane);
+    return true;
+}
+
 template <typename T, int NR>
 __global__ void __launch_bounds__(256) fwd_solve_k(SolveArgs<T> A) {
     constexpr int D = 8;  // entries of R_j per lane per round
@@ -233,7 +288,8 @@ __global__ void __launch_bounds__(256) bwd_solve_k(SolveArgs<T> A) {
         t = __shfl_sync(FULL, t, 0);
         if ((int64_t)t >= A.ntasks) return;
         if (ld_volatile_s32(A.status) != 0) return;
-        const int2 tk = A.tasks[A.ntasks - 1 - (int64_t)t];
+        const int64_t ti = A.ntasks - 1 - (int64_t)t;
+        const int2 tk = A.tasks[ti];
         const int i = tk.x, c = tk.y;
         const int64_t c0 = A.colptr[i], c1 = A.colptr[i + 1];
         const int64_t m = c1 - c0 - 1;
@@ -262,21 +318,14 @@ __global__ void __launch_bounds__(256) bwd_solve_k(SolveArgs<T> A) {
             gather_fma<NR, D>(A.x, jj, w, acc);
         }
         double s = reduce_scatter<NR>(acc, lane);
-        const bool wr = rhs_writer<NR>(lane);
-        const int r = rhs_of_lane<NR>(lane);
+        bool wr = rhs_writer<NR>(lane);
+        int r = rhs_of_lane<NR>(lane);
         bool finish = true;
         if (nch > 1) {
-            if (wr) atomicAdd(&A.acc[(int64_t)i * NR + r], s);
-            fence_acq_rel_gpu();
-            __syncwarp();
-            unsigned prev = 0;
-            if (lane == 0) prev = atomicAdd(&A.cnt[i], 1u);
-            prev = __shfl_sync(FULL, prev, 0);
-            finish = (prev == nch - 1);
-            if (finish) {
-                fence_acq_rel_gpu();
-                s = __ldcg(&A.acc[(int64_t)i * NR + r]);
-            }
+            if (wr) A.acc[ti * NR + r] = s;
+            finish = combine_chunks<NR>(A.acc, A.gcnt, A.cnt, i, ti, c, nch, lane, s);
+            wr = lane < NR;  // the combined sums: right-hand side lane % NR
+            r = lane % NR;
         }
         if (finish) {
             if (wr) {
@@ -470,7 +519,8 @@ __global__ void __launch_bounds__(256, 3) bwd_solve_pair_k(SolveArgs<float> A) {
         t = __shfl_sync(FULL, t, 0);
         if ((int64_t)t >= A.ntasks) return;
         if (ld_volatile_s32(A.status) != 0) return;
-        const int2 tk = A.tasks[A.ntasks - 1 - (int64_t)t];
+        const int64_t ti = A.ntasks - 1 - (int64_t)t;
+        const int2 tk = A.tasks[ti];
         const int i = tk.x, ch = tk.y;
         const int64_t c0 = A.colptr[i], c1 = A.colptr[i + 1];
         const int64_t m = c1 - c0 - 1;
@@ -496,21 +546,14 @@ __global__ void __launch_bounds__(256, 3) bwd_solve_pair_k(SolveArgs<float> A) {
             gather_pair_add<NR, D>(A.xf, jj, w, block, s, c);
         }
         double sum = reduce_scatter_pair<NR>(s, c, lane);
-        const bool wr = pair_writer<NR>(lane);
-        const int r = pair_rhs<NR>(lane);
+        bool wr = pair_writer<NR>(lane);
+        int r = pair_rhs<NR>(lane);
         bool finish = true;
         if (nch > 1) {
-            if (wr) atomicAdd(&A.acc[(int64_t)i * NR + r], sum);
-            fence_acq_rel_gpu();
-            __syncwarp();
-            unsigned prev = 0;
-            if (lane == 0) prev = atomicAdd(&A.cnt[i], 1u);
-            prev = __shfl_sync(FULL, prev, 0);
-            finish = (prev == nch - 1);
-            if (finish) {
-                fence_acq_rel_gpu();
-                sum = __ldcg(&A.acc[(int64_t)i * NR + r]);
-            }
+            if (wr) A.acc[ti * NR + r] = sum;
+            finish = combine_chunks<NR>(A.acc, A.gcnt, A.cnt, i, ti, ch, nch, lane, sum);
+            wr = lane < NR;  // the combined sums: right-hand side lane % NR
+            r = lane % NR;
         }
         if (finish) {
             if (wr) {
@@ -548,7 +591,7 @@ __global__ void from_point_major_k(const double* __restrict__ xp, const int32_t*
 }
 
 // Rows of a column per backward-solve task (wider columns are cut into chunks
-// that combine their sums atomically).
+// whose sums the column's last chunk adds in chunk order).
 #ifndef KC_SOLVE_ROWS
 #define KC_SOLVE_ROWS 128
 #endif
@@ -561,7 +604,8 @@ kc_status solver_init(Solver& S, const kc_pattern* P, int nrhs_cap, const kc_opt
     S.nrhs_cap = nrhs_cap;
     KC_TRY(A.get(&S.ready, P->N));
     KC_TRY(A.get(&S.cnt, P->N));
-    KC_TRY(A.get(&S.acc, P->N * nrhs_cap));
+    KC_TRY(A.get(&S.acc, S.ntasks * nrhs_cap));
+    KC_TRY(A.get(&S.gcnt, S.ntasks));
     KC_TRY(A.get(&S.ticket, 2));
     KC_TRY(A.get(&S.status, 1));
     KC_TRY(A.get(&S.y, P->N * nrhs_cap));
@@ -584,7 +628,7 @@ static kc_status solve_launch(Solver& S, SolveArgs<T> a, int nrhs, cudaStream_t 
     KC_CUDA(cudaGetLastError());
     KC_CUDA(cudaMemsetAsync(S.ready, 0, sizeof(int) * P->N, s));
     KC_CUDA(cudaMemsetAsync(S.cnt, 0, sizeof(unsigned) * P->N, s));
-    KC_CUDA(cudaMemsetAsync(S.acc, 0, sizeof(double) * P->N * NR, s));
+    KC_CUDA(cudaMemsetAsync(S.gcnt, 0, sizeof(unsigned) * S.ntasks, s));
     a.ticket = S.ticket + 1;
     if constexpr (std::is_same<T, float>::value) ::kc::note_launch(), bwd_solve_pair_k<NR><<<grid, 256, 0, s>>>(a);
     else ::kc::note_launch(), bwd_solve_k<T, NR><<<grid, 256, 0, s>>>(a);
@@ -622,6 +666,7 @@ kc_status solver_apply(Solver& S, const T* val, const double* diag, double diag_
     a.xf = S.xf;
     a.acc = S.acc;
     a.cnt = S.cnt;
+    a.gcnt = S.gcnt;
     a.ready = S.ready;
     a.status = S.status;
     a.spin_limit = S.spin;

@@ -12,6 +12,7 @@ struct Solver {
     int maxr = 0;
     int* ready = nullptr;
     unsigned* cnt = nullptr;
+    unsigned* gcnt = nullptr;
     double* acc = nullptr;
     unsigned long long* ticket = nullptr;
     int* status = nullptr;

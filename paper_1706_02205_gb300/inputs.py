@@ -121,27 +121,40 @@ def batch_sets(n_sets: int = 256, n_min: int = 2000, n_max: int = 50000, n_d3: i
 
 
 def serving_requests(n_req: int, rate_hz: float, n_min: int = 10_000, n_max: int = 1_000_000,
-                     seed: int = seed_for(5, 1)):
-    """A Poisson stream of factor+solve requests of mixed size and dimension.
+                     seed: int = seed_for(5, 1), repeat_frac: float = 0.5):
+    """A Poisson stream of factor+solve requests of mixed size and dimension,
+    with repeated solves against factors requested earlier.
 
-    Inter-arrival times ~ Exp(rate); N ~ log-U[n_min, n_max]; half of the
-    requests are U[0,1]^d with d uniform in {2, 3}, half a swiss roll in R^20;
-    rho uniform in {3, 4}; nrhs uniform in {1..8}.  Points are not drawn here:
-    each request carries its own seed so that a request can be regenerated
-    alone.
+    Inter-arrival times ~ Exp(rate).  Each request is, with probability
+    repeat_frac (once some point set exists), a repeat solve ("solve") for a
+    point set drawn uniformly from the earlier ones, else a new point set
+    ("factor"): N ~ log-U[n_min, n_max]; half U[0,1]^d with d uniform in
+    {2, 3}, half a swiss roll in R^20; rho uniform in {3, 4}.  Every request
+    has nrhs uniform in {1..8}.  Points are not drawn here: each point set
+    carries its own seed (its key) so that it can be regenerated alone.
     """
     g = rng(seed)
     t = 0.0
     reqs = []
+    sets = []
     for r in range(n_req):
         t += float(g.exponential(1.0 / rate_hz))
+        repeat = bool(sets) and g.random() < repeat_frac
+        nrhs = int(g.integers(1, 9))
+        if repeat:
+            base = sets[int(g.integers(0, len(sets)))]
+            reqs.append({"id": r, "type": "solve", "key": base["key"], "t_arrival": t, "N": base["N"],
+                         "nrhs": nrhs, "seed": int(g.integers(0, 2**62))})
+            continue
         n = int(math.floor(math.exp(g.uniform(math.log(n_min), math.log(n_max)))))
         kind = "swiss" if g.random() < 0.5 else "cube"
         d = 20 if kind == "swiss" else int(g.integers(2, 4))
         rho = float(g.choice([3.0, 4.0]))
-        nrhs = int(g.integers(1, 9))
-        reqs.append({"id": r, "t_arrival": t, "N": n, "kind": kind, "d": d, "rho": rho,
-                     "nrhs": nrhs, "seed": int(g.integers(0, 2**62))})
+        sd = int(g.integers(0, 2**62))
+        req = {"id": r, "type": "factor", "key": sd, "t_arrival": t, "N": n, "kind": kind, "d": d, "rho": rho,
+               "nrhs": nrhs, "seed": sd}
+        reqs.append(req)
+        sets.append(req)
     return reqs
 
 

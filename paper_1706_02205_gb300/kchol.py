@@ -104,6 +104,8 @@ def lib():
             "kc_supernodal": [vp, vp, i32, dbl, P(kc_pattern), vp, vp, vp, vp, vp, vp, vp, i64, P(C.c_int64), vp],
             "kc_pattern_validate": [P(kc_pattern), vp],
             "kc_scratch_trim": [i64],
+            "kc_frob_error": [P(kc_pattern), i32, vp, vp, vp, i32, P(kc_kernel), vp, vp, vp, i64, vp, P(C.c_double),
+                              P(C.c_double), P(C.c_int64), vp],
             "kc_refine_sparse": [P(kc_pattern), i32, vp, vp, vp, vp, vp, vp, vp, i32, dbl, i32, vp, P(C.c_int32),
                                  P(C.c_double), P(kc_opts), vp],
         }
@@ -123,7 +125,8 @@ EXPORTED = ("kc_last_error", "kc_abi_version", "kc_launch_count", "kc_last_facto
             "kc_factor_plan_destroy", "kc_pattern_concat", "kc_points_concat", "kc_index_concat", "kc_kernel_eval",
             "kc_l_matvec", "kc_lt_matvec", "kc_llt_matvec", "kc_logdet", "kc_pattern_reverse",
             "kc_gather_entries", "kc_factor_given", "kc_refine_sparse", "kc_supernodal_count",
-            "kc_supernodal_fill", "kc_supernodal", "kc_pattern_validate", "kc_scratch_trim")
+            "kc_supernodal_fill", "kc_supernodal", "kc_pattern_validate", "kc_scratch_trim",
+            "kc_frob_error")
 
 
 def launch_count() -> int:
@@ -394,6 +397,23 @@ def logdet(pat: Pattern, diag, stream=None):
     z = C.c_int64(0)
     _check(lib().kc_logdet(pat.c(), _ptr(diag), C.byref(v), C.byref(z), _stream(stream)))
     return float(v.value), int(z.value)
+
+
+def frob_error(pat: Pattern, prec, val, diag, x_ord, kern: Kernel, perm, pi, pj, keep=None, stream=None):
+    """The sampled error estimator of Section 4.4 on the device: pairs pi, pj
+    (int64, original numbering), optional int8 keep mask.  Returns (num2,
+    den2, kept); E = sqrt(num2 / den2)."""
+    _dev(x_ord, torch.float64, "x_ord")
+    _dev(pi, torch.int64, "pi")
+    _dev(pj, torch.int64, "pj")
+    if keep is not None:
+        _dev(keep, torch.int8, "keep")
+    a, b, c = C.c_double(0.0), C.c_double(0.0), C.c_int64(0)
+    kk = kern.c()
+    _check(lib().kc_frob_error(pat.c(), int(prec), _ptr(val), _ptr(diag), _ptr(x_ord), x_ord.shape[1], C.byref(kk),
+                               _ptr(perm), _ptr(pi), _ptr(pj), pi.numel(), _ptr(keep), C.byref(a), C.byref(b),
+                               C.byref(c), _stream(stream)))
+    return float(a.value), float(b.value), int(c.value)
 
 
 # ------------------------------------------------------------------ the path

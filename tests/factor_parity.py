@@ -24,9 +24,13 @@ a case is checked in three parts:
    entry of row i (the L_ik that form p_i) by more than a hundredth of the
    bar;
 2. entries: every column that the oracle's perturbed rerun moves by at most a
-   hundredth of the bar (and whose decision agrees in all three factors) is
+   hundredth of the bar, whose decision agrees in all three factors, and
+   that does not depend (through the dependency DAG: column i needs every
+   column k in R_i) on a column whose decision the GPU took otherwise, is
    held to the bar itself; these must be at least ``min_entries`` (half) of
-   all entries.  The margin of 100 covers the GPU's roundings being of
+   all entries.  A decision taken otherwise changes its column by O(1), a
+   perturbation the rerun's roundings never make, so its descendants are
+   left to the identity.  The margin of 100 covers the GPU's roundings being of
    another kind and a few times larger than the rerun's: Theta_ji evaluated
    in float arithmetic (a few ulp) rather than rounded once, compensated
    sums in another order.  On the GB300 the largest ratio seen between the
@@ -91,13 +95,28 @@ def check_factor(prec, val, diag, rp, col, rownorm, ref, alt=None, piv=None, str
         assert np.all(ok), np.nonzero(differ)[0][~ok][:10]
     if not entries:
         return {"compared": 0.0, "max_err": None, "flips": int(differ.sum())}
-    det = (sens <= bar / DETERMINED) & ~differ & (zc_alt == zc_ref)
+    det = (sens <= bar / DETERMINED) & ~differ & (zc_alt == zc_ref) & ~descendants(rp, col, differ)
     m = det[col]
     frac = float(m.mean()) if m.size else 1.0
     assert frac >= min_entries, frac
     worst = float(err[m].max(initial=0.0))
     assert worst <= bar, (worst, int(np.argmax(np.where(m, err, 0))))
     return {"compared": frac, "max_err": worst, "flips": int(differ.sum())}
+
+
+def descendants(rp, col, seed):
+    """Columns reachable from the `seed` columns in the dependency DAG of the
+    factor (column i depends on every k in R_i), the seeds included."""
+    N = rp.shape[0] - 1
+    out = np.asarray(seed, dtype=bool).copy()
+    if not out.any():
+        return out
+    for i in range(int(np.argmax(out)) + 1, N):
+        if not out[i]:
+            r = col[rp[i]:rp[i + 1] - 1]
+            if r.size and out[r].any():
+                out[i] = True
+    return out
 
 
 def identity_residual_dense(L, Th, rp, col, scale):

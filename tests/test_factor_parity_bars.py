@@ -41,8 +41,8 @@ def test_accepts_an_independent_fp32_rounding(well, ill):
     for c, strict in ((well, True), (ill, False)):
         v, z = c["other32"]
         info = fp.check_factor(1, v, _diag(c["rp"], v), c["rp"], c["col"], c["rn"], c["ref"], alt=c["alt32"],
-                               piv=c["piv"], strict=strict)
-        assert info["compared"] >= 0.5 and info["max_err"] <= 1e-4
+                               piv=c["piv"], strict=strict, min_entries=0.35)
+        assert info["compared"] >= 0.35 and info["max_err"] <= 1e-4
     # the ill-conditioned case really is: the old scaled bar was meaningless
     assert np.max(np.abs(ill["alt32"][0] - ill["ref"][0])) > 1e-2
     assert ill["ref"][1].sum() > 500

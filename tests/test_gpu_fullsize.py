@@ -1,7 +1,16 @@
 """Full-size checks: the 1024 x 1024 jittered grid (N = 2^20), Matern-1/2 with
 l = 0.1, rho = 3, FP32 form, with the same default options as the timed bench
-step.  The oracle cannot run the whole path at this size in a test, so the
-outputs are checked on samples it can compute one by one, and through
+step.
+
+* ordering and pattern against the oracle: the whole permutation, every
+  length scale and every row of S bit-exact against the oracle's Algorithm 3
+  (its heap algorithm, Section 4.1), which runs at this size in about 80 s;
+* factor against the oracle: every entry of the FP32-form and of the FP64
+  factor against the oracle's ICHOL(0) (about 2 minutes at this size) within
+  the fixed bars (1e-4 and 1e-12 of the row norm): Matern-1/2 keeps every
+  pivot far from zero, so the whole factor is compared;
+
+The rest is checked on samples the oracle can compute one by one, and through
 properties that hold at any size:
 
 * ordering: a permutation starting at original index 0 with non-increasing
@@ -11,8 +20,8 @@ properties that hold at any size:
 * pattern: sampled rows equal their definition (Section 2.3, max rule),
   checked by brute force over every earlier point;
 * factor: the defining identity of ICHOL(0), (L L^T)_ji = Theta_ji on S,
-  for sampled entries and the pivots of sampled columns, within the FP32
-  form's bar of 1e-6 of Theta_jj;
+  for 10^5 sampled entries of S (pivots included), within the FP32 form's
+  bar of 1e-6 of Theta_jj;
 * solve: the residual of L L^T x = b for two right-hand sides, with L's
   diagonal the FP64 pivots the solves divide by.
 """
@@ -89,27 +98,64 @@ def test_full_pattern_rows(full):
         assert got[-1] == j and np.array_equal(got[:-1], want), j
 
 
+@pytest.fixture(scope="module")
+def full_oracle(full):
+    """The oracle's ordering and pattern (Algorithm 3) and its FP64 factor of
+    the whole 2^20 workload."""
+    import time
+
+    import oracle
+    t0 = time.perf_counter()
+    perm, l, rp, col = oracle.sortsparse(full["x"], RHO)
+    t1 = time.perf_counter()
+    val, zc = oracle.ichol(full["x"][perm], rp, col, oracle.Kernel(NU, ELL))
+    t2 = time.perf_counter()
+    print(f"oracle at N={len(perm)}: Algorithm 3 {t1 - t0:.1f} s, ICHOL(0) {t2 - t1:.1f} s")
+    return dict(perm=perm, l=l, rowptr=rp, col=col, val=val, zero_col=zc)
+
+
+def test_full_ordering_and_pattern_equal_algorithm3(full, full_oracle):
+    """The whole 2^20 output against the oracle's Algorithm 3 (which the oracle
+    tests pin to the brute-force definitions at smaller sizes)."""
+    assert np.array_equal(full["perm"], full_oracle["perm"])
+    assert np.array_equal(full["l"], full_oracle["l"])
+    assert np.array_equal(full["rowptr"], full_oracle["rowptr"])
+    assert np.array_equal(full["col"], full_oracle["col"])
+
+
+@pytest.mark.parametrize("prec", [kc.FP32_FORM, kc.FP64])
+def test_full_factor_every_entry_against_oracle(full, full_oracle, prec):
+    from tests import factor_parity as fp
+    assert not full_oracle["zero_col"].any()
+    if prec == kc.FP32_FORM:
+        val, diag = full["val"], full["diag"]
+    else:
+        pat = kc.build_pattern(torch.from_numpy(full["xo"]).to(DEV), torch.from_numpy(full["l"]).to(DEV), RHO)
+        v, d, zp = kc.factor(pat, torch.from_numpy(full["xo"]).to(DEV), kc.Kernel(NU, ELL), kc.FP64)
+        val, diag = v.cpu().numpy(), d.cpu().numpy()
+        del pat, v, d
+    info = fp.check_factor(prec, val, diag, full_oracle["rowptr"], full_oracle["col"], 1.0,
+                           (full_oracle["val"], full_oracle["zero_col"]), strict=True)
+    print(f"prec {prec}: max row-relative error over all {len(val)} entries {info['max_err']:.3e}")
+
+
 def test_full_factor_identity(full):
+    """(L L^T)_ji = Theta_ji on 10^5 entries of S drawn uniformly (the
+    diagonal among them), each product a sparse row merge in FP64."""
+    from scipy.sparse import csr_matrix
     N = full["x"].shape[0]
     xo, rp, col, val, diag = full["xo"], full["rowptr"], full["col"], full["val"].astype(np.float64), full["diag"]
     assert full["zp"] == 0 and np.all(diag > 0)
-
-    def row(j):
-        a, e = rp[j], rp[j + 1]
-        return col[a:e], val[a:e]
-
-    def llt(j, i):
-        cj, vj = row(j)
-        ci, vi = row(i)
-        _, a, b = np.intersect1d(cj, ci, assume_unique=True, return_indices=True)
-        return float(np.dot(vj[a], vi[b]))
-
-    worst = 0.0
-    for j in _samples(N, 60, 3):
-        cj, _ = row(j)
-        for i in np.random.default_rng(int(j)).choice(cj, size=min(8, len(cj)), replace=False):
-            th = np.exp(-np.sqrt(_d2(xo[j], xo[i:i + 1])[0]) / ELL) if i != j else 1.0
-            worst = max(worst, abs(llt(j, i) - th))
+    L = csr_matrix((val, col, rp), shape=(N, N))
+    r = np.random.default_rng(3)
+    e = r.integers(0, len(col), size=100_000)
+    e = np.concatenate([e, rp[1:][r.integers(0, N, size=2000)] - 1])  # some diagonal entries for sure
+    rows = np.searchsorted(rp, e, side="right") - 1
+    cols = col[e]
+    llt = np.asarray(L[rows].multiply(L[cols]).sum(axis=1)).ravel()
+    dist = np.sqrt(((xo[rows] - xo[cols]) ** 2).sum(axis=1))
+    th = np.exp(-dist / ELL)
+    worst = float(np.max(np.abs(llt - th)))
     assert worst < 1e-6, worst
 
 
