@@ -535,6 +535,24 @@ def run_supernodal(args):
             for k, nm in enumerate(names):
                 ph[nm].append(ev[k].elapsed_time(ev[k + 1]))
     sn_factor_kernel = kc.last_factor_kernel_ms()
+    # the same pattern by column groups (the block factorisation), both forms
+    blocked = {}
+    for pname, pr in (("fp32_form", kc.FP32_FORM), ("fp64", kc.FP64)):
+        ks = []
+        for it in range(args.warmup + args.steps):
+            vb, db, zb = kc.factor_blocked(spat, x_new, kern, pr)
+            torch.cuda.synchronize()
+            if it >= args.warmup:
+                ks.append(kc.last_factor_kernel_ms())
+        km = statistics.median(ks)
+        blocked[pname] = {"kernel_ms": km, "kernel_nnz_per_s": spat.nnz / (km * 1e-3), "zero_pivots": zb}
+        del vb, db
+    ks64 = []
+    for it in range(1 + args.steps):
+        kc.factor(spat, x_new, kern, kc.FP64)
+        torch.cuda.synchronize()
+        if it >= 1:
+            ks64.append(kc.last_factor_kernel_ms())
     _, _, zp0 = kc.factor(pat0, xo, kern, kc.FP32_FORM)
     mm_factor_kernel = kc.last_factor_kernel_ms()
     med = {k: statistics.median(v_) for k, v_ in ph.items()}
@@ -542,6 +560,7 @@ def run_supernodal(args):
                         f"{kernel_name(kern)}, rho={args.rho}, FP32 form", "N": N, "nnz": spat.nnz,
             "depth": spat.depth, "zero_pivots": zp, "phases_ms": med,
             "factor_kernel_ms": sn_factor_kernel, "factor_nnz_per_s": spat.nnz / (sn_factor_kernel * 1e-3),
+            "factor_fp64_kernel_ms": statistics.median(ks64), "blocked": blocked,
             "maximin": {"nnz": pat0.nnz, "depth": pat0.depth, "factor_kernel_ms": mm_factor_kernel,
                         "zero_pivots": zp0}}
 

@@ -131,7 +131,7 @@ const char* kc_last_error(void);
  * kc_kernel_eval, kc_l_matvec, kc_lt_matvec, kc_llt_matvec, kc_logdet,
  * kc_pattern_reverse, kc_gather_entries, kc_factor_given, kc_refine_sparse,
  * kc_supernodal_count, kc_supernodal_fill, kc_supernodal, kc_pattern_validate.
- * 4: kc_scratch_trim, kc_frob_error; scratch from a private pool per device. */
+ * 4: kc_scratch_trim, kc_frob_error, kc_factor_blocked; scratch from a private pool per device. */
 #define KC_ABI_VERSION 4
 int32_t kc_abi_version(void);
 
@@ -203,6 +203,23 @@ kc_status kc_pattern_validate(const kc_pattern* pat, void* stream);
 kc_status kc_factor(const kc_pattern* pat, const double* x_ord, int32_t d, const kc_kernel* kern,
                     int32_t prec, void* val, double* diag, int64_t* zero_pivots_out,
                     const kc_opts* opts, void* stream);
+
+/* ---- the same factor by column groups (the supernodal block factorisation)  *
+ * Same arguments and result as kc_factor (up to the order of the sums), for
+ * entries from the covariance function.  Runs of consecutive columns whose
+ * rows share one list of earlier columns and whose columns share one set of
+ * later rows -- the supernodes of the supernodal multicolour ordering of the
+ * stability section -- are factored as blocks of at most 8 columns: the
+ * group's diagonal block by a small dense Cholesky with the zero-column rule,
+ * and every row below it with one pass over the row's prefix for all the
+ * group's columns, then a forward substitution (the block algorithm of the
+ * stability appendix, equal to Algorithm 2 on such a pattern).  On a pattern
+ * without such runs (the maximin pattern) every group is one column.  opts:
+ * spin_limit_cycles, rows_per_task (rows of one task, 0 -> 128),
+ * lanes_per_row (>= 8).  One persistent launch.  Synchronises. */
+kc_status kc_factor_blocked(const kc_pattern* pat, const double* x_ord, int32_t d, const kc_kernel* kern,
+                            int32_t prec, void* val, double* diag, int64_t* zero_pivots_out, const kc_opts* opts,
+                            void* stream);
 
 /* ---- factor plans: many point sets in one launch, capturable ------------ *
  * A plan keeps the task list and counters of one pattern, so that each

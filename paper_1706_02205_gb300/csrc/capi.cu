@@ -53,6 +53,8 @@ kc_status pca_error_impl(const double* x, int64_t N, int d, const kc_kernel* ker
 kc_status factor_matvec_impl(const kc_pattern* P, int prec, const void* val, const double* diag, const int32_t* perm,
                              const double* in, int nrhs, double* out, int which, cudaStream_t s);
 kc_status logdet_impl(const kc_pattern* P, const double* diag, double* logdet_out, int64_t* zero_out, cudaStream_t s);
+kc_status factor_blocked_impl(const kc_pattern* P, const double* x, int d, const kc_kernel* kern, int prec, void* val,
+                              double* diag, int64_t* zero_out, const kc_opts* o, cudaStream_t s);
 kc_status frob_error_impl(const kc_pattern* P, int prec, const void* val, const double* diag, const double* x_ord,
                           int d, const kc_kernel* kern, const int32_t* perm, const int64_t* pi, const int64_t* pj,
                           int64_t m, const int8_t* keep, double* num2_out, double* den2_out, int64_t* kept_out,
@@ -160,6 +162,16 @@ kc_status kc_factor(const kc_pattern* pat, const double* x_ord, int32_t d, const
     KC_TRY(check_points(x_ord, pat->N, d));
     if (!val || !diag) return fail(KC_EINVAL, "val and diag must be non-NULL");
     return factor_impl(pat, x_ord, d, kern, prec, val, diag, zero_pivots_out, opts, (cudaStream_t)stream);
+}
+
+kc_status kc_factor_blocked(const kc_pattern* pat, const double* x_ord, int32_t d, const kc_kernel* kern,
+                            int32_t prec, void* val, double* diag, int64_t* zero_pivots_out, const kc_opts* opts,
+                            void* stream) {
+    KC_RANGE("kc_factor_blocked");
+    KC_TRY(check_pattern(pat));
+    KC_TRY(check_points(x_ord, pat->N, d));
+    if (!val || !diag) return fail(KC_EINVAL, "val and diag must be non-NULL");
+    return factor_blocked_impl(pat, x_ord, d, kern, prec, val, diag, zero_pivots_out, opts, (cudaStream_t)stream);
 }
 
 kc_status kc_solve(const kc_pattern* pat, int32_t prec, const void* val, const double* diag, const kc_kernel* kern,

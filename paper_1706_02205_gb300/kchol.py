@@ -104,6 +104,7 @@ def lib():
             "kc_supernodal": [vp, vp, i32, dbl, P(kc_pattern), vp, vp, vp, vp, vp, vp, vp, i64, P(C.c_int64), vp],
             "kc_pattern_validate": [P(kc_pattern), vp],
             "kc_scratch_trim": [i64],
+            "kc_factor_blocked": [P(kc_pattern), vp, i32, P(kc_kernel), i32, vp, vp, P(C.c_int64), P(kc_opts), vp],
             "kc_frob_error": [P(kc_pattern), i32, vp, vp, vp, i32, P(kc_kernel), vp, vp, vp, i64, vp, P(C.c_double),
                               P(C.c_double), P(C.c_int64), vp],
             "kc_refine_sparse": [P(kc_pattern), i32, vp, vp, vp, vp, vp, vp, vp, i32, dbl, i32, vp, P(C.c_int32),
@@ -126,7 +127,7 @@ EXPORTED = ("kc_last_error", "kc_abi_version", "kc_launch_count", "kc_last_facto
             "kc_l_matvec", "kc_lt_matvec", "kc_llt_matvec", "kc_logdet", "kc_pattern_reverse",
             "kc_gather_entries", "kc_factor_given", "kc_refine_sparse", "kc_supernodal_count",
             "kc_supernodal_fill", "kc_supernodal", "kc_pattern_validate", "kc_scratch_trim",
-            "kc_frob_error")
+            "kc_frob_error", "kc_factor_blocked")
 
 
 def launch_count() -> int:
@@ -283,6 +284,23 @@ def factor(pat: Pattern, x_ord, kern: Kernel, prec=FP32_FORM, opts: kc_opts | No
     k = kern.c()
     _check(lib().kc_factor(pat.c(), _ptr(x_ord), d, C.byref(k), int(prec), _ptr(val), _ptr(diag), C.byref(zp),
                            C.byref(opts) if opts is not None else None, _stream(stream)))
+    return val, diag, int(zp.value)
+
+
+def factor_blocked(pat: Pattern, x_ord, kern: Kernel, prec=FP32_FORM, opts: kc_opts | None = None, val=None,
+                   diag=None, stream=None):
+    """The same factor by column groups (kc_factor_blocked) -> (val, diag, zero_pivots)."""
+    _dev(x_ord, torch.float64, "x_ord")
+    d = x_ord.shape[1]
+    dt = torch.float64 if prec == FP64 else torch.float32
+    if val is None:
+        val = torch.empty(pat.nnz, dtype=dt, device=x_ord.device)
+    if diag is None:
+        diag = torch.empty(pat.N, dtype=torch.float64, device=x_ord.device)
+    zp = C.c_int64(0)
+    k = kern.c()
+    _check(lib().kc_factor_blocked(pat.c(), _ptr(x_ord), d, C.byref(k), int(prec), _ptr(val), _ptr(diag),
+                                   C.byref(zp), C.byref(opts) if opts is not None else None, _stream(stream)))
     return val, diag, int(zp.value)
 
 

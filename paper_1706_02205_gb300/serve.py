@@ -203,8 +203,9 @@ def solve_resident(res: Resident, b_host: np.ndarray, stream):
 
 class Server:
     def __init__(self, max_inflight: int = 4, hbm_budget_bytes: int | None = None, prec=kc.FP32_FORM,
-                 keep_solutions: bool = False, group_n_max: int = 60_000, group_max: int = 32):
+                 keep_solutions: bool = False, group_n_max: int = 60_000, group_max: int = 32, solve_slots: int = 2):
         self.k = max_inflight
+        self.solve_slots = solve_slots
         if hbm_budget_bytes is None:
             free, total = torch.cuda.mem_get_info()
             hbm_budget_bytes = int(0.8 * free)
@@ -213,7 +214,7 @@ class Server:
         self.keep = keep_solutions
         self.group_n_max = group_n_max
         self.group_max = group_max
-        self.streams = [torch.cuda.Stream() for _ in range(max_inflight)]
+        self.streams = [torch.cuda.Stream() for _ in range(max_inflight + solve_slots)]
         self.cache = FactorCache()
         self.points = {}  # key -> (host points, the factor request) for refactoring after eviction
 
@@ -235,10 +236,11 @@ class Server:
             if r.get("type", "factor") == "factor":
                 self.points[r["key"]] = (payloads[i][0], r)
         cv = threading.Condition()
-        state = {"inflight": 0, "bytes": 0, "max_inflight": 0}
+        state = {"inflight": 0, "solves": 0, "bytes": 0, "max_inflight": 0}
         free_streams = list(range(self.k))
+        free_solve = list(range(self.k, self.k + self.solve_slots))
         records = [None] * len(requests)
-        ex = ThreadPoolExecutor(max_workers=self.k)
+        ex = ThreadPoolExecutor(max_workers=self.k + self.solve_slots)
         t0 = time.perf_counter()
         pending = []   # arrived, not admitted (indices)
         busy_keys = set()  # keys whose factor job is running
@@ -327,9 +329,13 @@ class Server:
                 if job["type"] == "factor":
                     for r in job["reqs"]:
                         busy_keys.discard(r["key"])
-                state["inflight"] -= 1
+                if job.get("lane") == "solve":
+                    state["solves"] -= 1
+                    free_solve.append(sid)
+                else:
+                    state["inflight"] -= 1
+                    free_streams.append(sid)
                 state["bytes"] -= need
-                free_streams.append(sid)
                 for m, i in enumerate(job["ids"]):
                     req = requests[i]
                     arr = req["t_arrival"] if realtime else 0.0
@@ -342,15 +348,45 @@ class Server:
                                   "x": sols[m] if self.keep else None, "error": err}
                 cv.notify_all()
 
-        def admissible():
-            """The first pending request that can start now: a solve waits while
-            its factor is still being computed (other requests go ahead)."""
-            for q in pending:
+        def try_admit():
+            """The next job that can start now, or None.  Factor requests start in
+            arrival order on the factor slots.  A solve on a resident factor may
+            pass a factor request that waits for a slot or for memory: it runs on
+            a solve lane (or a free factor slot); a solve whose factor is still
+            being computed waits for it."""
+            factor_seen = False
+            for q in list(pending):
                 rq = requests[q]
-                if rq.get("type", "factor") == "solve" and rq["key"] in busy_keys:
+                if rq.get("type", "factor") == "solve":
+                    if rq["key"] in busy_keys:
+                        continue
+                    if self.cache.get(rq["key"]) is not None:
+                        if state["solves"] >= self.solve_slots and state["inflight"] >= self.k:
+                            continue
+                        job = make_job(q)
+                        need = self._need(job)
+                        if fits(need) or state["inflight"] + state["solves"] == 0:
+                            return job, need
+                        continue
+                if factor_seen:
+                    continue  # factor requests (and refactors) in arrival order
+                factor_seen = True
+                if state["inflight"] >= self.k:
                     continue
-                return q
+                job = make_job(q)
+                need = self._need(job)
+                if fits(need) or state["inflight"] + state["solves"] == 0:
+                    return job, need  # (a job larger than the whole budget runs alone)
             return None
+
+        def fits(need):
+            """The memory next to the resident factors; evicts unpinned factors,
+            least recently used first, to make room."""
+            over = state["bytes"] + self.cache.bytes + need - self.budget
+            if over > 0:
+                self.cache.evict_until(max(0, self.cache.bytes - over))
+                over = state["bytes"] + self.cache.bytes + need - self.budget
+            return over <= 0
 
         while nxt < len(order) or pending:
             if not pending:
@@ -363,31 +399,28 @@ class Server:
             with cv:
                 while True:
                     arrived_until(now())
-                    head = admissible()
-                    if head is not None and state["inflight"] < self.k:
-                        job = make_job(head)
-                        need = self._need(job)
-                        # the memory next to the resident factors: evict unpinned
-                        # factors, least recently used first, to make room
-                        over = state["bytes"] + self.cache.bytes + need - self.budget
-                        if over > 0:
-                            self.cache.evict_until(max(0, self.cache.bytes - over))
-                            over = state["bytes"] + self.cache.bytes + need - self.budget
-                        if over <= 0 or state["inflight"] == 0:
-                            break  # (a job larger than the whole budget runs alone)
+                    got = try_admit()
+                    if got is not None:
+                        job, need = got
+                        break
                     # wait for a job to finish (or, in real time, for an arrival)
                     cv.wait(timeout=0.005 if realtime and nxt < len(order) else None)
                 for i in job["ids"]:
                     pending.remove(i)
+                lane_solve = job["type"] == "solve" and state["solves"] < self.solve_slots
+                job["lane"] = "solve" if lane_solve else "slot"
                 if job["type"] == "solve":
                     job["res"].pins += 1
                 else:
                     for r in job["reqs"]:
                         busy_keys.add(r["key"])
-                state["inflight"] += 1
+                if lane_solve:
+                    state["solves"] += 1
+                else:
+                    state["inflight"] += 1
                 state["bytes"] += need
                 state["max_inflight"] = max(state["max_inflight"], state["inflight"])
-                sid = free_streams.pop(0)
+                sid = (free_solve if lane_solve else free_streams).pop(0)
             ex.submit(work, job, sid, need, now())
         ex.shutdown(wait=True)
         self.max_inflight_seen = state["max_inflight"]
