@@ -47,9 +47,18 @@
 
 namespace kc {
 
-constexpr int BF_THREADS = 128;  // one task per CTA of four warps
+// One task per CTA of KC_BLOCK_THREADS threads; KC_BLOCK_MINB resident CTAs
+// per SM that the register budget is cut for.
+#ifndef KC_BLOCK_THREADS
+#define KC_BLOCK_THREADS 128
+#endif
+#ifndef KC_BLOCK_MINB
+#define KC_BLOCK_MINB 8
+#endif
+constexpr int BF_THREADS = KC_BLOCK_THREADS;
 constexpr int BF_WARPS = BF_THREADS / 32;
 constexpr int BF_MAXG = 8;       // columns per group at most
+constexpr int BU = 8;            // (column, value) loads per lane in flight while streaming a row
 
 template <typename T>
 struct GroupArgs {
@@ -101,20 +110,104 @@ __device__ __forceinline__ void tri_ts(int q, int& t, int& s) {
     s = q - t * (t + 1) / 2;
 }
 
+// The rows q in [qb, qe) of the CSC below a group of m <= M columns g0 ..
+// g0+m-1: each row's prefix streamed once by G lanes (BU loads per lane in
+// flight, one table lookup per entry feeding m compensated accumulators),
+// then the forward substitution with L_AA: each result (theta - sum -
+// sum_w x_w L_uw) times the stored reciprocal of L_uu (0 for a dropped pivot);
+// FP32 form in FP32 (the compensated sum's two parts subtracted in turn, as
+// the column kernel finishes an entry), FP64 form in FP64.
+template <typename T>
+__device__ __forceinline__ T fsub_dot(T v, T a, T b);
+template <>
+__device__ __forceinline__ float fsub_dot(float v, float a, float b) { return fmaf(-a, b, v); }
+template <>
+__device__ __forceinline__ double fsub_dot(double v, double a, double b) { return fma(-a, b, v); }
+
+template <typename T, int MM, bool GEN, int M>
+__device__ __forceinline__ void group_rows(const GroupArgs<T>& A, int64_t qb, int64_t qe, int g0, int m,
+                                           const unsigned long long* tab, int hb, const T* V, const T* Laa,
+                                           const double* Ld, const T* Linv) {
+    const unsigned FULL = 0xffffffffu;
+    const int lane = lane_id(), warp = threadIdx.x >> 5;
+    const int G = A.lanes, ngr = 32 / G, grp = lane / G, sub = lane % G;
+    for (int64_t q0 = qb + (int64_t)(warp * ngr); q0 < qe; q0 += (int64_t)BF_WARPS * ngr) {
+        const int64_t q = q0 + grp;
+        const bool act = q < qe;
+        int j = 0;
+        int64_t e = 0, es = 0;
+        if (act) {
+            j = __ldg(&A.rowidx[q]);
+            e = __ldg(&A.slot[q]);  // L_j,g0 lives at e, the prefix of row j is [es, e)
+            es = A.rowptr[j];
+        }
+        T th = (T)0;  // lane sub: Theta_j,(g0+sub)
+        if (act && sub < m)
+            th = theta_off<T, GEN>(A.kp, A.d, A.x + (int64_t)j * A.d, A.x + (int64_t)(g0 + sub) * A.d);
+        Acc<T> acc[M];
+        if (act) {
+            for (int64_t f0 = es + sub; f0 < e; f0 += (int64_t)BU * G) {
+                int k[BU];
+                T w[BU];
+#pragma unroll
+                for (int v = 0; v < BU; ++v) {
+                    const int64_t f = f0 + (int64_t)v * G;
+                    k[v] = f < e ? __ldg(&A.col[f]) : -1;
+                    w[v] = f < e ? ldcg(&A.val[f]) : (T)0;
+                }
+#pragma unroll
+                for (int v = 0; v < BU; ++v) {
+                    const int p = k[v] >= 0 ? prefix_find(tab, hb, k[v]) : -1;
+                    if (p >= 0) {
+                        const T* vp = V + (int64_t)p * MM;
+#pragma unroll
+                        for (int u = 0; u < M; ++u)
+                            if (u < m) acc[u].add(w[v], vp[u]);
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < M; ++u)
+            if (u < m) acc[u].group_reduce(G);
+        T x[M];
+#pragma unroll
+        for (int u = 0; u < M; ++u) {
+            const T thu = __shfl_sync(FULL, th, grp * G + (u < m ? u : 0));
+            if (u < m) {
+                if constexpr (sizeof(T) == 4) {
+                    float v = __fsub_rn(__fsub_rn(thu, acc[u].s), acc[u].c);
+#pragma unroll
+                    for (int w2 = 0; w2 < u; ++w2) v = fsub_dot(v, x[w2], Laa[u * MM + w2]);
+                    x[u] = __fmul_rn(v, Linv[u]);
+                } else {
+                    double v = thu - acc[u].total();
+#pragma unroll
+                    for (int w2 = 0; w2 < u; ++w2) v = fsub_dot(v, x[w2], Laa[u * MM + w2]);
+                    x[u] = v * Linv[u];  // (the GB300's FP64 divisions are slow)
+                }
+            }
+        }
+        if (act && sub == 0)
+#pragma unroll
+            for (int u = 0; u < M; ++u)
+                if (u < m) A.val[e + u] = x[u];
+    }
+}
+
 template <typename T, int MM, bool GEN>
-__global__ void __launch_bounds__(BF_THREADS) ichol_group_k(GroupArgs<T> A) {
+__global__ void __launch_bounds__(BF_THREADS, KC_BLOCK_MINB) ichol_group_k(GroupArgs<T> A) {
     extern __shared__ __align__(16) unsigned char smem[];
     // layout: D (FP64, lower triangle), the pivots' roots (FP64), L_AA (T),
     // control words, the prefix table (8-byte slots), the values V[p][t]
     double* D = (double*)smem;
     double* Ld = D + MM * (MM + 1) / 2;
     T* Laa = (T*)(Ld + MM);
-    int* ctl = (int*)(Laa + MM * MM);
+    T* Linv = Laa + MM * MM;  // the reciprocals of the pivots' roots (0 for a dropped pivot)
+    int* ctl = (int*)(Linv + MM);
     unsigned long long* tab = (unsigned long long*)(((uintptr_t)(ctl + 4) + 15) & ~(uintptr_t)15);
     T* V = (T*)(tab + (1 << A.hbits));
     const int tid = threadIdx.x, lane = lane_id(), warp = tid >> 5;
-    const unsigned FULL = 0xffffffffu;
-    const int G = A.lanes, ngr = 32 / G, grp = lane / G, sub = lane % G;
     for (;;) {
         __syncthreads();  // the previous task's shared reads are done
         if (tid == 0) {
@@ -145,19 +238,24 @@ __global__ void __launch_bounds__(BF_THREADS) ichol_group_k(GroupArgs<T> A) {
         }
         fence_acq_rel_gpu();  // acquire: the prefix values are visible from here on
 
-        // stage the prefix: table column -> position, values of the m rows
-        for (int h = tid; h < (1 << A.hbits); h += BF_THREADS) tab[h] = ~0ull;
+        // stage the prefix: table column -> position (sized to this prefix, load
+        // factor <= 3/4), values of the m rows
+        int hb = 5;
+        while (3 * (1 << hb) < 4 * P) ++hb;
+        for (int h = tid; h < (1 << hb); h += BF_THREADS) tab[h] = ~0ull;
+        int64_t rs[MM];
+#pragma unroll
+        for (int u = 0; u < MM; ++u) rs[u] = u < m ? A.rowptr[g0 + u] : 0;
         __syncthreads();
         {
-            const int mask = (1 << A.hbits) - 1;
+            const int mask = (1 << hb) - 1;
             for (int p = tid; p < P; p += BF_THREADS) {
                 const int k = __ldg(&A.col[a0 + p]);
                 const unsigned long long w = ((unsigned long long)(unsigned)p << 32) | (unsigned)k;
-                int h = gslot(k, A.hbits);
+                int h = gslot(k, hb);
                 while (atomicCAS(&tab[h], ~0ull, w) != ~0ull) h = (h + 1) & mask;
 #pragma unroll
-                for (int u = 0; u < MM; ++u)
-                    V[(int64_t)p * MM + u] = u < m ? ldcg(&A.val[A.rowptr[g0 + u] + p]) : (T)0;
+                for (int u = 0; u < MM; ++u) V[(int64_t)p * MM + u] = u < m ? ldcg(&A.val[rs[u] + p]) : (T)0;
             }
         }
         __syncthreads();
@@ -198,6 +296,7 @@ __global__ void __launch_bounds__(BF_THREADS) ichol_group_k(GroupArgs<T> A) {
                 if (lane == 0) {
                     Laa[s * MM + s] = (T)Lss;
                     Ld[s] = Lss;
+                    Linv[s] = zero ? (T)0 : (T)(1.0 / Lss);
                 }
                 __syncwarp();
             }
@@ -210,56 +309,12 @@ __global__ void __launch_bounds__(BF_THREADS) ichol_group_k(GroupArgs<T> A) {
         }
         __syncthreads();
 
-        // the rows below the group: column g0 of the CSC past its first m rows
+        // the rows below the group: column g0 of the CSC past its first m rows,
+        // with code for the group's exact size (no predicated-off accumulators)
         const int64_t qb = A.colptr[g0] + m + (int64_t)chunk * A.rpt;
         const int64_t qe = min(A.colptr[g0 + 1], qb + A.rpt);
-        for (int64_t q0 = qb + (int64_t)(warp * ngr); q0 < qe; q0 += (int64_t)BF_WARPS * ngr) {
-            const int64_t q = q0 + grp;
-            const bool act = q < qe;
-            int j = 0;
-            int64_t e = 0, es = 0;
-            if (act) {
-                j = __ldg(&A.rowidx[q]);
-                e = __ldg(&A.slot[q]);  // L_j,g0 lives at e, the prefix of row j is [es, e)
-                es = A.rowptr[j];
-            }
-            T th = (T)0;  // lane sub: Theta_j,(g0+sub)
-            if (act && sub < m)
-                th = theta_off<T, GEN>(kp, A.d, A.x + (int64_t)j * A.d, A.x + (int64_t)(g0 + sub) * A.d);
-            Acc<T> acc[MM];
-            if (act) {
-                for (int64_t f = es + sub; f < e; f += G) {
-                    const int k = __ldg(&A.col[f]);
-                    const T w = ldcg(&A.val[f]);
-                    const int p = prefix_find(tab, A.hbits, k);
-                    if (p >= 0) {
-                        const T* vp = V + (int64_t)p * MM;
-#pragma unroll
-                        for (int u = 0; u < MM; ++u)
-                            if (u < m) acc[u].add(w, vp[u]);
-                    }
-                }
-            }
-#pragma unroll
-            for (int u = 0; u < MM; ++u)
-                if (u < m) acc[u].group_reduce(G);
-            double x[MM];
-#pragma unroll
-            for (int u = 0; u < MM; ++u) {
-                const T thu = __shfl_sync(FULL, th, grp * G + (u < m ? u : 0));
-                if (u < m) {
-                    double v = (double)thu - acc[u].total();
-#pragma unroll
-                    for (int w2 = 0; w2 < u; ++w2) v -= x[w2] * (double)Laa[u * MM + w2];
-                    const double Luu = Ld[u];
-                    x[u] = Luu == 0.0 ? 0.0 : (double)(T)(v / Luu);
-                }
-            }
-            if (act && sub == 0)
-#pragma unroll
-                for (int u = 0; u < MM; ++u)
-                    if (u < m) A.val[e + u] = (T)x[u];
-        }
+        if (m <= 4) group_rows<T, MM, GEN, 4>(A, qb, qe, g0, m, tab, hb, V, Laa, Ld, Linv);
+        else group_rows<T, MM, GEN, MM>(A, qb, qe, g0, m, tab, hb, V, Laa, Ld, Linv);
         __syncthreads();
         if (tid == 0) {
             fence_acq_rel_gpu();
@@ -364,7 +419,7 @@ kc_status exclusive_scan_i64(const int64_t* in, int64_t* out, int64_t n, Arena& 
 
 template <typename T, int MM, bool GEN>
 static kc_status group_launch(const GroupArgs<T>& a, cudaStream_t s) {
-    const size_t smem = sizeof(double) * (MM * (MM + 1) / 2 + MM) + sizeof(T) * MM * MM + 16 + 16 +
+    const size_t smem = sizeof(double) * (MM * (MM + 1) / 2 + MM) + sizeof(T) * (MM * MM + MM) + 16 + 16 +
                         sizeof(unsigned long long) * ((size_t)1 << a.hbits) + sizeof(T) * (size_t)a.pmax * MM;
     auto kfn = ichol_group_k<T, MM, GEN>;
     KC_TRY(allow_dynamic_smem(kfn));

@@ -23,6 +23,7 @@
 // band points, so the dominance search uses a grid of band points with cell
 // size sqrt(vmax).  The updates scan a fixed fine grid of all points.
 // Finally the points are sorted by (v descending, index ascending).
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
@@ -203,13 +204,13 @@ __global__ void ord_dominance_k(Grid gb, const int32_t* __restrict__ bsorted, co
     if (dom) sel[atomicAdd(nsel, 1ULL)] = q;
 }
 
-// ---- greedy steps for the coarsest points: one launch selects the argmax of
-// the previous launch's per-block candidates and pushes it to every point.
+// ---- greedy steps for the coarsest points: each step selects the argmax of
+// the previous step's per-block candidates and pushes it to every point.
 constexpr int GREEDY_BLOCKS_PER_SM = 4;
 #ifndef KC_GREEDY_STEPS
 #define KC_GREEDY_STEPS 256
 #endif
-constexpr int64_t GREEDY_STEPS = KC_GREEDY_STEPS;  // coarsest points selected one per launch
+constexpr int64_t GREEDY_STEPS = KC_GREEDY_STEPS;  // coarsest points selected one at a time
 
 // Keys compare on the bit patterns of the squared distances: for v >= 0
 // (and +inf) IEEE doubles order like their bits as integers, and integer
@@ -253,55 +254,107 @@ __device__ void block_best(double v, int id, int g, double* sv, int* si, int* sg
     }
 }
 
-__global__ void ord_greedy_k(const double* __restrict__ xg, int d, const int32_t* __restrict__ idg,
-                             double* __restrict__ v2, int* __restrict__ stat, int64_t N,
-                             const double* __restrict__ pv_in, const int* __restrict__ pi_in,
-                             const int* __restrict__ pg_in, int nin, double* __restrict__ pv_out,
-                             int* __restrict__ pi_out, int* __restrict__ pg_out, int apply,
-                             const float* __restrict__ xgf, float delta) {
+// A grid-wide barrier for a cooperative launch (every block resident): the
+// last block to arrive resets the count and advances the generation; the
+// others poll the generation with backoff, at most `limit` cycles, after
+// which (or when another block has failed) the status word is set and false
+// returned.
+__device__ bool grid_barrier(unsigned* count, unsigned* gen, int* status, long long limit) {
+    __shared__ int ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        ok = 1;
+        const unsigned g = ld_acquire_u32(gen);
+        fence_acq_rel_gpu();  // this block's writes before its arrival
+        if (atomicAdd(count, 1u) == gridDim.x - 1) {
+            *count = 0u;
+            fence_acq_rel_gpu();
+            red_release_add_u32(gen, 1u);
+        } else {
+            const long long t0 = clock64();
+            unsigned ns = 32;
+            while (ld_acquire_u32(gen) == g) {
+                if (clock64() - t0 > limit || ld_volatile_s32(status) != 0) {
+                    atomicCAS(status, 0, DEV_TIMEOUT);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(ns);
+                if (ns < 256) ns <<= 1;
+            }
+        }
+        fence_acq_rel_gpu();  // acquire: the other blocks' writes
+    }
+    __syncthreads();
+    return ok != 0;
+}
+
+// All greedy steps in one cooperative launch: phase 0 leaves every block's
+// candidate (no winner yet); phase k >= 1 takes the winner of phase k-1's
+// candidates (every block computes the same), marks it, pushes it to the
+// block's points and leaves the block's new candidate.  The candidates
+// alternate between two buffers; a grid barrier separates the phases.
+__global__ void ord_greedy_loop_k(const double* __restrict__ xg, int d, const int32_t* __restrict__ idg,
+                                  double* __restrict__ v2, int* __restrict__ stat, int64_t N, int64_t steps,
+                                  double* pv0, int* pi0, int* pg0, double* pv1, int* pi1, int* pg1,
+                                  const float* __restrict__ xgf, float delta, unsigned* bar, int* status,
+                                  long long limit) {
     __shared__ double sv[32];
     __shared__ int si[32], sg[32];
     __shared__ double s_wv;
     __shared__ int s_wi, s_wg;
-    // winner of the previous candidates (every block computes the same)
-    {
-        double v = 0;
-        int i = 0, g = -1;
-        if (apply)
-            for (int b = threadIdx.x; b < nin; b += blockDim.x)
-                if (pg_in[b] >= 0 && (g < 0 || key_above(pv_in[b], pi_in[b], v, i))) {
-                    v = pv_in[b];
-                    i = pi_in[b];
-                    g = pg_in[b];
+    const int nin = gridDim.x;
+    for (int64_t k = 0; k <= steps; ++k) {
+        const double* pv_in = (k & 1) ? pv0 : pv1;
+        const int* pi_in = (k & 1) ? pi0 : pi1;
+        const int* pg_in = (k & 1) ? pg0 : pg1;
+        double* pv_out = (k & 1) ? pv1 : pv0;
+        int* pi_out = (k & 1) ? pi1 : pi0;
+        int* pg_out = (k & 1) ? pg1 : pg0;
+        {
+            double v = 0;
+            int i = 0, g = -1;
+            if (k > 0)
+                for (int b = threadIdx.x; b < nin; b += blockDim.x) {
+                    const int gb = __ldcg(&pg_in[b]);
+                    const double vb = __ldcg(&pv_in[b]);
+                    const int ib = __ldcg(&pi_in[b]);
+                    if (gb >= 0 && (g < 0 || key_above(vb, ib, v, i))) {
+                        v = vb;
+                        i = ib;
+                        g = gb;
+                    }
                 }
-        block_best(v, i, g, sv, si, sg, &s_wv, &s_wi, &s_wg);
-    }
-    __syncthreads();
-    const int w = s_wg;
-    if (w >= 0 && blockIdx.x == 0 && threadIdx.x == 0) stat[w] = 1;  // v2[w] keeps its final value l^2
-    double bv = 0;
-    int bi = 0, bg = -1;
-    const double* xw = w >= 0 ? xg + (int64_t)w * d : nullptr;
-    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < N; q += (int64_t)gridDim.x * blockDim.x) {
-        if (q == w || stat[q] != 0) continue;
-        double vq = v2[q];
-        if (w >= 0 &&
-            !(xgf && screen_f32(xgf + q * d, xgf + (int64_t)w * d, d, sqrtf((float)vq), delta) == 0)) {
-            const double dd = dist2_exact(xg + q * d, xw, d);
-            if (dd < vq) {
-                vq = dd;
-                v2[q] = dd;
+            block_best(v, i, g, sv, si, sg, &s_wv, &s_wi, &s_wg);
+        }
+        __syncthreads();
+        const int w = s_wg;
+        if (w >= 0 && blockIdx.x == 0 && threadIdx.x == 0) stat[w] = 1;  // v2[w] keeps its final value l^2
+        double bv = 0;
+        int bi = 0, bg = -1;
+        const double* xw = w >= 0 ? xg + (int64_t)w * d : nullptr;
+        for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < N; q += (int64_t)gridDim.x * blockDim.x) {
+            if (q == w || __ldcg(&stat[q]) != 0) continue;
+            double vq = v2[q];
+            if (w >= 0 &&
+                !(xgf && screen_f32(xgf + q * d, xgf + (int64_t)w * d, d, sqrtf((float)vq), delta) == 0)) {
+                const double dd = dist2_exact(xg + q * d, xw, d);
+                if (dd < vq) {
+                    vq = dd;
+                    v2[q] = dd;
+                }
+            }
+            const int iq = idg[q];
+            if (bg < 0 || key_above(vq, iq, bv, bi)) {
+                bv = vq;
+                bi = iq;
+                bg = (int)q;
             }
         }
-        const int iq = idg[q];
-        if (bg < 0 || key_above(vq, iq, bv, bi)) {
-            bv = vq;
-            bi = iq;
-            bg = (int)q;
-        }
+        __syncthreads();  // sv/si/sg are reused
+        block_best(bv, bi, bg, sv, si, sg, &pv_out[blockIdx.x], &pi_out[blockIdx.x], &pg_out[blockIdx.x]);
+        if (k < steps && !grid_barrier(bar, bar + 1, status, limit)) return;
     }
-    __syncthreads();  // sv/si/sg are reused
-    block_best(bv, bi, bg, sv, si, sg, &pv_out[blockIdx.x], &pi_out[blockIdx.x], &pg_out[blockIdx.x]);
 }
 
 __global__ void ord_mark_k(const int32_t* __restrict__ sel, int64_t ns, int* __restrict__ stat) {
@@ -441,11 +494,15 @@ kc_status order_impl(const double* x, int64_t N, int d, int32_t* perm, double* l
     item_sel = nullptr;
     const int sms = sm_count();
 
-    // Greedy phase: the coarsest points are selected one per launch (each
-    // launch updates every point), because while few points are selected the
-    // update balls cover the whole cloud and the band rounds would be quadratic.
+    // Greedy phase: the coarsest points are selected one at a time (every
+    // step updates every point), because while few points are selected the
+    // update balls cover the whole cloud and the band rounds would be
+    // quadratic.  All steps run in one cooperative launch with a grid barrier
+    // between them.
     {
-        const int nblk = sms * GREEDY_BLOCKS_PER_SM;
+        int per_sm = 0;
+        KC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ord_greedy_loop_k, 256, 0));
+        const int nblk = sms * std::max(1, std::min(per_sm, GREEDY_BLOCKS_PER_SM));
         double* pv[2];
         int *pi[2], *pg[2];
         for (int k = 0; k < 2; ++k) {
@@ -453,15 +510,26 @@ kc_status order_impl(const double* x, int64_t N, int d, int32_t* perm, double* l
             KC_TRY(A.get(&pi[k], nblk));
             KC_TRY(A.get(&pg[k], nblk));
         }
-        ::kc::note_launch(), ord_greedy_k<<<nblk, 256, 0, s>>>(xg, d, idg, v2, stat, N, nullptr, nullptr, nullptr, 0,
-                                                              pv[0], pi[0], pg[0], 0, xgf, delta);
-        const int64_t steps = N - 1 < GREEDY_STEPS ? N - 1 : GREEDY_STEPS;
-        for (int64_t k = 0; k < steps; ++k) {
-            const int a = (int)(k & 1), b = a ^ 1;
-            ::kc::note_launch(), ord_greedy_k<<<nblk, 256, 0, s>>>(xg, d, idg, v2, stat, N, pv[a], pi[a], pg[a], nblk,
-                                                                  pv[b], pi[b], pg[b], 1, xgf, delta);
-        }
-        KC_CUDA(cudaGetLastError());
+        unsigned* bar;
+        int* gst;
+        KC_TRY(A.get(&bar, 2));
+        KC_TRY(A.get(&gst, 1));
+        KC_CUDA(cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), s));
+        KC_CUDA(cudaMemsetAsync(gst, 0, sizeof(int), s));
+        int64_t steps = N - 1 < GREEDY_STEPS ? N - 1 : GREEDY_STEPS;
+        const double* a_xg = xg;
+        const int32_t* a_idg = idg;
+        const float* a_xgf = xgf;
+        long long limit = 4000000000LL;
+        void* args[] = {(void*)&a_xg, (void*)&d, (void*)&a_idg, (void*)&v2, (void*)&stat, (void*)&N, (void*)&steps,
+                        (void*)&pv[0], (void*)&pi[0], (void*)&pg[0], (void*)&pv[1], (void*)&pi[1], (void*)&pg[1],
+                        (void*)&a_xgf, (void*)&delta, (void*)&bar, (void*)&gst, (void*)&limit};
+        ::kc::note_launch();
+        KC_CUDA(cudaLaunchCooperativeKernel((const void*)ord_greedy_loop_k, dim3(nblk), dim3(256), args, 0, s));
+        int hst = 0;
+        KC_CUDA(cudaMemcpyAsync(&hst, gst, sizeof(int), cudaMemcpyDeviceToHost, s));
+        KC_CUDA(cudaStreamSynchronize(s));
+        if (hst != 0) return fail(KC_ETIMEOUT, "ordering: a grid barrier of the greedy phase ran out");
     }
     int rounds = 0;
     const bool stats = getenv("KC_ORDER_STATS") != nullptr;

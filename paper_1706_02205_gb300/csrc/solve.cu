@@ -36,6 +36,21 @@
 
 namespace kc {
 
+// Right-hand sides a lane of the FP32-form kernels keeps (an entry's NR are
+// split over NR / KC_SOLVE_NRL lanes), and the resident 256-thread CTAs per
+// SM their register budget is cut for.
+#ifndef KC_SOLVE_NRL
+#define KC_SOLVE_NRL 8
+#endif
+#ifndef KC_SOLVE_MINB
+#define KC_SOLVE_MINB 3
+#endif
+
+// Longest back-off (ns) between two polls of a readiness flag.
+#ifndef KC_SOLVE_BACKOFF_MAX
+#define KC_SOLVE_BACKOFF_MAX 512
+#endif
+
 template <typename T>
 struct SolveArgs {
     int64_t N;
@@ -78,7 +93,7 @@ __device__ __forceinline__ bool spin_flag(const int* f, const int* status, long 
     while (ld_relaxed_s32(f) == 0) {
         if (clock64() - t0 > limit || ld_volatile_s32(status) != 0) return false;
         __nanosleep(ns);  // back off so waiting warps do not flood L2 with polls
-        if (ns < 512) ns <<= 1;
+        if (ns < KC_SOLVE_BACKOFF_MAX) ns <<= 1;
     }
     return true;
 }
@@ -181,6 +196,20 @@ __device__ __forceinline__ void gather_fma(const double* v, const int (&k)[D], c
     }
 }
 
+// Publish a solved point: the warp's writes of its values, then its ready
+// flag with release semantics (KC_SOLVE_PUB_FENCE: with a fence of every lane
+// before the warp barrier as well).
+#ifndef KC_SOLVE_PUB_FENCE
+#define KC_SOLVE_PUB_FENCE 1
+#endif
+__device__ __forceinline__ void publish_ready(int* f, int lane) {
+#if KC_SOLVE_PUB_FENCE
+    fence_acq_rel_gpu();
+#endif
+    __syncwarp();
+    if (lane == 0) st_release_s32(f, 1);
+}
+
 // Sum over cnt slots of NR doubles (slot p0, p0 + stride, ...) in a fixed
 // order: lane l takes right-hand side l % NR and every (32 / NR)-th slot from
 // l / NR on; the lanes of one right-hand side then add their sums by a fixed
@@ -271,9 +300,7 @@ __global__ void __launch_bounds__(256) fwd_solve_k(SolveArgs<T> A) {
             if (!(dj > 0.0)) dj = A.diag_fallback;
             A.y[(int64_t)j * NR + r] = (A.b[(int64_t)j * NR + r] - s) / dj;
         }
-        fence_acq_rel_gpu();
-        __syncwarp();
-        if (lane == 0) st_release_s32(&A.ready[j], 1);
+        publish_ready(&A.ready[j], lane);
     }
 }
 
@@ -333,9 +360,7 @@ __global__ void __launch_bounds__(256) bwd_solve_k(SolveArgs<T> A) {
                 if (!(di > 0.0)) di = A.diag_fallback;
                 A.x[(int64_t)i * NR + r] = (A.y[(int64_t)i * NR + r] - s) / di;
             }
-            fence_acq_rel_gpu();
-            __syncwarp();
-            if (lane == 0) st_release_s32(&A.ready[i], 1);
+            publish_ready(&A.ready[i], lane);
         }
     }
 }
@@ -371,7 +396,7 @@ __device__ __forceinline__ double value_of(float2 p) { return (double)p.x + (dou
 // registers of one lane per entry at NR = 16, hence twice the resident warps.
 template <int NR>
 struct PairLayout {
-    static constexpr int NRL = NR > 8 ? 8 : NR;  // right-hand sides per lane
+    static constexpr int NRL = NR > KC_SOLVE_NRL ? KC_SOLVE_NRL : NR;  // right-hand sides per lane
     static constexpr int P = NR / NRL;           // lanes per entry (1 or 2)
     static constexpr int SLOTS = 32 / P;         // entries per warp and round
     static constexpr int L = NRL == 1 ? 0 : NRL == 2 ? 1 : NRL == 4 ? 2 : 3;  // halving levels
@@ -460,7 +485,7 @@ __device__ __forceinline__ void gather_pair_add(const float2* v, const int (&k)[
 }
 
 template <int NR>
-__global__ void __launch_bounds__(256, 3) fwd_solve_pair_k(SolveArgs<float> A) {
+__global__ void __launch_bounds__(256, KC_SOLVE_MINB) fwd_solve_pair_k(SolveArgs<float> A) {
     using PL = PairLayout<NR>;
     constexpr int D = PL::NRL >= 8 ? 6 : 8;  // entries per lane and round (within 80 registers)
     const int lane = lane_id();
@@ -500,14 +525,12 @@ __global__ void __launch_bounds__(256, 3) fwd_solve_pair_k(SolveArgs<float> A) {
             if (!(dj > 0.0)) dj = A.diag_fallback;
             A.yf[(int64_t)j * NR + r] = pair_of((A.b[(int64_t)j * NR + r] - sum) / dj);
         }
-        fence_acq_rel_gpu();
-        __syncwarp();
-        if (lane == 0) st_release_s32(&A.ready[j], 1);
+        publish_ready(&A.ready[j], lane);
     }
 }
 
 template <int NR>
-__global__ void __launch_bounds__(256, 3) bwd_solve_pair_k(SolveArgs<float> A) {
+__global__ void __launch_bounds__(256, KC_SOLVE_MINB) bwd_solve_pair_k(SolveArgs<float> A) {
     using PL = PairLayout<NR>;
     constexpr int D = 4;
     const int lane = lane_id();
@@ -563,9 +586,7 @@ __global__ void __launch_bounds__(256, 3) bwd_solve_pair_k(SolveArgs<float> A) {
                 A.xf[(int64_t)i * NR + r] = pair_of(xi);
                 A.x[(int64_t)i * NR + r] = xi;
             }
-            fence_acq_rel_gpu();
-            __syncwarp();
-            if (lane == 0) st_release_s32(&A.ready[i], 1);
+            publish_ready(&A.ready[i], lane);
         }
     }
 }
