@@ -7,8 +7,11 @@ Workload (default): N = 2^20 points on a 1024 x 1024 jittered grid in [0,1]^2
 One step = maximin ordering -> pattern S_rho -> schedule -> ICHOL(0) in the
 FP32 form -> solve L L^T x = b for the 16 right-hand sides, all on the GPU
 with inputs already resident.  The FP64 factor (+ solve) is timed on the same
-pattern for comparison.  Metric: nnz(L) per second of a whole step (and of
-the factor alone, the paper's t_ICHOL).
+pattern for comparison.
+Metric: nnz(L) per second of a whole step (and of the factor kernel, the
+paper's t_ICHOL).  The default line also carries the rho = 2 and 5 patterns,
+the sampled error estimator E of both factors, the supernodal block
+factorisation, a refined solve to 1e-10 and a serving run.
 
   python bench.py [--gpus N --steps K --warmup W] [--impl reference]
 
@@ -270,6 +273,7 @@ def run_ours(args, rank, world):
         return None
     hbm, peak_kind = peaks()
     bop = bytes_op(rowptr_h, N, d, 4)
+    ns = 1 << max(0, (args.nrhs - 1).bit_length())
     fk = statistics.mean(fk_ms)
     achieved = bop / (fk * 1e-3) / 1e9
     value = world * nnz * args.steps / (tot_ms * 1e-3)
@@ -308,9 +312,8 @@ def run_ours(args, rank, world):
         "gpu_launches": launches,
         "clocks": clocks,
     }
-    # the triangular solves: compulsory bytes (pattern and L read once per
-    # direction, the right-hand sides in and out) over the solve phase
-    ns = 1 << max(0, (args.nrhs - 1).bit_length())
+    # the triangular solves: compulsory bytes (pattern and L read once
+    # per direction, the right-hand sides in and out) over their time
     solve_bytes = (nnz * 8 + (N + 1) * 8) + (nnz * 16 + (N + 1) * 8) + 4 * N * ns * 8 + 2 * N * args.nrhs * 8
     solve_ms = statistics.mean(phase["solve"])
     line["solve_roofline"] = {"bound": "latency (dependency depth x row latency)", "algorithmic_bytes": solve_bytes,
@@ -319,6 +322,8 @@ def run_ours(args, rank, world):
                               "kernels": "fwd_solve_pair_k<16> + bwd_solve_pair_k<16> + permutations"}
     line["rho_sweep"] = rho_sweep
     line["accuracy_E"] = accuracy
+    if args.supernodal_leg:
+        line["supernodal"] = supernodal_leg(args, r["l"], xo, pat, kern)
     if args.refine_side > 0:
         line["refine_to_1e-10"] = run_refine(args)
     if args.serve_leg:
@@ -331,6 +336,39 @@ def run_ours(args, rank, world):
 
 
 # ------------------------------------------------ other workloads (ours)
+
+def supernodal_leg(args, l, xo, pat0, kern):
+    """The supernodal multicolour ordering and pattern built from the headline
+    step's maximin order and pattern, and the block factorisation on it (both
+    forms) beside the column-task kernel on the same pattern; kernel times
+    from CUDA events, median of the timed runs after one warm-up."""
+    import torch
+
+    from paper_1706_02205_gb300 import kchol as kc
+    stream = torch.cuda.current_stream()
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    e[0].record(stream)
+    sn = kc.supernodal(xo, l, args.rho, pat0, with_schedule=False)
+    e[1].record(stream)
+    spat = kc.schedule(sn["rowptr"], sn["col"], sn["x_new"])
+    e[2].record(stream)
+    torch.cuda.synchronize()
+    out = {"construction_ms": e[0].elapsed_time(e[1]), "schedule_ms": e[1].elapsed_time(e[2]), "nnz": spat.nnz,
+           "depth": spat.depth}
+    xn = sn["x_new"]
+    for name, fn, pr in (("blocked_fp32_form", kc.factor_blocked, kc.FP32_FORM),
+                         ("blocked_fp64", kc.factor_blocked, kc.FP64),
+                         ("column_fp32_form", kc.factor, kc.FP32_FORM)):
+        ks = []
+        for it in range(1 + max(1, args.steps // 2)):
+            _, _, zp = fn(spat, xn, kern, pr)
+            torch.cuda.synchronize()
+            if it >= 1:
+                ks.append(kc.last_factor_kernel_ms())
+        km = statistics.median(ks)
+        out[name] = {"kernel_ms": km, "kernel_nnz_per_s": spat.nnz / (km * 1e-3), "zero_pivots": zp}
+    return out
+
 
 # DRAM traffic of the FP32-form factor kernel per algorithmic byte, from the ncu capture of the factor
 # on the 512x512 jittered grid (dram read + write = 27.490 GB for
@@ -849,6 +887,7 @@ def main():
     ap.add_argument("--other-rho", type=float, nargs="*", default=[2.0, 5.0],
                     help="patterns of the configuration also factored (kernels timed)")
     ap.add_argument("--no-serve-leg", dest="serve_leg", action="store_false")
+    ap.add_argument("--no-supernodal-leg", dest="supernodal_leg", action="store_false")
     ap.add_argument("--e-reps", type=int, default=50, help="repetitions of the sampled error estimator")
     ap.add_argument("--slots", type=int, default=4)
     ap.add_argument("--serve-n-max", type=int, default=1_000_000)

@@ -304,6 +304,11 @@ __device__ __forceinline__ int lanes_per_row(int lanes) {
     return lanes > 0 ? lanes : (int)(32 / sizeof(T));
 }
 
+// Accumulators per lane in the merge rounds (1 or 2).
+#ifndef KC_FACTOR_ACCS
+#define KC_FACTOR_ACCS 1
+#endif
+
 // Merge of the prefix [es, be) of row j, read from global memory, against
 // row i: U (col, val) pairs per lane in flight; the ragged end is masked.
 template <typename T, int U>
@@ -321,11 +326,25 @@ __device__ __forceinline__ void merge_global(const FactorArgs<T>& A, const RowTa
             for (int u = 0; u < U; ++u) k[u] = __ldg(cp + t + u * G);
 #pragma unroll
             for (int u = 0; u < U; ++u) wv[u] = ldcg(vp + t + u * G);
+#if KC_FACTOR_ACCS == 2
+            // two interleaved accumulators: half the dependent chain per lane
+            Acc<T> acc2;
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                T hv;
+                if (tab.find(k[u], hv)) {
+                    if (u & 1) acc2.add(wv[u], hv);
+                    else acc.add(wv[u], hv);
+                }
+            }
+            acc.merge(acc2);
+#else
 #pragma unroll
             for (int u = 0; u < U; ++u) {
                 T hv;
                 if (tab.find(k[u], hv)) acc.add(wv[u], hv);
             }
+#endif
         }
         if (t < n) {  // the ragged end: one masked round
             int k[U];

@@ -288,15 +288,16 @@ __global__ void __launch_bounds__(BF_THREADS, KC_BLOCK_MINB) ichol_group_k(Group
                 }
                 const bool zero = !(p > 0.0);
                 const double Lss = zero ? 0.0 : sqrt(p);
+                const double rinv = zero ? 0.0 : 1.0 / Lss;  // one FP64 division per column
                 if (lane > s && lane < m) {
                     double v = D[lane * (lane + 1) / 2 + s];
                     for (int u = 0; u < s; ++u) v -= (double)Laa[lane * MM + u] * (double)Laa[s * MM + u];
-                    Laa[lane * MM + s] = zero ? (T)0 : (T)(v / Lss);
+                    Laa[lane * MM + s] = (T)(v * rinv);
                 }
                 if (lane == 0) {
                     Laa[s * MM + s] = (T)Lss;
                     Ld[s] = Lss;
-                    Linv[s] = zero ? (T)0 : (T)(1.0 / Lss);
+                    Linv[s] = (T)rinv;
                 }
                 __syncwarp();
             }

@@ -19,7 +19,7 @@
 // p its value is already below d2(p,q).
 //
 // Rounds run in bands of keys: with vmax the largest undecided v, the band
-// holds the undecided points with v >= vmax/4; only band points can dominate
+// holds the undecided points with v >= vmax/4 (KC_ORDER_BAND); only band points can dominate
 // band points, so the dominance search uses a grid of band points with cell
 // size sqrt(vmax).  The updates scan a fixed fine grid of all points.
 // Finally the points are sorted by (v descending, index ascending).
@@ -211,6 +211,10 @@ constexpr int GREEDY_BLOCKS_PER_SM = 4;
 #define KC_GREEDY_STEPS 256
 #endif
 constexpr int64_t GREEDY_STEPS = KC_GREEDY_STEPS;  // coarsest points selected one at a time
+// A band holds the undecided points with v >= KC_ORDER_BAND * (largest v).
+#ifndef KC_ORDER_BAND
+#define KC_ORDER_BAND 0.25
+#endif
 
 // Keys compare on the bit patterns of the squared distances: for v >= 0
 // (and +inf) IEEE doubles order like their bits as integers, and integer
@@ -542,7 +546,7 @@ kc_status order_impl(const double* x, int64_t N, int d, int32_t* perm, double* l
         if (h[1] == 0) break;
         double vmax;
         memcpy(&vmax, &h[0], sizeof(double));
-        const double T = vmax * 0.25;
+        const double T = vmax * KC_ORDER_BAND;
         KC_CUDA(cudaMemsetAsync(ctr + 2, 0, sizeof(unsigned long long), s));
         ::kc::note_launch(), ord_band_k<<<blocks_for(N, 256), 256, 0, s>>>(v2, stat, N, T, blist, ctr + 2);
         unsigned long long hnb = 0;

@@ -32,6 +32,7 @@
 // relative to the sums' magnitudes, where FP64 gives 2^-53.
 #include <type_traits>
 
+#include "pairs.cuh"
 #include "solver.cuh"
 
 namespace kc {
@@ -98,8 +99,23 @@ __device__ __forceinline__ bool spin_flag(const int* f, const int* status, long 
     return true;
 }
 
-// The NR values of point k (16-byte loads; values written during the launch,
-// so through L2).
+// Loads of a point's vector values, which other SMs write during the launch.
+// When one point's values fill whole 128-byte lines by themselves (LINE =
+// bytes per point = 128, i.e. 16 right-hand sides), no SM can read a line of
+// point k before k's ready flag is set, after its values were written, so the
+// line may be cached in L1 (KC_SOLVE_GATHER_L1); coarse points are gathered by
+// nearly every row.  Otherwise lines are shared by neighbouring points and the
+// loads go to L2.
+#ifndef KC_SOLVE_GATHER_L1
+#define KC_SOLVE_GATHER_L1 1
+#endif
+template <int LINE, typename V>
+__device__ __forceinline__ V ld_vec(const V* p) {
+    if constexpr (KC_SOLVE_GATHER_L1 && LINE == 128) return __ldca(p);
+    else return __ldcg(p);
+}
+
+// The NR values of point k (16-byte loads).
 template <int NR>
 __device__ __forceinline__ void gather(const double* v, int k, double* out) {
     if constexpr (NR == 1) {
@@ -108,7 +124,7 @@ __device__ __forceinline__ void gather(const double* v, int k, double* out) {
         const double2* p = (const double2*)(v + (int64_t)k * NR);
 #pragma unroll
         for (int q = 0; q < NR / 2; ++q) {
-            const double2 w = __ldcg(p + q);
+            const double2 w = ld_vec<NR * 8>(p + q);
             out[2 * q] = w.x;
             out[2 * q + 1] = w.y;
         }
@@ -366,30 +382,6 @@ __global__ void __launch_bounds__(256) bwd_solve_k(SolveArgs<T> A) {
 }
 
 // ------------------------------------------------ FP32 form: float pairs
-// (s, c) += w (hi + lo): TwoProduct of w hi, TwoSum into s, small terms into c.
-// The _rn intrinsics keep every rounding where the error-free steps need it.
-__device__ __forceinline__ void pair_add(float& s, float& c, float w, float hi, float lo) {
-    const float p = __fmul_rn(w, hi);
-    const float e = fmaf(w, hi, -p);
-    const float ns = __fadd_rn(s, p);
-    const float z = __fsub_rn(ns, s);
-    const float er = __fadd_rn(__fsub_rn(s, __fsub_rn(ns, z)), __fsub_rn(p, z));
-    s = ns;
-    c = fmaf(w, lo, __fadd_rn(c, __fadd_rn(er, e)));
-}
-__device__ __forceinline__ void pair_merge(float& s, float& c, float s2, float c2) {
-    const float t = __fadd_rn(s, s2);
-    const float z = __fsub_rn(t, s);
-    const float er = __fadd_rn(__fsub_rn(s, __fsub_rn(t, z)), __fsub_rn(s2, z));
-    s = t;
-    c = __fadd_rn(c, __fadd_rn(c2, er));
-}
-__device__ __forceinline__ float2 pair_of(double v) {
-    const float hi = __double2float_rn(v);
-    return make_float2(hi, __double2float_rn(v - (double)hi));
-}
-__device__ __forceinline__ double value_of(float2 p) { return (double)p.x + (double)p.y; }
-
 // Lane layout of the pair kernels: an entry's NR right-hand sides are split
 // over P lanes of NRL each (NR = 16: two lanes of 8; else one lane), so a lane
 // keeps NRL compensated sums and gathers NRL pairs per entry: half the
@@ -468,7 +460,7 @@ __device__ __forceinline__ void gather_pair_add(const float2* v, const int (&k)[
                 } else {
 #pragma unroll
                     for (int m = 0; m < NRL / 2; ++m) {
-                        const float4 x = __ldcg((const float4*)p + m);
+                        const float4 x = ld_vec<NR * 8>((const float4*)p + m);
                         hi[q][2 * m] = x.x;
                         lo[q][2 * m] = x.y;
                         hi[q][2 * m + 1] = x.z;
@@ -657,15 +649,32 @@ static kc_status solve_launch(Solver& S, SolveArgs<T> a, int nrhs, cudaStream_t 
     return KC_OK;
 }
 
+template <typename T>
+static SolveArgs<T> solve_args(Solver& S, const T* val, const double* diag, double diag_fallback, const double* rhs,
+                               double* z);
+
 // z = (L L^T)^{-1} rhs, point-major with stride nrhs (a power of two <= 16),
 // positions order.  Does not synchronise; the status word is checked by
 // solver_check.
 template <typename T>
 kc_status solver_apply(Solver& S, const T* val, const double* diag, double diag_fallback, const double* rhs,
                        double* z, int nrhs, cudaStream_t s) {
-    const kc_pattern* P = S.P;
     if (nrhs < 1 || nrhs > 16 || (nrhs & (nrhs - 1)) || nrhs > S.nrhs_cap)
         return fail(KC_EINVAL, "internal: solver stride must be a power of two <= 16");
+    SolveArgs<T> a = solve_args<T>(S, val, diag, diag_fallback, rhs, z);
+    switch (nrhs) {
+        case 1: return solve_launch<T, 1>(S, a, nrhs, s);
+        case 2: return solve_launch<T, 2>(S, a, nrhs, s);
+        case 4: return solve_launch<T, 4>(S, a, nrhs, s);
+        case 8: return solve_launch<T, 8>(S, a, nrhs, s);
+        default: return solve_launch<T, 16>(S, a, nrhs, s);
+    }
+}
+
+template <typename T>
+static SolveArgs<T> solve_args(Solver& S, const T* val, const double* diag, double diag_fallback, const double* rhs,
+                               double* z) {
+    const kc_pattern* P = S.P;
     SolveArgs<T> a;
     a.N = P->N;
     a.rowptr = P->rowptr;
@@ -691,13 +700,7 @@ kc_status solver_apply(Solver& S, const T* val, const double* diag, double diag_
     a.ready = S.ready;
     a.status = S.status;
     a.spin_limit = S.spin;
-    switch (nrhs) {
-        case 1: return solve_launch<T, 1>(S, a, nrhs, s);
-        case 2: return solve_launch<T, 2>(S, a, nrhs, s);
-        case 4: return solve_launch<T, 4>(S, a, nrhs, s);
-        case 8: return solve_launch<T, 8>(S, a, nrhs, s);
-        default: return solve_launch<T, 16>(S, a, nrhs, s);
-    }
+    return a;
 }
 template kc_status solver_apply<double>(Solver&, const double*, const double*, double, const double*, double*, int,
                                         cudaStream_t);
