@@ -109,7 +109,9 @@ typedef struct {
     int64_t spin_limit_cycles;     /* bound of every device wait; 0 -> ~4e9 cycles */
     int32_t rows_per_task;         /* rows of a column per task; 0 -> factor: about (nnz - N) / (depth x
                                       resident warps), a power of two in 16..128; backward solve: 128 */
-    int32_t ctas_per_sm;           /* persistent grid = SMs x this; 0 -> occupancy */
+    int32_t ctas_per_sm;           /* persistent grid = SMs x this; 0 -> occupancy; < 0 (factor) ->
+                                      occupancy + this (at least 1): leaves that many CTA slots per
+                                      SM to kernels on other streams (latency of concurrent solves) */
     int32_t warps_per_cta;         /* 0 -> the CTA size (8, 4, 2 or 1 warps) with the most resident warps */
     int32_t test_hold_column;      /* test hook: 0 = off; c+1 makes column c never signal
                                       ready, so a wait on it runs out (KC_ETIMEOUT) */

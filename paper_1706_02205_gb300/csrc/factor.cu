@@ -304,11 +304,6 @@ __device__ __forceinline__ int lanes_per_row(int lanes) {
     return lanes > 0 ? lanes : (int)(32 / sizeof(T));
 }
 
-// Accumulators per lane in the merge rounds (1 or 2).
-#ifndef KC_FACTOR_ACCS
-#define KC_FACTOR_ACCS 1
-#endif
-
 // Merge of the prefix [es, be) of row j, read from global memory, against
 // row i: U (col, val) pairs per lane in flight; the ragged end is masked.
 template <typename T, int U>
@@ -326,25 +321,11 @@ __device__ __forceinline__ void merge_global(const FactorArgs<T>& A, const RowTa
             for (int u = 0; u < U; ++u) k[u] = __ldg(cp + t + u * G);
 #pragma unroll
             for (int u = 0; u < U; ++u) wv[u] = ldcg(vp + t + u * G);
-#if KC_FACTOR_ACCS == 2
-            // two interleaved accumulators: half the dependent chain per lane
-            Acc<T> acc2;
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                T hv;
-                if (tab.find(k[u], hv)) {
-                    if (u & 1) acc2.add(wv[u], hv);
-                    else acc.add(wv[u], hv);
-                }
-            }
-            acc.merge(acc2);
-#else
 #pragma unroll
             for (int u = 0; u < U; ++u) {
                 T hv;
                 if (tab.find(k[u], hv)) acc.add(wv[u], hv);
             }
-#endif
         }
         if (t < n) {  // the ragged end: one masked round
             int k[U];
@@ -817,6 +798,7 @@ static kc_status launch_core(const FactorCore& F, T* val, double* diag, cudaStre
     const size_t smem = (size_t)warps * a.warp_smem;
     KC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, warps * 32, smem));
     if (F.ctas > 0 && F.ctas < per_sm) per_sm = F.ctas;
+    if (F.ctas < 0) per_sm = std::max(1, per_sm + F.ctas);  // leave -ctas CTA slots per SM to other streams
     if (per_sm < 1) return fail(KC_EINVAL, "factor: shared memory of one CTA exceeds the SM (stage_bytes too large?)");
     ::kc::note_launch(), done_init_k<<<blocks_for(F.P.N, 256), 256, 0, s>>>(F.P.colptr, F.P.rowptr, F.P.N, F.rpt,
                                                                            F.adaptive, F.done);
@@ -864,7 +846,7 @@ static kc_status apply_opts(FactorCore& F, const kc_opts* o) {
     F.warps_auto = !(o && o->warps_per_cta > 0);
     if (F.warps > 8) return fail(KC_EINVAL, "warps_per_cta must be <= 8");
     F.spin = (o && o->spin_limit_cycles > 0) ? o->spin_limit_cycles : 4000000000LL;
-    F.ctas = (o && o->ctas_per_sm > 0) ? o->ctas_per_sm : 0;
+    F.ctas = o ? o->ctas_per_sm : 0;
     F.hold = (o && o->test_hold_column > 0) ? o->test_hold_column - 1 : -1;
     F.lanes = 0;
     if (o && o->lanes_per_row > 0) {

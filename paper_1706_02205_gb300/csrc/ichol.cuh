@@ -19,12 +19,12 @@ struct Acc<double> {
     __device__ __forceinline__ void group_reduce(int G) {
         for (int o = G >> 1; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     }
-    __device__ __forceinline__ void merge(const Acc& o) { s += o.s; }
-    // (theta - sum) / L_ii, by the reciprocal formed once per column (the
-    // GB300's FP64 divisions are slow)
-    __device__ __forceinline__ double finish(double th, double, double inv) const { return (th - s) * inv; }
+    // (theta - sum) / L_ii, a correctly rounded division as Algorithm 2
+    // states it (a stored reciprocal moves ill-conditioned columns by more
+    // than the FP64 bar)
+    __device__ __forceinline__ double finish(double th, double Lii, double) const { return (th - s) / Lii; }
     __device__ __forceinline__ double total() const { return s; }
-    __device__ __forceinline__ static double recip(double Lii) { return 1.0 / Lii; }
+    __device__ __forceinline__ static double recip(double) { return 0.0; }  // finish divides
 };
 template <>
 struct Acc<float> {
@@ -51,14 +51,6 @@ struct Acc<float> {
             s = t;
             c = __fadd_rn(c, __fadd_rn(c2, e));
         }
-    }
-    // the sum of two compensated sums (TwoSum of the leading parts)
-    __device__ __forceinline__ void merge(const Acc& o) {
-        const float t = __fadd_rn(s, o.s);
-        const float z = __fsub_rn(t, s);
-        const float e = __fadd_rn(__fsub_rn(s, __fsub_rn(t, z)), __fsub_rn(o.s, z));
-        s = t;
-        c = __fadd_rn(c, __fadd_rn(o.c, e));
     }
     __device__ __forceinline__ float finish(float th, double, float inv) const {
         return __fmul_rn(__fsub_rn(__fsub_rn(th, s), c), inv);

@@ -146,7 +146,7 @@ def _kernel_of(req) -> kc.Kernel:
     return kc.Kernel(req.get("nu", SERVE_KERNEL["nu"]), req.get("ell", SERVE_KERNEL["ell"]))
 
 
-def factor_one(req, x_host: np.ndarray, b_host: np.ndarray, stream, prec=kc.FP32_FORM):
+def factor_one(req, x_host: np.ndarray, b_host: np.ndarray, stream, prec=kc.FP32_FORM, opts=None):
     """Order, pattern, schedule, factor and solve one point set on `stream`.
     Returns (solution on the host, Resident)."""
     with torch.cuda.stream(stream):
@@ -155,7 +155,7 @@ def factor_one(req, x_host: np.ndarray, b_host: np.ndarray, stream, prec=kc.FP32
         kern = _kernel_of(req)
         perm, l, xo = kc.order_points(x, stream=stream)
         pat = kc.build_pattern(xo, l, req["rho"], stream=stream)
-        val, diag, zp = kc.factor(pat, xo, kern, prec, stream=stream)
+        val, diag, zp = kc.factor(pat, xo, kern, prec, opts, stream=stream)
         xs = kc.solve(pat, prec, val, diag, kern, perm, b, stream=stream)
         out = xs.cpu()
         res = Resident(req["key"], x_host.shape[0], xo, perm, val, diag, kern, prec, pat.rowptr, pat.col, pat=pat)
@@ -163,7 +163,7 @@ def factor_one(req, x_host: np.ndarray, b_host: np.ndarray, stream, prec=kc.FP32
     return out.numpy(), res, {"nnz": pat.nnz, "zero_pivots": zp}
 
 
-def factor_group(reqs, xs_host, bs_host, stream, prec=kc.FP32_FORM):
+def factor_group(reqs, xs_host, bs_host, stream, prec=kc.FP32_FORM, opts=None):
     """Factor several small point sets in one persistent plan launch (their
     patterns concatenated block-diagonally) and solve them together.
     Returns per request (solution, Resident, info)."""
@@ -171,7 +171,7 @@ def factor_group(reqs, xs_host, bs_host, stream, prec=kc.FP32_FORM):
     with torch.cuda.stream(stream):
         xs = [torch.from_numpy(x).to("cuda", non_blocking=True) for x in xs_host]
         kerns = [_kernel_of(r) for r in reqs]
-        B = kb.BatchFactor(xs, kerns, reqs[0]["rho"], prec, n_streams=1, stream=stream)
+        B = kb.BatchFactor(xs, kerns, reqs[0]["rho"], prec, opts=opts, n_streams=1, stream=stream)
         zp = B.factor(stream=stream)
         nr = max(b.shape[0] for b in bs_host)
         bcat = np.zeros((nr, sum(B.Ns)))
@@ -203,7 +203,8 @@ def solve_resident(res: Resident, b_host: np.ndarray, stream):
 
 class Server:
     def __init__(self, max_inflight: int = 4, hbm_budget_bytes: int | None = None, prec=kc.FP32_FORM,
-                 keep_solutions: bool = False, group_n_max: int = 60_000, group_max: int = 32, solve_slots: int = 2):
+                 keep_solutions: bool = False, group_n_max: int = 60_000, group_max: int = 32, solve_slots: int = 2,
+                 headroom: int = 1):
         self.k = max_inflight
         self.solve_slots = solve_slots
         if hbm_budget_bytes is None:
@@ -214,7 +215,13 @@ class Server:
         self.keep = keep_solutions
         self.group_n_max = group_n_max
         self.group_max = group_max
-        self.streams = [torch.cuda.Stream() for _ in range(max_inflight + solve_slots)]
+        # the solve lanes' streams take their SM slots first whenever slots free up,
+        # and the persistent factor kernels leave `headroom` CTA slots per SM
+        # (kc_opts.ctas_per_sm < 0), so that a repeat solve does not wait for a
+        # running factorisation to end
+        self.streams = [torch.cuda.Stream() for _ in range(max_inflight)] + \
+                       [torch.cuda.Stream(priority=-1) for _ in range(solve_slots)]
+        self.factor_opts = kc.make_opts(ctas_per_sm=-headroom) if solve_slots > 0 and headroom > 0 else None
         self.cache = FactorCache()
         self.points = {}  # key -> (host points, the factor request) for refactoring after eviction
 
@@ -305,12 +312,13 @@ class Server:
                         infos[m] = {"nnz": job["res"].val.numel(), "cache": "hit"}
                         o += n
                 elif len(job["ids"]) == 1:
-                    x, res, info = factor_one(job["reqs"][0], job["xs"][0], job["bs"][0], st, self.prec)
+                    x, res, info = factor_one(job["reqs"][0], job["xs"][0], job["bs"][0], st, self.prec,
+                                              self.factor_opts)
                     sols[0] = x
                     infos[0] = dict(info, cache="miss" if job["refactor"] else "new", group=1)
                     job["new"] = [res]
                 else:
-                    outs, _ = factor_group(job["reqs"], job["xs"], job["bs"], st, self.prec)
+                    outs, _ = factor_group(job["reqs"], job["xs"], job["bs"], st, self.prec, self.factor_opts)
                     job["new"] = []
                     for m, (x, res, info) in enumerate(outs):
                         sols[m] = x
@@ -437,8 +445,11 @@ def summarize(records, wall_s):
     for typ in ("factor", "solve"):
         lt = np.array([r["latency_ms"] for r in records if r["type"] == typ])
         if lt.size:
+            wt = np.array([(r["t_admit"] - r["t_arrival"]) * 1e3 for r in records if r["type"] == typ])
+            sv = np.array([(r["t_done"] - r["t_admit"]) * 1e3 for r in records if r["type"] == typ])
             out[typ] = {"n": int(lt.size), "p50_ms": float(np.percentile(lt, 50)),
-                        "p99_ms": float(np.percentile(lt, 99))}
+                        "p99_ms": float(np.percentile(lt, 99)), "wait_p50_ms": float(np.percentile(wt, 50)),
+                        "service_p50_ms": float(np.percentile(sv, 50))}
     out["solve_cache_hits"] = sum(1 for r in records if r["type"] == "solve" and r["cache"] == "hit")
     out["refactors"] = sum(1 for r in records if r["cache"] == "miss")
     out["grouped_factor_requests"] = sum(1 for r in records if r["type"] == "factor" and (r["group"] or 1) > 1)

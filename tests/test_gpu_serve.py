@@ -139,3 +139,19 @@ def test_footprint_estimate_covers_measured_pattern():
                                    2 if r["kind"] == "swiss" else None)
         assert est >= 48 * info["nnz"]
         assert res.nbytes() < est
+
+
+def test_factor_headroom_gives_the_same_bits():
+    """A persistent factor that leaves CTA slots free (ctas_per_sm < 0, as the
+    server launches it next to its solve lanes) computes the same bits; a
+    request for more headroom than the SM has runs on one CTA per SM."""
+    reqs, pay = _reqs(1)
+    x = torch.from_numpy(pay[0][0]).cuda()
+    perm, l, xo = kc.order_points(x)
+    pat = kc.build_pattern(xo, l, 3.0)
+    kern = kc.Kernel(1.5, 0.1)
+    for prec in (kc.FP32_FORM, kc.FP64):
+        v0, d0, z0 = kc.factor(pat, xo, kern, prec)
+        for c in (-1, -64):
+            v1, d1, z1 = kc.factor(pat, xo, kern, prec, kc.make_opts(ctas_per_sm=c))
+            assert torch.equal(v0, v1) and torch.equal(d0, d1) and z0 == z1
