@@ -204,7 +204,7 @@ def solve_resident(res: Resident, b_host: np.ndarray, stream):
 class Server:
     def __init__(self, max_inflight: int = 4, hbm_budget_bytes: int | None = None, prec=kc.FP32_FORM,
                  keep_solutions: bool = False, group_n_max: int = 60_000, group_max: int = 32, solve_slots: int = 2,
-                 headroom: int = 1):
+                 headroom: int = 0):
         self.k = max_inflight
         self.solve_slots = solve_slots
         if hbm_budget_bytes is None:
