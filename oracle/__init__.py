@@ -315,6 +315,8 @@ def supernodal(x, rho):
     rowptr = np.zeros(N + 1, np.int64)
     cp = C.POINTER(C.c_int32)()
     nnz = lib().ko_supernodal(x, N, d, perm, l, float(rho), order, level, node, color, rowptr, C.byref(cp))
+    if nnz < 0:
+        raise MemoryError(f"oracle.supernodal: no memory for the dense {N} x {N} supernode set")
     try:
         col = np.ctypeslib.as_array(cp, shape=(nnz,)).copy() if nnz else np.zeros(0, np.int32)
     finally:

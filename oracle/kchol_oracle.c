@@ -588,6 +588,11 @@ i64 ko_supernodal(const double* x, i64 N, i32 d, const i32* perm, const double* 
     }
     /* supernode pattern as a dense N x N bit set over supernode indices */
     char* adj = (char*)calloc((size_t)(N * N), 1);
+    if (!adj) { /* too large for the dense set: report it instead of writing through NULL */
+        free(xo); free(lev); free(sup); free(node);
+        *col_out = NULL;
+        return -1;
+    }
     for (i64 a = 0; a < N; ++a)
         for (i64 b = 0; b <= a; ++b) {
             i32 kmin = lev[a] < lev[b] ? lev[a] : lev[b];

@@ -377,7 +377,9 @@ __device__ __forceinline__ void batch_rows(const FactorArgs<T>& A, const TaskCtx
 #define KC_FACTOR_MIN_BLOCKS 4
 #endif
 
-template <typename T, int U, int ENT>
+// GC > 0: lanes per row fixed at compile time (the default for the FP32 form:
+// the group loads' offsets become constants); 0: from A.lanes.
+template <typename T, int U, int ENT, int GC>
 __global__ void __launch_bounds__(256, U >= 16 ? 3 : KC_FACTOR_MIN_BLOCKS) ichol_persistent_k(FactorArgs<T> A) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = lane_id();
@@ -387,7 +389,7 @@ __global__ void __launch_bounds__(256, U >= 16 ? 3 : KC_FACTOR_MIN_BLOCKS) ichol
     TaskCtx<T> X;
     for (;;) {
         if (task_begin<T, ENT>(A, tab, lane, X) != 0) return;
-        const int G = lanes_per_row<T>(A.lanes);
+        const int G = GC > 0 ? GC : lanes_per_row<T>(A.lanes);
         const int ng = 32 / G, g = lane / G, sub = lane % G;
         const int rows = rows_of_task(A.rowptr, X.i, A.rpt, A.adaptive);
         const int64_t qs = A.colptr[X.i] + 1 + (int64_t)X.c * rows;
@@ -774,7 +776,9 @@ static kc_status launch_core(const FactorCore& F, T* val, double* diag, cudaStre
         warps = std::min(warps, optin / a.warp_smem);
         if (warps < 1) return fail(KC_EINVAL, "factor: stage_bytes too large for one warp's shared memory");
     }
-    auto kfn = ichol_persistent_k<T, U, ENT>;
+    auto kfn = ichol_persistent_k<T, U, ENT, 0>;
+    if constexpr (sizeof(T) == 4)
+        if (F.lanes == 0) kfn = ichol_persistent_k<T, U, ENT, 8>;  // lanes per row: 8, at compile time
     if constexpr (ENT == 0)
         if (bulk) kfn = ichol_bulk_k<T, U, 0>;
     int per_sm = 0;
