@@ -20,7 +20,10 @@
 // groups of G (one 32-byte sector of values per group load); a group owns one
 // row, each lane walks the row with stride G, loading U (col, val) pairs
 // ahead (the staging depth) so that enough loads are in flight to cover HBM
-// latency.  The task publishes by a release increment of done[i].
+// latency; in the FP32 form each lane also prefetches into L2 one sector of
+// the row its group takes next and one of its own row's second round, which
+// the merges would otherwise request only after the round before them.  The
+// task publishes by a release increment of done[i].
 //
 // A second form, on request, stages the row prefixes of a batch in shared
 // memory with bulk (TMA) copies into two buffers per warp completing on
@@ -348,6 +351,8 @@ __device__ __forceinline__ void merge_global(const FactorArgs<T>& A, const RowTa
     }
 }
 
+__device__ __forceinline__ void prefetch_l2(const void* p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
+
 // Row-j bookkeeping of the rows b0+lane of a batch: the slot of L_ji, the
 // start of row j, and Theta_ji (loads and exponentials overlap across lanes).
 template <typename T, int ENT>
@@ -406,6 +411,25 @@ __global__ void __launch_bounds__(256, U >= 16 ? 3 : KC_FACTOR_MIN_BLOCKS) ichol
                 const int64_t es = __shfl_sync(FULL, my_e0, src);
                 const int64_t be = __shfl_sync(FULL, my_b, src);  // L_ji lives at be; the prefix is [es, be)
                 const T th = __shfl_sync(FULL, my_th, src);
+                if constexpr (GC > 0) {
+                    // L2 prefetches that the merges below do not wait for: one sector per lane of the
+                    // group's row in the next round of rows (its first U*G entries), and of this row past
+                    // its first U*G entries (the second round, issued otherwise only after the first)
+                    constexpr int SEC = 32 / (int)sizeof(T);
+                    const int rn = r + ng;
+                    const bool pn = rn < nb && !X.zero;
+                    const int64_t esn = __shfl_sync(FULL, my_e0, pn ? rn : 0);
+                    const int64_t ben = __shfl_sync(FULL, my_b, pn ? rn : 0);
+                    const int64_t en = esn + sub * SEC, ec = es + U * G + sub * SEC;
+                    if (pn && en < ben) {
+                        prefetch_l2(A.col + en);
+                        prefetch_l2(A.val + en);
+                    }
+                    if (act && !X.zero && ec < be) {
+                        prefetch_l2(A.col + ec);
+                        prefetch_l2(A.val + ec);
+                    }
+                }
                 Acc<T> acc;
                 if (act && !X.zero) merge_global<T, U>(A, tab, X, es, be, sub, G, acc);
                 acc.group_reduce(G);
