@@ -128,8 +128,7 @@ def run_ours(args, rank, world):
         perm, l, xo = kc.order_points(x)
         if ev:
             ev[1].record(stream)
-        rowptr, nnz = kc.pattern_count(xo, l, args.rho)
-        col = kc.pattern_fill(xo, l, args.rho, rowptr, nnz)
+        rowptr, col = kc.pattern_rows(xo, l, args.rho)
         if ev:
             ev[2].record(stream)
         pat = kc.schedule(rowptr, col, xo)
@@ -556,8 +555,7 @@ def run_supernodal(args):
         ev[0].record(stream)
         perm0, l, xo = kc.order_points(x)
         ev[1].record(stream)
-        rowptr, nnz0 = kc.pattern_count(xo, l, args.rho)
-        col = kc.pattern_fill(xo, l, args.rho, rowptr, nnz0)
+        rowptr, col = kc.pattern_rows(xo, l, args.rho)
         ev[2].record(stream)
         pat0 = kc.schedule(rowptr, col, xo)
         ev[3].record(stream)
@@ -654,8 +652,7 @@ def run_cube3d(args):
         ev[0].record(stream)
         perm, l, xo = kc.order_points(x)
         ev[1].record(stream)
-        rowptr, nnz = kc.pattern_count(xo, l, 4.0)
-        col = kc.pattern_fill(xo, l, 4.0, rowptr, nnz)
+        rowptr, col = kc.pattern_rows(xo, l, 4.0)
         ev[2].record(stream)
         pat = kc.schedule(rowptr, col, xo)
         ev[3].record(stream)

@@ -133,8 +133,9 @@ const char* kc_last_error(void);
  * kc_kernel_eval, kc_l_matvec, kc_lt_matvec, kc_llt_matvec, kc_logdet,
  * kc_pattern_reverse, kc_gather_entries, kc_factor_given, kc_refine_sparse,
  * kc_supernodal_count, kc_supernodal_fill, kc_supernodal, kc_pattern_validate.
- * 4: kc_scratch_trim, kc_frob_error, kc_factor_blocked; scratch from a private pool per device. */
-#define KC_ABI_VERSION 4
+ * 4: kc_scratch_trim, kc_frob_error, kc_factor_blocked; scratch from a private pool per device.
+ * 5: kc_pattern_begin, kc_pattern_end, kc_pattern_abort; kc_opts.ctas_per_sm < 0. */
+#define KC_ABI_VERSION 5
 int32_t kc_abi_version(void);
 
 /* Number of kernels this library has launched in the process so far
@@ -169,6 +170,24 @@ kc_status kc_pattern_count(const double* x_ord, const double* l, int64_t N, int3
                            int32_t rule, int64_t* rowptr, int64_t* nnz_out, void* stream);
 kc_status kc_pattern_fill(const double* x_ord, const double* l, int64_t N, int32_t d, double rho,
                           int32_t rule, const int64_t* rowptr, int32_t* col, void* stream);
+
+/* The same pattern with one search instead of two: kc_pattern_begin runs the
+ * search once, fills rowptr (device int64[N+1]) and nnz_out (host) as
+ * kc_pattern_count does, and keeps the bucketing grid and one membership bit
+ * per candidate in scratch owned by *builder_out (synchronises).  x_ord, l and
+ * rowptr must stay valid and unchanged until the builder is released.
+ * kc_pattern_end writes col (device int32[nnz], ascending per row, diagonal
+ * last: the same array as kc_pattern_fill) from those bits on the stream
+ * given to kc_pattern_begin, synchronises, and releases the builder, whatever
+ * its status (col NULL: KC_EINVAL, released).  kc_pattern_abort releases a
+ * builder without filling (NULL: nothing).  On an error kc_pattern_begin
+ * leaves *builder_out NULL.  A builder is used by one thread at a time. */
+typedef struct kc_pattern_builder kc_pattern_builder;
+kc_status kc_pattern_begin(const double* x_ord, const double* l, int64_t N, int32_t d, double rho,
+                           int32_t rule, int64_t* rowptr, int64_t* nnz_out, kc_pattern_builder** builder_out,
+                           void* stream);
+kc_status kc_pattern_end(kc_pattern_builder* builder, int32_t* col);
+void kc_pattern_abort(kc_pattern_builder* builder);
 
 /* ---- a4: schedule ------------------------------------------------------ *
  * From the CSR rows: CSC (colptr int64[N+1], rowidx int32[nnz], slot

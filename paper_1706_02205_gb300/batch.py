@@ -27,8 +27,7 @@ def prepare_sets(xs, rho, n_streams=8, rule=kc.RULE_MAX, stream=None):
         with torch.cuda.stream(stream):
             for x in xs:
                 perm, l, xo = kc.order_points(x, stream=stream)
-                rowptr, nnz = kc.pattern_count(xo, l, rho, rule, stream=stream)
-                col = kc.pattern_fill(xo, l, rho, rowptr, nnz, rule, stream=stream)
+                rowptr, col = kc.pattern_rows(xo, l, rho, rule, stream=stream)
                 out.append({"perm": perm, "l": l, "x_ord": xo, "rowptr": rowptr, "col": col})
         stream.synchronize()
         return out
@@ -38,8 +37,7 @@ def prepare_sets(xs, rho, n_streams=8, rule=kc.RULE_MAX, stream=None):
         st = streams[k % len(streams)]
         with torch.cuda.stream(st):
             perm, l, xo = kc.order_points(xs[k], stream=st)
-            rowptr, nnz = kc.pattern_count(xo, l, rho, rule, stream=st)
-            col = kc.pattern_fill(xo, l, rho, rowptr, nnz, rule, stream=st)
+            rowptr, col = kc.pattern_rows(xo, l, rho, rule, stream=st)
         st.synchronize()
         return {"perm": perm, "l": l, "x_ord": xo, "rowptr": rowptr, "col": col}
 

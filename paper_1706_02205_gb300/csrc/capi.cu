@@ -20,6 +20,10 @@ kc_status pattern_count_impl(const double* x_ord, const double* l, int64_t N, in
                              int64_t* rowptr, int64_t* nnz_out, cudaStream_t s);
 kc_status pattern_fill_impl(const double* x_ord, const double* l, int64_t N, int d, double rho, int rule,
                             const int64_t* rowptr, int32_t* col, cudaStream_t s);
+kc_status pattern_begin_impl(const double* x_ord, const double* l, int64_t N, int d, double rho, int rule,
+                             int64_t* rowptr, int64_t* nnz_out, void** out, cudaStream_t s);
+kc_status pattern_end_impl(void* h, int32_t* col);
+void pattern_abort_impl(void* h);
 kc_status schedule_impl(int64_t N, const int64_t* rowptr, const int32_t* col, int64_t nnz, const double* x, int d,
                         int64_t* colptr, int32_t* rowidx, int64_t* slot, int32_t* level, int32_t* order,
                         int32_t* depth_out, cudaStream_t s);
@@ -138,6 +142,33 @@ kc_status kc_pattern_fill(const double* x_ord, const double* l, int64_t N, int32
     if (rule != KC_RULE_MAX && rule != KC_RULE_MIN) return fail(KC_EINVAL, "rule must be KC_RULE_MAX or KC_RULE_MIN");
     return pattern_fill_impl(x_ord, l, N, d, rho, rule, rowptr, col, (cudaStream_t)stream);
 }
+
+kc_status kc_pattern_begin(const double* x_ord, const double* l, int64_t N, int32_t d, double rho, int32_t rule,
+                           int64_t* rowptr, int64_t* nnz_out, kc_pattern_builder** builder_out, void* stream) {
+    KC_RANGE("kc_pattern_begin");
+    if (!builder_out) return fail(KC_EINVAL, "builder_out must be non-NULL");
+    *builder_out = nullptr;
+    KC_TRY(check_points(x_ord, N, d));
+    if (!l || !rowptr) return fail(KC_EINVAL, "l and rowptr must be non-NULL");
+    if (!(rho > 0.0)) return fail(KC_EINVAL, "rho must be > 0");
+    if (rule != KC_RULE_MAX && rule != KC_RULE_MIN) return fail(KC_EINVAL, "rule must be KC_RULE_MAX or KC_RULE_MIN");
+    void* h = nullptr;
+    KC_TRY(pattern_begin_impl(x_ord, l, N, d, rho, rule, rowptr, nnz_out, &h, (cudaStream_t)stream));
+    *builder_out = (kc_pattern_builder*)h;
+    return KC_OK;
+}
+
+kc_status kc_pattern_end(kc_pattern_builder* builder, int32_t* col) {
+    KC_RANGE("kc_pattern_end");
+    if (!builder) return fail(KC_EINVAL, "builder must be non-NULL");
+    if (!col) {
+        pattern_abort_impl(builder);
+        return fail(KC_EINVAL, "col must be non-NULL (the builder was released)");
+    }
+    return pattern_end_impl(builder, col);
+}
+
+void kc_pattern_abort(kc_pattern_builder* builder) { pattern_abort_impl(builder); }
 
 kc_status kc_schedule(int64_t N, const int64_t* rowptr, const int32_t* col, const double* x_ord, int32_t d,
                       int64_t* colptr, int32_t* rowidx, int64_t* slot, int32_t* level, int32_t* order,

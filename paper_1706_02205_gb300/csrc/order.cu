@@ -124,14 +124,22 @@ __global__ void ord_cellmax_k(const int32_t* __restrict__ bsorted, const int64_t
     cmax[cidx] = m;
 }
 
-// one thread per band point: is it dominant?
+#ifndef KC_DOM_BUDGET
+#define KC_DOM_BUDGET 256
+#endif
+constexpr int DOM_THREAD_BUDGET = KC_DOM_BUDGET;
+
+// One thread per band point: is it dominant?  Most band points meet a
+// dominator among their first candidates; a point whose scan would go past
+// DOM_THREAD_BUDGET candidates (an undominated point has to look at every
+// band point within sqrt(v)) is handed, undecided, to ord_dominance_warp_k.
 __global__ void ord_dominance_k(Grid gb, const int32_t* __restrict__ bsorted, const int64_t* __restrict__ bstart,
                                 int64_t nb, const double* __restrict__ xg, int d, const int32_t* __restrict__ idg,
                                 const double* __restrict__ v2, const int* __restrict__ stat, double T,
                                 int32_t* __restrict__ sel, unsigned long long* __restrict__ nsel,
                                 unsigned long long* __restrict__ nactive, const float* __restrict__ xgf,
                                 float delta, const long long* __restrict__ cmax, const double* __restrict__ gxg,
-                                int gs) {
+                                int gs, int32_t* __restrict__ hard, unsigned long long* __restrict__ nhard) {
     int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= nb) return;
     const int q = bsorted[e];
@@ -156,6 +164,7 @@ __global__ void ord_dominance_k(Grid gb, const int32_t* __restrict__ bsorted, co
         maxr = max(maxr, span_for(gb, R, t));
     }
     bool dom = true;
+    int budget = DOM_THREAD_BUDGET;  // candidates this thread examines before handing q to a warp
     for (int r = 0; r <= maxr && dom; ++r) {
         if (r >= 2 && (double)(r - 1) * gb.c > R) break;
         const int z0 = dg > 2 ? max(0, c[2] - r) : 0, z1 = dg > 2 ? min(gb.n[2] - 1, c[2] + r) : 0;
@@ -185,6 +194,11 @@ __global__ void ord_dominance_k(Grid gb, const int32_t* __restrict__ bsorted, co
                     for (int cx = seg[sg][0]; cx <= seg[sg][1] && dom; ++cx) {
                         if (cmax[base + cx] < bq) continue;  // no larger key in this cell
                         const int64_t f0 = bstart[base + cx], f1 = bstart[base + cx + 1];
+                        if (f1 - f0 > budget) {  // too many candidates left for one thread
+                            hard[atomicAdd(nhard, 1ULL)] = q;
+                            return;
+                        }
+                        budget -= (int)(f1 - f0);
                         for (int64_t f = f0; f < f1; ++f) {
                             const int p = bsorted[f];
                             if (p == q || stat[p] != 0) continue;
@@ -202,6 +216,88 @@ __global__ void ord_dominance_k(Grid gb, const int32_t* __restrict__ bsorted, co
             }
     }
     if (dom) sel[atomicAdd(nsel, 1ULL)] = q;
+}
+
+// The points the threads handed over, one warp each (grid-stride over the
+// list): the same scan in the same ring and cell order, a cell's points 32 at
+// a time, so a long scan costs a 32nd of a serial one (with a thread per
+// point those few scans were the whole duration of a round).
+__global__ void ord_dominance_warp_k(Grid gb, const int32_t* __restrict__ hard,
+                                     const unsigned long long* __restrict__ nhard, const int64_t* __restrict__ bstart,
+                                     const int32_t* __restrict__ bsorted, const double* __restrict__ xg, int d,
+                                     const int32_t* __restrict__ idg, const double* __restrict__ v2,
+                                     const int* __restrict__ stat, int32_t* __restrict__ sel,
+                                     unsigned long long* __restrict__ nsel, const float* __restrict__ xgf, float delta,
+                                     const long long* __restrict__ cmax, const double* __restrict__ gxg, int gs) {
+    const int lane = lane_id();
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int64_t nh = (int64_t)*nhard;
+    for (int64_t e = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; e < nh; e += nw) {
+        const int q = hard[e];
+        const double vq = v2[q];
+        const long long bq = __double_as_longlong(vq);
+        const long long* __restrict__ v2b = (const long long*)v2;
+        const double* xq = xg + (int64_t)q * d;
+        const float rq = sqrtf((float)vq);
+        const int idq = idg[q];
+        const double R = sqrt(vq);
+        const int dg = gb.dg;
+        int c[3] = {0, 0, 0};
+        int maxr = 0;
+        for (int t = 0; t < dg; ++t) {
+            c[t] = cell_coord(gb, gxg[(int64_t)q * gs + t], t);
+            maxr = max(maxr, span_for(gb, R, t));
+        }
+        bool dom = true;  // uniform across the warp
+        for (int r = 0; r <= maxr && dom; ++r) {
+            if (r >= 2 && (double)(r - 1) * gb.c > R) break;
+            const int z0 = dg > 2 ? max(0, c[2] - r) : 0, z1 = dg > 2 ? min(gb.n[2] - 1, c[2] + r) : 0;
+            const int y0 = dg > 1 ? max(0, c[1] - r) : 0, y1 = dg > 1 ? min(gb.n[1] - 1, c[1] + r) : 0;
+            for (int cz = z0; cz <= z1 && dom; ++cz)
+                for (int cy = y0; cy <= y1 && dom; ++cy) {
+                    const bool edge = r == 0 || (dg > 2 && abs(cz - c[2]) == r) || (dg > 1 && abs(cy - c[1]) == r);
+                    const int64_t base = ((int64_t)cz * gb.n[1] + cy) * gb.n[0];
+                    int seg[2][2];
+                    int nseg = 0;
+                    if (edge) {
+                        seg[0][0] = max(0, c[0] - r);
+                        seg[0][1] = min(gb.n[0] - 1, c[0] + r);
+                        nseg = 1;
+                    } else {
+                        if (c[0] - r >= 0) {
+                            seg[nseg][0] = seg[nseg][1] = c[0] - r;
+                            ++nseg;
+                        }
+                        if (c[0] + r <= gb.n[0] - 1) {
+                            seg[nseg][0] = seg[nseg][1] = c[0] + r;
+                            ++nseg;
+                        }
+                    }
+                    for (int sg = 0; sg < nseg && dom; ++sg)
+                        for (int cx = seg[sg][0]; cx <= seg[sg][1] && dom; ++cx) {
+                            if (cmax[base + cx] < bq) continue;  // no larger key in this cell
+                            const int64_t f0 = bstart[base + cx], f1 = bstart[base + cx + 1];
+                            for (int64_t fb = f0; fb < f1 && dom; fb += 32) {
+                                bool hit = false;
+                                const int64_t f = fb + lane;
+                                if (f < f1) {
+                                    const int p = bsorted[f];
+                                    if (p != q && stat[p] == 0) {
+                                        const long long bp = v2b[p];
+                                        if (bp > bq || (bp == bq && idg[p] < idq)) {
+                                            const bool far = xgf && screen_f32(xgf + (int64_t)p * d, xgf + (int64_t)q * d,
+                                                                               d, rq, delta) == 0;
+                                            hit = !far && dist2_exact(xg + (int64_t)p * d, xq, d) < vq;
+                                        }
+                                    }
+                                }
+                                if (__any_sync(0xffffffffu, hit)) dom = false;
+                            }
+                        }
+                }
+        }
+        if (dom && lane == 0) sel[atomicAdd(nsel, 1ULL)] = q;
+    }
 }
 
 // ---- greedy steps for the coarsest points: each step selects the argmax of
@@ -460,7 +556,7 @@ kc_status order_impl(const double* x, int64_t N, int d, int32_t* perm, double* l
     int32_t *idg, *blist, *bsorted, *sel, *item_sel;
     int* stat;
     int64_t *bstart, *icnt, *ioff;
-    unsigned long long* ctr;  // [0] vmax bits [1] undecided [2] nb [3] nsel [4] nactive
+    unsigned long long* ctr;  // [0] vmax bits [1] undecided [2] nb [3] nsel [4] nactive [5] handed to warps
     KC_TRY(A.get(&xg, N * d));
     KC_TRY(A.get(&v2, N));
     KC_TRY(A.get(&idg, N));
@@ -468,6 +564,8 @@ kc_status order_impl(const double* x, int64_t N, int d, int32_t* perm, double* l
     KC_TRY(A.get(&blist, N));
     KC_TRY(A.get(&bsorted, N));
     KC_TRY(A.get(&sel, N));
+    int32_t* hard;  // band points handed from the thread scan to the warp scan
+    KC_TRY(A.get(&hard, N));
     KC_TRY(A.get(&icnt, N));
     int4* sbox;
     KC_TRY(A.get(&sbox, N));
@@ -568,11 +666,14 @@ kc_status order_impl(const double* x, int64_t N, int d, int32_t* perm, double* l
         int64_t band_sel = 0, band_items = 0;
         for (;;) {
             if (++rounds > 1000000) return fail(KC_ECUDA, "ordering: too many rounds");
-            KC_CUDA(cudaMemsetAsync(ctr + 3, 0, 2 * sizeof(unsigned long long), s));
+            KC_CUDA(cudaMemsetAsync(ctr + 3, 0, 3 * sizeof(unsigned long long), s));
             ::kc::note_launch(), ord_cellmax_k<<<blocks_for(gb.ncells, 256), 256, 0, s>>>(bsorted, bstart, gb.ncells, v2,
                                                                                          stat, cmax);
-            ::kc::note_launch(), ord_dominance_k<<<blocks_for(nb, 128), 128, 0, s>>>(gb, bsorted, bstart, nb, xg, d, idg, v2, stat, T, sel,
-                                                                ctr + 3, ctr + 4, xgf, delta, cmax, gxg, gs);
+            ::kc::note_launch(), ord_dominance_k<<<blocks_for(nb, 128), 128, 0, s>>>(
+                gb, bsorted, bstart, nb, xg, d, idg, v2, stat, T, sel, ctr + 3, ctr + 4, xgf, delta, cmax, gxg, gs, hard,
+                ctr + 5);
+            ::kc::note_launch(), ord_dominance_warp_k<<<sms * 8, 256, 0, s>>>(
+                gb, hard, ctr + 5, bstart, bsorted, xg, d, idg, v2, stat, sel, ctr + 3, xgf, delta, cmax, gxg, gs);
             unsigned long long hs[2];
             KC_CUDA(cudaMemcpyAsync(hs, ctr + 3, sizeof(hs), cudaMemcpyDeviceToHost, s));
             KC_CUDA(cudaStreamSynchronize(s));

@@ -107,6 +107,86 @@ __global__ void pat_scan_k(PatArgs P, int* __restrict__ cnt, const int64_t* __re
     }
 }
 
+// Candidate range [a, b) (cell-sorted positions) of work item it, and its column.
+__device__ __forceinline__ int item_range(const PatArgs& P, int64_t it, int64_t& a, int64_t& b) {
+    const int i = P.item_col[it];
+    int lo[3], hi[3];
+    box_range(P.g, P.colbox[i], lo, hi);
+    const int64_t r = it - P.off[i];
+    const int ny = hi[1] - lo[1] + 1;
+    const int cy = lo[1] + (int)(r % ny);
+    const int cz = lo[2] + (int)(r / ny);
+    const int64_t base = ((int64_t)cz * P.g.n[1] + cy) * P.g.n[0];
+    a = P.cstart[base + lo[0]];
+    b = P.cstart[base + hi[0] + 1];
+    return i;
+}
+
+// Membership of candidate q (cell-sorted position) in column i: the same
+// tests as pat_scan_k.
+__device__ __forceinline__ bool pat_member(const PatArgs& P, int i, const double* xi, const float* xif, double R,
+                                           int64_t q, int& j) {
+    j = P.ps[q];
+    if (j <= i) return false;
+    const double Rj = P.rule == KC_RULE_MIN ? col_radius(P.rho, P.l[j]) : R;
+    if (isinf(Rj)) return true;
+    const int sc = screen_f32(P.xsf + q * P.d, xif, P.d, (float)Rj, P.delta);
+    if (sc == 0) return false;
+    return sc > 0 || in_s(dist2_exact(P.xs + q * P.d, xi, P.d), Rj);
+}
+
+// chunks of 32 candidates of every item (the hit masks' layout)
+__global__ void pat_chunks_k(PatArgs P, int64_t* __restrict__ nch) {
+    const int64_t it = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (it >= P.nitems) return;
+    int64_t a, b;
+    item_range(P, it, a, b);
+    nch[it] = (b - a + 31) / 32;
+}
+
+// Search pass of the builder: one warp per item; the row counts as in the
+// count pass, and every 32 candidates' memberships as one mask word.
+__global__ void pat_mask_k(PatArgs P, const int64_t* __restrict__ moff, int* __restrict__ cnt,
+                           uint32_t* __restrict__ masks) {
+    const int64_t it = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (it >= P.nitems) return;
+    const int lane = lane_id();
+    int64_t a, b;
+    const int i = item_range(P, it, a, b);
+    const double* xi = P.xo + (int64_t)i * P.d;
+    const float* xif = P.xof + (int64_t)i * P.d;
+    const double R = col_radius(P.rho, P.l[i]);
+    uint32_t* m = masks + moff[it];
+    for (int64_t q0 = a; q0 < b; q0 += 32) {
+        const int64_t q = q0 + lane;
+        int j = 0;
+        const bool hit = q < b && pat_member(P, i, xi, xif, R, q, j);
+        const unsigned w = __ballot_sync(0xffffffffu, hit);
+        if (lane == 0) m[(q0 - a) >> 5] = w;
+        if (hit) atomicAdd(&cnt[j], 1);
+    }
+}
+
+// Fill pass of the builder: the members from the masks, no distance tests.
+__global__ void pat_mask_fill_k(PatArgs P, const int64_t* __restrict__ moff, const uint32_t* __restrict__ masks,
+                                int* __restrict__ cnt, const int64_t* __restrict__ rowptr, int32_t* __restrict__ col) {
+    const int64_t it = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (it >= P.nitems) return;
+    const int lane = lane_id();
+    const int i = P.item_col[it];
+    const int64_t c0 = moff[it], c1 = moff[it + 1];
+    int64_t a, b;
+    item_range(P, it, a, b);
+    for (int64_t c = c0; c < c1; ++c) {
+        const uint32_t w = masks[c];
+        if ((w >> lane) & 1u) {
+            const int j = P.ps[a + ((c - c0) << 5) + lane];
+            const int slot = atomicAdd(&cnt[j], 1);
+            col[rowptr[j] + slot] = i;
+        }
+    }
+}
+
 __global__ void pat_gather_k(const double* __restrict__ xo, const int32_t* __restrict__ gs, int64_t N, int d,
                              Origin org, double* __restrict__ xs, float* __restrict__ xsf, float* __restrict__ xof) {
     int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -368,6 +448,115 @@ kc_status pattern_fill_impl(const double* xo, const double* l, int64_t N, int d,
     }
     KC_CUDA(cudaStreamSynchronize(s));
     return KC_OK;
+}
+
+
+// ---- one search for both phases: the builder keeps the grid and the hit
+// masks of the count pass for the fill (scratch held until end/abort)
+struct PatternBuilder {
+    cudaStream_t s;
+    Arena* A = nullptr;
+    PatSetup S;
+    PatArgs P;
+    int64_t N = 0;
+    int64_t* moff = nullptr;
+    uint32_t* masks = nullptr;
+    int* cnt = nullptr;
+    int64_t* rowptr = nullptr;
+    int64_t nnz = 0;
+};
+
+kc_status pattern_begin_impl(const double* xo, const double* l, int64_t N, int d, double rho, int rule,
+                             int64_t* rowptr, int64_t* nnz_out, void** out, cudaStream_t s) {
+    PatternBuilder* B = new PatternBuilder();
+    B->s = s;
+    B->A = new Arena(s);
+    B->N = N;
+    B->rowptr = rowptr;
+    auto fail_out = [&](kc_status st) {
+        delete B->A;
+        delete B;
+        return st;
+    };
+    kc_status st = pat_setup(xo, l, N, d, rho, B->S, *B->A, s);
+    if (st != KC_OK) return fail_out(st);
+    B->P = pat_args(B->S, xo, l, d, rho, rule);
+    const int64_t ni = B->S.nitems;
+    int64_t* nch;
+    if ((st = B->A->get(&nch, ni + 1)) != KC_OK) return fail_out(st);
+    if ((st = B->A->get(&B->moff, ni + 1)) != KC_OK) return fail_out(st);
+    if ((st = B->A->get(&B->cnt, N)) != KC_OK) return fail_out(st);
+    int32_t* len;
+    if ((st = B->A->get(&len, N)) != KC_OK) return fail_out(st);
+    if (ni > 0) ::kc::note_launch(), pat_chunks_k<<<blocks_for(ni, 256), 256, 0, s>>>(B->P, nch);
+    if ((st = exclusive_scan_i64(nch, B->moff, ni, *B->A, s)) != KC_OK) return fail_out(st);
+    int64_t nchunks = 0;
+    if (cudaMemcpyAsync(&nchunks, B->moff + ni, sizeof(int64_t), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return fail_out(fail(KC_ECUDA, "pattern: chunk count"));
+    if ((st = B->A->get(&B->masks, nchunks)) != KC_OK) return fail_out(st);
+    if (cudaMemsetAsync(B->cnt, 0, sizeof(int) * N, s) != cudaSuccess) return fail_out(fail(KC_ECUDA, "memset"));
+    if (ni > 0) ::kc::note_launch(), pat_mask_k<<<blocks_for(ni * 32, 256), 256, 0, s>>>(B->P, B->moff, B->cnt, B->masks);
+    ::kc::note_launch(), plus_one_k<<<blocks_for(N, 256), 256, 0, s>>>(B->cnt, N, len);
+    if (cudaGetLastError() != cudaSuccess) return fail_out(fail(KC_ECUDA, "pattern: search launch"));
+    if ((st = exclusive_scan_i32_to_i64(len, rowptr, N, *B->A, s)) != KC_OK) return fail_out(st);
+    if (cudaMemcpyAsync(&B->nnz, rowptr + N, sizeof(int64_t), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return fail_out(fail(KC_ECUDA, "pattern: nnz"));
+    if (nnz_out) *nnz_out = B->nnz;
+    *out = B;
+    return KC_OK;
+}
+
+void pattern_abort_impl(void* h) {
+    PatternBuilder* B = (PatternBuilder*)h;
+    if (!B) return;
+    delete B->A;  // frees the scratch on the builder's stream
+    delete B;
+}
+
+static kc_status pattern_fill_from(PatternBuilder* B, int32_t* col) {
+    const cudaStream_t s = B->s;
+    const int64_t N = B->N;
+    Arena& A = *B->A;
+    int* mx;
+    KC_TRY(A.get(&mx, 1));
+    KC_CUDA(cudaMemsetAsync(mx, 0, sizeof(int), s));
+    ::kc::note_launch(), max_len_k<<<blocks_for(N, 256), 256, 0, s>>>(B->rowptr, N, mx);
+    int hmx = 0;
+    KC_CUDA(cudaMemcpyAsync(&hmx, mx, sizeof(int), cudaMemcpyDeviceToHost, s));
+    KC_CUDA(cudaStreamSynchronize(s));
+    if (hmx > SORT_BLOCK_CAP) return fail(KC_EINVAL, "pattern row longer than 16384 entries");
+    KC_CUDA(cudaMemsetAsync(B->cnt, 0, sizeof(int) * N, s));
+    if (B->S.nitems > 0)
+        ::kc::note_launch(), pat_mask_fill_k<<<blocks_for(B->S.nitems * 32, 256), 256, 0, s>>>(B->P, B->moff, B->masks,
+                                                                                            B->cnt, B->rowptr, col);
+    KC_CUDA(cudaGetLastError());
+    int32_t* long_rows;
+    unsigned long long* nlong;
+    KC_TRY(A.get(&long_rows, N));
+    KC_TRY(A.get(&nlong, 1));
+    KC_CUDA(cudaMemsetAsync(nlong, 0, sizeof(unsigned long long), s));
+    ::kc::note_launch(), row_sort_warp_k<<<blocks_for(N, 8), 256, 0, s>>>(B->rowptr, N, col, long_rows, nlong);
+    KC_CUDA(cudaGetLastError());
+    unsigned long long hl = 0;
+    KC_CUDA(cudaMemcpyAsync(&hl, nlong, sizeof(hl), cudaMemcpyDeviceToHost, s));
+    KC_CUDA(cudaStreamSynchronize(s));
+    if (hl > 0) {
+        size_t sm = sizeof(int) * SORT_BLOCK_CAP;
+        KC_TRY(allow_dynamic_smem(row_sort_block_k));
+        ::kc::note_launch(), row_sort_block_k<<<(unsigned)hl, 1024, sm, s>>>(B->rowptr, col, long_rows);
+        KC_CUDA(cudaGetLastError());
+    }
+    KC_CUDA(cudaStreamSynchronize(s));
+    return KC_OK;
+}
+
+kc_status pattern_end_impl(void* h, int32_t* col) {
+    PatternBuilder* B = (PatternBuilder*)h;
+    const kc_status st = pattern_fill_from(B, col);
+    pattern_abort_impl(B);
+    return st;
 }
 
 }  // namespace kc

@@ -52,7 +52,7 @@ class kc_opts(C.Structure):
 
 
 _lib = None
-ABI_VERSION = 4  # KC_ABI_VERSION of include/kchol.h that these signatures follow
+ABI_VERSION = 5  # KC_ABI_VERSION of include/kchol.h that these signatures follow
 
 
 def lib():
@@ -75,6 +75,8 @@ def lib():
             "kc_order_points": [vp, i64, i32, vp, vp, vp, vp],
             "kc_pattern_count": [vp, vp, i64, i32, dbl, i32, vp, P(C.c_int64), vp],
             "kc_pattern_fill": [vp, vp, i64, i32, dbl, i32, vp, vp, vp],
+            "kc_pattern_begin": [vp, vp, i64, i32, dbl, i32, vp, P(C.c_int64), P(vp), vp],
+            "kc_pattern_end": [vp, vp],
             "kc_schedule": [i64, vp, vp, vp, i32, vp, vp, vp, vp, vp, P(C.c_int32), vp],
             "kc_factor": [P(kc_pattern), vp, i32, P(kc_kernel), i32, vp, vp, P(C.c_int64), P(kc_opts), vp],
             "kc_solve": [P(kc_pattern), i32, vp, vp, P(kc_kernel), vp, vp, i32, vp, P(kc_opts), vp],
@@ -116,6 +118,8 @@ def lib():
             f.restype = C.c_int
         L.kc_factor_plan_destroy.argtypes = [vp]
         L.kc_factor_plan_destroy.restype = None
+        L.kc_pattern_abort.argtypes = [vp]
+        L.kc_pattern_abort.restype = None
         _lib = L
     return _lib
 
@@ -127,7 +131,7 @@ EXPORTED = ("kc_last_error", "kc_abi_version", "kc_launch_count", "kc_last_facto
             "kc_l_matvec", "kc_lt_matvec", "kc_llt_matvec", "kc_logdet", "kc_pattern_reverse",
             "kc_gather_entries", "kc_factor_given", "kc_refine_sparse", "kc_supernodal_count",
             "kc_supernodal_fill", "kc_supernodal", "kc_pattern_validate", "kc_scratch_trim",
-            "kc_frob_error", "kc_factor_blocked")
+            "kc_frob_error", "kc_factor_blocked", "kc_pattern_begin", "kc_pattern_end", "kc_pattern_abort")
 
 
 def launch_count() -> int:
@@ -436,9 +440,29 @@ def frob_error(pat: Pattern, prec, val, diag, x_ord, kern: Kernel, perm, pi, pj,
 
 # ------------------------------------------------------------------ the path
 
+def pattern_rows(x_ord, l, rho, rule=RULE_MAX, stream=None):
+    """The CSR rows of S_rho (rowptr int64, col int32) with one search
+    (kc_pattern_begin / kc_pattern_end); the same arrays as pattern_count
+    followed by pattern_fill."""
+    _dev(x_ord, torch.float64, "x_ord")
+    _dev(l, torch.float64, "l")
+    N, d = x_ord.shape
+    rowptr = torch.empty(N + 1, dtype=torch.int64, device=x_ord.device)
+    nnz = C.c_int64(0)
+    h = C.c_void_p()
+    _check(lib().kc_pattern_begin(_ptr(x_ord), _ptr(l), N, d, float(rho), int(rule), _ptr(rowptr), C.byref(nnz),
+                                  C.byref(h), _stream(stream)))
+    try:
+        col = torch.empty(int(nnz.value), dtype=torch.int32, device=x_ord.device)
+    except BaseException:
+        lib().kc_pattern_abort(h)
+        raise
+    _check(lib().kc_pattern_end(h, _ptr(col)))
+    return rowptr, col
+
+
 def build_pattern(x_ord, l, rho, rule=RULE_MAX, stream=None) -> Pattern:
-    rowptr, nnz = pattern_count(x_ord, l, rho, rule, stream)
-    col = pattern_fill(x_ord, l, rho, rowptr, nnz, rule, stream)
+    rowptr, col = pattern_rows(x_ord, l, rho, rule, stream)
     return schedule(rowptr, col, x_ord, stream)
 
 

@@ -82,6 +82,9 @@ def test_pattern_bit_exact(N, d, rho, rule):
     assert nnz == rp_ref[-1]
     assert np.array_equal(H(rowptr), rp_ref)
     assert np.array_equal(H(col), col_ref)
+    # one search for both phases (kc_pattern_begin / kc_pattern_end): the same arrays
+    rp2, col2 = kc.pattern_rows(T(xo), T(l_ref), rho, rule)
+    assert np.array_equal(H(rp2), rp_ref) and np.array_equal(H(col2), col_ref)
 
 
 @pytest.mark.parametrize("rho,rule", [(3.0, 0), (4.0, 1)])
@@ -94,6 +97,8 @@ def test_pattern_bit_exact_swiss_roll_r20(rho, rule):
     rowptr, nnz = kc.pattern_count(T(xo), T(l_ref), rho, rule)
     col = kc.pattern_fill(T(xo), T(l_ref), rho, rowptr, nnz, rule)
     assert np.array_equal(H(rowptr), rp_ref) and np.array_equal(H(col), col_ref)
+    rp2, col2 = kc.pattern_rows(T(xo), T(l_ref), rho, rule)
+    assert np.array_equal(H(rp2), rp_ref) and np.array_equal(H(col2), col_ref)
 
 
 def test_pattern_duplicates_and_ties():
@@ -106,6 +111,38 @@ def test_pattern_duplicates_and_ties():
         rowptr, nnz = kc.pattern_count(T(xo), T(l_ref), rho)
         col = kc.pattern_fill(T(xo), T(l_ref), rho, rowptr, nnz)
         assert np.array_equal(H(rowptr), rp_ref) and np.array_equal(H(col), col_ref)
+        rp2, col2 = kc.pattern_rows(T(xo), T(l_ref), rho)
+        assert np.array_equal(H(rp2), rp_ref) and np.array_equal(H(col2), col_ref)
+
+
+def test_pattern_builder_release_and_errors():
+    """A builder released without filling, an end without col, bad arguments:
+    errors are reported and the next build is unaffected."""
+    import ctypes as C
+    x = inputs.uniform(800, 2, seed=19)
+    p_ref, l_ref = oracle.maximin_brute(x)
+    xo, l = T(x[p_ref]), T(l_ref)
+    rp_ref, col_ref = oracle.pattern(x[p_ref], l_ref, 3.0)
+    L = kc.lib()
+    stream = C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    rowptr = torch.empty(801, dtype=torch.int64, device=DEV)
+    nnz, h = C.c_int64(0), C.c_void_p()
+    assert L.kc_pattern_begin(C.c_void_p(xo.data_ptr()), C.c_void_p(l.data_ptr()), 800, 2, 3.0, 0,
+                              C.c_void_p(rowptr.data_ptr()), C.byref(nnz), C.byref(h), stream) == kc.KC_OK
+    assert nnz.value == rp_ref[-1] and h.value
+    L.kc_pattern_abort(h)
+    L.kc_pattern_abort(None)
+    h2 = C.c_void_p()
+    assert L.kc_pattern_begin(C.c_void_p(xo.data_ptr()), C.c_void_p(l.data_ptr()), 800, 2, 3.0, 0,
+                              C.c_void_p(rowptr.data_ptr()), C.byref(nnz), C.byref(h2), stream) == kc.KC_OK
+    assert L.kc_pattern_end(h2, None) == kc.KC_EINVAL  # released all the same
+    h3 = C.c_void_p(1)
+    assert L.kc_pattern_begin(C.c_void_p(xo.data_ptr()), C.c_void_p(l.data_ptr()), 800, 2, -1.0, 0,
+                              C.c_void_p(rowptr.data_ptr()), C.byref(nnz), C.byref(h3), stream) == kc.KC_EINVAL
+    assert not h3.value
+    assert L.kc_pattern_end(None, C.c_void_p(rowptr.data_ptr())) == kc.KC_EINVAL
+    rp2, col2 = kc.pattern_rows(xo, l, 3.0)
+    assert np.array_equal(H(rp2), rp_ref) and np.array_equal(H(col2), col_ref)
 
 
 # ------------------------------------------------------------------ schedule
