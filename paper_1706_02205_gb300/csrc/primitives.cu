@@ -340,10 +340,12 @@ __global__ void rs_hist_k(const K* __restrict__ key, int64_t n, int shift, int64
     for (int i = threadIdx.x; i < 256; i += blockDim.x) hist[(int64_t)i * ntiles + blockIdx.x] = cnt[i];
 }
 
-// Scatter of one tile: each warp ranks its elements by digit (match_any, in
-// element order, so the sort is stable), the tile is rearranged in shared
-// memory in digit order, and every digit's run is then written to its global
-// offset with consecutive threads writing consecutive addresses.
+// Scatter of one tile: each warp ranks its elements by digit once (match_any,
+// in element order, so the sort is stable), keeping each element's key and
+// its position among the warp's elements of the same digit in registers; the
+// tile is then rearranged in shared memory in digit order, and every digit's
+// run is written to its global offset with consecutive threads writing
+// consecutive addresses.
 template <typename K>
 __global__ void __launch_bounds__(RS_WARPS * 32) rs_scatter_k(const K* __restrict__ kin, const int64_t* __restrict__ vin,
                                                                int64_t n, int shift, int64_t ntiles,
@@ -352,7 +354,7 @@ __global__ void __launch_bounds__(RS_WARPS * 32) rs_scatter_k(const K* __restric
     extern __shared__ __align__(16) unsigned char rs_smem[];
     int64_t* sval = (int64_t*)rs_smem;            // [RS_TILE]
     K* skey = (K*)(sval + RS_TILE);               // [RS_TILE]
-    __shared__ int wcnt[RS_WARPS][256];           // per-warp digit counts, then offsets in the tile
+    __shared__ int wcnt[RS_WARPS][256];           // per-warp digit counts, then the warps' starts in the tile
     __shared__ int dstart[257];                   // tile-local start of every digit
     __shared__ long long gbase[256];              // global start of every digit of this tile
     __shared__ int wsum[RS_WARPS];
@@ -362,11 +364,19 @@ __global__ void __launch_bounds__(RS_WARPS * 32) rs_scatter_k(const K* __restric
     const int64_t tbase = (int64_t)blockIdx.x * RS_TILE;
     const int64_t wbase = tbase + (int64_t)w * RS_ROUNDS * 32;
     const unsigned lt = (1u << lane) - 1u;
+    K kr[RS_ROUNDS];
+    int rank[RS_ROUNDS];  // digit in the high bits, position among the warp's same-digit elements below
+#pragma unroll
     for (int r = 0; r < RS_ROUNDS; ++r) {
         const int64_t e = wbase + r * 32 + lane;
-        const int dg = e < n ? (int)((kin[e] >> shift) & 0xFF) : 256 + lane;
+        const bool ok = e < n;
+        kr[r] = ok ? kin[e] : (K)0;
+        const int dg = ok ? (int)((kr[r] >> shift) & 0xFF) : 256 + lane;
         const unsigned peers = __match_any_sync(0xffffffffu, dg);
-        if (e < n && lane == 31 - __clz(peers)) wcnt[w][dg] += __popc(peers);
+        const int before = ok ? wcnt[w][dg] : 0;
+        __syncwarp();
+        if (ok && lane == 31 - __clz(peers)) wcnt[w][dg] = before + __popc(peers);
+        rank[r] = ok ? (dg << 16) | (before + __popc(peers & lt)) : -1;
         __syncwarp();
     }
     __syncthreads();
@@ -397,20 +407,13 @@ __global__ void __launch_bounds__(RS_WARPS * 32) rs_scatter_k(const K* __restric
         }
     }
     __syncthreads();
+#pragma unroll
     for (int r = 0; r < RS_ROUNDS; ++r) {
-        const int64_t e = wbase + r * 32 + lane;
-        const bool ok = e < n;
-        const K kv = ok ? kin[e] : (K)0;
-        const int dg = ok ? (int)((kv >> shift) & 0xFF) : 256 + lane;
-        const unsigned peers = __match_any_sync(0xffffffffu, dg);
-        if (ok) {
-            const int pos = wcnt[w][dg] + __popc(peers & lt);
-            skey[pos] = kv;
-            sval[pos] = vin[e];
+        if (rank[r] >= 0) {
+            const int pos = wcnt[w][rank[r] >> 16] + (rank[r] & 0xFFFF);
+            skey[pos] = kr[r];
+            sval[pos] = vin[wbase + r * 32 + lane];
         }
-        __syncwarp();
-        if (ok && lane == 31 - __clz(peers)) wcnt[w][dg] += __popc(peers);
-        __syncwarp();
     }
     __syncthreads();
     const int cnt = (int)min((int64_t)RS_TILE, n - tbase);
