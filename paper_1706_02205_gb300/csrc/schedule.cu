@@ -135,6 +135,48 @@ __global__ void order_out_k(const int64_t* __restrict__ sval, int64_t N, int32_t
     if (p < N) order[p] = (int32_t)sval[p];
 }
 
+#ifndef KC_LEVELS_BLOCKS_PER_SM
+#define KC_LEVELS_BLOCKS_PER_SM 2
+#endif
+
+// A second stream for work that runs beside the caller's stream `home`:
+// fork() makes it wait for the work enqueued on home so far, join() makes
+// home wait for it.  Going out of scope joins (if not joined yet) and
+// releases the stream and events, so that scratch freed on home afterwards
+// (an Arena declared before this object) is never freed under the second
+// stream's work, whichever way the function returns.
+struct AuxStream {
+    cudaStream_t home = nullptr, s = nullptr;
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    bool joined = true;
+    kc_status fork(cudaStream_t from) {
+        home = from;
+        KC_CUDA(cudaEventCreateWithFlags(&ev[0], cudaEventDisableTiming));
+        KC_CUDA(cudaEventCreateWithFlags(&ev[1], cudaEventDisableTiming));
+        KC_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+        KC_CUDA(cudaEventRecord(ev[0], from));
+        KC_CUDA(cudaStreamWaitEvent(s, ev[0], 0));
+        joined = false;
+        return KC_OK;
+    }
+    kc_status join() {
+        if (joined) return KC_OK;
+        joined = true;
+        KC_CUDA(cudaEventRecord(ev[1], s));
+        KC_CUDA(cudaStreamWaitEvent(home, ev[1], 0));
+        return KC_OK;
+    }
+    ~AuxStream() {
+        if (!joined && s) {
+            cudaEventRecord(ev[1], s);
+            cudaStreamWaitEvent(home, ev[1], 0);
+        }
+        for (cudaEvent_t e : ev)
+            if (e) cudaEventDestroy(e);
+        if (s) cudaStreamDestroy(s);
+    }
+};
+
 static int bits_for(int64_t v) {
     int b = 1;
     while (b < 63 && ((int64_t)1 << b) <= v) ++b;
@@ -145,23 +187,9 @@ kc_status schedule_impl(int64_t N, const int64_t* rowptr, const int32_t* col, in
                         int64_t* colptr, int32_t* rowidx, int64_t* slot, int32_t* level, int32_t* order,
                         int32_t* depth_out, cudaStream_t s) {
     Arena A(s);
-    // CSC by a stable sort of the CSR entries by column
-    const int pb = bits_for(nnz);
-    if (pb + bits_for(N) > 63) return fail(KC_EINVAL, "schedule: N and nnz too large for packed sort values");
-    uint32_t *k0, *k1;
-    int64_t *v0, *v1;
-    KC_TRY(A.get(&k0, nnz));
-    KC_TRY(A.get(&k1, nnz));
-    KC_TRY(A.get(&v0, nnz));
-    KC_TRY(A.get(&v1, nnz));
-    int sms = sm_count();
-    ::kc::note_launch(), col_keys_k<<<sms * 8, 256, 0, s>>>(rowptr, col, N, pb, k0, v0);
-    KC_CUDA(cudaGetLastError());
-    KC_TRY(radix_sort_u32_i64(k0, v0, k1, v1, nnz, bits_for(N), A, s));
-    ::kc::note_launch(), csc_finish_k<<<blocks_for(nnz, 256), 256, 0, s>>>(k1, v1, nnz, N, pb, colptr, rowidx, slot);
-    KC_CUDA(cudaGetLastError());
-
-    // levels
+    // The levels (a dependency chain, latency-bound) run on a second stream next to the CSC sort
+    // (bound by its ranking): both read only the CSR rows.  The level kernel takes a quarter of the
+    // SMs' thread slots so that the sort's blocks find room.
     unsigned long long* ticket;
     int* dev_depth;
     int* status;
@@ -172,8 +200,31 @@ kc_status schedule_impl(int64_t N, const int64_t* rowptr, const int32_t* col, in
     KC_CUDA(cudaMemsetAsync(dev_depth, 0, sizeof(int), s));
     KC_CUDA(cudaMemsetAsync(status, 0, sizeof(int), s));
     KC_CUDA(cudaMemsetAsync(level, 0, sizeof(int) * N, s));
-    ::kc::note_launch(), levels_k<<<sms * 8, 256, 0, s>>>(rowptr, col, N, level, ticket, dev_depth, status, 4000000000LL);
+    AuxStream aux;
+    KC_TRY(aux.fork(s));
+    const int sms = sm_count();
+    ::kc::note_launch(), levels_k<<<sms * KC_LEVELS_BLOCKS_PER_SM, 256, 0, aux.s>>>(rowptr, col, N, level, ticket,
+                                                                               dev_depth, status, 4000000000LL);
     KC_CUDA(cudaGetLastError());
+
+    // CSC by a stable sort of the CSR entries by column
+    const int pb = bits_for(nnz);
+    if (pb + bits_for(N) > 63) {
+        return fail(KC_EINVAL, "schedule: N and nnz too large for packed sort values");
+    }
+    uint32_t *k0, *k1;
+    int64_t *v0, *v1;
+    KC_TRY(A.get(&k0, nnz));
+    KC_TRY(A.get(&k1, nnz));
+    KC_TRY(A.get(&v0, nnz));
+    KC_TRY(A.get(&v1, nnz));
+    ::kc::note_launch(), col_keys_k<<<sms * 8, 256, 0, s>>>(rowptr, col, N, pb, k0, v0);
+    KC_CUDA(cudaGetLastError());
+    KC_TRY(radix_sort_u32_i64(k0, v0, k1, v1, nnz, bits_for(N), A, s));
+    ::kc::note_launch(), csc_finish_k<<<blocks_for(nnz, 256), 256, 0, s>>>(k1, v1, nnz, N, pb, colptr, rowidx, slot);
+    KC_CUDA(cudaGetLastError());
+
+    KC_TRY(aux.join());  // the levels are complete on s from here on
     int h_depth = 0, h_status = 0;
     KC_CUDA(cudaMemcpyAsync(&h_depth, dev_depth, sizeof(int), cudaMemcpyDeviceToHost, s));
     KC_CUDA(cudaMemcpyAsync(&h_status, status, sizeof(int), cudaMemcpyDeviceToHost, s));
