@@ -307,9 +307,13 @@ __device__ __forceinline__ int lanes_per_row(int lanes) {
     return lanes > 0 ? lanes : (int)(32 / sizeof(T));
 }
 
+__device__ __forceinline__ void prefetch_l2(const void* p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
+
 // Merge of the prefix [es, be) of row j, read from global memory, against
 // row i: U (col, val) pairs per lane in flight; the ragged end is masked.
-template <typename T, int U>
+// PF (long rows): each full round also prefetches into L2 the round after
+// the next, which the loads would otherwise request one round late.
+template <typename T, int U, int PF = 0>
 __device__ __forceinline__ void merge_global(const FactorArgs<T>& A, const RowTable<T>& tab, const TaskCtx<T>& X,
                                              int64_t es, int64_t be, int sub, int G, Acc<T>& acc) {
     if (X.staged) {
@@ -320,6 +324,18 @@ __device__ __forceinline__ void merge_global(const FactorArgs<T>& A, const RowTa
         for (; t + (U - 1) * G < n; t += U * G) {  // full rounds
             int k[U];
             T wv[U];
+            if constexpr (PF) {
+                constexpr int SEC = 32 / (int)sizeof(T);
+                const int base2 = t - sub + 2 * U * G;
+#pragma unroll
+                for (int h = 0; h < U / SEC; ++h) {  // U*G entries = U/SEC sectors per lane
+                    const int e2 = base2 + (h * G + sub) * SEC;
+                    if (e2 < n) {
+                        prefetch_l2(cp + e2);
+                        prefetch_l2(vp + e2);
+                    }
+                }
+            }
 #pragma unroll
             for (int u = 0; u < U; ++u) k[u] = __ldg(cp + t + u * G);
 #pragma unroll
@@ -351,8 +367,6 @@ __device__ __forceinline__ void merge_global(const FactorArgs<T>& A, const RowTa
     }
 }
 
-__device__ __forceinline__ void prefetch_l2(const void* p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
-
 // Row-j bookkeeping of the rows b0+lane of a batch: the slot of L_ji, the
 // start of row j, and Theta_ji (loads and exponentials overlap across lanes).
 template <typename T, int ENT>
@@ -383,8 +397,9 @@ __device__ __forceinline__ void batch_rows(const FactorArgs<T>& A, const TaskCtx
 #endif
 
 // GC > 0: lanes per row fixed at compile time (the default for the FP32 form:
-// the group loads' offsets become constants); 0: from A.lanes.
-template <typename T, int U, int ENT, int GC>
+// the group loads' offsets become constants); 0: from A.lanes.  PF: the
+// merges prefetch two rounds ahead (patterns with long rows).
+template <typename T, int U, int ENT, int GC, int PF>
 __global__ void __launch_bounds__(256, U >= 16 ? 3 : KC_FACTOR_MIN_BLOCKS) ichol_persistent_k(FactorArgs<T> A) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = lane_id();
@@ -431,7 +446,7 @@ __global__ void __launch_bounds__(256, U >= 16 ? 3 : KC_FACTOR_MIN_BLOCKS) ichol
                     }
                 }
                 Acc<T> acc;
-                if (act && !X.zero) merge_global<T, U>(A, tab, X, es, be, sub, G, acc);
+                if (act && !X.zero) merge_global<T, U, PF>(A, tab, X, es, be, sub, G, acc);
                 acc.group_reduce(G);
                 if (act && sub == 0) A.val[be] = X.zero ? (T)0 : acc.finish(th, X.Lii, X.inv);
             }
@@ -800,9 +815,14 @@ static kc_status launch_core(const FactorCore& F, T* val, double* diag, cudaStre
         warps = std::min(warps, optin / a.warp_smem);
         if (warps < 1) return fail(KC_EINVAL, "factor: stage_bytes too large for one warp's shared memory");
     }
-    auto kfn = ichol_persistent_k<T, U, ENT, 0>;
+    auto kfn = ichol_persistent_k<T, U, ENT, 0, 0>;
     if constexpr (sizeof(T) == 4)
-        if (F.lanes == 0) kfn = ichol_persistent_k<T, U, ENT, 8>;  // lanes per row: 8, at compile time
+        if (F.lanes == 0) kfn = ichol_persistent_k<T, U, ENT, 8, 0>;  // lanes per row: 8, at compile time
+    if constexpr (ENT == 0)
+        if (F.P.nnz >= 400 * F.P.N) {  // long rows (the 3-D workloads): prefetch two rounds ahead
+            if constexpr (sizeof(T) == 4) kfn = F.lanes == 0 ? ichol_persistent_k<T, U, 0, 8, 1> : ichol_persistent_k<T, U, 0, 0, 1>;
+            else kfn = ichol_persistent_k<T, U, 0, 0, 1>;
+        }
     if constexpr (ENT == 0)
         if (bulk) kfn = ichol_bulk_k<T, U, 0>;
     int per_sm = 0;

@@ -63,10 +63,26 @@ __global__ void pat_items_k(Grid g, const double* __restrict__ gxo, int gst, con
     box_range(g, b, lo, hi);
     cnt[i] = (int64_t)(hi[1] - lo[1] + 1) * (hi[2] - lo[2] + 1);
 }
-__global__ void pat_item_fill_k(const int64_t* __restrict__ off, int64_t N, int32_t* __restrict__ item_col) {
-    int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (i >= N) return;
-    for (int64_t t = off[i] + lane_id(); t < off[i + 1]; t += 32) item_col[t] = (int32_t)i;
+// item counts in the cell order of the grid (gs[q]: the column at cell rank q)
+__global__ void pat_cell_counts_k(const int32_t* __restrict__ gs, const int64_t* __restrict__ cnt, int64_t N,
+                                  int64_t* __restrict__ cq) {
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q < N) cq[q] = cnt[gs[q]];
+}
+// the first item of every column, indexed by column
+__global__ void pat_cell_offsets_k(const int32_t* __restrict__ gs, const int64_t* __restrict__ oq, int64_t N,
+                                   int64_t* __restrict__ off) {
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q < N) off[gs[q]] = oq[q];
+    if (q == 0) off[N] = oq[N];
+}
+// the column of every item, columns in cell order
+__global__ void pat_item_fill_cell_k(const int32_t* __restrict__ gs, const int64_t* __restrict__ oq, int64_t N,
+                                     int32_t* __restrict__ item_col) {
+    const int64_t q = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (q >= N) return;
+    const int32_t i = gs[q];
+    for (int64_t t = oq[q] + lane_id(); t < oq[q + 1]; t += 32) item_col[t] = i;
 }
 
 template <bool FILL>
@@ -245,11 +261,21 @@ static kc_status pat_setup(const double* xo, const double* l, int64_t N, int d, 
     KC_TRY(A.get(&S.colbox, N));
     ::kc::note_launch(), pat_items_k<<<blocks_for(N, 256), 256, 0, s>>>(S.g, gxo, gst, l, N, rho, cnt, S.colbox);
     KC_CUDA(cudaGetLastError());
-    KC_TRY(exclusive_scan_i64(cnt, S.off, N, A, s));
-    KC_CUDA(cudaMemcpyAsync(&S.nitems, S.off + N, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    // The work items go column by column in the grid's cell order (neighbouring columns next to each
+    // other), so that the rows a stretch of items writes into are few and stay in L2 meanwhile; off[i]
+    // stays indexed by column.
+    int64_t *cq, *oq;
+    KC_TRY(A.get(&cq, N));
+    KC_TRY(A.get(&oq, N + 1));
+    ::kc::note_launch(), pat_cell_counts_k<<<blocks_for(N, 256), 256, 0, s>>>(S.gs, cnt, N, cq);
+    KC_CUDA(cudaGetLastError());
+    KC_TRY(exclusive_scan_i64(cq, oq, N, A, s));
+    ::kc::note_launch(), pat_cell_offsets_k<<<blocks_for(N, 256), 256, 0, s>>>(S.gs, oq, N, S.off);
+    KC_CUDA(cudaGetLastError());
+    KC_CUDA(cudaMemcpyAsync(&S.nitems, oq + N, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     KC_CUDA(cudaStreamSynchronize(s));
     KC_TRY(A.get(&S.item_col, S.nitems));
-    ::kc::note_launch(), pat_item_fill_k<<<blocks_for(N * 32, 256), 256, 0, s>>>(S.off, N, S.item_col);
+    ::kc::note_launch(), pat_item_fill_cell_k<<<blocks_for(N * 32, 256), 256, 0, s>>>(S.gs, oq, N, S.item_col);
     KC_CUDA(cudaGetLastError());
     return KC_OK;
 }
