@@ -674,6 +674,7 @@ def run_cube3d(args):
     t2 = time.perf_counter()
     e0 = kc.pca_error(x, kern, L64[:0], v0, iters=50)  # ||Theta||_2 for scale
     fk = statistics.mean(ph["factor"])
+    nnz = pat.nnz
     return {"workload": f"uniform [0,1]^3, N={N}, Matern-5/2 l=0.3 nugget 1e-6, rho=4, FP32 form",
             "N": N, "nnz": nnz, "nnz_per_row": nnz / N, "depth": pat.depth, "zero_pivots": zp,
             "phases_ms": {k: statistics.mean(v) for k, v in ph.items()},
