@@ -11,7 +11,8 @@ pattern for comparison.
 Metric: nnz(L) per second of a whole step (and of the factor kernel, the
 paper's t_ICHOL).  The default line also carries the rho = 2 and 5 patterns,
 the sampled error estimator E of both factors, the supernodal block
-factorisation, a refined solve to 1e-10 and a serving run.
+factorisation, a refined solve to 1e-10, the 3-D configuration with its
+rank-k PCA, the 256-set batched launch and a serving run.
 
   python bench.py [--gpus N --steps K --warmup W] [--impl reference]
 
@@ -325,6 +326,11 @@ def run_ours(args, rank, world):
         line["supernodal"] = supernodal_leg(args, r["l"], xo, pat, kern)
     if args.refine_side > 0:
         line["refine_to_1e-10"] = run_refine(args)
+    if args.config_legs and world == 1:
+        # the 3-D configuration (factor, rank-k PCA and its error) and the 256-set batched launch
+        small = argparse.Namespace(**dict(vars(args), steps=2, warmup=1))
+        line["config3_cube3d"] = run_cube3d(small)
+        line["config4_batch"] = run_batch(small)
     if args.serve_leg:
         from paper_1706_02205_gb300 import serve
         args.serve_fracs = (0.8,)
@@ -377,7 +383,7 @@ def supernodal_leg(args, l, xo, pat0, kern):
 TRAFFIC_CAPTURE = {"sources": ("paper_1706_02205_gb300/csrc/factor.cu", "paper_1706_02205_gb300/csrc/common.cuh",
                                "paper_1706_02205_gb300/csrc/grid.cuh", "paper_1706_02205_gb300/csrc/covariance.cuh",
                                "paper_1706_02205_gb300/csrc/ichol.cuh"),
-                   "sha256": "130aac3afc93eb0a007131deb25241d08761fc91bd08950947fd19f397e90e1a",
+                   "sha256": "c5116e557deef04bec67567413686605b69b2985ad7105fa046902e1ceec735f",
                    "dram_per_algorithmic_byte": (27.158938 + 0.959845) / 26.387813}
 
 
@@ -887,6 +893,8 @@ def main():
                     help="patterns of the configuration also factored (kernels timed)")
     ap.add_argument("--no-serve-leg", dest="serve_leg", action="store_false")
     ap.add_argument("--no-supernodal-leg", dest="supernodal_leg", action="store_false")
+    ap.add_argument("--no-config-legs", dest="config_legs", action="store_false",
+                    help="leave out the 3-D configuration and the batched launch from the default line")
     ap.add_argument("--e-reps", type=int, default=50, help="repetitions of the sampled error estimator")
     ap.add_argument("--slots", type=int, default=4)
     ap.add_argument("--serve-n-max", type=int, default=1_000_000)

@@ -815,12 +815,14 @@ static kc_status launch_core(const FactorCore& F, T* val, double* diag, cudaStre
         warps = std::min(warps, optin / a.warp_smem);
         if (warps < 1) return fail(KC_EINVAL, "factor: stage_bytes too large for one warp's shared memory");
     }
+    // FP32 form with 8 lanes per row (the default, or chosen by a plan's tuner): the lanes at compile time
+    const bool g8 = sizeof(T) == 4 && (F.lanes == 0 || F.lanes == 8);
     auto kfn = ichol_persistent_k<T, U, ENT, 0, 0>;
     if constexpr (sizeof(T) == 4)
-        if (F.lanes == 0) kfn = ichol_persistent_k<T, U, ENT, 8, 0>;  // lanes per row: 8, at compile time
+        if (g8) kfn = ichol_persistent_k<T, U, ENT, 8, 0>;
     if constexpr (ENT == 0)
         if (F.P.nnz >= 400 * F.P.N) {  // long rows (the 3-D workloads): prefetch two rounds ahead
-            if constexpr (sizeof(T) == 4) kfn = F.lanes == 0 ? ichol_persistent_k<T, U, 0, 8, 1> : ichol_persistent_k<T, U, 0, 0, 1>;
+            if constexpr (sizeof(T) == 4) kfn = g8 ? ichol_persistent_k<T, U, 0, 8, 1> : ichol_persistent_k<T, U, 0, 0, 1>;
             else kfn = ichol_persistent_k<T, U, 0, 0, 1>;
         }
     if constexpr (ENT == 0)
