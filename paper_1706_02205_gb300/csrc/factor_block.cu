@@ -124,13 +124,13 @@ __device__ __forceinline__ float fsub_dot(float v, float a, float b) { return fm
 template <>
 __device__ __forceinline__ double fsub_dot(double v, double a, double b) { return fma(-a, b, v); }
 
-template <typename T, int MM, bool GEN, int M>
+template <typename T, int MM, bool GEN, int M, int GC>
 __device__ __forceinline__ void group_rows(const GroupArgs<T>& A, int64_t qb, int64_t qe, int g0, int m,
                                            const unsigned long long* tab, int hb, const T* V, const T* Laa,
                                            const double* Ld, const T* Linv) {
     const unsigned FULL = 0xffffffffu;
     const int lane = lane_id(), warp = threadIdx.x >> 5;
-    const int G = A.lanes, ngr = 32 / G, grp = lane / G, sub = lane % G;
+    const int G = GC > 0 ? GC : A.lanes, ngr = 32 / G, grp = lane / G, sub = lane % G;
     for (int64_t q0 = qb + (int64_t)(warp * ngr); q0 < qe; q0 += (int64_t)BF_WARPS * ngr) {
         const int64_t q = q0 + grp;
         const bool act = q < qe;
@@ -195,7 +195,8 @@ __device__ __forceinline__ void group_rows(const GroupArgs<T>& A, int64_t qb, in
     }
 }
 
-template <typename T, int MM, bool GEN>
+// GC > 0: the lanes per row at compile time (the FP32 form's default 8).
+template <typename T, int MM, bool GEN, int GC>
 __global__ void __launch_bounds__(BF_THREADS, KC_BLOCK_MINB) ichol_group_k(GroupArgs<T> A) {
     extern __shared__ __align__(16) unsigned char smem[];
     // layout: D (FP64, lower triangle), the pivots' roots (FP64), L_AA (T),
@@ -314,8 +315,8 @@ __global__ void __launch_bounds__(BF_THREADS, KC_BLOCK_MINB) ichol_group_k(Group
         // with code for the group's exact size (no predicated-off accumulators)
         const int64_t qb = A.colptr[g0] + m + (int64_t)chunk * A.rpt;
         const int64_t qe = min(A.colptr[g0 + 1], qb + A.rpt);
-        if (m <= 4) group_rows<T, MM, GEN, 4>(A, qb, qe, g0, m, tab, hb, V, Laa, Ld, Linv);
-        else group_rows<T, MM, GEN, MM>(A, qb, qe, g0, m, tab, hb, V, Laa, Ld, Linv);
+        if (m <= 4) group_rows<T, MM, GEN, 4, GC>(A, qb, qe, g0, m, tab, hb, V, Laa, Ld, Linv);
+        else group_rows<T, MM, GEN, MM, GC>(A, qb, qe, g0, m, tab, hb, V, Laa, Ld, Linv);
         __syncthreads();
         if (tid == 0) {
             fence_acq_rel_gpu();
@@ -422,7 +423,9 @@ template <typename T, int MM, bool GEN>
 static kc_status group_launch(const GroupArgs<T>& a, cudaStream_t s) {
     const size_t smem = sizeof(double) * (MM * (MM + 1) / 2 + MM) + sizeof(T) * (MM * MM + MM) + 16 + 16 +
                         sizeof(unsigned long long) * ((size_t)1 << a.hbits) + sizeof(T) * (size_t)a.pmax * MM;
-    auto kfn = ichol_group_k<T, MM, GEN>;
+    auto kfn = ichol_group_k<T, MM, GEN, 0>;
+    if constexpr (sizeof(T) == 4)
+        if (a.lanes == 8) kfn = ichol_group_k<T, MM, GEN, 8>;  // (the FP64 form measured no gain)
     KC_TRY(allow_dynamic_smem(kfn));
     int per_sm = 0;
     KC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, BF_THREADS, smem));
