@@ -716,18 +716,95 @@ kc_status solver_check(Solver& S, cudaStream_t s) {
     return KC_OK;
 }
 
+// The permutations between original-order right-hand sides b[r*N + i] and
+// point-major vectors in position order v[k*stride + r] (perm[k] = i), by
+// tiles of 32 points in original order: the rows of b are read and written
+// coalesced, and each point's stride values form one line (128 bytes at
+// stride 16) written or read whole; the inverse permutation is formed first.
+constexpr int PM_WARPS = 8;
+// pos starts at -1; an index outside 0..N-1 is ignored, and a point without a
+// position is skipped by the tiled kernels (no access outside the arrays for
+// a perm that is not a permutation)
+__global__ void pm_inverse_perm_k(const int32_t* __restrict__ perm, int64_t N, int32_t* __restrict__ pos) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < N) {
+        const int32_t i = perm[k];
+        if (i >= 0 && i < N) pos[i] = (int32_t)k;
+    }
+}
+__global__ void __launch_bounds__(PM_WARPS * 32) to_point_major_tiled_k(const double* __restrict__ b,
+                                                                       const int32_t* __restrict__ pos, int64_t N,
+                                                                       int nrhs, int stride, double* __restrict__ out) {
+    __shared__ double tile[PM_WARPS][32][17];
+    const int lane = lane_id(), w = threadIdx.x >> 5;
+    const int64_t i0 = ((int64_t)blockIdx.x * PM_WARPS + w) * 32;
+    if (i0 >= N) return;
+    const bool in = i0 + lane < N;
+    for (int r = 0; r < stride; ++r) tile[w][lane][r] = (in && r < nrhs) ? b[(int64_t)r * N + i0 + lane] : 0.0;
+    __syncwarp();
+    for (int e = lane; e < 32 * stride; e += 32) {
+        const int p = e / stride, r = e - p * stride;
+        const int32_t k = i0 + p < N ? pos[i0 + p] : -1;
+        if (k >= 0) out[(int64_t)k * stride + r] = tile[w][p][r];
+    }
+}
+__global__ void __launch_bounds__(PM_WARPS * 32) from_point_major_tiled_k(const double* __restrict__ xp,
+                                                                         const int32_t* __restrict__ pos, int64_t N,
+                                                                         int nrhs, int stride, double* __restrict__ x) {
+    __shared__ double tile[PM_WARPS][32][17];
+    const int lane = lane_id(), w = threadIdx.x >> 5;
+    const int64_t i0 = ((int64_t)blockIdx.x * PM_WARPS + w) * 32;
+    if (i0 >= N) return;
+    for (int e = lane; e < 32 * stride; e += 32) {
+        const int p = e / stride, r = e - p * stride;
+        const int32_t k = i0 + p < N ? pos[i0 + p] : -1;
+        tile[w][p][r] = k >= 0 ? xp[(int64_t)k * stride + r] : 0.0;
+    }
+    __syncwarp();
+    if (i0 + lane < N)
+        for (int r = 0; r < nrhs; ++r) x[(int64_t)r * N + i0 + lane] = tile[w][lane][r];
+}
+
+static kc_status inverse_perm(const int32_t* perm, int64_t N, int32_t** pos, cudaStream_t s) {
+    KC_TRY(scratch_alloc((void**)pos, sizeof(int32_t) * (size_t)(N > 0 ? N : 1), s));
+    KC_CUDA(cudaMemsetAsync(*pos, 0xFF, sizeof(int32_t) * (size_t)(N > 0 ? N : 1), s));
+    ::kc::note_launch(), pm_inverse_perm_k<<<blocks_for(N, 256), 256, 0, s>>>(perm, N, *pos);
+    KC_CUDA(cudaGetLastError());
+    return KC_OK;
+}
+
 kc_status to_point_major(const double* b, const int32_t* perm, int64_t N, int nrhs, double* out, cudaStream_t s,
                          int stride) {
     if (stride < nrhs) stride = nrhs;
-    ::kc::note_launch(), to_point_major_k<<<blocks_for(N * stride, 256), 256, 0, s>>>(b, perm, N, nrhs, stride, out);
-    KC_CUDA(cudaGetLastError());
+    if (stride > 16) {
+        ::kc::note_launch(), to_point_major_k<<<blocks_for(N * stride, 256), 256, 0, s>>>(b, perm, N, nrhs, stride, out);
+        KC_CUDA(cudaGetLastError());
+        return KC_OK;
+    }
+    int32_t* pos = nullptr;
+    KC_TRY(inverse_perm(perm, N, &pos, s));
+    ::kc::note_launch(), to_point_major_tiled_k<<<blocks_for(N, PM_WARPS * 32), PM_WARPS * 32, 0, s>>>(b, pos, N, nrhs,
+                                                                                                   stride, out);
+    const cudaError_t e = cudaGetLastError();
+    cudaFreeAsync(pos, s);
+    if (e != cudaSuccess) return cuda_fail(e, "to_point_major_tiled_k");
     return KC_OK;
 }
 kc_status from_point_major(const double* xp, const int32_t* perm, int64_t N, int nrhs, double* x, cudaStream_t s,
                            int stride) {
     if (stride < nrhs) stride = nrhs;
-    ::kc::note_launch(), from_point_major_k<<<blocks_for(N * nrhs, 256), 256, 0, s>>>(xp, perm, N, nrhs, stride, x);
-    KC_CUDA(cudaGetLastError());
+    if (stride > 16) {
+        ::kc::note_launch(), from_point_major_k<<<blocks_for(N * nrhs, 256), 256, 0, s>>>(xp, perm, N, nrhs, stride, x);
+        KC_CUDA(cudaGetLastError());
+        return KC_OK;
+    }
+    int32_t* pos = nullptr;
+    KC_TRY(inverse_perm(perm, N, &pos, s));
+    ::kc::note_launch(), from_point_major_tiled_k<<<blocks_for(N, PM_WARPS * 32), PM_WARPS * 32, 0, s>>>(xp, pos, N, nrhs,
+                                                                                                     stride, x);
+    const cudaError_t e = cudaGetLastError();
+    cudaFreeAsync(pos, s);
+    if (e != cudaSuccess) return cuda_fail(e, "from_point_major_tiled_k");
     return KC_OK;
 }
 
