@@ -84,3 +84,25 @@ def test_non_finite_points_rejected(bad, where):
     # the same call on the clean input still works and agrees with itself
     rp, nnz = kc.pattern_count(xo, l, 3.0)
     assert nnz == kc.build_pattern(xo, l, 3.0).nnz
+
+
+@pytest.mark.parametrize("bad", ["repeated", "out_of_range"])
+def test_solve_with_a_perm_that_is_no_permutation(bad):
+    """The permutation steps of the solve touch nothing outside their arrays
+    when perm is not a permutation (repeated or out-of-range indices): the
+    call completes and the context stays usable; a later solve with the real
+    permutation gives its usual result bit for bit."""
+    x, perm, l, xo, pat = _pattern()
+    kern = kc.Kernel(0.5, 0.2)
+    val, diag, _ = kc.factor(pat, xo, kern, kc.FP64)
+    b = torch.from_numpy(inputs.rhs(2000, 3, seed=122)).to(DEV)
+    ref = kc.solve(pat, kc.FP64, val, diag, kern, perm, b)
+    wrong = perm.clone()
+    if bad == "repeated":
+        wrong[:1000] = wrong[1000:]
+    else:
+        wrong[::7] = 10**6
+    kc.solve(pat, kc.FP64, val, diag, kern, wrong, b)
+    torch.cuda.synchronize()
+    again = kc.solve(pat, kc.FP64, val, diag, kern, perm, b)
+    assert torch.equal(again, ref)
