@@ -70,3 +70,26 @@ def test_solve_payload_shapes():
         assert (x is None) == (r["type"] == "solve")
         if x is not None:
             assert x.shape == (r["N"], r["d"]) and np.isfinite(x).all()
+
+
+def test_summary_splits_latency_into_wait_and_service():
+    """p50/p99 over all requests and per type; a request's latency is its
+    queue wait (arrival to admission) plus its service (admission to done)."""
+    recs = []
+    for i in range(10):
+        typ = "factor" if i % 2 == 0 else "solve"
+        arr, adm, done = 0.1 * i, 0.1 * i + 0.01 * i, 0.1 * i + 0.01 * i + (0.2 if typ == "factor" else 0.05)
+        recs.append({"id": i, "type": typ, "key": i, "N": 10, "nnz": 100 if typ == "factor" else 0,
+                     "cache": "new" if typ == "factor" else "hit", "group": 1, "t_arrival": arr, "t_admit": adm,
+                     "t_done": done, "latency_ms": (done - arr) * 1e3, "x": None, "error": None})
+    s = serve.summarize(recs, wall_s=2.0)
+    assert s["requests"] == 10 and s["errors"] == 0 and s["throughput_req_s"] == 5.0
+    assert s["factor"]["n"] == 5 and s["solve"]["n"] == 5
+    for typ, service in (("factor", 200.0), ("solve", 50.0)):
+        assert s[typ]["service_p50_ms"] == pytest.approx(service)
+        waits = [(r["t_admit"] - r["t_arrival"]) * 1e3 for r in recs if r["type"] == typ]
+        assert s[typ]["wait_p50_ms"] == pytest.approx(float(np.percentile(waits, 50)))
+        lat = [r["latency_ms"] for r in recs if r["type"] == typ]
+        assert s[typ]["p50_ms"] == pytest.approx(float(np.percentile(lat, 50)))
+    assert s["solve_cache_hits"] == 5 and s["refactors"] == 0
+    assert s["factor_nnz_per_s"] == pytest.approx(5 * 100 / 2.0)
