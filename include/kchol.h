@@ -236,8 +236,9 @@ kc_status kc_factor(const kc_pattern* pat, const double* x_ord, int32_t d, const
  * group's columns, then a forward substitution (the block algorithm of the
  * stability appendix, equal to Algorithm 2 on such a pattern).  On a pattern
  * without such runs (the maximin pattern) every group is one column.  opts:
- * spin_limit_cycles, rows_per_task (rows of one task, 0 -> 128),
- * lanes_per_row (>= 8).  One persistent launch.  Synchronises. */
+ * spin_limit_cycles, rows_per_task (rows of one task; 0 -> (nnz - N) / (depth x
+ * resident CTAs) as the nearest power of two in 64..512), lanes_per_row (>= 8).
+ * One persistent launch.  Synchronises. */
 kc_status kc_factor_blocked(const kc_pattern* pat, const double* x_ord, int32_t d, const kc_kernel* kern,
                             int32_t prec, void* val, double* diag, int64_t* zero_pivots_out, const kc_opts* opts,
                             void* stream);

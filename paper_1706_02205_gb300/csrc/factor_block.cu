@@ -58,7 +58,11 @@ namespace kc {
 constexpr int BF_THREADS = KC_BLOCK_THREADS;
 constexpr int BF_WARPS = BF_THREADS / 32;
 constexpr int BF_MAXG = 8;       // columns per group at most
-constexpr int BU = 8;            // (column, value) loads per lane in flight while streaming a row
+// (column, value) loads per lane in flight while streaming a row
+#ifndef KC_BLOCK_BU
+#define KC_BLOCK_BU 4
+#endif
+constexpr int BU = KC_BLOCK_BU;
 
 template <typename T>
 struct GroupArgs {
@@ -110,7 +114,7 @@ __device__ __forceinline__ void tri_ts(int q, int& t, int& s) {
     s = q - t * (t + 1) / 2;
 }
 
-// The rows q in [qb, qe) of the CSC below a group of m <= M columns g0 ..
+// The rows q in [qb, qe) of the CSC below a group of m <= M4 <= MM columns g0 ..
 // g0+m-1: each row's prefix streamed once by G lanes (BU loads per lane in
 // flight, one table lookup per entry feeding m compensated accumulators),
 // then the forward substitution with L_AA: each result (theta - sum -
@@ -124,7 +128,7 @@ __device__ __forceinline__ float fsub_dot(float v, float a, float b) { return fm
 template <>
 __device__ __forceinline__ double fsub_dot(double v, double a, double b) { return fma(-a, b, v); }
 
-template <typename T, int MM, bool GEN, int M, int GC>
+template <typename T, int MM, bool GEN, int GC, int M4 = MM>
 __device__ __forceinline__ void group_rows(const GroupArgs<T>& A, int64_t qb, int64_t qe, int g0, int m,
                                            const unsigned long long* tab, int hb, const T* V, const T* Laa,
                                            const double* Ld, const T* Linv) {
@@ -144,7 +148,7 @@ __device__ __forceinline__ void group_rows(const GroupArgs<T>& A, int64_t qb, in
         T th = (T)0;  // lane sub: Theta_j,(g0+sub)
         if (act && sub < m)
             th = theta_off<T, GEN>(A.kp, A.d, A.x + (int64_t)j * A.d, A.x + (int64_t)(g0 + sub) * A.d);
-        Acc<T> acc[M];
+        Acc<T> acc[M4];
         if (act) {
             for (int64_t f0 = es + sub; f0 < e; f0 += (int64_t)BU * G) {
                 int k[BU];
@@ -161,18 +165,18 @@ __device__ __forceinline__ void group_rows(const GroupArgs<T>& A, int64_t qb, in
                     if (p >= 0) {
                         const T* vp = V + (int64_t)p * MM;
 #pragma unroll
-                        for (int u = 0; u < M; ++u)
+                        for (int u = 0; u < M4; ++u)
                             if (u < m) acc[u].add(w[v], vp[u]);
                     }
                 }
             }
         }
 #pragma unroll
-        for (int u = 0; u < M; ++u)
+        for (int u = 0; u < M4; ++u)
             if (u < m) acc[u].group_reduce(G);
-        T x[M];
+        T x[M4];
 #pragma unroll
-        for (int u = 0; u < M; ++u) {
+        for (int u = 0; u < M4; ++u) {
             const T thu = __shfl_sync(FULL, th, grp * G + (u < m ? u : 0));
             if (u < m) {
                 if constexpr (sizeof(T) == 4) {
@@ -190,7 +194,7 @@ __device__ __forceinline__ void group_rows(const GroupArgs<T>& A, int64_t qb, in
         }
         if (act && sub == 0)
 #pragma unroll
-            for (int u = 0; u < M; ++u)
+            for (int u = 0; u < M4; ++u)
                 if (u < m) A.val[e + u] = x[u];
     }
 }
@@ -312,11 +316,18 @@ __global__ void __launch_bounds__(BF_THREADS, KC_BLOCK_MINB) ichol_group_k(Group
         __syncthreads();
 
         // the rows below the group: column g0 of the CSC past its first m rows,
-        // with code for the group's exact size (no predicated-off accumulators)
+        // FP32 form: one code path for every group size, accumulators past m predicated off (with a
+        // second path for groups of at most 4 columns, instruction fetches missed the cache: 56.7
+        // against 50.5 ms on the 2^20 supernodal pattern); FP64 keeps that second path (126.6 against
+        // 138.4 ms)
         const int64_t qb = A.colptr[g0] + m + (int64_t)chunk * A.rpt;
         const int64_t qe = min(A.colptr[g0 + 1], qb + A.rpt);
-        if (m <= 4) group_rows<T, MM, GEN, 4, GC>(A, qb, qe, g0, m, tab, hb, V, Laa, Ld, Linv);
-        else group_rows<T, MM, GEN, MM, GC>(A, qb, qe, g0, m, tab, hb, V, Laa, Ld, Linv);
+        if constexpr (sizeof(T) == 8) {
+            if (m <= 4) group_rows<T, MM, GEN, GC, 4>(A, qb, qe, g0, m, tab, hb, V, Laa, Ld, Linv);
+            else group_rows<T, MM, GEN, GC>(A, qb, qe, g0, m, tab, hb, V, Laa, Ld, Linv);
+        } else {
+            group_rows<T, MM, GEN, GC>(A, qb, qe, g0, m, tab, hb, V, Laa, Ld, Linv);
+        }
         __syncthreads();
         if (tid == 0) {
             fence_acq_rel_gpu();
@@ -441,7 +452,16 @@ kc_status factor_blocked_impl(const kc_pattern* P, const double* x, int d, const
     KernelParams kp;
     KC_TRY(kernel_params(kern, &kp));
     const int64_t N = P->N;
-    const int rpt = (o && o->rows_per_task > 0) ? o->rows_per_task : 128;
+    // rows per task: about one task per resident CTA and dependency level, (nnz - N) / (depth x
+    // resident CTAs), as the nearest power of two in 64..512 (longer tasks spread the prologue over
+    // more rows; shorter ones keep the SMs busy on narrow levels)
+    int rpt = 64;
+    if (o && o->rows_per_task > 0) {
+        rpt = o->rows_per_task;
+    } else {
+        const double per = (double)(P->nnz - N) / ((double)std::max(P->depth, 1) * sm_count() * KC_BLOCK_MINB);
+        while (rpt < 512 && per >= rpt * 1.4142135623730951) rpt *= 2;
+    }
     const long long spin = (o && o->spin_limit_cycles > 0) ? o->spin_limit_cycles : 4000000000LL;
     // lanes per row: at least the group size (lane u of a row's lanes
     // evaluates Theta for column g0 + u)
