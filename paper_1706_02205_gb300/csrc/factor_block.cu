@@ -340,26 +340,65 @@ __global__ void __launch_bounds__(BF_THREADS, KC_BLOCK_MINB) ichol_group_k(Group
 
 // same[a] = 1 when column a joins the group of column a-1: row a is row a-1
 // with a appended, and column a-1 below a is column a below a.  A warp per
-// column; the comparisons run over the lanes.
+// column; the comparisons run over the lanes.  A comparison longer than
+// GRP_CHUNK entries (the coarsest columns hold nearly every row) is only
+// sized here: nchunk[a] chunks of GRP_CHUNK entries, which grp_same_long_k
+// spreads over the grid (one warp walking a column of 10^6 rows took 14 ms).
+constexpr int64_t GRP_CHUNK = 1024;
 __global__ void grp_same_k(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
                            const int64_t* __restrict__ colptr, const int32_t* __restrict__ rowidx, int64_t N,
-                           int* __restrict__ same) {
+                           int* __restrict__ same, int64_t* __restrict__ nchunk) {
     const int64_t a = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = lane_id();
     if (a >= N) return;
     int ok = a > 0;
+    int64_t nc = 0;
     if (ok) {
         const int64_t r1 = rowptr[a - 1], n1 = rowptr[a] - r1, r2 = rowptr[a], n2 = rowptr[a + 1] - r2;
         const int64_t c1 = colptr[a - 1], m1 = colptr[a] - c1, c2 = colptr[a], m2 = colptr[a + 1] - c2;
         ok = n2 == n1 + 1 && m1 == m2 + 1 && m1 >= 2 && rowidx[c1 + 1] == (int32_t)a;
-        if (ok) {
+        const int64_t total = n1 + m2 - 1;  // row entries, then column entries below a
+        if (ok && total > GRP_CHUNK) {
+            nc = (total + GRP_CHUNK - 1) / GRP_CHUNK;  // same[a] = 1 until a chunk differs
+        } else if (ok) {
             bool bad = false;
             for (int64_t p = lane; p < n1 && !bad; p += 32) bad = col[r2 + p] != col[r1 + p];
             for (int64_t q = lane; q + 1 < m2 && !bad; q += 32) bad = rowidx[c1 + 2 + q] != rowidx[c2 + 1 + q];
             ok = !__any_sync(0xffffffffu, bad);
         }
     }
-    if (lane == 0) same[a] = ok;
+    if (lane == 0) {
+        same[a] = ok;
+        nchunk[a] = nc;
+    }
+}
+
+// The long comparisons of grp_same_k: chunk w of all of them (choff = the
+// exclusive scan of nchunk, choff[N] chunks in all) goes to one warp, which
+// finds its column by binary search in choff; a difference clears same[a]
+// (every writer stores the same 0).
+__global__ void grp_same_long_k(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                                const int64_t* __restrict__ colptr, const int32_t* __restrict__ rowidx, int64_t N,
+                                const int64_t* __restrict__ choff, int* __restrict__ same) {
+    const int lane = lane_id();
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int64_t nch = choff[N];
+    for (int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < nch; w += nw) {
+        int64_t lo = 0, hi = N;  // the last a with choff[a] <= w (its chunks hold w)
+        while (hi - lo > 1) {
+            const int64_t mid = (lo + hi) >> 1;
+            if (choff[mid] <= w) lo = mid;
+            else hi = mid;
+        }
+        const int64_t a = lo;
+        const int64_t r1 = rowptr[a - 1], n1 = rowptr[a] - r1, r2 = rowptr[a];
+        const int64_t c1 = colptr[a - 1], c2 = colptr[a], m2 = colptr[a + 1] - c2;
+        const int64_t t0 = (w - choff[a]) * GRP_CHUNK, t1 = min(n1 + m2 - 1, t0 + GRP_CHUNK);
+        bool bad = false;
+        for (int64_t t = t0 + lane; t < t1; t += 32)
+            bad |= t < n1 ? col[r2 + t] != col[r1 + t] : rowidx[c1 + 2 + (t - n1)] != rowidx[c2 + 1 + (t - n1)];
+        if (__any_sync(0xffffffffu, bad) && lane == 0) same[a] = 0;
+    }
 }
 
 // sflag[a] = 1 where a run of columns begins (same[a] == 0)
@@ -485,8 +524,15 @@ kc_status factor_blocked_impl(const kc_pattern* P, const double* x, int d, const
     KC_TRY(A.get(&gex, N + 1));
     KC_TRY(A.get(&gstart, N + 1));
     KC_TRY(A.get(&group_of, N));
+    int64_t *nchunk, *choff;
+    KC_TRY(A.get(&nchunk, N));
+    KC_TRY(A.get(&choff, N + 1));
     ::kc::note_launch(), grp_same_k<<<blocks_for(N * 32, 256), 256, 0, s>>>(P->rowptr, P->col, P->colptr, P->rowidx, N,
-                                                                             same);
+                                                                             same, nchunk);
+    KC_CUDA(cudaGetLastError());
+    KC_TRY(exclusive_scan_i64(nchunk, choff, N, A, s));
+    ::kc::note_launch(), grp_same_long_k<<<sm_count() * 8, 256, 0, s>>>(P->rowptr, P->col, P->colptr, P->rowidx, N,
+                                                                         choff, same);
     KC_CUDA(cudaGetLastError());
     // incl[a] = number of runs starting at or before a (exclusive scan of the
     // run-start flags, plus the flag)
