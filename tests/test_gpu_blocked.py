@@ -130,3 +130,20 @@ def test_blocked_rejects_bad_options():
         kc.factor_blocked(pat, T(xs), kc.Kernel(0.5, 0.2), kc.FP32_FORM, kc.make_opts(lanes_per_row=3))
     with pytest.raises(kc.KcError):
         kc.factor_blocked(pat, T(xs), kc.Kernel(0.5, 0.2), 7)
+
+
+@pytest.mark.parametrize("prec", [kc.FP64, kc.FP32_FORM])
+@pytest.mark.parametrize("d", [2, 3])
+def test_blocked_same_bits_for_every_task_size(d, prec):
+    """Rows per task only split the rows below a group among tasks, and the
+    group detection only decides which columns form groups: the default
+    choice, explicit sizes (odd, one row, longer than any column) and a
+    second call give the same bits.  The coarsest columns here hold every
+    later row, so the group detection's long comparisons run in many chunks."""
+    xs, ref = _supernodal_case(3000 if d == 2 else 2500, d, seed=160 + d)
+    kg = kc.Kernel(0.5, 0.2)
+    pat = kc.schedule(T(ref["rowptr"]), T(ref["col"]), T(xs))
+    v0, d0, z0 = kc.factor_blocked(pat, T(xs), kg, prec)
+    for rpt in (1, 7, 64, 300, 512, 4096, 0):
+        v, dg, z = kc.factor_blocked(pat, T(xs), kg, prec, kc.make_opts(rows_per_task=rpt))
+        assert torch.equal(v, v0) and torch.equal(dg, d0) and z == z0, rpt
