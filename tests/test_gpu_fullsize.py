@@ -23,7 +23,11 @@ properties that hold at any size:
   for 10^5 sampled entries of S (pivots included), within the FP32 form's
   bar of 1e-6 of Theta_jj;
 * solve: the residual of L L^T x = b for two right-hand sides, with L's
-  diagonal the FP64 pivots the solves divide by.
+  diagonal the FP64 pivots the solves divide by;
+* the block factorisation by column groups on the supernodal multicolour
+  pattern of the same points (default options, as the bench times it): the
+  same bits with another task size, and the defining identity on 10^5
+  sampled entries of the columns it keeps.
 """
 import numpy as np
 import pytest
@@ -171,3 +175,39 @@ def test_full_solve_residual(full):
         bp = full["b"][r][perm]
         res = L @ (L.T @ xp) - bp
         assert np.linalg.norm(res) <= 1e-9 * np.linalg.norm(bp), r
+
+
+def test_full_supernodal_block_factor(full):
+    """kc_factor_blocked on the supernodal multicolour pattern built from this
+    maximin order and pattern (the bench's supernodal leg): default options
+    (512 rows per task here) and 96 rows per task give the same bits, and
+    (L L^T)_ji = Theta_ji holds on 10^5 sampled entries of S whose column i
+    is kept (a dropped column is zero, diagonal included), within the FP32
+    form's bar of 1e-6."""
+    from scipy.sparse import csr_matrix
+    xo_d = torch.from_numpy(full["xo"]).to(DEV)
+    l_d = torch.from_numpy(full["l"]).to(DEV)
+    pat0 = kc.build_pattern(xo_d, l_d, RHO)
+    sn = kc.supernodal(xo_d, l_d, RHO, pat0, with_schedule=False)
+    del pat0
+    spat = kc.schedule(sn["rowptr"], sn["col"], sn["x_new"])
+    kern = kc.Kernel(NU, ELL)
+    v, d, zp = kc.factor_blocked(spat, sn["x_new"], kern, kc.FP32_FORM)
+    v2, d2, zp2 = kc.factor_blocked(spat, sn["x_new"], kern, kc.FP32_FORM, kc.make_opts(rows_per_task=96))
+    assert torch.equal(v, v2) and torch.equal(d, d2) and zp == zp2
+    del v2, d2
+    xn, rp, col = sn["x_new"].cpu().numpy(), spat.rowptr.cpu().numpy(), spat.col.cpu().numpy()
+    val, diag = v.cpu().numpy(), d.cpu().numpy()
+    del v, d, spat, sn
+    N = xn.shape[0]
+    assert np.array_equal(diag == 0.0, val[rp[1:] - 1] == 0.0) and int((diag == 0.0).sum()) == zp
+    L = csr_matrix((val.astype(np.float64), col, rp), shape=(N, N))
+    r = np.random.default_rng(5)
+    e = np.concatenate([r.integers(0, len(col), size=100_000), rp[1:][r.integers(0, N, size=2000)] - 1])
+    e = e[diag[col[e]] > 0]
+    rows = np.searchsorted(rp, e, side="right") - 1
+    cols = col[e]
+    llt = np.asarray(L[rows].multiply(L[cols]).sum(axis=1)).ravel()
+    th = np.exp(-np.sqrt(((xn[rows] - xn[cols]) ** 2).sum(axis=1)) / ELL)
+    worst = float(np.max(np.abs(llt - th)))
+    assert worst < 1e-6, worst
