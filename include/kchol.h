@@ -108,7 +108,8 @@ typedef struct {
 typedef struct {
     int64_t spin_limit_cycles;     /* bound of every device wait; 0 -> ~4e9 cycles */
     int32_t rows_per_task;         /* rows of a column per task; 0 -> factor: about (nnz - N) / (depth x
-                                      resident warps), a power of two in 16..128; backward solve: 128 */
+                                      resident warps), a power of two in 16..128; factor by column groups:
+                                      see kc_factor_blocked; backward solve: 128 */
     int32_t ctas_per_sm;           /* persistent grid = SMs x this; 0 -> occupancy; < 0 (factor) ->
                                       occupancy + this (at least 1): leaves that many CTA slots per
                                       SM to kernels on other streams (latency of concurrent solves) */
